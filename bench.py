@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark of the Gribov-copy enumerator on the 4D 4^4 compact U(1) workload.
+
+Workload: 4D 4^4 periodic lattice (1024 links), eight von Mises orbits with
+kappa_j = 0.5 + 1.5 j/7 (seeds 1-8), 2^20 random starts per orbit, mixed
+precision (FP32 sweeps to max div^2 < 1e-10, FP64 polish to 1e-24),
+overrelaxation omega = 1.7, Faddeev-Popov Lanczos test, FP64 dedup.
+One step = the whole path (starts -> sweeps -> polish -> dedup -> FP test) for
+one orbit's 2^20 starts; step k uses orbit k mod 8.
+
+Prints one JSON line.  `value` = converged copies per second with the orbit
+resident on the device (CUDA events on the library's stream around the
+gc_enumerate_copies calls of the K timed steps); `e2e` = the same metric
+through the C ABI with host buffers (link angles uploaded, distinct copies
+read back, every step).  The plain FP64 path is timed on a sample beside it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import orbit_inputs as oi  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 148
+SM_MAX_MHZ = 2032.0
+FP32_LANES_PER_SM = 128
+FP64_NOMINAL_TFLOPS = 1.25          # B300 dense FP64 (DFMA = 2 flops)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=8)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--starts", type=int, default=1 << 20, help="starts per orbit (one step)")
+    p.add_argument("--plain-starts", type=int, default=1 << 16)
+    p.add_argument("--cpu-starts", type=int, default=1536)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--check-every", type=int, default=4)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for _, _, flags in rows for n, v in zip(names, flags) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": rows[0][1],
+                "samples": len(rows), "reasons": reasons}
+
+
+# ----------------------------------------------------------------------------
+# CPU legs: the oracle on host cores
+# ----------------------------------------------------------------------------
+
+def oracle_sample(orbit, n_starts, start0=0):
+    """Whole oracle pipeline on a bounded sample; returns (converged, seconds, threads)."""
+    import oracle
+    t = time.perf_counter()
+    relaxed, cp = oracle.enumerate_copies(orbit.d, orbit.L, orbit.phi, 1, orbit.orbit_id,
+                                          n_starts, omega=1.7, eps=1e-24, start0=start0)
+    dt = time.perf_counter() - t
+    return int((relaxed.status == oracle.CONVERGED).sum()), dt, oracle.max_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = oi.workload_4d_4to4(args.starts)
+    per_step = max(64, min(args.cpu_starts, 512))
+    for k in range(args.warmup):
+        oracle_sample(w.orbits[k % 8], 32, start0=10_000_000 + k)
+    conv = 0
+    secs = 0.0
+    threads = 1
+    for k in range(args.steps):
+        c, dt, threads = oracle_sample(w.orbits[k % 8], per_step)
+        conv += c
+        secs += dt
+    v = conv / secs
+    sample = f"{per_step} starts of orbit k mod 8 per step (of 2^20), full oracle pipeline"
+    out = {
+        "impl": "reference", "metric": "converged_copies_per_s", "value": v,
+        "unit": "copies/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "4d_L4_vonmises_x8", "lattice": "4^4", "orbits": 8,
+                   "starts_per_orbit": per_step, "omega": 1.7, "eps": 1e-24},
+        "cpu_baseline": {"value": v, "unit": "copies/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "copies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+# ----------------------------------------------------------------------------
+# GPU leg
+# ----------------------------------------------------------------------------
+
+def stats_delta(a, b):
+    return {k: b[k] - a[k] for k in b}
+
+
+def run_ours(args):
+    import torch
+    import paper_1403_0555_b300 as gb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    gb.use_torch_allocator()
+    stream = torch.cuda.current_stream()
+
+    w = oi.workload_4d_4to4(args.starts)
+    orbits = w.orbits
+    d, L = 4, 4
+    V = L ** d
+    opt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=args.check_every,
+                                fp_mode=gb.GC_FP_AUTO, stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def orbit_for(k):
+        return orbits[(k * world + rank) % len(orbits)]
+
+    # warm-up on separate orbit objects (same shapes)
+    for k in range(args.warmup):
+        o = orbit_for(k)
+        h = gb.gc_create_orbit(d, L, o.phi, o.orbit_id)
+        gb.gc_enumerate_copies(h, args.starts, w.omega, w.eps, opt)
+        gb.gc_destroy_orbit(h)
+
+    # --- device-resident timed region
+    handles = []
+    for k in range(args.steps):
+        o = orbit_for(k)
+        handles.append(gb.gc_create_orbit(d, L, o.phi, o.orbit_id))
+    before = [gb.gc_orbit_stats(h) for h in handles]
+    clk = ClockSampler(torch.cuda.current_device())
+    barrier()
+    clk.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for h in handles:
+        gb.gc_enumerate_copies(h, args.starts, w.omega, w.eps, opt)
+    ev1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1)
+    after = [gb.gc_orbit_stats(h) for h in handles]
+    deltas = [stats_delta(a, b) for a, b in zip(before, after)]
+    tot = {k: sum(dl[k] for dl in deltas) for k in deltas[0]}
+    n_distinct = [a["n_distinct"] for a in after]
+    for h in handles:
+        gb.gc_destroy_orbit(h)
+    conv = tot["n_converged"]
+    ms_max = ms
+    conv_all = conv
+    if dist is not None:
+        t = torch.tensor([ms, conv], dtype=torch.float64, device="cuda")
+        m = t.clone()
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_max, conv_all = float(m[0]), float(t[1])
+    value = conv_all / (ms_max / 1000.0)
+    upd = tot["site_updates_fp32"] + tot["site_updates_fp64"]
+
+    # --- end to end through the C ABI with host buffers
+    barrier()
+    t0 = time.perf_counter()
+    e2e_conv = 0
+    h2d = d2h = 0
+    for k in range(args.steps):
+        o = orbit_for(k)
+        phi = np.ascontiguousarray(o.phi)
+        h = gb.gc_create_orbit(d, L, phi, o.orbit_id)
+        h2d += phi.nbytes
+        gb.gc_enumerate_copies(h, args.starts, w.omega, w.eps, opt)
+        res = gb.gc_fetch_copies(h, V)
+        d2h += sum(res[k].nbytes for k in ("F", "theta", "first_start", "count", "lambda2", "region"))
+        e2e_conv += gb.gc_orbit_stats(h)["n_converged"]
+        gb.gc_destroy_orbit(h)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s, e2e_conv], dtype=torch.float64, device="cuda")
+        m = t.clone()
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        e2e_s, e2e_conv = float(m[0]), float(t[1])
+    e2e = {"value": e2e_conv / e2e_s, "unit": "copies/s",
+           "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # --- plain FP64 path on a sample of orbit 0 (same options otherwise)
+    o = orbits[0]
+    popt = gb.gc_options_default(precision=gb.GC_FP64, check_every=args.check_every,
+                                 fp_mode=gb.GC_FP_AUTO, stream=stream)
+    h = gb.gc_create_orbit(d, L, o.phi, o.orbit_id)
+    gb.gc_enumerate_copies(h, 2048, w.omega, w.eps, popt)       # warm-up
+    s0 = gb.gc_orbit_stats(h)
+    barrier()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    gb.gc_enumerate_copies(h, args.plain_starts, w.omega, w.eps, popt)
+    p1.record(stream)
+    barrier()
+    pms = p0.elapsed_time(p1)
+    ps = stats_delta(s0, gb.gc_orbit_stats(h))
+    gb.gc_destroy_orbit(h)
+    plain = {"value": ps["n_converged"] / (pms / 1000.0), "unit": "copies/s",
+             "site_updates_per_s": ps["site_updates_fp64"] / (pms / 1000.0),
+             "sample": f"{args.plain_starts} starts of orbit kappa=0.5",
+             "mixed_over_plain": value / (ps["n_converged"] / (pms / 1000.0))}
+
+    # --- roofline of the dominant kernel (per-stage CUDA events inside the library)
+    stage_ms = {"relax_fp32": tot["ms_relax"], "polish_fp64": tot["ms_polish"],
+                "dedup": tot["ms_dedup"], "fp_test": tot["ms_fptest"]}
+    dom = max(stage_ms, key=stage_ms.get)
+    fp32_per_update = 8 * d + 11 + (8 * d + 3) / args.check_every
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    fp64_peak = FP64_NOMINAL_TFLOPS / 2.0                        # DFMA per second, 1e12
+    if dom == "relax_fp32":
+        achieved = tot["site_updates_fp32"] * fp32_per_update / (stage_ms[dom] / 1e3) / 1e12
+        roof = {"kernel": "relax_kernel<Fast32>", "bound": "alu", "achieved": achieved,
+                "peak": fp32_peak, "unit": "TOP/s (FP32 pipe ops)", "frac": achieved / fp32_peak,
+                "traffic": None}
+    elif dom == "polish_fp64":
+        dfma = tot["fp64_residual_passes"] * V * (10 * d + 2) + tot["site_updates_fp64"] * (8 * d + 30)
+        achieved = dfma / (stage_ms[dom] / 1e3) / 1e12
+        roof = {"kernel": "polish_kernel", "bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                "unit": "T DFMA/s (FP64 pipe ops)", "frac": achieved / fp64_peak, "traffic": None}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None}
+    roof["peak_source"] = "derived: 148 SMs x lanes x 2032 MHz (recipe unit counts and clock)"
+    roof["stage_ms"] = stage_ms
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        c, dt, threads = oracle_sample(orbits[0], args.cpu_starts)
+        cpu = {"value": c / dt, "unit": "copies/s", "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_starts} starts of the kappa=0.5 orbit, full oracle pipeline "
+                         f"(FP64 relaxation, dense eigensolve per distinct copy), {dt:.1f} s"}
+
+    out = {
+        "metric": "converged_copies_per_s", "value": value, "unit": "copies/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "4d_L4_vonmises_x8", "lattice": "4^4", "orbits": 8,
+                   "starts_per_orbit": args.starts, "omega": 1.7, "eps32": 1e-10, "eps": 1e-24,
+                   "check_every": args.check_every, "precision": "fp32 sweeps + fp64 polish",
+                   "fp_test": "lanczos fp32 screen + fp64", "parallelism": f"weak x{world}",
+                   "l2": "working set > L2 (1 GiB staging per batch + copy pool)"},
+        "site_updates_per_s": upd / (ms_max / 1000.0),
+        "site_updates_fp32": tot["site_updates_fp32"], "site_updates_fp64": tot["site_updates_fp64"],
+        "distinct_copies_per_orbit": n_distinct,
+        "plain_fp64": plain,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": int(tot["kernel_launches"]),
+    }
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

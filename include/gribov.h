@@ -1,0 +1,156 @@
+/*
+ * gribov.h -- C ABI of the B300 Gribov-copy enumerator for compact U(1)
+ * lattice Landau gauge in d = 1..4 dimensions.
+ *
+ * Method (Mehta & Schroeck, arXiv:1403.0555):
+ *   links      U_{x,mu} = exp(i phi_{x,mu}), gauge g_x = exp(i theta_x);
+ *   functional F(theta) = sum_{x,mu} (1 - cos(phi_{x,mu} + theta_{x+mu} - theta_x))      (Eq. 3)
+ *   a Gribov copy is a stationary point of F; the copies counted are those in
+ *   the first Gribov region, where the Faddeev-Popov operator (the Hessian of
+ *   F in theta) is non-negative apart from its constant zero mode (Section I);
+ *   they are found by relaxation (local maximisation of Eq. 4 with K_x of
+ *   Eq. 5, checkerboard order) from many random gauge starts (Section III),
+ *   stopped when the largest squared lattice divergence is below eps, and
+ *   told apart after fixing the global phase theta_{(N,...,N)} = 0 (Section II).
+ *
+ * Lattice layout used by every array below: V = L^d sites, site index
+ * idx(x) = sum_mu x_mu L^mu (x_0 fastest); link (x, mu) at idx(x)*d + mu.
+ *
+ * Conventions: every entry point returns GC_OK (0) or a negative GC_E* code
+ * and then leaves a message for gc_last_error() (per thread).  Host pointers
+ * are owned by the caller; all device memory is owned by the library, which
+ * allocates it through gc_set_allocator's hooks (cudaMalloc when none are set).
+ * The library uses whichever CUDA device is current when an orbit is created.
+ */
+#ifndef GRIBOV_H
+#define GRIBOV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define GC_OK 0
+#define GC_EINVAL (-1)     /* bad argument (message says which)             */
+#define GC_ENOMEM (-2)     /* device or host allocation refused             */
+#define GC_ECUDA (-3)      /* a CUDA call failed (message has the CUDA text) */
+#define GC_ETIMEDOUT (-4)  /* a bounded device wait ran out                 */
+#define GC_ESTATE (-5)     /* call not valid in the orbit's current state   */
+
+/* precision of the relaxation */
+#define GC_FP64 0   /* FP64 sweeps, every operation an IEEE-rounded step (no FMA) */
+#define GC_MIXED 1  /* FP32 sweeps to eps32, then FP64 polish to eps             */
+
+/* Faddeev-Popov test */
+#define GC_FP_AUTO 0     /* FP32 Lanczos screen, FP64 Lanczos near lambda_2 = 0 */
+#define GC_FP_LANCZOS 1  /* FP64 Lanczos for every copy                         */
+#define GC_FP_DENSE 2    /* FP64 Lanczos, full reorthogonalisation, dim V-1     */
+#define GC_FP_NONE 3     /* no test (region reported as -1)                     */
+
+/* per-start status */
+#define GC_START_CONVERGED 1
+#define GC_START_NOT_CONVERGED 2
+#define GC_START_DEDUP_FAILED 3
+
+/* region flag of a distinct copy */
+#define GC_REGION_UNTESTED (-1)
+#define GC_REGION_OUT 0       /* lambda_2 < -fp_tau: a saddle          */
+#define GC_REGION_IN 1        /* lambda_2 > fp_tau: a minimum           */
+#define GC_REGION_MARGINAL 2  /* |lambda_2| <= fp_tau                   */
+
+typedef struct gc_orbit_s* gc_orbit;
+
+typedef struct {
+  int precision;        /* GC_FP64 or GC_MIXED                                      */
+  int check_every;      /* sweeps between residual checks, >= 1                     */
+  int max_sweeps;       /* sweep cap per start (rounded up to a multiple of
+                           check_every); a start that reaches it is NOT_CONVERGED  */
+  double eps32;         /* GC_MIXED: the FP32 phase stops at max div^2 < eps32     */
+  double dedup_delta;   /* copies are one when max_x |g'_A - g'_B| <= delta        */
+  double fp_tau;        /* marginal band of the Faddeev-Popov test                 */
+  int fp_mode;          /* GC_FP_*                                                  */
+  int lanczos_k;        /* cap on FP64 Lanczos steps (<= V-1 is used)               */
+  uint64_t seed;        /* start generator key word 0 (word 1 is the orbit id)     */
+  int keep_per_start;   /* keep the last call's per-start records for fetch_starts */
+  int newton_inner;     /* GC_MIXED: cap on FP32 SOR sweeps per Newton polish step */
+  int newton_max;       /* GC_MIXED: Newton steps before FP64 relaxation fallback  */
+  int batch_starts;     /* starts per device batch, 0 = automatic                  */
+  void* stream;         /* cudaStream_t the work is ordered on (NULL = default)    */
+} gc_options;
+
+typedef struct {
+  uint64_t n_starts;             /* starts relaxed so far (all calls)            */
+  uint64_t n_converged;          /* reached eps (FP64 residual)                  */
+  uint64_t n_not_converged;
+  uint64_t n_dedup_failed;       /* lock wait ran out or copy pool full          */
+  uint64_t n_distinct;           /* distinct canonical copies                    */
+  uint64_t n_distinct_F8;        /* distinct floor(F/(dV) * 1e8) (Section III)   */
+  uint64_t n_in, n_marginal, n_out, n_untested;   /* region flags of copies   */
+  uint64_t sweeps_fp32, sweeps_fp64;               /* summed over starts       */
+  uint64_t site_updates_fp32, site_updates_fp64;
+  uint64_t newton_steps, newton_inner_sweeps, polish_fallbacks, fp64_residual_passes;
+  uint64_t fp_tests, fp_tests_fp64, lanczos_steps;
+  double ms_relax, ms_polish, ms_dedup, ms_fptest; /* device ms, all calls      */
+  uint64_t kernel_launches;      /* kernels the library launched for this orbit */
+} gc_stats;
+
+/* Device memory hooks (e.g. a framework's caching allocator).  alloc returns
+ * NULL on failure; both are called on the orbit's stream.  Set before creating
+ * orbits; NULL hooks restore cudaMalloc / cudaFree. */
+typedef void* (*gc_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*gc_free_fn)(void* ptr, void* stream, void* ctx);
+int gc_set_allocator(gc_alloc_fn alloc, gc_free_fn free_fn, void* ctx);
+
+/* Defaults: GC_FP64, check_every 1, max_sweeps 100000, eps32 1e-10,
+ * dedup_delta 1e-6, fp_tau 1e-9, GC_FP_AUTO, lanczos_k 300, seed 1,
+ * keep_per_start 0, newton_inner 320, newton_max 6, batch automatic. */
+int gc_options_default(gc_options* opt);
+
+/* Orbit from link angles phi (host, V*d doubles, radians, any range).
+ * The library stores (cos phi, sin phi) in FP64 and FP32 (no trigonometry in
+ * the sweeps).  orbit_id keys the random starts together with the seed.
+ * max_copies sizes the first copy pool (0 = automatic; it grows on demand).
+ * d in 1..4, L >= 2, and the lattice must fit the shared-memory path
+ * (V*d links of 16 bytes plus tables; e.g. up to 6^4, 14^3, 63^2). */
+int gc_create_orbit(int dim, int L, const double* link_angles, uint64_t orbit_id,
+                    size_t max_copies, gc_orbit* out);
+
+/* Relax n_starts new random starts (indices continue across calls, so two
+ * calls of n equal one call of 2n), keep the converged ones, deduplicate them
+ * into the orbit's table and test each new distinct copy.  omega in (0, 2) is
+ * the overrelaxation parameter (1 = the paper's plain relaxation), eps > 0 the
+ * stop on max_x div(x)^2.  Returns when the work is complete on opt->stream.
+ * GC_ETIMEDOUT: some start's table lock wait ran out (it is counted in
+ * n_dedup_failed, everything else is valid). */
+int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
+                        const gc_options* opt);
+
+/* Distinct copies sorted by (F, first_start).  capacity = 0 only sets
+ * *n_distinct.  Otherwise the first min(capacity, n) copies are written to
+ * every non-NULL array: F[n], theta[n*V] (canonical angles, theta'_{V-1} = 0),
+ * first_start[n] (lowest start index reaching the copy), count[n] (starts
+ * reaching it), lambda2[n] (NaN when untested), region[n] (GC_REGION_*). */
+int gc_fetch_copies(gc_orbit o, size_t capacity, size_t* n_distinct, double* F, double* theta,
+                    uint64_t* first_start, uint64_t* count, double* lambda2, int* region);
+
+/* Per-start records of the last gc_enumerate_copies call (needs
+ * keep_per_start): starts first .. first+n-1 must lie in that call's range.
+ * copy_idx is the position in gc_fetch_copies' order, -1 if not converged. */
+int gc_fetch_starts(gc_orbit o, uint64_t first, uint64_t n, int* status, int* sweeps,
+                    double* F, int64_t* copy_idx);
+
+int gc_orbit_stats(gc_orbit o, gc_stats* out);
+int gc_destroy_orbit(gc_orbit o);
+
+/* message of the last failing call on this thread ("" if none) */
+const char* gc_last_error(void);
+/* library version string */
+const char* gc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRIBOV_H */

@@ -357,8 +357,12 @@ def enumerate_copies(d, L, phi, seed, orbit_id, n_starts, omega=1.7, eps=1e-24,
     order = np.lexsort((cfirst, cF)) if m else np.zeros(0, np.int64)
     inv = np.empty(m, np.int64)
     inv[order] = np.arange(m)
-    copy_of = np.where(rep_of >= 0, inv[np.maximum(rep_of, 0)], -1)
+    copy_of = np.full(len(rep_of), -1, np.int64)
+    copy_of[rep_of >= 0] = inv[rep_of[rep_of >= 0]]
     q = np.floor(f_norm(F[conv], d, L) * 1e8).astype(np.int64)
+    if m == 0:
+        lam = np.zeros(0)
+        reg = np.zeros(0, np.int32)
     copies = Copies(cF[order], cth[order], cfirst[order], ccount[order], lam[order],
                     reg[order], copy_of, int(np.unique(q).size))
     return relaxed, copies

@@ -1,0 +1,253 @@
+"""Python binding of the B300 Gribov-copy enumerator (C ABI in include/gribov.h).
+
+Argument marshalling only: every step of the enumeration runs in the CUDA
+kernels of ``libgribov.so``.  PyTorch supplies device memory (its caching
+allocator, through the library's allocator hooks) and streams.  There is no
+CPU fallback: if the library cannot be loaded, importing the binding's entry
+points raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+GC_OK = 0
+GC_EINVAL = -1
+GC_ENOMEM = -2
+GC_ECUDA = -3
+GC_ETIMEDOUT = -4
+GC_ESTATE = -5
+
+GC_FP64 = 0
+GC_MIXED = 1
+
+GC_FP_AUTO = 0
+GC_FP_LANCZOS = 1
+GC_FP_DENSE = 2
+GC_FP_NONE = 3
+
+GC_START_CONVERGED = 1
+GC_START_NOT_CONVERGED = 2
+GC_START_DEDUP_FAILED = 3
+
+GC_REGION_UNTESTED = -1
+GC_REGION_OUT = 0
+GC_REGION_IN = 1
+GC_REGION_MARGINAL = 2
+
+
+class GribovError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class gc_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("check_every", ctypes.c_int),
+        ("max_sweeps", ctypes.c_int),
+        ("eps32", ctypes.c_double),
+        ("dedup_delta", ctypes.c_double),
+        ("fp_tau", ctypes.c_double),
+        ("fp_mode", ctypes.c_int),
+        ("lanczos_k", ctypes.c_int),
+        ("seed", ctypes.c_uint64),
+        ("keep_per_start", ctypes.c_int),
+        ("newton_inner", ctypes.c_int),
+        ("newton_max", ctypes.c_int),
+        ("batch_starts", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class gc_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "n_starts", "n_converged", "n_not_converged", "n_dedup_failed", "n_distinct",
+        "n_distinct_F8", "n_in", "n_marginal", "n_out", "n_untested", "sweeps_fp32",
+        "sweeps_fp64", "site_updates_fp32", "site_updates_fp64", "newton_steps",
+        "newton_inner_sweeps", "polish_fallbacks", "fp64_residual_passes", "fp_tests", "fp_tests_fp64",
+        "lanczos_steps")] + [(n, ctypes.c_double) for n in (
+        "ms_relax", "ms_polish", "ms_dedup", "ms_fptest")] + [("kernel_launches", ctypes.c_uint64)]
+
+
+EXPORTED = ("gc_set_allocator", "gc_options_default", "gc_create_orbit", "gc_enumerate_copies",
+            "gc_fetch_copies", "gc_fetch_starts", "gc_orbit_stats", "gc_destroy_orbit",
+            "gc_last_error", "gc_version")
+
+_lib = None
+_lock = threading.Lock()
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_hooks = []
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_stale: bool = True):
+    """Load libgribov.so (compiling it first when stale and nvcc is present)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_stale and not _build.up_to_date():
+            if os.path.exists("/usr/local/cuda/bin/nvcc") or os.environ.get("NVCC"):
+                _build.build()
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"libgribov.so not built at {_build.LIB}; run "
+                              "python -m paper_1403_0555_b300.build")
+        L = ctypes.CDLL(_build.LIB)
+        p_d = ctypes.POINTER(ctypes.c_double)
+        p_u64 = ctypes.POINTER(ctypes.c_uint64)
+        p_i = ctypes.POINTER(ctypes.c_int)
+        L.gc_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, ctypes.c_void_p]
+        L.gc_options_default.argtypes = [ctypes.POINTER(gc_options)]
+        L.gc_create_orbit.argtypes = [ctypes.c_int, ctypes.c_int, p_d, ctypes.c_uint64,
+                                      ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]
+        L.gc_enumerate_copies.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double,
+                                          ctypes.c_double, ctypes.POINTER(gc_options)]
+        L.gc_fetch_copies.argtypes = [ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.POINTER(ctypes.c_size_t), p_d, p_d, p_u64, p_u64,
+                                      p_d, p_i]
+        L.gc_fetch_starts.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, p_i,
+                                      p_i, p_d, ctypes.POINTER(ctypes.c_int64)]
+        L.gc_orbit_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(gc_stats)]
+        L.gc_destroy_orbit.argtypes = [ctypes.c_void_p]
+        L.gc_last_error.restype = ctypes.c_char_p
+        L.gc_version.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _check(rc):
+    if rc != GC_OK:
+        raise GribovError(rc, load().gc_last_error().decode())
+    return rc
+
+
+def _ptr(a, ct):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    import torch
+    live = {}
+
+    def _alloc(n, stream, ctx):
+        try:
+            p = torch.cuda.caching_allocator_alloc(int(n), stream=int(stream or 0))
+        except Exception:
+            return None
+        live[p] = True
+        return p
+
+    def _free(p, stream, ctx):
+        if p in live:
+            live.pop(p)
+            torch.cuda.caching_allocator_delete(p)
+
+    a, f = _ALLOC_FN(_alloc), _FREE_FN(_free)
+    _hooks[:] = [a, f, live]
+    _check(load().gc_set_allocator(a, f, None))
+
+
+def use_cuda_allocator():
+    _check(load().gc_set_allocator(_ALLOC_FN(), _FREE_FN(), None))
+    _hooks.clear()
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one wrapper per entry point
+# ---------------------------------------------------------------------------
+
+def gc_set_allocator(alloc=None, free_fn=None, ctx=None):
+    """Install device-memory hooks (Python callables alloc(n, stream, ctx) -> ptr
+    and free_fn(ptr, stream, ctx)); no arguments restores cudaMalloc/cudaFree."""
+    if alloc is None and free_fn is None:
+        _hooks.clear()
+        _check(load().gc_set_allocator(_ALLOC_FN(), _FREE_FN(), None))
+        return
+    a, f = _ALLOC_FN(alloc), _FREE_FN(free_fn)
+    _hooks[:] = [a, f]
+    _check(load().gc_set_allocator(a, f, ctx))
+
+
+def gc_version() -> str:
+    return load().gc_version().decode()
+
+
+def gc_last_error() -> str:
+    return load().gc_last_error().decode()
+
+
+def gc_options_default(**overrides) -> gc_options:
+    opt = gc_options()
+    _check(load().gc_options_default(ctypes.byref(opt)))
+    for k, v in overrides.items():
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = int(v.cuda_stream)
+        setattr(opt, k, v)
+    return opt
+
+
+def gc_create_orbit(dim: int, L: int, link_angles, orbit_id: int = 0, max_copies: int = 0):
+    phi = np.ascontiguousarray(link_angles, dtype=np.float64)
+    if phi.size != L ** dim * dim:
+        raise ValueError(f"link_angles has {phi.size} entries, expected {L ** dim * dim}")
+    h = ctypes.c_void_p()
+    _check(load().gc_create_orbit(dim, L, _ptr(phi, ctypes.c_double), orbit_id, max_copies,
+                                  ctypes.byref(h)))
+    return h
+
+
+def gc_enumerate_copies(orbit, n_starts: int, omega: float, eps: float, opt: gc_options | None = None):
+    _check(load().gc_enumerate_copies(orbit, n_starts, omega, eps,
+                                      None if opt is None else ctypes.byref(opt)))
+
+
+def gc_fetch_copies(orbit, V: int, capacity: int | None = None, theta: bool = True) -> dict:
+    lib = load()
+    n = ctypes.c_size_t()
+    _check(lib.gc_fetch_copies(orbit, 0, ctypes.byref(n), None, None, None, None, None, None))
+    m = n.value if capacity is None else min(capacity, n.value)
+    F = np.zeros(m)
+    th = np.zeros((m, V)) if theta else None
+    first = np.zeros(m, np.uint64)
+    count = np.zeros(m, np.uint64)
+    lam = np.zeros(m)
+    reg = np.zeros(m, np.int32)
+    if m:
+        _check(lib.gc_fetch_copies(orbit, m, ctypes.byref(n), _ptr(F, ctypes.c_double),
+                                   _ptr(th, ctypes.c_double), _ptr(first, ctypes.c_uint64),
+                                   _ptr(count, ctypes.c_uint64), _ptr(lam, ctypes.c_double),
+                                   _ptr(reg, ctypes.c_int)))
+    return {"n_distinct": n.value, "F": F, "theta": th, "first_start": first, "count": count,
+            "lambda2": lam, "region": reg}
+
+
+def gc_fetch_starts(orbit, first: int, n: int) -> dict:
+    st = np.zeros(n, np.int32)
+    sw = np.zeros(n, np.int32)
+    F = np.zeros(n)
+    ci = np.zeros(n, np.int64)
+    _check(load().gc_fetch_starts(orbit, first, n, _ptr(st, ctypes.c_int), _ptr(sw, ctypes.c_int),
+                                  _ptr(F, ctypes.c_double), _ptr(ci, ctypes.c_int64)))
+    return {"status": st, "sweeps": sw, "F": F, "copy_idx": ci}
+
+
+def gc_orbit_stats(orbit) -> dict:
+    s = gc_stats()
+    _check(load().gc_orbit_stats(orbit, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in gc_stats._fields_}
+
+
+def gc_destroy_orbit(orbit):
+    _check(load().gc_destroy_orbit(orbit))

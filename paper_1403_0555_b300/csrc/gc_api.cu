@@ -1,0 +1,783 @@
+// C ABI and host runtime of the Gribov-copy enumerator: orbit objects, memory
+// admission, batch planning and kernel launches (declarations: gribov.h).
+#include "gribov.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "gc_common.cuh"
+#include "gc_fptest.cuh"
+#include "gc_relax.cuh"
+#include "gc_table.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define GC_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return fail(GC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+gc_alloc_fn g_alloc = nullptr;
+gc_free_fn g_free = nullptr;
+void* g_actx = nullptr;
+
+void* dev_alloc(size_t n, cudaStream_t s) {
+  if (n == 0) n = 16;
+  if (g_alloc) return g_alloc(n, (void*)s, g_actx);
+  void* p = nullptr;
+  if (cudaMalloc(&p, n) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return p;
+}
+void dev_free(void* p, cudaStream_t s) {
+  if (!p) return;
+  if (g_free) g_free(p, (void*)s, g_actx);
+  else cudaFree(p);
+}
+
+struct Buf {
+  void* p = nullptr;
+  size_t n = 0;
+  bool ensure(size_t bytes, cudaStream_t s) {
+    if (bytes <= n && p) return true;
+    dev_free(p, s);
+    p = dev_alloc(bytes, s);
+    n = p ? bytes : 0;
+    return p != nullptr;
+  }
+  void release(cudaStream_t s) { dev_free(p, s); p = nullptr; n = 0; }
+  template <class T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+unsigned next_pow2(unsigned long long v) {
+  unsigned long long p = 1;
+  while (p < v) p <<= 1;
+  return (unsigned)p;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+size_t max_smem_optin() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return n > 0 ? (size_t)n : 48 * 1024;
+}
+
+}  // namespace
+
+enum StatSlot {
+  kSweeps = 0, kUpdates = 1, kConv = 2, kNConv = 3, kNewton = 4, kFallback = 5, kUpd64 = 6,
+  kPass = 7, kPConv = 8, kPNConv = 9, kNew = 10, kHit = 11, kDFail = 12, kTests = 13,
+  kTests64 = 14, kLanczos = 15, kSweeps32 = 16, kUpdates32 = 17, kConv32 = 18, kNConv32 = 19, kInner = 20, kUpd32Fallback = 21,
+  kNumStats = 24
+};
+
+struct gc_orbit_s {
+  int d = 0, L = 0, V = 0, ncolor = 0;
+  uint64_t orbit_id = 0;
+  gc::Geom geom{};
+  int team = 32;
+  cudaStream_t alloc_stream = nullptr;
+  Buf links64, links32;
+  // copy table
+  unsigned cap = 0, nb = 0, nl = 0, f8cap = 0;
+  Buf t_cfg, t_F, t_q, t_t, t_first, t_count, t_next, t_lam, t_region, t_head, t_lock, t_f8;
+  Buf t_counters;    // n_entries, n_new (u32) | n_f8 (u64) | err[4] (i32)
+  Buf t_newlist;
+  // batch staging
+  Buf s_status, s_sweeps, s_resid, s_F, s_fprint, s_config, s_state32, s_copy;
+  Buf work, stats, scratch, theta_tmp;
+  size_t batch_cap = 0;
+  uint64_t next_start = 0;
+  // per-start records of the last call
+  uint64_t rec_first = 0, rec_n = 0;
+  std::vector<int8_t> rec_status;
+  std::vector<int32_t> rec_sweeps;
+  std::vector<double> rec_F;
+  std::vector<int32_t> rec_copy;
+  // host-side accumulators
+  uint64_t n_starts = 0;
+  double ms[4] = {0, 0, 0, 0};
+  uint64_t launches = 0;   // kernels this orbit launched
+  int last_precision = GC_FP64;
+  cudaEvent_t ev[8] = {};
+
+  unsigned* n_entries() const { return t_counters.as<unsigned>(); }
+  unsigned* n_new() const { return t_counters.as<unsigned>() + 1; }
+  unsigned long long* n_f8() const { return reinterpret_cast<unsigned long long*>(t_counters.as<char>() + 8); }
+  int* err() const { return reinterpret_cast<int*>(t_counters.as<char>() + 16); }
+
+  gc::TableView view() const {
+    gc::TableView T{};
+    T.cfg = t_cfg.as<double2>();
+    T.F = t_F.as<double>();
+    T.q = t_q.as<long long>();
+    T.t = t_t.as<int>();
+    T.first_start = t_first.as<unsigned long long>();
+    T.count = t_count.as<unsigned long long>();
+    T.next = t_next.as<int>();
+    T.lambda2 = t_lam.as<double>();
+    T.region = t_region.as<int>();
+    T.head = t_head.as<int>();
+    T.lock = t_lock.as<int>();
+    T.n_entries = n_entries();
+    T.new_list = t_newlist.as<unsigned>();
+    T.n_new = n_new();
+    T.f8 = t_f8.as<unsigned long long>();
+    T.n_f8 = n_f8();
+    T.err = err();
+    T.cap = cap;
+    T.nb_mask = nb - 1;
+    T.nl_mask = nl - 1;
+    T.f8_mask = f8cap - 1;
+    return T;
+  }
+};
+
+namespace {
+
+void fill_i32(int* p, int v, size_t n, cudaStream_t s) {
+  if (!n) return;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+  gc::fill_int_kernel<<<blocks, 256, 0, s>>>(p, v, n);
+}
+void fill_u64(unsigned long long* p, unsigned long long v, size_t n, cudaStream_t s) {
+  if (!n) return;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+  gc::fill_u64_kernel<<<blocks, 256, 0, s>>>(p, v, n);
+}
+
+// Re-insert the keys of an old F8 set into a new one.
+__global__ void f8_rehash_kernel(const unsigned long long* old_set, unsigned old_n,
+                                 unsigned long long* set, unsigned mask, int* err) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < old_n; i += gridDim.x * blockDim.x) {
+    const unsigned long long k = old_set[i];
+    if (k == gc::kF8Empty) continue;
+    unsigned slot = (unsigned)(gc::mix64(k) & mask);
+    bool placed = false;
+    for (unsigned p = 0; p <= mask; ++p) {
+      if (atomicCAS(&set[slot], gc::kF8Empty, k) == gc::kF8Empty) { placed = true; break; }
+      slot = (slot + 1) & mask;
+    }
+    if (!placed) atomicExch(&err[2], 1);
+  }
+}
+
+// Grow (or create) the copy pool so that it holds at least `need` entries.
+int table_reserve(gc_orbit o, unsigned long long need, unsigned cur, cudaStream_t s) {
+  if (need <= o->cap && o->cap) return GC_OK;
+  unsigned long long want = std::max<unsigned long long>(need, o->cap ? 2ULL * o->cap : 1024ULL);
+  if (want > 0x7fffffffULL) return fail(GC_ENOMEM, "copy pool would exceed 2^31 entries");
+  const unsigned ncap = (unsigned)want;
+  const size_t V = o->V;
+  Buf cfg, F, q, t, first, count, next, lam, region;
+  bool ok = cfg.ensure(ncap * V * sizeof(double2), s) && F.ensure(ncap * 8ull, s) &&
+            q.ensure(ncap * 8ull, s) && t.ensure(ncap * 4ull, s) && first.ensure(ncap * 8ull, s) &&
+            count.ensure(ncap * 8ull, s) && next.ensure(ncap * 4ull, s) && lam.ensure(ncap * 8ull, s) &&
+            region.ensure(ncap * 4ull, s);
+  Buf newlist;
+  ok = ok && newlist.ensure(ncap * 4ull, s);
+  const unsigned nnb = next_pow2(2ull * ncap);
+  Buf head;
+  ok = ok && head.ensure(nnb * 4ull, s);
+  const unsigned nf8 = next_pow2(4ull * ncap);
+  Buf f8;
+  ok = ok && f8.ensure(nf8 * 8ull, s);
+  if (!ok) {
+    for (Buf* b : {&cfg, &F, &q, &t, &first, &count, &next, &lam, &region, &newlist, &head, &f8}) b->release(s);
+    return fail(GC_ENOMEM, "cannot admit a copy pool of %u entries (%.1f MiB)", ncap,
+                ncap * (V * 16.0 + 64.0) / 1048576.0);
+  }
+  if (cur) {
+    GC_CUDA(cudaMemcpyAsync(cfg.p, o->t_cfg.p, cur * V * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    GC_CUDA(cudaMemcpyAsync(F.p, o->t_F.p, cur * 8ull, cudaMemcpyDeviceToDevice, s));
+    GC_CUDA(cudaMemcpyAsync(q.p, o->t_q.p, cur * 8ull, cudaMemcpyDeviceToDevice, s));
+    GC_CUDA(cudaMemcpyAsync(t.p, o->t_t.p, cur * 4ull, cudaMemcpyDeviceToDevice, s));
+    GC_CUDA(cudaMemcpyAsync(first.p, o->t_first.p, cur * 8ull, cudaMemcpyDeviceToDevice, s));
+    GC_CUDA(cudaMemcpyAsync(count.p, o->t_count.p, cur * 8ull, cudaMemcpyDeviceToDevice, s));
+    GC_CUDA(cudaMemcpyAsync(lam.p, o->t_lam.p, cur * 8ull, cudaMemcpyDeviceToDevice, s));
+    GC_CUDA(cudaMemcpyAsync(region.p, o->t_region.p, cur * 4ull, cudaMemcpyDeviceToDevice, s));
+  }
+  fill_i32(head.as<int>(), -1, nnb, s);
+  fill_u64(f8.as<unsigned long long>(), gc::kF8Empty, nf8, s);
+  o->launches += 2;
+  if (o->f8cap) {
+    const unsigned blocks = std::min<unsigned>((o->f8cap + 255) / 256, 4096);
+    f8_rehash_kernel<<<blocks, 256, 0, s>>>(o->t_f8.as<unsigned long long>(), o->f8cap,
+                                              f8.as<unsigned long long>(), nf8 - 1, o->err());
+    ++o->launches;
+  }
+  for (Buf* b : {&o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_count, &o->t_next, &o->t_lam,
+                 &o->t_region, &o->t_newlist, &o->t_head, &o->t_f8})
+    b->release(s);
+  o->t_cfg = cfg; o->t_F = F; o->t_q = q; o->t_t = t; o->t_first = first; o->t_count = count;
+  o->t_next = next; o->t_lam = lam; o->t_region = region; o->t_newlist = newlist; o->t_head = head;
+  o->t_f8 = f8;
+  o->cap = ncap; o->nb = nnb; o->f8cap = nf8;
+  if (cur) {
+    const unsigned blocks = std::min<unsigned>((cur + 255) / 256, 4096);
+    gc::relink_kernel<<<blocks, 256, 0, s>>>(o->view(), cur);
+    ++o->launches;
+  }
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+int team_size(const gc::Geom& G) {
+  int maxc = 0;
+  for (int c = 0; c < G.ncolor; ++c) maxc = std::max(maxc, G.color_off[c + 1] - G.color_off[c]);
+  return (int)std::min<unsigned>(32u, next_pow2((unsigned)std::max(1, maxc)));
+}
+
+template <class K>
+int launch_grid(K kernel, int threads, size_t smem, long long work_items_per_block, long long items,
+                int* grid) {
+  if (smem > 48 * 1024) GC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
+  if (per_sm < 1) return fail(GC_EINVAL, "kernel does not fit an SM (%zu bytes shared memory)", smem);
+  long long want = (items + work_items_per_block - 1) / work_items_per_block;
+  *grid = (int)std::max<long long>(1, std::min<long long>((long long)per_sm * sm_count(), want));
+  return GC_OK;
+}
+
+// Pick warps per CTA so the shared-memory footprint fits; returns 0 if even one warp does not.
+template <class F>
+int fit_warps(int max_warps, F bytes_for) {
+  const size_t lim = max_smem_optin();
+  for (int w = max_warps; w >= 1; --w)
+    if (bytes_for(w) <= lim) return w;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gc_set_allocator(gc_alloc_fn alloc, gc_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(GC_EINVAL, "gc_set_allocator: give both hooks or neither");
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_actx = ctx;
+  return GC_OK;
+}
+
+int gc_options_default(gc_options* opt) {
+  if (!opt) return fail(GC_EINVAL, "gc_options_default: opt is NULL");
+  std::memset(opt, 0, sizeof *opt);
+  opt->precision = GC_FP64;
+  opt->check_every = 1;
+  opt->max_sweeps = 100000;
+  opt->eps32 = 1e-10;
+  opt->dedup_delta = 1e-6;
+  opt->fp_tau = 1e-9;
+  opt->fp_mode = GC_FP_AUTO;
+  opt->lanczos_k = 300;
+  opt->seed = 1;
+  opt->keep_per_start = 0;
+  opt->newton_inner = 320;
+  opt->newton_max = 6;
+  opt->batch_starts = 0;
+  opt->stream = nullptr;
+  return GC_OK;
+}
+
+const char* gc_last_error(void) { return g_err.c_str(); }
+const char* gc_version(void) { return "gribov-b300 0.1 (sm_103a)"; }
+
+int gc_create_orbit(int dim, int L, const double* link_angles, uint64_t orbit_id, size_t max_copies,
+                    gc_orbit* out) {
+  if (!out) return fail(GC_EINVAL, "gc_create_orbit: out is NULL");
+  *out = nullptr;
+  if (dim < 1 || dim > gc::kMaxDim) return fail(GC_EINVAL, "dimension %d not in 1..4", dim);
+  if (L < 2) return fail(GC_EINVAL, "L = %d < 2", L);
+  if (!link_angles) return fail(GC_EINVAL, "link_angles is NULL");
+  double Vd = std::pow((double)L, dim);
+  if (Vd > gc::kMaxSites) return fail(GC_EINVAL, "lattice of %.0f sites exceeds %d", Vd, gc::kMaxSites);
+  const int V = (int)Vd;
+  // the FP64 sweep keeps links, tables and one lattice in shared memory
+  const size_t need = gc::Smem(V, dim, 16, (size_t)V * 16, 1).total;
+  if (need > max_smem_optin())
+    return fail(GC_EINVAL, "lattice %d^%d needs %zu bytes of shared memory (limit %zu)", L, dim, need,
+                max_smem_optin());
+  for (int i = 0; i < V * dim; ++i)
+    if (!std::isfinite(link_angles[i])) return fail(GC_EINVAL, "link angle %d is not finite", i);
+
+  gc_orbit o = new (std::nothrow) gc_orbit_s;
+  if (!o) return fail(GC_ENOMEM, "host allocation failed");
+  o->d = dim; o->L = L; o->V = V; o->orbit_id = orbit_id;
+  o->ncolor = (L % 2 == 0) ? 2 : 3;
+  gc::Geom& G = o->geom;
+  G.d = dim; G.L = L; G.V = V; G.ncolor = o->ncolor;
+  int cnt[3] = {0, 0, 0};
+  for (int x = 0; x < V; ++x) cnt[gc::site_color(x, dim, L)]++;
+  G.color_off[0] = 0;
+  for (int c = 0; c < 3; ++c) G.color_off[c + 1] = G.color_off[c] + (c < o->ncolor ? cnt[c] : 0);
+  {
+    // site V-1 is the last site of its colour in colour-major order
+    const int cl = gc::site_color(V - 1, dim, L);
+    G.pos_last = G.color_off[cl + 1] - 1;
+  }
+  o->team = team_size(G);
+
+  std::vector<double2> u64((size_t)V * dim);
+  std::vector<float2> u32((size_t)V * dim);
+  for (size_t i = 0; i < u64.size(); ++i) {
+    u64[i] = make_double2(std::cos(link_angles[i]), std::sin(link_angles[i]));
+    u32[i] = make_float2((float)u64[i].x, (float)u64[i].y);
+  }
+  cudaStream_t s = nullptr;
+  int rc = GC_OK;
+  if (!o->links64.ensure(u64.size() * sizeof(double2), s) || !o->links32.ensure(u32.size() * sizeof(float2), s) ||
+      !o->t_counters.ensure(64, s) || !o->stats.ensure(kNumStats * 8, s) || !o->work.ensure(64, s) ||
+      !o->t_lock.ensure((size_t)(o->nl = 1u << 16) * 4, s)) {
+    rc = fail(GC_ENOMEM, "cannot admit orbit buffers");
+  }
+  if (rc == GC_OK) {
+    cudaError_t e = cudaMemcpy(o->links64.p, u64.data(), u64.size() * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(o->links32.p, u32.data(), u32.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(o->t_counters.p, 0, 64);
+    if (e == cudaSuccess) e = cudaMemset(o->stats.p, 0, kNumStats * 8);
+    if (e == cudaSuccess) e = cudaMemset(o->t_lock.p, 0, (size_t)o->nl * 4);
+    if (e != cudaSuccess) rc = fail(GC_ECUDA, "orbit upload: %s", cudaGetErrorString(e));
+  }
+  if (rc == GC_OK) {
+    const unsigned long long first = max_copies ? max_copies : 4096;
+    rc = table_reserve(o, first, 0, s);
+  }
+  if (rc == GC_OK) {
+    for (auto& e : o->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) { rc = fail(GC_ECUDA, "cudaEventCreate failed"); break; }
+  }
+  if (rc == GC_OK && cudaDeviceSynchronize() != cudaSuccess) rc = fail(GC_ECUDA, "orbit set-up: %s", cudaGetErrorString(cudaGetLastError()));
+  if (rc != GC_OK) {
+    gc_destroy_orbit(o);
+    return rc;
+  }
+  *out = o;
+  return GC_OK;
+}
+
+int gc_destroy_orbit(gc_orbit o) {
+  if (!o) return fail(GC_EINVAL, "gc_destroy_orbit: NULL orbit");
+  cudaDeviceSynchronize();
+  cudaStream_t s = nullptr;
+  for (Buf* b : {&o->links64, &o->links32, &o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_count,
+                 &o->t_next, &o->t_lam, &o->t_region, &o->t_head, &o->t_lock, &o->t_f8, &o->t_counters,
+                 &o->t_newlist, &o->s_status, &o->s_sweeps, &o->s_resid, &o->s_F, &o->s_fprint,
+                 &o->s_config, &o->s_state32, &o->s_copy, &o->work, &o->stats, &o->scratch, &o->theta_tmp})
+    b->release(s);
+  for (auto& e : o->ev)
+    if (e) cudaEventDestroy(e);
+  delete o;
+  return GC_OK;
+}
+
+int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps, const gc_options* opt_in) {
+  if (!o) return fail(GC_EINVAL, "gc_enumerate_copies: NULL orbit");
+  gc_options opt;
+  if (opt_in) opt = *opt_in; else gc_options_default(&opt);
+  if (!(omega > 0.0 && omega < 2.0)) return fail(GC_EINVAL, "omega = %g not in (0, 2)", omega);
+  if (!(eps > 0.0)) return fail(GC_EINVAL, "eps = %g must be > 0", eps);
+  if (opt.precision != GC_FP64 && opt.precision != GC_MIXED) return fail(GC_EINVAL, "unknown precision %d", opt.precision);
+  if (opt.check_every < 1) return fail(GC_EINVAL, "check_every = %d < 1", opt.check_every);
+  if (opt.max_sweeps < 1) return fail(GC_EINVAL, "max_sweeps = %d < 1", opt.max_sweeps);
+  if (opt.fp_mode < GC_FP_AUTO || opt.fp_mode > GC_FP_NONE) return fail(GC_EINVAL, "unknown fp_mode %d", opt.fp_mode);
+  if (opt.precision == GC_MIXED && !(opt.eps32 > 0.0)) return fail(GC_EINVAL, "eps32 = %g must be > 0", opt.eps32);
+  if (!(opt.dedup_delta > 0.0 && opt.dedup_delta < 0.1)) return fail(GC_EINVAL, "dedup_delta = %g not in (0, 0.1)", opt.dedup_delta);
+  if (!(opt.fp_tau >= 0.0)) return fail(GC_EINVAL, "fp_tau = %g < 0", opt.fp_tau);
+  if (opt.lanczos_k < 2) return fail(GC_EINVAL, "lanczos_k = %d < 2", opt.lanczos_k);
+  if (opt.newton_inner < 1 || opt.newton_max < 0) return fail(GC_EINVAL, "bad Newton polish settings");
+  if (n_starts == 0) return GC_OK;
+  const int max_sweeps = ((opt.max_sweeps + opt.check_every - 1) / opt.check_every) * opt.check_every;
+  cudaStream_t s = (cudaStream_t)opt.stream;
+  const int V = o->V, d = o->d;
+  const bool mixed = opt.precision == GC_MIXED;
+  o->last_precision = opt.precision;
+
+  // batch size: staging of at most ~1 GiB
+  const size_t per_start = (size_t)V * 16 + (mixed ? (size_t)V * 8 : 0) + 48;
+  size_t B = opt.batch_starts > 0 ? (size_t)opt.batch_starts : std::max<size_t>(4096, (1ull << 30) / per_start);
+  B = std::min<size_t>(B, n_starts);
+  if (!o->s_status.ensure(B, s) || !o->s_sweeps.ensure(B * 4, s) || !o->s_resid.ensure(B * 8, s) ||
+      !o->s_F.ensure(B * 8, s) || !o->s_fprint.ensure(B * 8, s) || !o->s_config.ensure(B * V * 16, s) ||
+      !o->s_copy.ensure(B * 4, s) || (mixed && !o->s_state32.ensure(B * V * 8, s)))
+    return fail(GC_ENOMEM, "cannot admit a batch of %zu starts (%.1f MiB staging)", B, B * per_start / 1048576.0);
+
+  if (opt.keep_per_start) {
+    o->rec_first = o->next_start;
+    o->rec_n = n_starts;
+    o->rec_status.assign(n_starts, 0);
+    o->rec_sweeps.assign(n_starts, 0);
+    o->rec_F.assign(n_starts, 0.0);
+    o->rec_copy.assign(n_starts, -1);
+  } else {
+    o->rec_n = 0;
+  }
+
+  // launch shapes
+  const int T = o->team;
+  const int tpw = 32 / T;
+  auto relax_bytes = [&](int warps, int site_bytes) {
+    return gc::Smem(V, d, site_bytes, (size_t)V * site_bytes, warps * tpw).total;
+  };
+  const int site_bytes = mixed ? 8 : 16;
+  const int r_warps = fit_warps(8, [&](int w) { return relax_bytes(w, site_bytes); });
+  if (!r_warps) return fail(GC_EINVAL, "relaxation does not fit shared memory");
+  const size_t r_smem = relax_bytes(r_warps, site_bytes);
+  auto polish_bytes = [&](int warps) {
+    return gc::Smem(V, d, sizeof(double2), gc::polish_team_bytes(V, d), warps * tpw).total;
+  };
+  // two CTAs per SM when that fits: the polish is latency bound at low occupancy
+  int p_warps = mixed ? fit_warps(8, [&](int w) { return 2 * polish_bytes(w) + 2048; }) : 0;
+  if (mixed && !p_warps) p_warps = fit_warps(8, polish_bytes);
+  if (mixed && !p_warps) return fail(GC_EINVAL, "polish does not fit shared memory");
+  const size_t p_smem = mixed ? polish_bytes(p_warps) : 0;
+  const int kmax64 = std::min(opt.lanczos_k, std::max(1, V - 1));
+  const int kmax32 = std::min(160, kmax64);
+  const int kmax_sm = std::max(kmax64, kmax32);
+  const int f_warps = fit_warps(4, [&](int w) { return gc::FpSmem(V, d, kmax_sm, w).total; });
+  if (!f_warps) return fail(GC_EINVAL, "Faddeev-Popov test does not fit shared memory");
+  const size_t f_smem = gc::FpSmem(V, d, kmax_sm, f_warps).total;
+
+  unsigned long long* wctr = o->work.as<unsigned long long>();
+  unsigned long long* stats = o->stats.as<unsigned long long>();
+  GC_CUDA(cudaMemsetAsync(o->err(), 0, 16, s));
+
+  for (uint64_t done = 0; done < n_starts;) {
+    const long long b = (long long)std::min<uint64_t>(B, n_starts - done);
+    // admission: the pool must hold every start of the batch as a new copy
+    unsigned cur = 0;
+    GC_CUDA(cudaMemcpyAsync(&cur, o->n_entries(), 4, cudaMemcpyDeviceToHost, s));
+    GC_CUDA(cudaStreamSynchronize(s));
+    if ((unsigned long long)cur + b > o->cap) {
+      int rc = table_reserve(o, (unsigned long long)cur + b, cur, s);
+      if (rc != GC_OK) return rc;
+    }
+    GC_CUDA(cudaMemsetAsync(wctr, 0, 16, s));
+    GC_CUDA(cudaMemsetAsync(o->n_new(), 0, 4, s));
+
+    // relaxation
+    gc::RelaxArgs ra{};
+    ra.geom = o->geom;
+    ra.links64 = o->links64.as<double2>();
+    ra.links32 = o->links32.as<float2>();
+    ra.seed = opt.seed;
+    ra.orbit_id = o->orbit_id;
+    ra.start0 = o->next_start;
+    ra.n = b;
+    ra.work_ctr = wctr;
+    ra.omega = omega;
+    ra.om1 = 1.0 - omega;
+    ra.eps = eps;
+    ra.omega32 = (float)omega;
+    ra.om1_32 = (float)(1.0 - omega);
+    ra.eps32 = (float)opt.eps32;
+    ra.check_every = opt.check_every;
+    ra.max_sweeps = max_sweeps;
+    ra.team = T;
+    ra.stat_base = mixed ? kSweeps32 : kSweeps;
+    ra.status = o->s_status.as<int8_t>();
+    ra.sweeps = o->s_sweeps.as<int32_t>();
+    ra.resid = o->s_resid.as<double>();
+    ra.F = o->s_F.as<double>();
+    ra.fprint = o->s_fprint.as<double>();
+    ra.config = o->s_config.as<double2>();
+    ra.state32 = o->s_state32.as<float2>();
+    ra.stats = stats;
+    int grid = 0;
+    GC_CUDA(cudaEventRecord(o->ev[0], s));
+    if (mixed) {
+      if (int rc = launch_grid(gc::relax_kernel<gc::Fast32>, r_warps * 32, r_smem, (long long)r_warps * tpw, b, &grid)) return rc;
+      gc::relax_kernel<gc::Fast32><<<grid, r_warps * 32, r_smem, s>>>(ra);
+      ++o->launches;
+    } else {
+      if (int rc = launch_grid(gc::relax_kernel<gc::Exact64>, r_warps * 32, r_smem, (long long)r_warps * tpw, b, &grid)) return rc;
+      gc::relax_kernel<gc::Exact64><<<grid, r_warps * 32, r_smem, s>>>(ra);
+      ++o->launches;
+    }
+    GC_CUDA(cudaGetLastError());
+    GC_CUDA(cudaEventRecord(o->ev[1], s));
+    if (mixed) {
+      gc::PolishArgs pa{};
+      pa.geom = o->geom;
+      pa.links64 = ra.links64;
+      pa.links32 = ra.links32;
+      pa.n = b;
+      pa.work_ctr = wctr + 1;
+      pa.omega = omega;
+      pa.om1 = 1.0 - omega;
+      pa.eps = eps;
+      pa.omega_in = (float)omega;
+      pa.lin_tol = 4e-5f;
+      pa.inner_max = opt.newton_inner;
+      pa.newton_max = opt.newton_max;
+      pa.max_sweeps = max_sweeps;
+      pa.check_every = opt.check_every;
+      pa.team = T;
+      pa.status = ra.status;
+      pa.sweeps = ra.sweeps;
+      pa.resid = ra.resid;
+      pa.state32 = ra.state32;
+      pa.F = ra.F;
+      pa.fprint = ra.fprint;
+      pa.config = ra.config;
+      pa.stats = stats;
+      if (int rc = launch_grid(gc::polish_kernel, p_warps * 32, p_smem, (long long)p_warps * tpw, b, &grid)) return rc;
+      gc::polish_kernel<<<grid, p_warps * 32, p_smem, s>>>(pa);
+      ++o->launches;
+      GC_CUDA(cudaGetLastError());
+    }
+    GC_CUDA(cudaEventRecord(o->ev[2], s));
+    // deduplication
+    gc::DedupArgs da{};
+    da.tab = o->view();
+    da.tab.wF = 1e-9 * std::max(1.0, (double)d * V * 1e-3);
+    da.tab.wT = 1e-5;
+    da.tab.tolF = da.tab.wF;
+    da.tab.delta2 = opt.dedup_delta * opt.dedup_delta;
+    da.tab.f8_links = (double)d * V;
+    da.V = V;
+    da.n = b;
+    da.start0 = o->next_start;
+    da.status = ra.status;
+    da.F = ra.F;
+    da.fprint = ra.fprint;
+    da.config = ra.config;
+    da.copy_of = o->s_copy.as<int>();
+    da.stats = stats;
+    {
+      const int blocks = (int)std::max<long long>(1, std::min<long long>((b + 7) / 8, (long long)sm_count() * 8));
+      gc::dedup_kernel<<<blocks, 256, 0, s>>>(da);
+      ++o->launches;
+      GC_CUDA(cudaGetLastError());
+    }
+    GC_CUDA(cudaEventRecord(o->ev[3], s));
+    // Faddeev-Popov test of the copies this batch created
+    if (opt.fp_mode != GC_FP_NONE) {
+      gc::FpArgs fa{};
+      fa.geom = o->geom;
+      fa.cfg = o->t_cfg.as<double2>();
+      fa.first_start = o->t_first.as<unsigned long long>();
+      fa.links64 = ra.links64;
+      fa.links32 = ra.links32;
+      fa.list = o->t_newlist.as<unsigned>();
+      fa.n_list = o->n_new();
+      fa.lambda2 = o->t_lam.as<double>();
+      fa.region = o->t_region.as<int>();
+      fa.mode = opt.fp_mode;
+      fa.kmax32 = kmax32;
+      fa.kmax64 = kmax64;
+      fa.tau = opt.fp_tau;
+      fa.margin32 = 1e-3;
+      fa.tol32 = 1e-5;
+      fa.tol64 = 1e-12;
+      fa.seed = opt.seed;
+      fa.stats = stats;
+      int fgrid = 0;
+      if (int rc = launch_grid(gc::fp_test_kernel, f_warps * 32, f_smem, f_warps, b, &fgrid)) return rc;
+      if (opt.fp_mode == GC_FP_DENSE) {
+        const size_t slot = (size_t)V * V * 8;
+        const size_t max_slots = std::max<size_t>(1, (1ull << 30) / slot);
+        fgrid = (int)std::min<size_t>(fgrid, std::max<size_t>(1, max_slots / f_warps));
+        if (!o->scratch.ensure((size_t)fgrid * f_warps * slot, s))
+          return fail(GC_ENOMEM, "cannot admit %zu bytes of Lanczos basis scratch", (size_t)fgrid * f_warps * slot);
+        fa.scratch = o->scratch.as<double>();
+      }
+      gc::fp_test_kernel<<<fgrid, f_warps * 32, f_smem, s>>>(fa);
+      ++o->launches;
+      GC_CUDA(cudaGetLastError());
+    }
+    GC_CUDA(cudaEventRecord(o->ev[4], s));
+    if (opt.keep_per_start) {
+      const size_t off = done;
+      GC_CUDA(cudaMemcpyAsync(o->rec_status.data() + off, ra.status, b, cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaMemcpyAsync(o->rec_sweeps.data() + off, ra.sweeps, b * 4, cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaMemcpyAsync(o->rec_F.data() + off, ra.F, b * 8, cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaMemcpyAsync(o->rec_copy.data() + off, da.copy_of, b * 4, cudaMemcpyDeviceToHost, s));
+    }
+    GC_CUDA(cudaStreamSynchronize(s));
+    float t01 = 0, t12 = 0, t23 = 0, t34 = 0;
+    cudaEventElapsedTime(&t01, o->ev[0], o->ev[1]);
+    cudaEventElapsedTime(&t12, o->ev[1], o->ev[2]);
+    cudaEventElapsedTime(&t23, o->ev[2], o->ev[3]);
+    cudaEventElapsedTime(&t34, o->ev[3], o->ev[4]);
+    o->ms[0] += t01; o->ms[1] += t12; o->ms[2] += t23; o->ms[3] += t34;
+    o->next_start += b;
+    o->n_starts += b;
+    done += b;
+  }
+  int err[4] = {0, 0, 0, 0};
+  GC_CUDA(cudaMemcpy(err, o->err(), 16, cudaMemcpyDeviceToHost));
+  if (err[1]) return fail(GC_ENOMEM, "copy pool overflow");
+  if (err[2]) return fail(GC_ENOMEM, "quantised-minimum set overflow");
+  if (err[0]) return fail(GC_ETIMEDOUT, "a copy-table lock wait ran out (affected starts are marked)");
+  return GC_OK;
+}
+
+namespace {
+
+struct Meta {
+  std::vector<double> F, lam;
+  std::vector<unsigned long long> first, count;
+  std::vector<int> region;
+  std::vector<unsigned> order;  // sorted position -> entry
+};
+
+int read_meta(gc_orbit o, Meta& m, unsigned* n_out) {
+  GC_CUDA(cudaDeviceSynchronize());
+  unsigned n = 0;
+  GC_CUDA(cudaMemcpy(&n, o->n_entries(), 4, cudaMemcpyDeviceToHost));
+  n = std::min(n, o->cap);
+  m.F.resize(n); m.lam.resize(n); m.first.resize(n); m.count.resize(n); m.region.resize(n);
+  if (n) {
+    GC_CUDA(cudaMemcpy(m.F.data(), o->t_F.p, n * 8ull, cudaMemcpyDeviceToHost));
+    GC_CUDA(cudaMemcpy(m.lam.data(), o->t_lam.p, n * 8ull, cudaMemcpyDeviceToHost));
+    GC_CUDA(cudaMemcpy(m.first.data(), o->t_first.p, n * 8ull, cudaMemcpyDeviceToHost));
+    GC_CUDA(cudaMemcpy(m.count.data(), o->t_count.p, n * 8ull, cudaMemcpyDeviceToHost));
+    GC_CUDA(cudaMemcpy(m.region.data(), o->t_region.p, n * 4ull, cudaMemcpyDeviceToHost));
+  }
+  m.order.resize(n);
+  std::iota(m.order.begin(), m.order.end(), 0u);
+  std::sort(m.order.begin(), m.order.end(), [&](unsigned a, unsigned b) {
+    if (m.F[a] != m.F[b]) return m.F[a] < m.F[b];
+    return m.first[a] < m.first[b];
+  });
+  *n_out = n;
+  return GC_OK;
+}
+
+}  // namespace
+
+int gc_fetch_copies(gc_orbit o, size_t capacity, size_t* n_distinct, double* F, double* theta,
+                    uint64_t* first_start, uint64_t* count, double* lambda2, int* region) {
+  if (!o) return fail(GC_EINVAL, "gc_fetch_copies: NULL orbit");
+  if (!n_distinct) return fail(GC_EINVAL, "gc_fetch_copies: n_distinct is NULL");
+  Meta m;
+  unsigned n = 0;
+  if (int rc = read_meta(o, m, &n)) return rc;
+  *n_distinct = n;
+  if (capacity == 0) return GC_OK;
+  const size_t k = std::min<size_t>(capacity, n);
+  const size_t V = o->V;
+  for (size_t i = 0; i < k; ++i) {
+    const unsigned e = m.order[i];
+    if (F) F[i] = m.F[e];
+    if (first_start) first_start[i] = m.first[e];
+    if (count) count[i] = m.count[e];
+    if (lambda2) lambda2[i] = m.lam[e];
+    if (region) region[i] = m.region[e];
+  }
+  if (theta && k) {
+    if (!o->theta_tmp.ensure((size_t)n * V * 8, nullptr)) return fail(GC_ENOMEM, "cannot admit fetch buffer");
+    const size_t tot = (size_t)n * V;
+    const int blocks = (int)std::min<size_t>((tot + 255) / 256, 8192);
+    gc::angles_kernel<<<blocks, 256>>>(o->t_cfg.as<double2>(), o->theta_tmp.as<double>(), tot);
+    ++o->launches;
+    GC_CUDA(cudaGetLastError());
+    std::vector<double> all(tot);
+    GC_CUDA(cudaMemcpy(all.data(), o->theta_tmp.p, tot * 8, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < k; ++i) std::memcpy(theta + i * V, all.data() + (size_t)m.order[i] * V, V * 8);
+  }
+  return GC_OK;
+}
+
+int gc_fetch_starts(gc_orbit o, uint64_t first, uint64_t n, int* status, int* sweeps, double* F,
+                    int64_t* copy_idx) {
+  if (!o) return fail(GC_EINVAL, "gc_fetch_starts: NULL orbit");
+  if (o->rec_n == 0) return fail(GC_ESTATE, "no per-start records (enable keep_per_start)");
+  if (first < o->rec_first || first + n > o->rec_first + o->rec_n)
+    return fail(GC_EINVAL, "starts [%llu, %llu) outside the last call's range [%llu, %llu)",
+                (unsigned long long)first, (unsigned long long)(first + n),
+                (unsigned long long)o->rec_first, (unsigned long long)(o->rec_first + o->rec_n));
+  std::vector<int64_t> pos;
+  if (copy_idx) {
+    Meta m;
+    unsigned ne = 0;
+    if (int rc = read_meta(o, m, &ne)) return rc;
+    pos.assign(ne, -1);
+    for (unsigned i = 0; i < ne; ++i) pos[m.order[i]] = i;
+  }
+  for (uint64_t i = 0; i < n; ++i) {
+    const size_t r = (size_t)(first - o->rec_first + i);
+    if (status) status[i] = o->rec_status[r];
+    if (sweeps) sweeps[i] = o->rec_sweeps[r];
+    if (F) F[i] = o->rec_F[r];
+    if (copy_idx) {
+      const int c = o->rec_copy[r];
+      copy_idx[i] = (c >= 0 && (size_t)c < pos.size()) ? pos[c] : -1;
+    }
+  }
+  return GC_OK;
+}
+
+int gc_orbit_stats(gc_orbit o, gc_stats* out) {
+  if (!o || !out) return fail(GC_EINVAL, "gc_orbit_stats: NULL argument");
+  std::memset(out, 0, sizeof *out);
+  GC_CUDA(cudaDeviceSynchronize());
+  unsigned long long st[kNumStats] = {};
+  GC_CUDA(cudaMemcpy(st, o->stats.p, sizeof st, cudaMemcpyDeviceToHost));
+  unsigned long long nf8 = 0;
+  GC_CUDA(cudaMemcpy(&nf8, o->n_f8(), 8, cudaMemcpyDeviceToHost));
+  Meta m;
+  unsigned n = 0;
+  if (int rc = read_meta(o, m, &n)) return rc;
+  out->n_starts = o->n_starts;
+  out->n_converged = st[kConv] + st[kPConv];
+  out->n_not_converged = st[kNConv] + st[kPNConv];
+  out->n_dedup_failed = st[kDFail];
+  out->n_distinct = n;
+  out->n_distinct_F8 = nf8;
+  for (unsigned i = 0; i < n; ++i) {
+    switch (m.region[i]) {
+      case GC_REGION_IN: out->n_in++; break;
+      case GC_REGION_OUT: out->n_out++; break;
+      case GC_REGION_MARGINAL: out->n_marginal++; break;
+      default: out->n_untested++; break;
+    }
+  }
+  out->sweeps_fp32 = st[kSweeps32];
+  out->site_updates_fp32 = st[kUpdates32] + st[kUpd32Fallback];
+  out->sweeps_fp64 = st[kSweeps] + st[kUpd64] / (unsigned long long)o->V;
+  out->site_updates_fp64 = st[kUpdates] + st[kUpd64];
+  out->newton_steps = st[kNewton];
+  out->newton_inner_sweeps = st[kInner];
+  out->polish_fallbacks = st[kFallback];
+  out->fp64_residual_passes = st[kPass];
+  out->fp_tests = st[kTests];
+  out->fp_tests_fp64 = st[kTests64];
+  out->lanczos_steps = st[kLanczos];
+  out->ms_relax = o->ms[0];
+  out->ms_polish = o->ms[1];
+  out->ms_dedup = o->ms[2];
+  out->ms_fptest = o->ms[3];
+  out->kernel_launches = o->launches;
+  return GC_OK;
+}
+
+}  // extern "C"

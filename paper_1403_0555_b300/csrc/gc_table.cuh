@@ -1,0 +1,282 @@
+// Device table of distinct canonical copies (deduplication after fixing the
+// global phase) and the paper-style set of quantised minima.
+//
+// Identity: two canonical copies (theta'_{V-1} = 0) are the same iff
+// max_x |g'_A(x) - g'_B(x)| <= delta (chord distance, = angle to O(delta^3)).
+// Copies of one stationary point share F to far below the bucket width wF and
+// share the fingerprint c0 = cos(phi^theta) of link (site 0, mu 0) to far
+// below wT, so candidates live in the 3 x 3 neighbouring (F, c0) buckets.
+//
+// Concurrency: an insert holds the locks of its three F-neighbour buckets
+// (taken in ascending lock index, so no cycle can form); every entry it may
+// read or change has q within +-1 of its own and so sits under a held lock.
+// That makes the outcome independent of the interleaving: each distinct copy
+// ends with count = number of starts that reached it, first_start = the
+// lowest of those start indices, and the representative configuration and F
+// of that lowest start.  Every lock wait is bounded; a start whose wait runs
+// out is marked kDedupFailed and the call reports a timeout.
+#pragma once
+#include "gc_common.cuh"
+
+namespace gc {
+
+struct TableView {
+  double2* cfg;            // cap * V
+  double* F;
+  long long* q;            // F bucket
+  int* t;                  // fingerprint bucket
+  unsigned long long* first_start;
+  unsigned long long* count;
+  int* next;
+  double* lambda2;
+  int* region;             // -1 untested, 0 out, 1 in, 2 marginal
+  int* head;               // nb buckets
+  int* lock;               // nl locks
+  unsigned int* n_entries;
+  unsigned int* new_list;  // entries created by the current batch
+  unsigned int* n_new;
+  unsigned long long* f8;  // open-addressing set of floor(F_norm * 1e8)
+  unsigned long long* n_f8;
+  int* err;                // [0] lock timeout, [1] pool overflow, [2] F8 set full
+  unsigned int cap;
+  unsigned int nb_mask, nl_mask, f8_mask;
+  double wF, wT, tolF, delta2, f8_links;  // f8_links = d V (F_norm = F / (d V))
+};
+
+constexpr unsigned long long kF8Empty = ~0ULL;
+constexpr long long kLockSpins = 1LL << 22;
+
+__device__ __forceinline__ unsigned bucket_of(const TableView& T, long long q, int t) {
+  return (unsigned)(mix64((unsigned long long)q * 0x9E3779B97F4A7C15ULL + (unsigned)t) & T.nb_mask);
+}
+__device__ __forceinline__ unsigned lock_of(const TableView& T, long long q) {
+  return (unsigned)(mix64((unsigned long long)q) & T.nl_mask);
+}
+
+__device__ inline bool acquire(int* lk) {
+  unsigned ns = 32;
+  for (long long s = 0; s < kLockSpins; ++s) {
+    if (atomicCAS(lk, 0, 1) == 0) { __threadfence(); return true; }
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+  }
+  return false;
+}
+__device__ inline void release(int* lk) {
+  __threadfence();
+  atomicExch(lk, 0);
+}
+
+// warp-wide configuration comparison (all 32 lanes)
+__device__ inline bool same_copy(const double2* __restrict__ a, const double2* __restrict__ b, int V,
+                                 double delta2, int lane) {
+  for (int x0 = 0; x0 < V; x0 += 32) {
+    const int x = x0 + lane;
+    bool ok = true;
+    if (x < V) {
+      const double2 p = __ldcg(a + x), r = b[x];
+      const double dx = p.x - r.x, dy = p.y - r.y;
+      ok = dx * dx + dy * dy <= delta2;
+    }
+    if (!__all_sync(0xffffffffu, ok)) return false;
+  }
+  return true;
+}
+
+// Search the 3 x 3 (F, fingerprint) neighbourhood for a copy equal to `mine`.
+// Safe without locks: entries are only ever prepended, and a representative
+// that is being replaced differs from its successor far below delta.
+__device__ inline int table_search(const TableView& T, long long q, int t, double F,
+                                   const double2* mine, int V, int lane) {
+  for (int dq = -1; dq <= 1; ++dq) {
+    for (int dt = -1; dt <= 1; ++dt) {
+      const long long qq = q + dq;
+      const int tt = t + dt;
+      unsigned guard = 0;
+      for (int e = __ldcg(T.head + bucket_of(T, qq, tt)); e >= 0 && guard <= T.cap;
+           e = __ldcg(T.next + e), ++guard) {
+        if (__ldcg(T.q + e) != qq || __ldcg(T.t + e) != tt) continue;
+        if (fabs(__ldcg(T.F + e) - F) > T.tolF) continue;
+        if (same_copy(T.cfg + (size_t)e * V, mine, V, T.delta2, lane)) return e;
+      }
+    }
+  }
+  return -1;
+}
+
+struct DedupArgs {
+  TableView tab;
+  int V;
+  long long n;
+  uint64_t start0;
+  int8_t* status;
+  const double* F;
+  const double* fprint;
+  const double2* config;     // n * V canonical copies of this batch
+  int* copy_of;              // out: pool entry of each start (-1 none)
+  unsigned long long* stats; // [10] new, [11] hits, [12] failures
+};
+
+__global__ void __launch_bounds__(256) dedup_kernel(const DedupArgs a) {
+  const TableView& T = a.tab;
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int V = a.V;
+  unsigned long long c_new = 0, c_hit = 0, c_fail = 0;
+  for (long long i = warp0; i < a.n; i += nwarps) {
+    if (a.status[i] != kConverged) { if (lane == 0) a.copy_of[i] = -1; continue; }
+    const double F = a.F[i];
+    const long long q = (long long)floor(F / T.wF);
+    const int t = (int)floor((a.fprint[i] + 1.0) / T.wT);
+    const unsigned long long start = a.start0 + (unsigned long long)i;
+    const double2* mine = a.config + (size_t)i * V;
+    // paper-style quantised minimum (lock-free set)
+    if (lane == 0) {
+      const unsigned long long k8 = (unsigned long long)floor((F / T.f8_links) * 1e8);
+      unsigned slot = (unsigned)(mix64(k8) & T.f8_mask);
+      bool placed = false;
+      for (unsigned p = 0; p <= T.f8_mask; ++p) {
+        const unsigned long long prev = atomicCAS(&T.f8[slot], kF8Empty, k8);
+        if (prev == kF8Empty) { atomicAdd(T.n_f8, 1ULL); placed = true; break; }
+        if (prev == k8) { placed = true; break; }
+        slot = (slot + 1) & T.f8_mask;
+      }
+      if (!placed) atomicExch(&T.err[2], 1);
+    }
+    // fast path: most starts land on a copy that is already in the table
+    int e = table_search(T, q, t, F, mine, V, lane);
+    bool locked = false;
+    unsigned l0 = 0, l1 = 0, l2 = 0;
+    if (e < 0) {
+      // slow path: hold the three F-neighbour locks (ascending, distinct), search again, insert
+      unsigned tmp;
+      l0 = lock_of(T, q - 1); l1 = lock_of(T, q); l2 = lock_of(T, q + 1);
+      if (l0 > l1) { tmp = l0; l0 = l1; l1 = tmp; }
+      if (l1 > l2) { tmp = l1; l1 = l2; l2 = tmp; }
+      if (l0 > l1) { tmp = l0; l0 = l1; l1 = tmp; }
+      int ok = 1;
+      if (lane == 0) {
+        const bool got0 = acquire(&T.lock[l0]);
+        const bool got1 = got0 && (l1 == l0 || acquire(&T.lock[l1]));
+        const bool got2 = got1 && (l2 == l1 || acquire(&T.lock[l2]));
+        ok = got2;
+        if (!ok) {
+          if (got1 && l1 != l0) release(&T.lock[l1]);
+          if (got0) release(&T.lock[l0]);
+          atomicExch(&T.err[0], 1);
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) { a.status[i] = kDedupFailed; a.copy_of[i] = -1; }
+        ++c_fail;
+        continue;
+      }
+      locked = true;
+      __syncwarp();
+      e = table_search(T, q, t, F, mine, V, lane);
+      if (e < 0) {
+        if (lane == 0) e = (int)atomicAdd(T.n_entries, 1u);
+        e = __shfl_sync(0xffffffffu, e, 0);
+        if ((unsigned)e >= T.cap) {
+          if (lane == 0) { atomicExch(&T.err[1], 1); a.status[i] = kDedupFailed; }
+          e = -2;
+          ++c_fail;
+        } else {
+          for (int x = lane; x < V; x += 32) T.cfg[(size_t)e * V + x] = mine[x];
+          if (lane == 0) {
+            T.F[e] = F; T.q[e] = q; T.t[e] = t;
+            T.first_start[e] = start; T.count[e] = 1ULL;
+            T.lambda2[e] = __longlong_as_double(0x7ff8000000000000LL);
+            T.region[e] = -1;
+            // Lock-free prepend: two q values may hash to one list, and their
+            // inserters hold different locks.  next[e] and the entry's data are
+            // visible before e is published.
+            const unsigned b = bucket_of(T, q, t);
+            int old = __ldcg(T.head + b);
+            for (int tries = 0; tries < (1 << 24); ++tries) {
+              T.next[e] = old;
+              __threadfence();
+              const int seen = atomicCAS(T.head + b, old, e);
+              if (seen == old) break;
+              old = seen;
+            }
+            T.new_list[atomicAdd(T.n_new, 1u)] = (unsigned)e;
+          }
+          ++c_new;
+          e = -3 - e;   // marks "newly inserted" (decoded below)
+        }
+      }
+    }
+    if (e >= 0) {
+      // existing copy: count it; the lowest start index keeps its configuration
+      unsigned long long old = 0;
+      if (lane == 0) {
+        atomicAdd(&T.count[e], 1ULL);
+        old = atomicMin(&T.first_start[e], start);
+      }
+      old = __shfl_sync(0xffffffffu, old, 0);
+      if (start < old) {
+        // rewrite the representative under the lock of the entry's F bucket
+        // (held already on the slow path)
+        const unsigned le = lock_of(T, __ldcg(T.q + e));
+        int ok = 1;
+        const bool have = locked && (le == l0 || le == l1 || le == l2);
+        if (lane == 0 && !have) ok = acquire(&T.lock[le]);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (ok) {
+          __syncwarp();
+          const bool still = __ldcg(T.first_start + e) == start;
+          if (still) {
+            for (int x = lane; x < V; x += 32) T.cfg[(size_t)e * V + x] = mine[x];
+            if (lane == 0) T.F[e] = F;
+          }
+          __syncwarp();
+          if (lane == 0 && !have) release(&T.lock[le]);
+        } else if (lane == 0) {
+          atomicExch(&T.err[0], 1);
+        }
+      }
+      ++c_hit;
+    }
+    __syncwarp();
+    if (locked && lane == 0) {
+      if (l2 != l1) release(&T.lock[l2]);
+      if (l1 != l0) release(&T.lock[l1]);
+      release(&T.lock[l0]);
+    }
+    if (lane == 0) a.copy_of[i] = e >= 0 ? e : (e == -2 ? -1 : -3 - e);
+    __syncwarp();
+  }
+  if (lane == 0 && (c_new | c_hit | c_fail)) {
+    atomicAdd(&a.stats[10], c_new);
+    atomicAdd(&a.stats[11], c_hit);
+    atomicAdd(&a.stats[12], c_fail);
+  }
+}
+
+// Re-thread every pool entry into a (larger) bucket array after growth.
+__global__ void relink_kernel(TableView T, unsigned n) {
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const unsigned b = bucket_of(T, T.q[e], T.t[e]);
+    T.next[e] = atomicExch(&T.head[b], (int)e);
+  }
+}
+
+__global__ void fill_int_kernel(int* p, int v, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+__global__ void fill_u64_kernel(unsigned long long* p, unsigned long long v, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// theta'_x = arg g'_x for the first n entries (fetch)
+__global__ void angles_kernel(const double2* __restrict__ cfg, double* __restrict__ theta, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 z = cfg[i];
+    theta[i] = atan2(z.y, z.x);
+  }
+}
+
+}  // namespace gc
