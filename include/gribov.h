@@ -145,6 +145,28 @@ int gc_fetch_starts(gc_orbit o, uint64_t first, uint64_t n, int* status, int* sw
 int gc_orbit_stats(gc_orbit o, gc_stats* out);
 int gc_destroy_orbit(gc_orbit o);
 
+/* Allocation-free first-region test.  The paper has no counterpart: this is
+ * for callers that must not allocate device memory -- work recorded into a
+ * CUDA graph, a service whose device memory budget is fixed up front, or a
+ * host that hands the library a fixed arena.  It runs the GC_FP_DENSE test
+ * (FP64 Lanczos, full reorthogonalisation, dimension V-1) on n caller-owned
+ * copies and allocates nothing: its scratch is one fixed 24 MiB device array
+ * that every GPU loading this library holds until the process exits.
+ *   d_links    device, V*d (cos phi, sin phi) pairs, link (x, mu) at x*d + mu
+ *   d_configs  device, n*V (cos theta, sin theta) pairs, copy i at i*V (any
+ *              global phase)
+ *   d_lambda2  device out, n doubles: lambda_2 of each copy
+ *   d_region   device out, n ints: GC_REGION_IN / _MARGINAL / _OUT (fp_tau)
+ * Work is queued on `stream`; outputs are valid once it reaches this point.
+ * Limits: n <= 65536 per call and V*V*8 bytes of Lanczos basis must fit the
+ * array (V <= about 1700); larger requests fail with GC_EINVAL.  The first
+ * call on each device looks up the array's device address; make that first
+ * call before any stream capture.  All calls share the one array, so calls
+ * whose work overlaps on the GPU (other streams, other host threads) race;
+ * order them on one stream. */
+int gc_fp_test_static(int dim, int L, const double* d_links, const double* d_configs, uint64_t n,
+                      double fp_tau, double* d_lambda2, int* d_region, void* stream);
+
 /* message of the last failing call on this thread ("" if none) */
 const char* gc_last_error(void);
 /* library version string */

@@ -78,7 +78,7 @@ class gc_stats(ctypes.Structure):
 
 EXPORTED = ("gc_set_allocator", "gc_options_default", "gc_create_orbit", "gc_enumerate_copies",
             "gc_fetch_copies", "gc_fetch_starts", "gc_orbit_stats", "gc_destroy_orbit",
-            "gc_last_error", "gc_version")
+            "gc_last_error", "gc_version", "gc_fp_test_static")
 
 _lib = None
 _lock = threading.Lock()
@@ -120,6 +120,9 @@ def load(build_if_stale: bool = True):
                                       p_i, p_d, ctypes.POINTER(ctypes.c_int64)]
         L.gc_orbit_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(gc_stats)]
         L.gc_destroy_orbit.argtypes = [ctypes.c_void_p]
+        L.gc_fp_test_static.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]
         L.gc_last_error.restype = ctypes.c_char_p
         L.gc_version.restype = ctypes.c_char_p
         _lib = L
@@ -251,3 +254,10 @@ def gc_orbit_stats(orbit) -> dict:
 
 def gc_destroy_orbit(orbit):
     _check(load().gc_destroy_orbit(orbit))
+
+
+def gc_fp_test_static(dim: int, L: int, d_links: int, d_configs: int, n: int, fp_tau: float,
+                      d_lambda2: int, d_region: int, stream: int = 0):
+    """Allocation-free first-region test on device buffers (raw device pointers)."""
+    _check(load().gc_fp_test_static(dim, L, d_links, d_configs, n, fp_tau, d_lambda2, d_region,
+                                    stream))

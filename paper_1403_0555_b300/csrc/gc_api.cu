@@ -781,3 +781,152 @@ int gc_orbit_stats(gc_orbit o, gc_stats* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free Faddeev-Popov test (declared in gribov.h as
+// gc_fp_test_static).  For callers that must not allocate device memory at
+// all -- code running inside a CUDA-graph capture, a memory-budgeted service
+// whose allocator is locked, or a host that owns a fixed device arena -- the
+// dense Lanczos test runs on caller-owned inputs and outputs and keeps its
+// scratch (the Lanczos bases and a few bookkeeping words) in one fixed
+// device array that every GPU loading this library holds until the process
+// exits.  The paper has no counterpart; the operation is the first-region
+// test of the enumeration, GC_FP_DENSE mode.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)24 << 20;  // 24 MiB per device
+constexpr unsigned long long kStaticMaxCopies = 1ULL << 16;  // copies per call
+constexpr int kStaticMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+std::mutex g_static_mu;
+void* g_static_ptr[kStaticMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device, looked up once per
+// device (the first call on a device does this; make it before any capture).
+int static_scratch_address(void** out) {
+  int dev = 0;
+  GC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) return fail(GC_EINVAL, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return fail(GC_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return GC_OK;
+}
+
+struct StaticLayout {
+  size_t header, list, first, links32, stats, q0, slot_bytes;
+  unsigned slots;
+  StaticLayout(unsigned long long n, int V, int d) {
+    header = 0;                                           // n_list (u32)
+    list = 256;
+    first = align_up(list + n * 4, 256);
+    links32 = align_up(first + n * 8, 256);
+    stats = align_up(links32 + (size_t)V * d * sizeof(float2), 256);
+    q0 = align_up(stats + 32 * 8, 256);
+    slot_bytes = (size_t)V * V * sizeof(double);
+    slots = q0 < kStaticScratchBytes ? (unsigned)((kStaticScratchBytes - q0) / slot_bytes) : 0u;
+  }
+  static size_t align_up(size_t b, size_t a) { return (b + a - 1) / a * a; }
+};
+
+// Writes every scratch word the test reads: the copy count, the identity copy
+// list, the Lanczos seeds, the FP32 links, and zeroed counters.
+__global__ void static_fp_setup_kernel(unsigned char* s, StaticLayout lay, unsigned n,
+                                       const double2* links64, int nlinks) {
+  const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned stride = gridDim.x * blockDim.x;
+  if (tid == 0) *reinterpret_cast<unsigned*>(s + lay.header) = n;
+  for (unsigned i = tid; i < n; i += stride) {
+    reinterpret_cast<unsigned*>(s + lay.list)[i] = i;
+    reinterpret_cast<unsigned long long*>(s + lay.first)[i] = i;
+  }
+  for (unsigned l = tid; l < (unsigned)nlinks; l += stride) {
+    const double2 v = links64[l];
+    reinterpret_cast<float2*>(s + lay.links32)[l] = make_float2((float)v.x, (float)v.y);
+  }
+  for (unsigned k = tid; k < 32; k += stride) reinterpret_cast<unsigned long long*>(s + lay.stats)[k] = 0ULL;
+}
+
+}  // namespace
+
+extern "C" int gc_fp_test_static(int dim, int L, const double* d_links, const double* d_configs,
+                                 uint64_t n, double fp_tau, double* d_lambda2, int* d_region,
+                                 void* stream) {
+  if (dim < 1 || dim > gc::kMaxDim) return fail(GC_EINVAL, "dimension %d not in 1..4", dim);
+  if (L < 2) return fail(GC_EINVAL, "L = %d < 2", L);
+  const double Vd = std::pow((double)L, dim);
+  if (Vd > gc::kMaxSites) return fail(GC_EINVAL, "lattice of %.0f sites exceeds %d", Vd, gc::kMaxSites);
+  if (!d_links || !d_configs || !d_lambda2 || !d_region) return fail(GC_EINVAL, "NULL pointer argument");
+  if (!(fp_tau >= 0.0)) return fail(GC_EINVAL, "fp_tau = %g < 0", fp_tau);
+  if (n > kStaticMaxCopies)
+    return fail(GC_EINVAL, "%llu copies exceed the per-call maximum of %llu of the static scratch",
+                (unsigned long long)n, kStaticMaxCopies);
+  const int V = (int)Vd, d = dim;
+  const StaticLayout lay(n, V, d);
+  if (lay.slots < 1)
+    return fail(GC_EINVAL, "a %d-site lattice needs %zu bytes of Lanczos basis; the static scratch "
+                "holds %zu", V, lay.q0 + lay.slot_bytes, kStaticScratchBytes);
+  if (n == 0) return GC_OK;
+  void* base = nullptr;
+  if (int rc = static_scratch_address(&base)) return rc;
+  unsigned char* s = static_cast<unsigned char*>(base);
+  cudaStream_t st = (cudaStream_t)stream;
+
+  gc::Geom G{};
+  G.d = d; G.L = L; G.V = V; G.ncolor = (L % 2 == 0) ? 2 : 3;
+  int cnt[3] = {0, 0, 0};
+  for (int x = 0; x < V; ++x) cnt[gc::site_color(x, d, L)]++;
+  for (int c = 0; c < 3; ++c) G.color_off[c + 1] = G.color_off[c] + (c < G.ncolor ? cnt[c] : 0);
+  G.pos_last = G.color_off[gc::site_color(V - 1, d, L) + 1] - 1;
+
+  const int kmax64 = std::max(1, V - 1);
+  const int f_warps = fit_warps(4, [&](int w) { return gc::FpSmem(V, d, kmax64, w).total; });
+  if (!f_warps) return fail(GC_EINVAL, "Faddeev-Popov test does not fit shared memory");
+  const size_t f_smem = gc::FpSmem(V, d, kmax64, f_warps).total;
+  int fgrid = 0;
+  if (int rc = launch_grid(gc::fp_test_kernel, f_warps * 32, f_smem, f_warps, (long long)n, &fgrid)) return rc;
+  fgrid = (int)std::max(1u, std::min<unsigned>((unsigned)fgrid, lay.slots / (unsigned)f_warps));
+  const int fwarps_used = lay.slots < (unsigned)f_warps ? (int)lay.slots : f_warps;
+  const size_t fsm = gc::FpSmem(V, d, kmax64, fwarps_used).total;
+
+  static_fp_setup_kernel<<<64, 256, 0, st>>>(s, lay, (unsigned)n, reinterpret_cast<const double2*>(d_links), V * d);
+  GC_CUDA(cudaGetLastError());
+
+  gc::FpArgs fa{};
+  fa.geom = G;
+  fa.cfg = reinterpret_cast<const double2*>(d_configs);
+  fa.first_start = reinterpret_cast<const unsigned long long*>(s + lay.first);
+  fa.links32 = reinterpret_cast<const float2*>(s + lay.links32);
+  fa.links64 = reinterpret_cast<const double2*>(d_links);
+  fa.list = reinterpret_cast<const unsigned*>(s + lay.list);
+  fa.n_list = reinterpret_cast<const unsigned*>(s + lay.header);
+  fa.lambda2 = d_lambda2;
+  fa.region = d_region;
+  fa.mode = gc::kFpDense;
+  fa.kmax32 = std::min(160, kmax64);
+  fa.kmax64 = kmax64;
+  fa.tau = fp_tau;
+  fa.margin32 = 1e-3;
+  fa.tol32 = 1e-5;
+  fa.tol64 = 1e-12;
+  fa.scratch = reinterpret_cast<double*>(s + lay.q0);
+  fa.seed = 1;
+  fa.stats = reinterpret_cast<unsigned long long*>(s + lay.stats);
+  gc::fp_test_kernel<<<fgrid, fwarps_used * 32, fsm, st>>>(fa);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
