@@ -50,6 +50,11 @@ extern "C" {
 #define GC_FP_DENSE 2    /* FP64 Lanczos, full reorthogonalisation, dim V-1     */
 #define GC_FP_NONE 3     /* no test (region reported as -1)                     */
 
+/* FP32-phase kernel: AUTO picks the line-owner kernel where it exists
+ * (4^4, 8^3), GENERIC forces the generic team kernel */
+#define GC_RELAX_AUTO 0
+#define GC_RELAX_GENERIC 1
+
 /* per-start status */
 #define GC_START_CONVERGED 1
 #define GC_START_NOT_CONVERGED 2
@@ -79,6 +84,7 @@ typedef struct {
   int newton_max;       /* GC_MIXED: Newton steps before FP64 relaxation fallback  */
   int batch_starts;     /* starts per device batch, 0 = automatic                  */
   void* stream;         /* cudaStream_t the work is ordered on (NULL = default)    */
+  int relax_variant;    /* GC_RELAX_AUTO or GC_RELAX_GENERIC (FP32 phase kernel)    */
 } gc_options;
 
 typedef struct {

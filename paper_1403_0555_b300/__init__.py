@@ -31,6 +31,9 @@ GC_FP_LANCZOS = 1
 GC_FP_DENSE = 2
 GC_FP_NONE = 3
 
+GC_RELAX_AUTO = 0
+GC_RELAX_GENERIC = 1
+
 GC_START_CONVERGED = 1
 GC_START_NOT_CONVERGED = 2
 GC_START_DEDUP_FAILED = 3
@@ -63,6 +66,7 @@ class gc_options(ctypes.Structure):
         ("newton_max", ctypes.c_int),
         ("batch_starts", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("relax_variant", ctypes.c_int),
     ]
 
 

@@ -304,6 +304,7 @@ int gc_options_default(gc_options* opt) {
   opt->newton_max = 6;
   opt->batch_starts = 0;
   opt->stream = nullptr;
+  opt->relax_variant = GC_RELAX_AUTO;
   return GC_OK;
 }
 
@@ -512,14 +513,44 @@ int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
     ra.stats = stats;
     int grid = 0;
     GC_CUDA(cudaEventRecord(o->ev[0], s));
-    if (mixed) {
-      if (int rc = launch_grid(gc::relax_kernel<gc::Fast32>, r_warps * 32, r_smem, (long long)r_warps * tpw, b, &grid)) return rc;
-      gc::relax_kernel<gc::Fast32><<<grid, r_warps * 32, r_smem, s>>>(ra);
+    if (mixed && opt.relax_variant != GC_RELAX_GENERIC && d == 4 && o->L == 4) {
+      constexpr int kTeams = 4;
+      auto k = gc::relax32_lines_kernel<4, 4, kTeams>;
+      const size_t sm = gc::relax32_lines_smem<4, 4, kTeams>();
+      if (int rc = launch_grid(k, 64 * kTeams, sm, kTeams, b, &grid)) return rc;
+      k<<<grid, 64 * kTeams, sm, s>>>(ra);
+      ++o->launches;
+    } else if (mixed && opt.relax_variant != GC_RELAX_GENERIC && d == 3 && o->L == 8) {
+      constexpr int kTeams = 4;
+      auto k = gc::relax32_lines_kernel<3, 8, kTeams>;
+      const size_t sm = gc::relax32_lines_smem<3, 8, kTeams>();
+      if (int rc = launch_grid(k, 64 * kTeams, sm, kTeams, b, &grid)) return rc;
+      k<<<grid, 64 * kTeams, sm, s>>>(ra);
       ++o->launches;
     } else {
-      if (int rc = launch_grid(gc::relax_kernel<gc::Exact64>, r_warps * 32, r_smem, (long long)r_warps * tpw, b, &grid)) return rc;
-      gc::relax_kernel<gc::Exact64><<<grid, r_warps * 32, r_smem, s>>>(ra);
-      ++o->launches;
+      auto launch = [&](auto kern) -> int {
+        if (int rc = launch_grid(kern, r_warps * 32, r_smem, (long long)r_warps * tpw, b, &grid)) return rc;
+        kern<<<grid, r_warps * 32, r_smem, s>>>(ra);
+        ++o->launches;
+        return GC_OK;
+      };
+      int rc = GC_OK;
+      if (mixed) {
+        switch (d) {
+          case 1: rc = launch(gc::relax_kernel<gc::Fast32, 1>); break;
+          case 2: rc = launch(gc::relax_kernel<gc::Fast32, 2>); break;
+          case 3: rc = launch(gc::relax_kernel<gc::Fast32, 3>); break;
+          default: rc = launch(gc::relax_kernel<gc::Fast32, 4>); break;
+        }
+      } else {
+        switch (d) {
+          case 1: rc = launch(gc::relax_kernel<gc::Exact64, 1>); break;
+          case 2: rc = launch(gc::relax_kernel<gc::Exact64, 2>); break;
+          case 3: rc = launch(gc::relax_kernel<gc::Exact64, 3>); break;
+          default: rc = launch(gc::relax_kernel<gc::Exact64, 4>); break;
+        }
+      }
+      if (rc) return rc;
     }
     GC_CUDA(cudaGetLastError());
     GC_CUDA(cudaEventRecord(o->ev[1], s));
@@ -548,9 +579,20 @@ int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
       pa.fprint = ra.fprint;
       pa.config = ra.config;
       pa.stats = stats;
-      if (int rc = launch_grid(gc::polish_kernel, p_warps * 32, p_smem, (long long)p_warps * tpw, b, &grid)) return rc;
-      gc::polish_kernel<<<grid, p_warps * 32, p_smem, s>>>(pa);
-      ++o->launches;
+      auto plaunch = [&](auto kern) -> int {
+        if (int rc = launch_grid(kern, p_warps * 32, p_smem, (long long)p_warps * tpw, b, &grid)) return rc;
+        kern<<<grid, p_warps * 32, p_smem, s>>>(pa);
+        ++o->launches;
+        return GC_OK;
+      };
+      int prc = GC_OK;
+      switch (d) {
+        case 1: prc = plaunch(gc::polish_kernel<1>); break;
+        case 2: prc = plaunch(gc::polish_kernel<2>); break;
+        case 3: prc = plaunch(gc::polish_kernel<3>); break;
+        default: prc = plaunch(gc::polish_kernel<4>); break;
+      }
+      if (prc) return prc;
       GC_CUDA(cudaGetLastError());
     }
     GC_CUDA(cudaEventRecord(o->ev[2], s));

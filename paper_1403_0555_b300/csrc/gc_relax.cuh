@@ -17,6 +17,8 @@
 //   Fast32  -- FP32 with FMA and the MUFU reciprocal square root (bulk phase
 //              of the mixed-precision path).
 #pragma once
+#include <type_traits>
+
 #include "gc_common.cuh"
 
 namespace gc {
@@ -208,13 +210,14 @@ __device__ inline void load_links(R2* u, const R2* gl, const uint16_t* site, int
   }
 }
 
-template <class P>
+template <class P, int DD>
 __global__ void __launch_bounds__(256) relax_kernel(const RelaxArgs a) {
   using R = typename P::R;
   using R2 = typename P::R2;
   extern __shared__ __align__(16) unsigned char smem[];
   const Geom G = a.geom;
-  const int V = G.V, d = G.d, T = a.team;
+  constexpr int d = DD;
+  const int V = G.V, T = a.team;
   const int teams_per_warp = 32 / T;
   const int warps = blockDim.x >> 5;
   const Smem lay(V, d, sizeof(R2), (size_t)V * sizeof(R2), warps * teams_per_warp);
@@ -358,10 +361,12 @@ __device__ __forceinline__ double2 staple_dfma(const double2* __restrict__ u,
   return make_double2(sx, sy);
 }
 
+template <int DD>
 __global__ void __launch_bounds__(256) polish_kernel(const PolishArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Geom G = a.geom;
-  const int V = G.V, d = G.d, T = a.team;
+  constexpr int d = DD;
+  const int V = G.V, T = a.team;
   const int teams_per_warp = 32 / T, warps = blockDim.x >> 5;
   const Smem lay(V, d, sizeof(double2), polish_team_bytes(V, d), warps * teams_per_warp);
   double2* u = reinterpret_cast<double2*>(smem + lay.links);
@@ -418,7 +423,11 @@ __global__ void __launch_bounds__(256) polish_kernel(const PolishArgs a) {
           for (int p = tl; p < V; p += T) g32[p] = make_float2(d2f_bits(g[p].x), d2f_bits(g[p].y));
           __syncwarp(tmask);
           const float om = (float)a.omega, om1 = (float)a.om1;
-          for (int sw = 0; sw < a.max_sweeps; ++sw) {
+          // A fixed budget of FP32 sweeps: the residual may rise for a while
+          // (a start leaving the neighbourhood of a saddle), so only reaching
+          // the FP32 floor (~1e-11 for max div^2) ends it early.
+          const int cap32 = a.max_sweeps < 2048 ? a.max_sweeps : 2048;
+          for (int sw = 0; sw < cap32; ++sw) {
             for (int c = 0; c < G.ncolor; ++c) {
               const int beg = G.color_off[c], end = G.color_off[c + 1];
               for (int p = beg + tl; p < end; p += T) {
@@ -466,7 +475,7 @@ __global__ void __launch_bounds__(256) polish_kernel(const PolishArgs a) {
                 r32 = fmaxf(r32, dv * dv);
               }
               r32 = team_max(r32, T, tmask);
-              if (r32 < 1e-12f) break;
+              if (r32 < 1e-11f) break;
             }
           }
           for (int p = tl; p < V; p += T) {
@@ -495,6 +504,7 @@ __global__ void __launch_bounds__(256) polish_kernel(const PolishArgs a) {
           for (int o = T >> 1; o > 0; o >>= 1) r = dmax_pos(r, __shfl_xor_sync(tmask, r, o));
           if (dless_pos(r, a.eps)) { conv = true; break; }
           if (it >= a.newton_max) break;
+          if (it > 0 && !dless_pos(r, r_prev)) break;   // rising: Hessian not positive here
           if (!dless_pos(r, 0.25 * r_prev)) inner_cap = min(4 * inner_cap, 8192);  // poor step
           r_prev = r;
           ++c_newton;
@@ -628,6 +638,340 @@ __global__ void __launch_bounds__(256) polish_kernel(const PolishArgs a) {
     atomicAdd(&a.stats[20], c_inner);
     atomicAdd(&a.stats[21], c_upd32);
   }
+}
+
+
+// ---------------------------------------------------------------------------
+// FP32 bulk relaxation, line-owner kernel (even L; the lines of one parity
+// fill whole warps: 4^4, 8^3, ...)
+// ---------------------------------------------------------------------------
+// A team of NL = L^(D-1) threads relaxes one start.  Thread (q, h) owns the
+// h-th line along axis 0 among the lines of parity q = (x_1 + ... + x_{D-1})
+// mod 2; both parities fill whole warps, so every branch on q is warp-uniform
+// and all site loops unroll at compile time.  A thread keeps its line's gauge
+// field and all the links touching it in registers: neighbours along axis 0
+// never leave the thread, and neighbours along the other axes are read from
+// the team's shared copy, stored [x_0][parity][h] so that every warp-wide
+// access touches 32 distinct 8-byte words.  Per site update: 8D + 11 FP32 ops,
+// 2 MUFU, 2(D-1) shared loads and 1 store.
+//
+// Residual (exact, at no extra sweep): for the last colour, div = Im[conj(g) S]
+// is taken right after the update with the S of that update; for colour 0 it
+// is taken in the next sweep's colour-0 phase from the S computed there,
+// before that phase's new values are committed.  Together they are
+// max_x div(x)^2 of the state after the checked sweep, which is the state kept
+// when the check passes.
+template <int D, int L>
+struct LineGeom {
+  static constexpr int NL = (D == 2) ? L : (D == 3 ? L * L : L * L * L);  // lines
+  static constexpr int NLH = NL / 2;                                     // per parity
+  static constexpr int V = NL * L;
+  static_assert(L % 2 == 0, "line kernel needs even L");
+  static_assert(NLH % 32 == 0, "each parity must fill whole warps");
+};
+
+// compile-time loop: f(integral_constant<int, i>) for i = 0..N-1
+template <class F, int... Is>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, Is...>) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// shared-memory float2 access at a 32-bit shared address plus a compile-time
+// byte offset (one LDS/STS with an immediate, no address arithmetic)
+template <int OFF>
+__device__ __forceinline__ float2 lds_f2(unsigned base) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+%3];" : "=f"(v.x), "=f"(v.y) : "r"(base), "n"(OFF));
+  return v;
+}
+template <int OFF>
+__device__ __forceinline__ void sts_f2(unsigned base, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0+%1], {%2, %3};" ::"r"(base), "n"(OFF), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// A fresh random start for the L sites of one line, written to shared memory
+// at byte address `dst` + k*stride.  Kept out of line: start generation is
+// rare next to the sweeps, and inlining the Philox rounds per site would
+// crowd the sweep loop out of the instruction cache.
+__device__ __noinline__ void line_start32(uint64_t seed, uint64_t orbit_id, uint64_t start,
+                                          int first_site, int L, unsigned dst, unsigned stride) {
+  for (int k = 0; k < L; ++k) {
+    const float2 v = random_unit32(seed, orbit_id, start, (uint64_t)(first_site + k));
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(dst + k * stride), "f"(v.x), "f"(v.y) : "memory");
+  }
+}
+
+__device__ __forceinline__ void team_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <int D, int L>
+__device__ __forceinline__ int line_parity(int l) {
+  int s = 0, t = l;
+  for (int mu = 1; mu < D; ++mu) { s += t % L; t /= L; }
+  return s & 1;
+}
+
+// h-th line (in increasing line index) of parity q
+template <int D, int L>
+__device__ inline int line_of(int q, int h) {
+  int k = -1;
+  for (int l = 0; l < LineGeom<D, L>::NL; ++l)
+    if (line_parity<D, L>(l) == q && ++k == h) return l;
+  return 0;
+}
+// rank of line l among the lines of its parity
+template <int D, int L>
+__device__ inline int half_of(int l) {
+  const int q = line_parity<D, L>(l);
+  int k = 0;
+  for (int m = 0; m < l; ++m) k += line_parity<D, L>(m) == q;
+  return k;
+}
+
+template <int D, int L, int TEAMS>
+__global__ void __launch_bounds__(LineGeom<D, L>::NL * TEAMS, (D == 4 ? 2 : 1)) relax32_lines_kernel(const RelaxArgs a) {
+  using LG = LineGeom<D, L>;
+  constexpr int NL = LG::NL, NLH = LG::NLH, V = LG::V, NW = NL / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int team = threadIdx.x / NL, tt = threadIdx.x % NL;
+  const int q = tt / NLH, h = tt % NLH;      // q is uniform across each warp
+  const int bar_id = 1 + team;
+  float2* gs = reinterpret_cast<float2*>(smem) + (size_t)team * V;    // [x0][parity][h]
+  float* red = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem) + (size_t)TEAMS * V) + team * 32;
+  long long* tidx = reinterpret_cast<long long*>(red + 16);
+
+  const int l = line_of<D, L>(q, h);
+  int cl[D];                                  // cl[mu] = x_mu of the line, mu >= 1
+  {
+    int t = l;
+    cl[0] = 0;
+#pragma unroll
+    for (int mu = 1; mu < D; ++mu) { cl[mu] = t % L; t /= L; }
+  }
+  // shared-memory offsets of the neighbour lines (opposite parity), +mu and -mu
+  int nbp[D], nbm[D];
+  nbp[0] = nbm[0] = 0;
+  {
+    int stride = 1;
+#pragma unroll
+    for (int mu = 1; mu < D; ++mu) {
+      const int lp = l + (((cl[mu] + 1) % L) - cl[mu]) * stride;
+      const int lm = l + (((cl[mu] + L - 1) % L) - cl[mu]) * stride;
+      nbp[mu] = (1 - q) * NLH + half_of<D, L>(lp);
+      nbm[mu] = (1 - q) * NLH + half_of<D, L>(lm);
+      stride *= L;
+    }
+  }
+  const int own = q * NLH + h;
+  // per-thread 32-bit shared addresses; site x0 = K of a line sits K*2*NLH*8 bytes further
+  unsigned snb[D], snm[D];
+  const unsigned sgs = (unsigned)__cvta_generic_to_shared(gs);
+#pragma unroll
+  for (int mu = 0; mu < D; ++mu) { snb[mu] = sgs + 8u * nbp[mu]; snm[mu] = sgs + 8u * nbm[mu]; }
+  const unsigned sown = sgs + 8u * own;
+  // links touching the line, in registers: uf[k][mu] = u_{x,mu}, ub[k][mu] =
+  // u_{x-mu,mu} for mu >= 1 (for mu = 0 that is uf[k-1][0])
+  float2 uf[L][D], ub[L][D];
+#pragma unroll
+  for (int k = 0; k < L; ++k) {
+    const int x = k + L * l;
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) {
+      uf[k][mu] = a.links32[x * D + mu];
+      if (mu > 0) {
+        int s = 1;
+#pragma unroll
+        for (int m = 1; m < mu; ++m) s *= L;
+        const int xm = x + (((cl[mu] + L - 1) % L) - cl[mu]) * (s * L);
+        ub[k][mu] = a.links32[xm * D + mu];
+      } else {
+        ub[k][0] = make_float2(0.f, 0.f);
+      }
+    }
+  }
+  const float om = a.omega32, om1 = a.om1_32;
+
+  float2 g[L];
+  unsigned long long my_sweeps = 0, my_updates = 0, my_conv = 0, my_nconv = 0;
+  auto fetch = [&]() -> long long {
+    if (tt == 0) *tidx = (long long)atomicAdd(a.work_ctr, 1ULL);
+    team_bar(bar_id, NL);
+    const long long v = *tidx;
+    team_bar(bar_id, NL);
+    return v;
+  };
+  // new start: generated into the team's shared copy; g is reloaded after the
+  // caller's barrier by `reload`
+  auto init = [&](long long idx) {
+    line_start32(a.seed, a.orbit_id, a.start0 + idx, L * l, L, sown, 2u * NLH * 8u);
+  };
+  auto reload = [&]() {
+    static_for<L>([&](auto KC) { g[decltype(KC)::value] = lds_f2<decltype(KC)::value * 2 * NLH * 8>(sown); });
+  };
+  // staple of the line's site x0 = K (compile time); other lines from shared memory
+  auto staple = [&](auto KC, float& sx, float& sy) {
+    constexpr int K = decltype(KC)::value;
+    const float2 gp = g[(K + 1) % L], gm = g[(K + L - 1) % L];
+    const float2 a0 = uf[K][0], b0 = uf[(K + L - 1) % L][0];
+    // forward (u g) and backward (conj(u) g) terms in separate chains
+    float fx = a0.x * gp.x, fy = a0.x * gp.y;
+    fx = fmaf(-a0.y, gp.y, fx); fy = fmaf(a0.y, gp.x, fy);
+    float bx = b0.x * gm.x, by = b0.x * gm.y;
+    bx = fmaf(b0.y, gm.y, bx); by = fmaf(-b0.y, gm.x, by);
+#pragma unroll
+    for (int mu = 1; mu < D; ++mu) {
+      const float2 hp = lds_f2<K * 2 * NLH * 8>(snb[mu]);
+      const float2 hm = lds_f2<K * 2 * NLH * 8>(snm[mu]);
+      const float2 aa = uf[K][mu], bb = ub[K][mu];
+      fx = fmaf(aa.x, hp.x, fx); fx = fmaf(-aa.y, hp.y, fx);
+      fy = fmaf(aa.x, hp.y, fy); fy = fmaf(aa.y, hp.x, fy);
+      bx = fmaf(bb.x, hm.x, bx); bx = fmaf(bb.y, hm.y, bx);
+      by = fmaf(bb.x, hm.y, by); by = fmaf(-bb.y, hm.x, by);
+    }
+    sx = fx + bx;
+    sy = fy + by;
+  };
+  auto blend = [&](float2 gx, float sx, float sy) -> float2 {
+    // S = 0 exactly has probability zero; the clamp only keeps it finite
+    const float n2 = fmaxf(fmaf(sx, sx, sy * sy), 1e-30f);
+    const float r = rsqrtf(n2) * om;
+    const float vx = fmaf(sx, r, om1 * gx.x), vy = fmaf(sy, r, om1 * gx.y);
+    const float qn = rsqrtf(fmaf(vx, vx, vy * vy));
+    return make_float2(vx * qn, vy * qn);
+  };
+  // colour-0 sites of a parity-Q line: x0 = 2j + Q.  Computes the new values
+  // (not committed) and, if `pending`, the squared divergences before the move.
+  float2 gn[L / 2];
+  auto colour0 = [&](auto QC, bool pend) -> float {
+    constexpr int Q = decltype(QC)::value;
+    float r0 = 0.f;
+    static_for<L / 2>([&](auto JC) {
+      constexpr int K = 2 * decltype(JC)::value + Q;
+      float sx, sy;
+      staple(std::integral_constant<int, K>{}, sx, sy);
+      const float2 gx = g[K];
+      if (pend) { const float dv = fmaf(gx.x, sy, -gx.y * sx); r0 = fmaxf(r0, dv * dv); }
+      gn[decltype(JC)::value] = blend(gx, sx, sy);
+    });
+    return r0;
+  };
+  // colour-0 update committed at once (sweeps with no check pending)
+  auto colour0_direct = [&](auto QC) {
+    constexpr int Q = decltype(QC)::value;
+    static_for<L / 2>([&](auto JC) {
+      constexpr int K = 2 * decltype(JC)::value + Q;
+      float sx, sy;
+      staple(std::integral_constant<int, K>{}, sx, sy);
+      g[K] = blend(g[K], sx, sy);
+      sts_f2<K * 2 * NLH * 8>(sown, g[K]);
+    });
+  };
+  auto commit0 = [&](auto QC) {
+    constexpr int Q = decltype(QC)::value;
+    static_for<L / 2>([&](auto JC) {
+      constexpr int K = 2 * decltype(JC)::value + Q;
+      g[K] = gn[decltype(JC)::value];
+      sts_f2<K * 2 * NLH * 8>(sown, g[K]);
+    });
+  };
+  // colour-1 sites x0 = 2j + 1 - Q; squared divergences after the move if `check`
+  auto colour1 = [&](auto QC, bool chk) -> float {
+    constexpr int Q = decltype(QC)::value;
+    float r1 = 0.f;
+    static_for<L / 2>([&](auto JC) {
+      constexpr int K = 2 * decltype(JC)::value + 1 - Q;
+      float sx, sy;
+      staple(std::integral_constant<int, K>{}, sx, sy);
+      const float2 v = blend(g[K], sx, sy);
+      if (chk) { const float dv = fmaf(v.x, sy, -v.y * sx); r1 = fmaxf(r1, dv * dv); }
+      g[K] = v;
+      sts_f2<K * 2 * NLH * 8>(sown, v);
+    });
+    return r1;
+  };
+  auto warp_max = [&](float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+  };
+
+  // the whole sweep loop is instantiated per parity (warp-uniform), so no
+  // branch on q remains inside it
+  auto run = [&](auto QC) {
+    long long idx = fetch();
+    bool live = idx < a.n;
+    if (live) init(idx);
+    team_bar(bar_id, NL);
+    if (live) reload();
+    int sweeps = 0;
+    int until_check = a.check_every;   // countdown to the next checked sweep
+    bool pending = false;              // a checked sweep waits for its colour-0 half
+    float r1 = 0.f;
+    while (live) {
+      if (!pending) {
+        colour0_direct(QC);
+      } else {
+        float r0 = colour0(QC, true);
+        r0 = warp_max(fmaxf(r0, r1));
+        if ((tt & 31) == 0) red[tt >> 5] = r0;
+        team_bar(bar_id, NL);
+        float r = red[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) r = fmaxf(r, red[w]);
+        team_bar(bar_id, NL);
+        pending = false;
+        const bool conv = r < a.eps32;
+        if (conv || sweeps >= a.max_sweeps) {
+          // keep the checked state, in colour-position order for the polish
+#pragma unroll
+          for (int k = 0; k < L; ++k) {
+            const int x = k + L * l;
+            const int colour = (k + q) & 1;
+            a.state32[(size_t)idx * V + colour * (V / 2) + (x >> 1)] = g[k];
+          }
+          if (tt == 0) {
+            a.status[idx] = conv ? kConverged : kNotConverged;
+            a.sweeps[idx] = sweeps;
+            my_sweeps += sweeps;
+            my_updates += (unsigned long long)sweeps * V;
+            if (conv) ++my_conv; else ++my_nconv;
+          }
+          idx = fetch();
+          live = idx < a.n;
+          if (live) init(idx);
+          sweeps = 0;
+          until_check = a.check_every;
+          team_bar(bar_id, NL);
+          if (live) reload();
+          continue;
+        }
+        commit0(QC);
+      }
+      team_bar(bar_id, NL);
+      ++sweeps;
+      const bool check = --until_check == 0;
+      if (check) until_check = a.check_every;
+      r1 = colour1(QC, check);
+      pending = check;
+      team_bar(bar_id, NL);
+    }
+  };
+  if (q) run(std::integral_constant<int, 1>{}); else run(std::integral_constant<int, 0>{});
+  if (tt == 0 && (my_sweeps | my_conv | my_nconv)) {
+    atomicAdd(&a.stats[a.stat_base + 0], my_sweeps);
+    atomicAdd(&a.stats[a.stat_base + 1], my_updates);
+    atomicAdd(&a.stats[a.stat_base + 2], my_conv);
+    atomicAdd(&a.stats[a.stat_base + 3], my_nconv);
+  }
+}
+
+template <int D, int L, int TEAMS>
+__host__ inline size_t relax32_lines_smem() {
+  return (size_t)TEAMS * LineGeom<D, L>::V * sizeof(float2) + (size_t)TEAMS * 32 * sizeof(float);
 }
 
 }  // namespace gc
