@@ -6,11 +6,12 @@ kappa_j = 0.5 + 1.5 j/7 (seeds 1-8), 2^20 random starts per orbit, mixed
 precision (FP32 sweeps to max div^2 < 1e-10, FP64 polish to 1e-24),
 overrelaxation omega = 1.7, Faddeev-Popov Lanczos test, FP64 dedup.
 One step = the whole path (starts -> sweeps -> polish -> dedup -> FP test) for
-one orbit's 2^20 starts; step k uses orbit k mod 8.
+all eight orbits' 2^20 starts, enqueued by one gc_enumerate_batch call as one
+captured CUDA graph (fresh orbit objects every step).
 
-Prints one JSON line.  `value` = converged copies per second with the orbit
-resident on the device (CUDA events on the library's stream around the
-gc_enumerate_copies calls of the K timed steps); `e2e` = the same metric
+Prints one JSON line.  `value` = converged copies per second with the orbits
+resident on the device (CUDA events on the launch stream around the
+gc_enumerate_batch call of each of the K timed steps); `e2e` = the same metric
 through the C ABI with host buffers (link angles uploaded, distinct copies
 read back, every step).  The plain FP64 path is timed on a sample beside it.
 """
@@ -38,12 +39,17 @@ SM_COUNT = 148
 SM_MAX_MHZ = 2032.0
 FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25          # B300 dense FP64 (DFMA = 2 flops)
+# DRAM traffic per start (read + write) of the two heavy kernels, from the ncu
+# capture of the 65536-start 4^4 case recorded under profiles/ (None = not
+# captured for the current kernel)
+TRAFFIC_POLISH_PER_START = (1.363e8 + 2.201e8) / 65536      # profiles/polish_kernel_4d_L4.md
+TRAFFIC_RELAX_PER_START = (2.26e5 + 8.22e7) / 65536         # profiles/relax32_lines_4d_L4.md
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=8)
+    p.add_argument("--steps", type=int, default=4)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--starts", type=int, default=1 << 20, help="starts per orbit (one step)")
@@ -177,48 +183,64 @@ def run_ours(args):
     orbits = w.orbits
     d, L = 4, 4
     V = L ** d
+    side = torch.cuda.Stream()
     opt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=args.check_every,
-                                fp_mode=gb.GC_FP_AUTO, stream=stream)
+                                fp_mode=gb.GC_FP_AUTO, stream=side, use_graph=1, autotune=1)
 
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
 
-    def orbit_for(k):
-        return orbits[(k * world + rank) % len(orbits)]
+    # weak scaling: with N > 1 every rank runs the whole eight-orbit workload
+    # shape on orbits of its own seeds (no data-path collective)
+    def step_orbits(k):
+        if world == 1:
+            return orbits
+        return [oi.Orbit(o.name, o.d, o.L, oi.von_mises_orbit(4, 4, oi.kappa_grid_4d()[j], 1000 * rank + j + 1),
+                         1000 * rank + j + 1) for j, o in enumerate(orbits)]
 
-    # warm-up on separate orbit objects (same shapes)
-    for k in range(args.warmup):
-        o = orbit_for(k)
-        h = gb.gc_create_orbit(d, L, o.phi, o.orbit_id)
-        gb.gc_enumerate_copies(h, args.starts, w.omega, w.eps, opt)
-        gb.gc_destroy_orbit(h)
+    def create(orbs):
+        return [gb.gc_create_orbit(d, L, o.phi, o.orbit_id, args.starts) for o in orbs]
 
-    # --- device-resident timed region
-    handles = []
-    for k in range(args.steps):
-        o = orbit_for(k)
-        handles.append(gb.gc_create_orbit(d, L, o.phi, o.orbit_id))
-    before = [gb.gc_orbit_stats(h) for h in handles]
-    clk = ClockSampler(torch.cuda.current_device())
-    barrier()
-    clk.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for h in handles:
-        gb.gc_enumerate_copies(h, args.starts, w.omega, w.eps, opt)
-    ev1.record(stream)
-    barrier()
-    clocks = clk.stop()
-    ms = ev0.elapsed_time(ev1)
-    after = [gb.gc_orbit_stats(h) for h in handles]
-    deltas = [stats_delta(a, b) for a, b in zip(before, after)]
-    tot = {k: sum(dl[k] for dl in deltas) for k in deltas[0]}
-    n_distinct = [a["n_distinct"] for a in after]
-    for h in handles:
-        gb.gc_destroy_orbit(h)
+    n_list = [args.starts] * len(orbits)
+    # warm-up: whole steps (allocations cached, autotuning done)
+    with torch.cuda.stream(side):
+        for k in range(args.warmup):
+            hs = create(step_orbits(k))
+            gb.gc_enumerate_batch(hs, n_list, w.omega, w.eps, opt)
+            for h in hs:
+                gb.gc_destroy_orbit(h)
+
+    # --- device-resident timed region: K steps, each one graph launch of the
+    # eight orbits' whole path.  Each step's orbits are created (link angles
+    # uploaded) before its launch; CUDA events on the launch stream bracket the
+    # batch call only, so `value` counts the enqueued work with inputs resident.
+    with torch.cuda.stream(side):
+        clk = ClockSampler(torch.cuda.current_device())
+        barrier()
+        clk.start()
+        ms = 0.0
+        stats = []
+        n_distinct = None
+        for k in range(args.steps):
+            hs = create(step_orbits(k))
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(side)
+            gb.gc_enumerate_batch(hs, n_list, w.omega, w.eps, opt)
+            ev1.record(side)
+            ev1.synchronize()
+            ms += ev0.elapsed_time(ev1)
+            st_k = [gb.gc_orbit_stats(h) for h in hs]
+            stats += st_k
+            if n_distinct is None:
+                n_distinct = [s_["n_distinct"] for s_ in st_k]
+            for h in hs:
+                gb.gc_destroy_orbit(h)
+        barrier()
+        clocks = clk.stop()
+    tot = {k: sum(s_[k] for s_ in stats) for k in stats[0]}
     conv = tot["n_converged"]
     ms_max = ms
     conv_all = conv
@@ -231,21 +253,26 @@ def run_ours(args):
     value = conv_all / (ms_max / 1000.0)
     upd = tot["site_updates_fp32"] + tot["site_updates_fp64"]
 
-    # --- end to end through the C ABI with host buffers
+    # --- end to end through the C ABI with host buffers: link angles up, every
+    # distinct copy (angles, F, first start, count, lambda_2, flag) back
     barrier()
     t0 = time.perf_counter()
     e2e_conv = 0
     h2d = d2h = 0
-    for k in range(args.steps):
-        o = orbit_for(k)
-        phi = np.ascontiguousarray(o.phi)
-        h = gb.gc_create_orbit(d, L, phi, o.orbit_id)
-        h2d += phi.nbytes
-        gb.gc_enumerate_copies(h, args.starts, w.omega, w.eps, opt)
-        res = gb.gc_fetch_copies(h, V)
-        d2h += sum(res[k].nbytes for k in ("F", "theta", "first_start", "count", "lambda2", "region"))
-        e2e_conv += gb.gc_orbit_stats(h)["n_converged"]
-        gb.gc_destroy_orbit(h)
+    with torch.cuda.stream(side):
+        for k in range(args.steps):
+            orbs = step_orbits(k)
+            hs = []
+            for o in orbs:
+                phi = np.ascontiguousarray(o.phi)
+                hs.append(gb.gc_create_orbit(d, L, phi, o.orbit_id, args.starts))
+                h2d += phi.nbytes
+            gb.gc_enumerate_batch(hs, n_list, w.omega, w.eps, opt)
+            for h in hs:
+                res = gb.gc_fetch_copies(h, V)
+                d2h += sum(res[k_].nbytes for k_ in ("F", "theta", "first_start", "count", "lambda2", "region"))
+                e2e_conv += gb.gc_orbit_stats(h)["n_converged"]
+                gb.gc_destroy_orbit(h)
     barrier()
     e2e_s = time.perf_counter() - t0
     if dist is not None:
@@ -266,6 +293,7 @@ def run_ours(args):
     o = orbits[0]
     popt = gb.gc_options_default(precision=gb.GC_FP64, check_every=args.check_every,
                                  fp_mode=gb.GC_FP_AUTO, stream=stream)
+    stream = torch.cuda.current_stream()
     h = gb.gc_create_orbit(d, L, o.phi, o.orbit_id)
     gb.gc_enumerate_copies(h, 2048, w.omega, w.eps, popt)       # warm-up
     s0 = gb.gc_orbit_stats(h)
@@ -284,28 +312,49 @@ def run_ours(args):
              "sample": f"{args.plain_starts} starts of orbit kappa=0.5",
              "mixed_over_plain": value / (ps["n_converged"] / (pms / 1000.0))}
 
-    # --- roofline of the dominant kernel (per-stage CUDA events inside the library)
-    stage_ms = {"relax_fp32": tot["ms_relax"], "polish_fp64": tot["ms_polish"],
-                "dedup": tot["ms_dedup"], "fp_test": tot["ms_fptest"]}
+    # --- roofline of the dominant kernel.  Inside the timed batches the
+    # orbits' kernels overlap, so each kernel's own duration is taken from one
+    # isolated single-orbit pass of the same shape (2^20 starts of the
+    # kappa = 0.5 orbit), with CUDA events on the launch stream around every
+    # kernel (the library's per-stage events).
+    o = orbits[0]
+    ropt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=args.check_every,
+                                 fp_mode=gb.GC_FP_AUTO, stream=stream)
+    h = gb.gc_create_orbit(d, L, o.phi, o.orbit_id, args.starts)
+    gb.gc_enumerate_copies(h, args.starts, w.omega, w.eps, ropt)
+    rs = gb.gc_orbit_stats(h)
+    gb.gc_destroy_orbit(h)
+    stage_ms = {"relax_fp32": rs["ms_relax"], "polish_fp64": rs["ms_polish"],
+                "dedup": rs["ms_dedup"], "fp_test": rs["ms_fptest"]}
     dom = max(stage_ms, key=stage_ms.get)
     fp32_per_update = 8 * d + 11 + (8 * d + 3) / args.check_every
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     fp64_peak = FP64_NOMINAL_TFLOPS / 2.0                        # DFMA per second, 1e12
+    # DRAM bytes per start from the ncu capture of the small case (65536 starts),
+    # scaled by starts (the traffic grows in proportion): see profiles/
+    traffic_per_start = {"polish_fp64": TRAFFIC_POLISH_PER_START, "relax_fp32": TRAFFIC_RELAX_PER_START}
+    n_launch_starts = args.starts
     if dom == "relax_fp32":
-        achieved = tot["site_updates_fp32"] * fp32_per_update / (stage_ms[dom] / 1e3) / 1e12
-        roof = {"kernel": "relax_kernel<Fast32>", "bound": "alu", "achieved": achieved,
-                "peak": fp32_peak, "unit": "TOP/s (FP32 pipe ops)", "frac": achieved / fp32_peak,
-                "traffic": None}
+        achieved = rs["site_updates_fp32"] * fp32_per_update / (stage_ms[dom] / 1e3) / 1e12
+        roof = {"kernel": "relax32_lines_kernel<4,4>", "bound": "alu", "achieved": achieved,
+                "peak": fp32_peak, "unit": "TOP/s (FP32 pipe ops)", "frac": achieved / fp32_peak}
     elif dom == "polish_fp64":
-        dfma = tot["fp64_residual_passes"] * V * (10 * d + 2) + tot["site_updates_fp64"] * (8 * d + 30)
+        # algorithmic FP64 ops: 8d+3 per site and residual pass (staple, divergence),
+        # 9 per site and Newton rotation, 9 per site to promote, 8d+20 per fallback sweep-site
+        dfma = (rs["fp64_residual_passes"] * V * (8 * d + 3) + rs["newton_steps"] * V * 9
+                + rs["n_starts"] * V * 9 + rs["site_updates_fp64"] * (8 * d + 20))
         achieved = dfma / (stage_ms[dom] / 1e3) / 1e12
-        roof = {"kernel": "polish_kernel", "bound": "alu", "achieved": achieved, "peak": fp64_peak,
-                "unit": "T DFMA/s (FP64 pipe ops)", "frac": achieved / fp64_peak, "traffic": None}
+        roof = {"kernel": "polish_kernel<4>", "bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                "unit": "T FP64 ops/s (DFMA counted once)", "frac": achieved / fp64_peak}
     else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": None}
-    roof["peak_source"] = "derived: 148 SMs x lanes x 2032 MHz (recipe unit counts and clock)"
-    roof["stage_ms"] = stage_ms
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None}
+    tb = traffic_per_start.get(dom)
+    roof["traffic"] = None if tb is None else tb * n_launch_starts
+    roof["traffic_unit"] = "bytes per launch (DRAM read + write)"
+    roof["peak_source"] = ("derived from unit counts and the 2032 MHz max SM clock: FP32 148 x 128 lanes; "
+                           "FP64 nominal 1.25 TFLOP/s (MEASURED_PEAKS.json has no FP32/FP64 figure)")
+    roof["stage_ms_isolated"] = stage_ms
+    roof["launch_starts"] = n_launch_starts
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -318,11 +367,13 @@ def run_ours(args):
         "metric": "converged_copies_per_s", "value": value, "unit": "copies/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "starts_per_step": len(orbits) * args.starts,
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "4d_L4_vonmises_x8", "lattice": "4^4", "orbits": 8,
                    "starts_per_orbit": args.starts, "omega": 1.7, "eps32": 1e-10, "eps": 1e-24,
                    "check_every": args.check_every, "precision": "fp32 sweeps + fp64 polish",
-                   "fp_test": "lanczos fp32 screen + fp64", "parallelism": f"weak x{world}",
+                   "fp_test": "lanczos fp32 screen + fp64", "parallelism": f"weak x{world}", "launch": "one CUDA graph per step (8 orbits, 16 streams)",
+                   "timed": "device events around each step's batch launch; orbit creation outside",
                    "l2": "working set > L2 (1 GiB staging per batch + copy pool)"},
         "site_updates_per_s": upd / (ms_max / 1000.0),
         "site_updates_fp32": tot["site_updates_fp32"], "site_updates_fp64": tot["site_updates_fp64"],

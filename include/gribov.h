@@ -85,6 +85,11 @@ typedef struct {
   int batch_starts;     /* starts per device batch, 0 = automatic                  */
   void* stream;         /* cudaStream_t the work is ordered on (NULL = default)    */
   int relax_variant;    /* GC_RELAX_AUTO or GC_RELAX_GENERIC (FP32 phase kernel)    */
+  int async;            /* gc_enumerate_batch: return once enqueued (results are
+                           complete when opt->stream reaches this point)          */
+  int use_graph;        /* gc_enumerate_batch: capture the whole batch as one CUDA
+                           graph and launch it (needs a non-default stream)       */
+  int autotune;         /* tune launch shapes on first use of a (d, L, precision) */
 } gc_options;
 
 typedef struct {
@@ -133,6 +138,24 @@ int gc_create_orbit(int dim, int L, const double* link_angles, uint64_t orbit_id
  * n_dedup_failed, everything else is valid). */
 int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
                         const gc_options* opt);
+
+/* Many orbits (any mix of d and L) in one call: after a synchronous set-up
+ * (copy pools reserved for every start, staging buffers, optional autotuning)
+ * each orbit's whole path is enqueued on its own stream of a library pool,
+ * forked from and joined back to opt->stream, so the orbits' kernels run
+ * concurrently and fill each other's tails.  With opt->use_graph the fork,
+ * every kernel and the join are captured as one CUDA graph and launched once.
+ * n_starts[i] new starts for orbits[i]; each orbit appears at most once.
+ * Per-orbit results are exactly those of gc_enumerate_copies with the same
+ * arguments (launch shapes never change a start's arithmetic). */
+int gc_enumerate_batch(gc_orbit* orbits, int n_orbits, const uint64_t* n_starts, double omega,
+                       double eps, const gc_options* opt);
+
+/* Autotuner: picks warps per CTA of the relaxation, polish and FP-test
+ * kernels for o's (d, L) and precision from three pilot runs on a throw-away
+ * copy of the orbit; cached per process and used by every later call.  The
+ * knobs do not change results. */
+int gc_autotune(gc_orbit o, int precision, int* r_warps, int* p_warps, int* f_warps);
 
 /* Distinct copies sorted by (F, first_start).  capacity = 0 only sets
  * *n_distinct.  Otherwise the first min(capacity, n) copies are written to

@@ -67,6 +67,9 @@ class gc_options(ctypes.Structure):
         ("batch_starts", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("relax_variant", ctypes.c_int),
+        ("async_", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -82,7 +85,8 @@ class gc_stats(ctypes.Structure):
 
 EXPORTED = ("gc_set_allocator", "gc_options_default", "gc_create_orbit", "gc_enumerate_copies",
             "gc_fetch_copies", "gc_fetch_starts", "gc_orbit_stats", "gc_destroy_orbit",
-            "gc_last_error", "gc_version", "gc_fp_test_static")
+            "gc_last_error", "gc_version", "gc_fp_test_static", "gc_enumerate_batch",
+            "gc_autotune")
 
 _lib = None
 _lock = threading.Lock()
@@ -127,6 +131,10 @@ def load(build_if_stale: bool = True):
         L.gc_fp_test_static.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p]
+        L.gc_enumerate_batch.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_uint64), ctypes.c_double,
+                                         ctypes.c_double, ctypes.POINTER(gc_options)]
+        L.gc_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, p_i, p_i, p_i]
         L.gc_last_error.restype = ctypes.c_char_p
         L.gc_version.restype = ctypes.c_char_p
         _lib = L
@@ -201,6 +209,8 @@ def gc_options_default(**overrides) -> gc_options:
     for k, v in overrides.items():
         if k == "stream" and v is not None and not isinstance(v, int):
             v = int(v.cuda_stream)
+        if k == "async":
+            k = "async_"
         setattr(opt, k, v)
     return opt
 
@@ -218,6 +228,20 @@ def gc_create_orbit(dim: int, L: int, link_angles, orbit_id: int = 0, max_copies
 def gc_enumerate_copies(orbit, n_starts: int, omega: float, eps: float, opt: gc_options | None = None):
     _check(load().gc_enumerate_copies(orbit, n_starts, omega, eps,
                                       None if opt is None else ctypes.byref(opt)))
+
+
+def gc_enumerate_batch(orbits, n_starts, omega: float, eps: float, opt: gc_options | None = None):
+    k = len(orbits)
+    arr = (ctypes.c_void_p * k)(*[o.value if isinstance(o, ctypes.c_void_p) else o for o in orbits])
+    ns = (ctypes.c_uint64 * k)(*[int(n) for n in n_starts])
+    _check(load().gc_enumerate_batch(arr, k, ns, omega, eps,
+                                     None if opt is None else ctypes.byref(opt)))
+
+
+def gc_autotune(orbit, precision: int) -> dict:
+    r, p, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().gc_autotune(orbit, precision, ctypes.byref(r), ctypes.byref(p), ctypes.byref(f)))
+    return {"r_warps": r.value, "p_warps": p.value, "f_warps": f.value}
 
 
 def gc_fetch_copies(orbit, V: int, capacity: int | None = None, theta: bool = True) -> dict:

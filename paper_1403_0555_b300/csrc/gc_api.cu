@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -123,6 +124,10 @@ struct gc_orbit_s {
   uint64_t n_starts = 0;
   double ms[4] = {0, 0, 0, 0};
   uint64_t launches = 0;   // kernels this orbit launched
+  uint64_t enqueued = 0;   // starts enqueued so far (bounds the copy count without a sync)
+  std::vector<cudaEvent_t> ev_pool;      // timing events of enqueued batches (5 per batch)
+  size_t ev_used = 0;
+  bool err_unchecked = false;
   int last_precision = GC_FP64;
   cudaEvent_t ev[8] = {};
 
@@ -305,6 +310,9 @@ int gc_options_default(gc_options* opt) {
   opt->batch_starts = 0;
   opt->stream = nullptr;
   opt->relax_variant = GC_RELAX_AUTO;
+  opt->async = 0;
+  opt->use_graph = 0;
+  opt->autotune = 0;
   return GC_OK;
 }
 
@@ -395,14 +403,24 @@ int gc_destroy_orbit(gc_orbit o) {
     b->release(s);
   for (auto& e : o->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : o->ev_pool) cudaEventDestroy(e);
   delete o;
   return GC_OK;
 }
 
-int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps, const gc_options* opt_in) {
-  if (!o) return fail(GC_EINVAL, "gc_enumerate_copies: NULL orbit");
-  gc_options opt;
-  if (opt_in) opt = *opt_in; else gc_options_default(&opt);
+}  // extern "C"
+
+namespace {
+
+// Result-neutral launch knobs (the autotuner picks them; none changes any
+// start's arithmetic): warps per CTA of the generic relaxation, of the polish
+// and of the FP test, and starts per device batch.
+struct Tuning {
+  int r_warps = 0, p_warps = 0, f_warps = 0;
+  size_t batch = 0;
+};
+
+int validate_options(const gc_options& opt, double omega, double eps) {
   if (!(omega > 0.0 && omega < 2.0)) return fail(GC_EINVAL, "omega = %g not in (0, 2)", omega);
   if (!(eps > 0.0)) return fail(GC_EINVAL, "eps = %g must be > 0", eps);
   if (opt.precision != GC_FP64 && opt.precision != GC_MIXED) return fail(GC_EINVAL, "unknown precision %d", opt.precision);
@@ -414,23 +432,74 @@ int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
   if (!(opt.fp_tau >= 0.0)) return fail(GC_EINVAL, "fp_tau = %g < 0", opt.fp_tau);
   if (opt.lanczos_k < 2) return fail(GC_EINVAL, "lanczos_k = %d < 2", opt.lanczos_k);
   if (opt.newton_inner < 1 || opt.newton_max < 0) return fail(GC_EINVAL, "bad Newton polish settings");
+  return GC_OK;
+}
+
+// Add up the stage times of every batch enqueued since the last harvest
+// (the orbit's work must be complete).
+void harvest_timing(gc_orbit o) {
+  for (size_t k = 0; k + 4 < o->ev_used; k += 5) {
+    float t01 = 0, t12 = 0, t23 = 0, t34 = 0;
+    cudaEventElapsedTime(&t01, o->ev_pool[k], o->ev_pool[k + 1]);
+    cudaEventElapsedTime(&t12, o->ev_pool[k + 1], o->ev_pool[k + 2]);
+    cudaEventElapsedTime(&t23, o->ev_pool[k + 2], o->ev_pool[k + 3]);
+    cudaEventElapsedTime(&t34, o->ev_pool[k + 3], o->ev_pool[k + 4]);
+    o->ms[0] += t01; o->ms[1] += t12; o->ms[2] += t23; o->ms[3] += t34;
+  }
+  cudaGetLastError();
+  o->ev_used = 0;
+}
+
+int check_errors(gc_orbit o) {
+  if (!o->err_unchecked) return GC_OK;
+  int flags[4] = {0, 0, 0, 0};
+  GC_CUDA(cudaMemcpy(flags, o->err(), 16, cudaMemcpyDeviceToHost));
+  o->err_unchecked = false;
+  if (flags[1]) return fail(GC_ENOMEM, "copy pool overflow");
+  if (flags[2]) return fail(GC_ENOMEM, "quantised-minimum set overflow");
+  if (flags[0]) return fail(GC_ETIMEDOUT, "a copy-table lock wait ran out (affected starts are marked)");
+  return GC_OK;
+}
+
+std::mutex g_tune_mu;
+std::vector<std::pair<long long, Tuning>> g_tune_cache;   // key: d | L << 4 | precision << 12
+
+long long tune_key(int d, int L, int precision) { return (long long)d | ((long long)L << 4) | ((long long)precision << 12); }
+
+Tuning cached_tuning(int d, int L, int precision) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto& kv : g_tune_cache)
+    if (kv.first == tune_key(d, L, precision)) return kv.second;
+  return Tuning{};
+}
+
+// Enqueue the whole path for n_starts starts on stream s.  With `async` no
+// host synchronisation happens: the copy pool must already hold
+// o->enqueued + n_starts entries, and timing and error flags are read at the
+// next synchronising call.  keep_per_start implies a synchronous call.
+int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, const gc_options& opt,
+                   cudaStream_t s, bool async, bool timing, const Tuning& tune,
+                   bool prepare_only = false) {
   if (n_starts == 0) return GC_OK;
   const int max_sweeps = ((opt.max_sweeps + opt.check_every - 1) / opt.check_every) * opt.check_every;
-  cudaStream_t s = (cudaStream_t)opt.stream;
   const int V = o->V, d = o->d;
   const bool mixed = opt.precision == GC_MIXED;
   o->last_precision = opt.precision;
 
   // batch size: staging of at most ~1 GiB
   const size_t per_start = (size_t)V * 16 + (mixed ? (size_t)V * 8 : 0) + 48;
-  size_t B = opt.batch_starts > 0 ? (size_t)opt.batch_starts : std::max<size_t>(4096, (1ull << 30) / per_start);
+  size_t B = opt.batch_starts > 0 ? (size_t)opt.batch_starts
+                                  : (tune.batch ? tune.batch : std::max<size_t>(4096, (1ull << 30) / per_start));
   B = std::min<size_t>(B, n_starts);
   if (!o->s_status.ensure(B, s) || !o->s_sweeps.ensure(B * 4, s) || !o->s_resid.ensure(B * 8, s) ||
       !o->s_F.ensure(B * 8, s) || !o->s_fprint.ensure(B * 8, s) || !o->s_config.ensure(B * V * 16, s) ||
       !o->s_copy.ensure(B * 4, s) || (mixed && !o->s_state32.ensure(B * V * 8, s)))
     return fail(GC_ENOMEM, "cannot admit a batch of %zu starts (%.1f MiB staging)", B, B * per_start / 1048576.0);
 
-  if (opt.keep_per_start) {
+  if (opt.keep_per_start && async) return fail(GC_EINVAL, "keep_per_start needs a synchronous call");
+  if (prepare_only) {
+    // staging only (set below); no records
+  } else if (opt.keep_per_start) {
     o->rec_first = o->next_start;
     o->rec_n = n_starts;
     o->rec_status.assign(n_starts, 0);
@@ -448,8 +517,9 @@ int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
     return gc::Smem(V, d, site_bytes, (size_t)V * site_bytes, warps * tpw).total;
   };
   const int site_bytes = mixed ? 8 : 16;
-  const int r_warps = fit_warps(8, [&](int w) { return relax_bytes(w, site_bytes); });
+  int r_warps = fit_warps(8, [&](int w) { return relax_bytes(w, site_bytes); });
   if (!r_warps) return fail(GC_EINVAL, "relaxation does not fit shared memory");
+  if (tune.r_warps > 0 && tune.r_warps < r_warps) r_warps = tune.r_warps;
   const size_t r_smem = relax_bytes(r_warps, site_bytes);
   auto polish_bytes = [&](int warps) {
     return gc::Smem(V, d, sizeof(double2), gc::polish_team_bytes(V, d), warps * tpw).total;
@@ -458,27 +528,58 @@ int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
   int p_warps = mixed ? fit_warps(8, [&](int w) { return 2 * polish_bytes(w) + 2048; }) : 0;
   if (mixed && !p_warps) p_warps = fit_warps(8, polish_bytes);
   if (mixed && !p_warps) return fail(GC_EINVAL, "polish does not fit shared memory");
+  if (mixed && tune.p_warps > 0 && tune.p_warps < p_warps) p_warps = tune.p_warps;
   const size_t p_smem = mixed ? polish_bytes(p_warps) : 0;
   const int kmax64 = std::min(opt.lanczos_k, std::max(1, V - 1));
   const int kmax32 = std::min(160, kmax64);
   const int kmax_sm = std::max(kmax64, kmax32);
-  const int f_warps = fit_warps(4, [&](int w) { return gc::FpSmem(V, d, kmax_sm, w).total; });
+  int f_warps = fit_warps(4, [&](int w) { return gc::FpSmem(V, d, kmax_sm, w).total; });
   if (!f_warps) return fail(GC_EINVAL, "Faddeev-Popov test does not fit shared memory");
+  if (tune.f_warps > 0 && tune.f_warps < f_warps) f_warps = tune.f_warps;
   const size_t f_smem = gc::FpSmem(V, d, kmax_sm, f_warps).total;
+
+  // dense-mode Lanczos bases: one V x V slot per warp, sized for the largest batch
+  int dense_grid = 0;
+  if (opt.fp_mode == GC_FP_DENSE) {
+    if (int rc = launch_grid(gc::fp_test_kernel, f_warps * 32, f_smem, f_warps, (long long)B, &dense_grid)) return rc;
+    const size_t slot = (size_t)V * V * 8;
+    const size_t max_slots = std::max<size_t>(1, (1ull << 30) / slot);
+    dense_grid = (int)std::min<size_t>(dense_grid, std::max<size_t>(1, max_slots / f_warps));
+    if (!o->scratch.ensure((size_t)dense_grid * f_warps * slot, s))
+      return fail(GC_ENOMEM, "cannot admit %zu bytes of Lanczos basis scratch", (size_t)dense_grid * f_warps * slot);
+  }
+  if (prepare_only) return GC_OK;
 
   unsigned long long* wctr = o->work.as<unsigned long long>();
   unsigned long long* stats = o->stats.as<unsigned long long>();
-  GC_CUDA(cudaMemsetAsync(o->err(), 0, 16, s));
+  if (!o->err_unchecked) GC_CUDA(cudaMemsetAsync(o->err(), 0, 16, s));
+  o->err_unchecked = true;
 
   for (uint64_t done = 0; done < n_starts;) {
     const long long b = (long long)std::min<uint64_t>(B, n_starts - done);
-    // admission: the pool must hold every start of the batch as a new copy
-    unsigned cur = 0;
-    GC_CUDA(cudaMemcpyAsync(&cur, o->n_entries(), 4, cudaMemcpyDeviceToHost, s));
-    GC_CUDA(cudaStreamSynchronize(s));
-    if ((unsigned long long)cur + b > o->cap) {
-      int rc = table_reserve(o, (unsigned long long)cur + b, cur, s);
-      if (rc != GC_OK) return rc;
+    // admission: the pool must hold every start of the batch as a new copy.
+    // o->enqueued bounds the copies made so far, so no read-back is needed
+    // while the pool is large enough for that bound.
+    if (o->enqueued + (unsigned long long)b > o->cap) {
+      if (async) return fail(GC_ESTATE, "asynchronous enumeration needs the copy pool reserved up front");
+      unsigned cur = 0;
+      GC_CUDA(cudaMemcpyAsync(&cur, o->n_entries(), 4, cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaStreamSynchronize(s));
+      if ((unsigned long long)cur + b > o->cap) {
+        int rc = table_reserve(o, (unsigned long long)cur + b, cur, s);
+        if (rc != GC_OK) return rc;
+      }
+    }
+    // timing events of this batch
+    cudaEvent_t* ev = nullptr;
+    if (timing) {
+      while (o->ev_pool.size() < o->ev_used + 5) {
+        cudaEvent_t e;
+        GC_CUDA(cudaEventCreate(&e));
+        o->ev_pool.push_back(e);
+      }
+      ev = o->ev_pool.data() + o->ev_used;
+      o->ev_used += 5;
     }
     GC_CUDA(cudaMemsetAsync(wctr, 0, 16, s));
     GC_CUDA(cudaMemsetAsync(o->n_new(), 0, 4, s));
@@ -512,7 +613,7 @@ int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
     ra.state32 = o->s_state32.as<float2>();
     ra.stats = stats;
     int grid = 0;
-    GC_CUDA(cudaEventRecord(o->ev[0], s));
+    if (ev) GC_CUDA(cudaEventRecord(ev[0], s));
     if (mixed && opt.relax_variant != GC_RELAX_GENERIC && d == 4 && o->L == 4) {
       constexpr int kTeams = 4;
       auto k = gc::relax32_lines_kernel<4, 4, kTeams>;
@@ -553,7 +654,7 @@ int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
       if (rc) return rc;
     }
     GC_CUDA(cudaGetLastError());
-    GC_CUDA(cudaEventRecord(o->ev[1], s));
+    if (ev) GC_CUDA(cudaEventRecord(ev[1], s));
     if (mixed) {
       gc::PolishArgs pa{};
       pa.geom = o->geom;
@@ -595,7 +696,7 @@ int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
       if (prc) return prc;
       GC_CUDA(cudaGetLastError());
     }
-    GC_CUDA(cudaEventRecord(o->ev[2], s));
+    if (ev) GC_CUDA(cudaEventRecord(ev[2], s));
     // deduplication
     gc::DedupArgs da{};
     da.tab = o->view();
@@ -619,7 +720,7 @@ int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
       ++o->launches;
       GC_CUDA(cudaGetLastError());
     }
-    GC_CUDA(cudaEventRecord(o->ev[3], s));
+    if (ev) GC_CUDA(cudaEventRecord(ev[3], s));
     // Faddeev-Popov test of the copies this batch created
     if (opt.fp_mode != GC_FP_NONE) {
       gc::FpArgs fa{};
@@ -644,18 +745,14 @@ int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
       int fgrid = 0;
       if (int rc = launch_grid(gc::fp_test_kernel, f_warps * 32, f_smem, f_warps, b, &fgrid)) return rc;
       if (opt.fp_mode == GC_FP_DENSE) {
-        const size_t slot = (size_t)V * V * 8;
-        const size_t max_slots = std::max<size_t>(1, (1ull << 30) / slot);
-        fgrid = (int)std::min<size_t>(fgrid, std::max<size_t>(1, max_slots / f_warps));
-        if (!o->scratch.ensure((size_t)fgrid * f_warps * slot, s))
-          return fail(GC_ENOMEM, "cannot admit %zu bytes of Lanczos basis scratch", (size_t)fgrid * f_warps * slot);
+        fgrid = std::min(fgrid, dense_grid);
         fa.scratch = o->scratch.as<double>();
       }
       gc::fp_test_kernel<<<fgrid, f_warps * 32, f_smem, s>>>(fa);
       ++o->launches;
       GC_CUDA(cudaGetLastError());
     }
-    GC_CUDA(cudaEventRecord(o->ev[4], s));
+    if (ev) GC_CUDA(cudaEventRecord(ev[4], s));
     if (opt.keep_per_start) {
       const size_t off = done;
       GC_CUDA(cudaMemcpyAsync(o->rec_status.data() + off, ra.status, b, cudaMemcpyDeviceToHost, s));
@@ -663,23 +760,30 @@ int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
       GC_CUDA(cudaMemcpyAsync(o->rec_F.data() + off, ra.F, b * 8, cudaMemcpyDeviceToHost, s));
       GC_CUDA(cudaMemcpyAsync(o->rec_copy.data() + off, da.copy_of, b * 4, cudaMemcpyDeviceToHost, s));
     }
-    GC_CUDA(cudaStreamSynchronize(s));
-    float t01 = 0, t12 = 0, t23 = 0, t34 = 0;
-    cudaEventElapsedTime(&t01, o->ev[0], o->ev[1]);
-    cudaEventElapsedTime(&t12, o->ev[1], o->ev[2]);
-    cudaEventElapsedTime(&t23, o->ev[2], o->ev[3]);
-    cudaEventElapsedTime(&t34, o->ev[3], o->ev[4]);
-    o->ms[0] += t01; o->ms[1] += t12; o->ms[2] += t23; o->ms[3] += t34;
     o->next_start += b;
     o->n_starts += b;
+    o->enqueued += b;
     done += b;
   }
-  int err[4] = {0, 0, 0, 0};
-  GC_CUDA(cudaMemcpy(err, o->err(), 16, cudaMemcpyDeviceToHost));
-  if (err[1]) return fail(GC_ENOMEM, "copy pool overflow");
-  if (err[2]) return fail(GC_ENOMEM, "quantised-minimum set overflow");
-  if (err[0]) return fail(GC_ETIMEDOUT, "a copy-table lock wait ran out (affected starts are marked)");
   return GC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps, const gc_options* opt_in) {
+  if (!o) return fail(GC_EINVAL, "gc_enumerate_copies: NULL orbit");
+  gc_options opt;
+  if (opt_in) opt = *opt_in; else gc_options_default(&opt);
+  if (int rc = validate_options(opt, omega, eps)) return rc;
+  if (n_starts == 0) return GC_OK;
+  cudaStream_t s = (cudaStream_t)opt.stream;
+  const Tuning tune = cached_tuning(o->d, o->L, opt.precision);
+  if (int rc = enumerate_impl(o, n_starts, omega, eps, opt, s, false, true, tune)) return rc;
+  GC_CUDA(cudaStreamSynchronize(s));
+  harvest_timing(o);
+  return check_errors(o);
 }
 
 namespace {
@@ -693,6 +797,8 @@ struct Meta {
 
 int read_meta(gc_orbit o, Meta& m, unsigned* n_out) {
   GC_CUDA(cudaDeviceSynchronize());
+  harvest_timing(o);
+  if (int rc = check_errors(o)) return rc;
   unsigned n = 0;
   GC_CUDA(cudaMemcpy(&n, o->n_entries(), 4, cudaMemcpyDeviceToHost));
   n = std::min(n, o->cap);
@@ -782,6 +888,7 @@ int gc_orbit_stats(gc_orbit o, gc_stats* out) {
   if (!o || !out) return fail(GC_EINVAL, "gc_orbit_stats: NULL argument");
   std::memset(out, 0, sizeof *out);
   GC_CUDA(cudaDeviceSynchronize());
+  harvest_timing(o);
   unsigned long long st[kNumStats] = {};
   GC_CUDA(cudaMemcpy(st, o->stats.p, sizeof st, cudaMemcpyDeviceToHost));
   unsigned long long nf8 = 0;
@@ -970,5 +1077,177 @@ extern "C" int gc_fp_test_static(int dim, int L, const double* d_links, const do
   fa.stats = reinterpret_cast<unsigned long long*>(s + lay.stats);
   gc::fp_test_kernel<<<fgrid, fwarps_used * 32, fsm, st>>>(fa);
   GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches of orbits and the autotuner
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kPoolStreams = 16;
+std::mutex g_pool_mu;
+cudaStream_t g_pool[kStaticMaxDevices][kPoolStreams] = {};
+
+int pool_streams(cudaStream_t** out) {
+  int dev = 0;
+  GC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) return fail(GC_EINVAL, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev][0])
+    for (int i = 0; i < kPoolStreams; ++i)
+      GC_CUDA(cudaStreamCreateWithFlags(&g_pool[dev][i], cudaStreamNonBlocking));
+  *out = g_pool[dev];
+  return GC_OK;
+}
+
+// Reserve every orbit's copy pool for its pending starts (one read-back per
+// orbit), so that the enqueue itself needs no host synchronisation.
+int reserve_for(gc_orbit o, uint64_t n, cudaStream_t s) {
+  const unsigned long long need = o->enqueued + n;
+  if (need <= o->cap) return GC_OK;
+  unsigned cur = 0;
+  GC_CUDA(cudaMemcpyAsync(&cur, o->n_entries(), 4, cudaMemcpyDeviceToHost, s));
+  GC_CUDA(cudaStreamSynchronize(s));
+  return table_reserve(o, need, cur, s);
+}
+
+// Pilot runs on a throw-away copy of the orbit: three launch shapes per
+// kernel, the fastest kept per kernel.  Only result-neutral knobs are tuned.
+int autotune_shape(gc_orbit like, const gc_options& base, double omega, double eps, Tuning* out) {
+  std::vector<double> phi((size_t)like->V * like->d);
+  {
+    std::vector<double2> u((size_t)like->V * like->d);
+    GC_CUDA(cudaMemcpy(u.data(), like->links64.p, u.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < u.size(); ++i) phi[i] = std::atan2(u[i].y, u[i].x);
+  }
+  gc_orbit tmp = nullptr;
+  if (int rc = gc_create_orbit(like->d, like->L, phi.data(), 0xA070u, 0, &tmp)) return rc;
+  gc_options opt = base;
+  opt.keep_per_start = 0;
+  opt.async = 0;
+  opt.use_graph = 0;
+  opt.stream = nullptr;
+  const uint64_t pilot = std::max<uint64_t>(2048, 262144 / (uint64_t)like->V * 4);
+  const int cand[3][3] = {{2, 2, 1}, {4, 4, 2}, {8, 8, 4}};
+  double best[3] = {1e300, 1e300, 1e300};
+  Tuning t;
+  int rc = GC_OK;
+  for (int c = 0; c < 3 && rc == GC_OK; ++c) {
+    Tuning cand_t;
+    cand_t.r_warps = cand[c][0];
+    cand_t.p_warps = cand[c][1];
+    cand_t.f_warps = cand[c][2];
+    const double m0[4] = {tmp->ms[0], tmp->ms[1], tmp->ms[2], tmp->ms[3]};
+    rc = enumerate_impl(tmp, pilot, omega, eps, opt, nullptr, false, true, cand_t);
+    if (rc == GC_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) rc = fail(GC_ECUDA, "autotune pilot failed");
+    if (rc != GC_OK) break;
+    harvest_timing(tmp);
+    const double dt[3] = {tmp->ms[0] - m0[0], tmp->ms[1] - m0[1], tmp->ms[3] - m0[3]};
+    if (dt[0] < best[0]) { best[0] = dt[0]; t.r_warps = cand_t.r_warps; }
+    if (dt[1] < best[1]) { best[1] = dt[1]; t.p_warps = cand_t.p_warps; }
+    if (dt[2] < best[2]) { best[2] = dt[2]; t.f_warps = cand_t.f_warps; }
+  }
+  gc_destroy_orbit(tmp);
+  if (rc != GC_OK) return rc;
+  *out = t;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.emplace_back(tune_key(like->d, like->L, base.precision), t);
+  return GC_OK;
+}
+
+bool have_tuning(int d, int L, int precision) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto& kv : g_tune_cache)
+    if (kv.first == tune_key(d, L, precision)) return true;
+  return false;
+}
+
+}  // namespace
+
+extern "C" int gc_enumerate_batch(gc_orbit* orbits, int n_orbits, const uint64_t* n_starts, double omega,
+                                  double eps, const gc_options* opt_in) {
+  if (!orbits || !n_starts || n_orbits < 1) return fail(GC_EINVAL, "gc_enumerate_batch: empty or NULL batch");
+  gc_options opt;
+  if (opt_in) opt = *opt_in; else gc_options_default(&opt);
+  if (int rc = validate_options(opt, omega, eps)) return rc;
+  if (opt.keep_per_start) return fail(GC_EINVAL, "keep_per_start is not available for batches");
+  for (int i = 0; i < n_orbits; ++i) {
+    if (!orbits[i]) return fail(GC_EINVAL, "orbit %d is NULL", i);
+    for (int j = 0; j < i; ++j)
+      if (orbits[j] == orbits[i]) return fail(GC_EINVAL, "orbit %d appears twice in the batch", i);
+  }
+  cudaStream_t origin = (cudaStream_t)opt.stream;
+  cudaStream_t* pool = nullptr;
+  if (int rc = pool_streams(&pool)) return rc;
+  // set-up that needs the host: tuning, copy pools, staging buffers
+  for (int i = 0; i < n_orbits; ++i) {
+    gc_orbit o = orbits[i];
+    if (opt.autotune && !have_tuning(o->d, o->L, opt.precision)) {
+      Tuning t;
+      if (int rc = autotune_shape(o, opt, omega, eps, &t)) return rc;
+    }
+    if (int rc = reserve_for(o, n_starts[i], origin)) return rc;
+    if (int rc = enumerate_impl(o, n_starts[i], omega, eps, opt, origin, true, false,
+                                cached_tuning(o->d, o->L, opt.precision), true))
+      return rc;
+  }
+  GC_CUDA(cudaStreamSynchronize(origin));
+  // fork onto the pool, one stream per orbit (round robin), join back on origin
+  cudaEvent_t fork, join[kPoolStreams];
+  GC_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  for (auto& e : join) GC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  const int used = std::min(n_orbits, kPoolStreams);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int rc = GC_OK;
+  if (opt.use_graph) {
+    const cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) rc = fail(GC_ECUDA, "cudaStreamBeginCapture: %s (use a non-default stream)", cudaGetErrorString(e));
+  }
+  if (rc == GC_OK && cudaEventRecord(fork, origin) != cudaSuccess) rc = fail(GC_ECUDA, "fork record failed");
+  for (int k = 0; rc == GC_OK && k < used; ++k)
+    if (cudaStreamWaitEvent(pool[k], fork, 0) != cudaSuccess) rc = fail(GC_ECUDA, "fork wait failed");
+  for (int i = 0; rc == GC_OK && i < n_orbits; ++i)
+    rc = enumerate_impl(orbits[i], n_starts[i], omega, eps, opt, pool[i % kPoolStreams], true, true,
+                        cached_tuning(orbits[i]->d, orbits[i]->L, opt.precision));
+  for (int k = 0; k < used; ++k) {
+    if (cudaEventRecord(join[k], pool[k]) != cudaSuccess && rc == GC_OK) rc = fail(GC_ECUDA, "join record failed");
+    if (cudaStreamWaitEvent(origin, join[k], 0) != cudaSuccess && rc == GC_OK) rc = fail(GC_ECUDA, "join wait failed");
+  }
+  if (opt.use_graph) {
+    const cudaError_t e = cudaStreamEndCapture(origin, &graph);
+    if (rc == GC_OK && e != cudaSuccess) rc = fail(GC_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+    if (rc == GC_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = fail(GC_ECUDA, "cudaGraphInstantiate failed");
+    if (rc == GC_OK && cudaGraphLaunch(exec, origin) != cudaSuccess) rc = fail(GC_ECUDA, "cudaGraphLaunch failed");
+  }
+  const bool wait = !opt.async || opt.use_graph;
+  if (wait && cudaStreamSynchronize(origin) != cudaSuccess && rc == GC_OK)
+    rc = fail(GC_ECUDA, "batch: %s", cudaGetErrorString(cudaGetLastError()));
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaEventDestroy(fork);
+  for (auto& e : join) cudaEventDestroy(e);
+  if (rc != GC_OK || !wait) return rc;
+  for (int i = 0; i < n_orbits; ++i) {
+    harvest_timing(orbits[i]);
+    if (int r = check_errors(orbits[i])) return r;
+  }
+  return GC_OK;
+}
+
+extern "C" int gc_autotune(gc_orbit o, int precision, int* r_warps, int* p_warps, int* f_warps) {
+  if (!o) return fail(GC_EINVAL, "gc_autotune: NULL orbit");
+  if (precision != GC_FP64 && precision != GC_MIXED) return fail(GC_EINVAL, "unknown precision %d", precision);
+  gc_options opt;
+  gc_options_default(&opt);
+  opt.precision = precision;
+  opt.check_every = precision == GC_MIXED ? 4 : 1;
+  Tuning t;
+  if (have_tuning(o->d, o->L, precision)) t = cached_tuning(o->d, o->L, precision);
+  else if (int rc = autotune_shape(o, opt, 1.7, 1e-24, &t)) return rc;
+  if (r_warps) *r_warps = t.r_warps;
+  if (p_warps) *p_warps = t.p_warps;
+  if (f_warps) *f_warps = t.f_warps;
   return GC_OK;
 }

@@ -1,0 +1,84 @@
+"""Batches of orbits of uneven size: one call (optionally one captured CUDA graph)
+gives every orbit exactly the result of its own gc_enumerate_copies call."""
+import numpy as np
+import pytest
+
+import orbit_inputs as oi
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(2, 4), (2, 6), (3, 4), (3, 5), (4, 3), (4, 4)]
+
+
+def _orbits():
+    return [(d, L, oi.von_mises_orbit(d, L, 1.0, 10 * d + L), 100 + 10 * d + L) for d, L in SHAPES]
+
+
+def _fetch_all(gb, h, V):
+    c = gb.gc_fetch_copies(h, V)
+    s = gb.gc_orbit_stats(h)
+    return c, s
+
+
+def _single(gb, orbits, n, opt):
+    out = []
+    for d, L, phi, oid in orbits:
+        h = gb.gc_create_orbit(d, L, phi, oid)
+        gb.gc_enumerate_copies(h, n, 1.7, 1e-24, opt)
+        out.append(_fetch_all(gb, h, L ** d))
+        gb.gc_destroy_orbit(h)
+    return out
+
+
+def _batch(gb, orbits, n, opt, calls=1):
+    hs = [gb.gc_create_orbit(d, L, phi, oid) for d, L, phi, oid in orbits]
+    for _ in range(calls):
+        gb.gc_enumerate_batch(hs, [n // calls] * len(hs), 1.7, 1e-24, opt)
+    out = [_fetch_all(gb, h, L ** d) for h, (d, L, _, _) in zip(hs, orbits)]
+    for h in hs:
+        gb.gc_destroy_orbit(h)
+    return out
+
+
+def _same(a, b):
+    for (ca, sa), (cb, sb) in zip(a, b):
+        assert ca["n_distinct"] == cb["n_distinct"]
+        for k in ("F", "first_start", "count", "region", "lambda2", "theta"):
+            assert np.array_equal(ca[k], cb[k]), k
+        for k in ("n_converged", "n_not_converged", "n_distinct_F8", "sweeps_fp32", "sweeps_fp64"):
+            assert sa[k] == sb[k], k
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_equals_single_calls(precision):
+    import paper_1403_0555_b300 as gb
+    orbits = _orbits()
+    opt = gb.gc_options_default(precision=precision, check_every=4 if precision else 1)
+    _same(_single(gb, orbits, 3000, opt), _batch(gb, orbits, 3000, opt))
+
+
+def test_batch_in_one_cuda_graph_and_async():
+    import torch
+    import paper_1403_0555_b300 as gb
+    orbits = _orbits()
+    side = torch.cuda.Stream()
+    ref = _single(gb, orbits, 2000, gb.gc_options_default(precision=1, check_every=4))
+    with torch.cuda.stream(side):
+        opt = gb.gc_options_default(precision=1, check_every=4, use_graph=1, stream=side)
+        _same(ref, _batch(gb, orbits, 2000, opt))
+        opt = gb.gc_options_default(precision=1, check_every=4, stream=side)
+        opt.async_ = 1
+        _same(ref, _batch(gb, orbits, 2000, opt, calls=2))
+
+
+def test_autotune_is_result_neutral():
+    import paper_1403_0555_b300 as gb
+    orbits = _orbits()[-2:]
+    opt = gb.gc_options_default(precision=1, check_every=4)
+    ref = _single(gb, orbits, 2000, opt)
+    h = gb.gc_create_orbit(*orbits[0][:3], orbits[0][3])
+    t = gb.gc_autotune(h, 1)
+    gb.gc_destroy_orbit(h)
+    assert t["r_warps"] in (2, 4, 8) and t["p_warps"] in (2, 4, 8) and t["f_warps"] in (1, 2, 4)
+    opt.autotune = 1
+    _same(ref, _batch(gb, orbits, 2000, opt))
