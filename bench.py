@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--cpu-starts", type=int, default=1536)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--check-every", type=int, default=4)
+    p.add_argument("--serve-requests", type=int, default=100,
+                   help="requests of the Poisson serving leg (0 skips it)")
     return p.parse_args()
 
 
@@ -154,6 +156,69 @@ def run_reference(args):
         "e2e": {"value": v, "unit": "copies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
+
+
+# ----------------------------------------------------------------------------
+# serving leg: Poisson arrivals at 200 requests/s of mixed-dimension requests
+# ----------------------------------------------------------------------------
+
+def serve_leg(gb, n_requests, opt):
+    import threading
+    reqs = oi.request_stream(n_requests, rate_hz=200.0, seed=7)
+    srv = gb.gc_server_create(8, 0, opt)
+    results = []
+    tickets = []
+    failures = []
+    lock = threading.Lock()
+    done = threading.Event()
+
+    def collector():
+        i = 0
+        while True:
+            with lock:
+                have = i < len(tickets)
+                t = tickets[i] if have else None
+            if not have:
+                if done.is_set():
+                    with lock:
+                        if i >= len(tickets):
+                            return
+                    continue
+                time.sleep(0.0005)
+                continue
+            status, latency, orb = gb.gc_server_wait(srv, t[0], -1.0)
+            if status != 0:
+                r = t[1]
+                failures.append(f"{r.d}D L={r.L} n={r.n_starts}: {gb.gc_last_error()}")
+            conv = gb.gc_orbit_stats(orb)["n_converged"] if orb is not None else 0
+            if orb is not None:
+                gb.gc_destroy_orbit(orb)
+            results.append((status, latency, conv, time.perf_counter()))
+            i += 1
+
+    th = threading.Thread(target=collector)
+    th.start()
+    t0 = time.perf_counter()
+    for r in reqs:
+        wait = r.arrival_s - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        tk = gb.gc_server_submit(srv, r.d, r.L, r.phi, r.seed, r.n_starts)
+        with lock:
+            tickets.append((tk, r))
+    done.set()
+    th.join()
+    span = max(x[3] for x in results) - t0
+    gb.gc_server_destroy(srv)
+    lat = np.array([x[1] for x in results])
+    conv = sum(x[2] for x in results)
+    offered = sum(r.n_starts for r in reqs) / reqs[-1].arrival_s
+    return {"requests": n_requests, "rate_hz": 200.0, "workers": 8,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "converged_copies_per_s": conv / span, "offered_starts_per_s": offered,
+            "failed": int(sum(1 for x in results if x[0] != 0)), "failures": failures[:5], "span_s": span,
+            "mix": "dim in {2,3,4}, L from {4,6,8,12,16}/{4,5,6,8}/{3,4,5,6}, "
+                   "n_starts log-uniform in [1e3, 1e6], von Mises(1.0) orbits"}
 
 
 # ----------------------------------------------------------------------------
@@ -356,6 +421,12 @@ def run_ours(args):
     roof["stage_ms_isolated"] = stage_ms
     roof["launch_starts"] = n_launch_starts
 
+    serving = None
+    if args.serve_requests > 0:
+        sopt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=args.check_every,
+                                     fp_mode=gb.GC_FP_AUTO)
+        serving = serve_leg(gb, args.serve_requests, sopt)
+
     cpu = None
     if not args.no_cpu_baseline:
         c, dt, threads = oracle_sample(orbits[0], args.cpu_starts)
@@ -379,6 +450,7 @@ def run_ours(args):
         "site_updates_fp32": tot["site_updates_fp32"], "site_updates_fp64": tot["site_updates_fp64"],
         "distinct_copies_per_orbit": n_distinct,
         "plain_fp64": plain,
+        "serving": serving,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -157,6 +157,31 @@ int gc_enumerate_batch(gc_orbit* orbits, int n_orbits, const uint64_t* n_starts,
  * knobs do not change results. */
 int gc_autotune(gc_orbit o, int precision, int* r_warps, int* p_warps, int* f_warps);
 
+/* Serving with continuous batching.  Requests (an orbit and a start count)
+ * queue in arrival order; `workers` threads, each on its own stream, start the
+ * head request as soon as its device-memory estimate fits the budget, so
+ * requests that arrive while others run are admitted as memory frees up and
+ * their kernels overlap on the GPU.  A request's state stays on the device;
+ * its result is a finished orbit handed to the caller (fetch, then destroy).
+ * A request's result does not depend on what else runs.
+ *   mem_budget_bytes: 0 = half the free device memory at creation.
+ *   gc_server_submit: GC_ENOMEM if the request alone exceeds the budget.
+ *   gc_server_wait:   blocks up to timeout_s (< 0: no limit); GC_ETIMEDOUT if
+ *     not finished (the ticket stays valid).  On completion *status is the
+ *     request's own result code, *latency_s the time from submission to
+ *     completion, and *orbit the finished orbit (NULL on failure; if the
+ *     caller passes NULL for orbit, the library destroys it).  The ticket is
+ *     then retired.
+ *   gc_server_destroy: finishes queued and running requests, frees orbits
+ *     nobody collected. */
+typedef struct gc_server_s* gc_server;
+int gc_server_create(int workers, size_t mem_budget_bytes, const gc_options* opt, gc_server* out);
+int gc_server_submit(gc_server s, int dim, int L, const double* link_angles, uint64_t orbit_id,
+                     uint64_t n_starts, double omega, double eps, uint64_t* ticket);
+int gc_server_wait(gc_server s, uint64_t ticket, double timeout_s, int* status, double* latency_s,
+                   gc_orbit* orbit);
+int gc_server_destroy(gc_server s);
+
 /* Distinct copies sorted by (F, first_start).  capacity = 0 only sets
  * *n_distinct.  Otherwise the first min(capacity, n) copies are written to
  * every non-NULL array: F[n], theta[n*V] (canonical angles, theta'_{V-1} = 0),

@@ -86,7 +86,8 @@ class gc_stats(ctypes.Structure):
 EXPORTED = ("gc_set_allocator", "gc_options_default", "gc_create_orbit", "gc_enumerate_copies",
             "gc_fetch_copies", "gc_fetch_starts", "gc_orbit_stats", "gc_destroy_orbit",
             "gc_last_error", "gc_version", "gc_fp_test_static", "gc_enumerate_batch",
-            "gc_autotune")
+            "gc_autotune", "gc_server_create", "gc_server_submit", "gc_server_wait",
+            "gc_server_destroy")
 
 _lib = None
 _lock = threading.Lock()
@@ -135,6 +136,14 @@ def load(build_if_stale: bool = True):
                                          ctypes.POINTER(ctypes.c_uint64), ctypes.c_double,
                                          ctypes.c_double, ctypes.POINTER(gc_options)]
         L.gc_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, p_i, p_i, p_i]
+        L.gc_server_create.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(gc_options),
+                                       ctypes.POINTER(ctypes.c_void_p)]
+        L.gc_server_submit.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, p_d, ctypes.c_uint64,
+                                       ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_uint64)]
+        L.gc_server_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double, p_i,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p)]
+        L.gc_server_destroy.argtypes = [ctypes.c_void_p]
         L.gc_last_error.restype = ctypes.c_char_p
         L.gc_version.restype = ctypes.c_char_p
         _lib = L
@@ -289,3 +298,33 @@ def gc_fp_test_static(dim: int, L: int, d_links: int, d_configs: int, n: int, fp
     """Allocation-free first-region test on device buffers (raw device pointers)."""
     _check(load().gc_fp_test_static(dim, L, d_links, d_configs, n, fp_tau, d_lambda2, d_region,
                                     stream))
+
+
+def gc_server_create(workers: int = 8, mem_budget_bytes: int = 0, opt: gc_options | None = None):
+    h = ctypes.c_void_p()
+    _check(load().gc_server_create(workers, mem_budget_bytes, None if opt is None else ctypes.byref(opt),
+                                   ctypes.byref(h)))
+    return h
+
+
+def gc_server_submit(server, dim: int, L: int, link_angles, orbit_id: int, n_starts: int,
+                     omega: float = 1.7, eps: float = 1e-24) -> int:
+    phi = np.ascontiguousarray(link_angles, dtype=np.float64)
+    t = ctypes.c_uint64()
+    _check(load().gc_server_submit(server, dim, L, _ptr(phi, ctypes.c_double), orbit_id, n_starts,
+                                   omega, eps, ctypes.byref(t)))
+    return t.value
+
+
+def gc_server_wait(server, ticket: int, timeout_s: float = -1.0, keep_orbit: bool = True):
+    """Returns (status, latency_s, orbit or None)."""
+    st = ctypes.c_int()
+    lat = ctypes.c_double()
+    orb = ctypes.c_void_p()
+    _check(load().gc_server_wait(server, ticket, timeout_s, ctypes.byref(st), ctypes.byref(lat),
+                                 ctypes.byref(orb) if keep_orbit else None))
+    return st.value, lat.value, (orb if orb.value else None)
+
+
+def gc_server_destroy(server):
+    _check(load().gc_server_destroy(server))

@@ -128,6 +128,7 @@ struct gc_orbit_s {
   std::vector<cudaEvent_t> ev_pool;      // timing events of enqueued batches (5 per batch)
   size_t ev_used = 0;
   bool err_unchecked = false;
+  cudaStream_t last_stream = nullptr;    // stream of the orbit's most recent work
   int last_precision = GC_FP64;
   cudaEvent_t ev[8] = {};
 
@@ -383,7 +384,8 @@ int gc_create_orbit(int dim, int L, const double* link_angles, uint64_t orbit_id
     for (auto& e : o->ev)
       if (cudaEventCreate(&e) != cudaSuccess) { rc = fail(GC_ECUDA, "cudaEventCreate failed"); break; }
   }
-  if (rc == GC_OK && cudaDeviceSynchronize() != cudaSuccess) rc = fail(GC_ECUDA, "orbit set-up: %s", cudaGetErrorString(cudaGetLastError()));
+  if (rc == GC_OK && cudaStreamSynchronize(nullptr) != cudaSuccess)
+    rc = fail(GC_ECUDA, "orbit set-up: %s", cudaGetErrorString(cudaGetLastError()));
   if (rc != GC_OK) {
     gc_destroy_orbit(o);
     return rc;
@@ -394,7 +396,7 @@ int gc_create_orbit(int dim, int L, const double* link_angles, uint64_t orbit_id
 
 int gc_destroy_orbit(gc_orbit o) {
   if (!o) return fail(GC_EINVAL, "gc_destroy_orbit: NULL orbit");
-  cudaDeviceSynchronize();
+  cudaStreamSynchronize(o->last_stream);
   cudaStream_t s = nullptr;
   for (Buf* b : {&o->links64, &o->links32, &o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_count,
                  &o->t_next, &o->t_lam, &o->t_region, &o->t_head, &o->t_lock, &o->t_f8, &o->t_counters,
@@ -554,6 +556,7 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
   unsigned long long* stats = o->stats.as<unsigned long long>();
   if (!o->err_unchecked) GC_CUDA(cudaMemsetAsync(o->err(), 0, 16, s));
   o->err_unchecked = true;
+  o->last_stream = s;
 
   for (uint64_t done = 0; done < n_starts;) {
     const long long b = (long long)std::min<uint64_t>(B, n_starts - done);
@@ -796,7 +799,7 @@ struct Meta {
 };
 
 int read_meta(gc_orbit o, Meta& m, unsigned* n_out) {
-  GC_CUDA(cudaDeviceSynchronize());
+  GC_CUDA(cudaStreamSynchronize(o->last_stream));
   harvest_timing(o);
   if (int rc = check_errors(o)) return rc;
   unsigned n = 0;
@@ -842,14 +845,15 @@ int gc_fetch_copies(gc_orbit o, size_t capacity, size_t* n_distinct, double* F, 
     if (region) region[i] = m.region[e];
   }
   if (theta && k) {
-    if (!o->theta_tmp.ensure((size_t)n * V * 8, nullptr)) return fail(GC_ENOMEM, "cannot admit fetch buffer");
+    if (!o->theta_tmp.ensure((size_t)n * V * 8, o->last_stream)) return fail(GC_ENOMEM, "cannot admit fetch buffer");
     const size_t tot = (size_t)n * V;
     const int blocks = (int)std::min<size_t>((tot + 255) / 256, 8192);
-    gc::angles_kernel<<<blocks, 256>>>(o->t_cfg.as<double2>(), o->theta_tmp.as<double>(), tot);
+    gc::angles_kernel<<<blocks, 256, 0, o->last_stream>>>(o->t_cfg.as<double2>(), o->theta_tmp.as<double>(), tot);
     ++o->launches;
     GC_CUDA(cudaGetLastError());
     std::vector<double> all(tot);
-    GC_CUDA(cudaMemcpy(all.data(), o->theta_tmp.p, tot * 8, cudaMemcpyDeviceToHost));
+    GC_CUDA(cudaMemcpyAsync(all.data(), o->theta_tmp.p, tot * 8, cudaMemcpyDeviceToHost, o->last_stream));
+    GC_CUDA(cudaStreamSynchronize(o->last_stream));
     for (size_t i = 0; i < k; ++i) std::memcpy(theta + i * V, all.data() + (size_t)m.order[i] * V, V * 8);
   }
   return GC_OK;
@@ -887,7 +891,7 @@ int gc_fetch_starts(gc_orbit o, uint64_t first, uint64_t n, int* status, int* sw
 int gc_orbit_stats(gc_orbit o, gc_stats* out) {
   if (!o || !out) return fail(GC_EINVAL, "gc_orbit_stats: NULL argument");
   std::memset(out, 0, sizeof *out);
-  GC_CUDA(cudaDeviceSynchronize());
+  GC_CUDA(cudaStreamSynchronize(o->last_stream));
   harvest_timing(o);
   unsigned long long st[kNumStats] = {};
   GC_CUDA(cudaMemcpy(st, o->stats.p, sizeof st, cudaMemcpyDeviceToHost));
@@ -1249,5 +1253,204 @@ extern "C" int gc_autotune(gc_orbit o, int precision, int* r_warps, int* p_warps
   if (r_warps) *r_warps = t.r_warps;
   if (p_warps) *p_warps = t.p_warps;
   if (f_warps) *f_warps = t.f_warps;
+  return GC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving: continuous batching of enumeration requests
+// ---------------------------------------------------------------------------
+// Requests (an orbit and a start count) queue in arrival order.  Worker
+// threads, each with its own stream, take the head request whenever the
+// device-memory budget admits it, so requests that arrive while others run
+// start as soon as resources free up and their kernels overlap on the GPU.
+// A request's state (links, copy table, staging) lives on the device for its
+// whole life; its result is the orbit itself, handed to the caller.  Results
+// do not depend on the mix: a request touches only its own orbit object, and
+// every kernel's per-start arithmetic and the dedup outcome are independent of
+// what else runs.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <thread>
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t ticket = 0;
+  int dim = 0, L = 0;
+  std::vector<double> phi;
+  uint64_t orbit_id = 0, n = 0;
+  double omega = 1.7, eps = 1e-24;
+  size_t bytes = 0;            // admitted device memory estimate
+  Clock::time_point submitted, finished;
+  int status = GC_OK;
+  std::string message;
+  bool done = false;
+  gc_orbit orbit = nullptr;
+};
+
+// Device bytes a request holds while it runs: links, a copy pool sized for
+// min(n, 65536) copies (it grows on demand), the quantised-minimum set,
+// buckets and one staging batch.
+size_t request_bytes(int dim, int L, uint64_t n, int precision) {
+  const double V = std::pow((double)L, dim);
+  const double cap = (double)std::min<uint64_t>(n, 65536);
+  const double per_copy = V * 16 + 64 + 4 * 8 + 2 * 4;
+  const double per_start = V * 16 + (precision == GC_MIXED ? V * 8 : 0) + 48;
+  const double batch = std::min((double)n, std::max(4096.0, (double)(1ull << 30) / per_start));
+  return (size_t)(V * dim * 24 + cap * per_copy + batch * per_start + (1 << 20));
+}
+
+}  // namespace
+
+struct gc_server_s {
+  gc_options opt{};
+  size_t budget = 0, in_use = 0;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<Request>> queue;
+  std::map<uint64_t, std::shared_ptr<Request>> all;
+  uint64_t next_ticket = 1;
+  bool stopping = false;
+  std::vector<std::thread> workers;
+  std::vector<cudaStream_t> streams;
+
+  void worker(int k) {
+    cudaSetDevice(device);
+    for (;;) {
+      std::shared_ptr<Request> r;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_work.wait(lk, [&] {
+          return stopping || (!queue.empty() && in_use + queue.front()->bytes <= budget);
+        });
+        if (stopping && queue.empty()) return;
+        if (queue.empty() || in_use + queue.front()->bytes > budget) continue;
+        r = queue.front();
+        queue.pop_front();
+        in_use += r->bytes;
+      }
+      cv_work.notify_all();
+      gc_options o = opt;
+      o.stream = streams[k];
+      o.keep_per_start = 0;
+      gc_orbit orb = nullptr;
+      int rc = gc_create_orbit(r->dim, r->L, r->phi.data(), r->orbit_id, 0, &orb);
+      if (rc == GC_OK) rc = gc_enumerate_copies(orb, r->n, r->omega, r->eps, &o);
+      std::string msg = rc == GC_OK ? "" : gc_last_error();
+      if (orb) {
+        // keep the results (copy table), release the staging of the batches
+        for (Buf* b : {&orb->s_status, &orb->s_sweeps, &orb->s_resid, &orb->s_F, &orb->s_fprint,
+                       &orb->s_config, &orb->s_state32, &orb->s_copy})
+          b->release(streams[k]);
+        cudaStreamSynchronize(streams[k]);
+      }
+      if (rc != GC_OK && orb) {
+        gc_destroy_orbit(orb);
+        orb = nullptr;
+      }
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        r->status = rc;
+        r->message = msg;
+        r->orbit = orb;
+        r->finished = Clock::now();
+        r->done = true;
+        in_use -= r->bytes;
+      }
+      cv_done.notify_all();
+      cv_work.notify_all();
+    }
+  }
+};
+
+extern "C" int gc_server_create(int workers, size_t mem_budget_bytes, const gc_options* opt, gc_server* out) {
+  if (!out) return fail(GC_EINVAL, "gc_server_create: out is NULL");
+  *out = nullptr;
+  if (workers < 1 || workers > 64) return fail(GC_EINVAL, "workers = %d not in 1..64", workers);
+  gc_server s = new (std::nothrow) gc_server_s;
+  if (!s) return fail(GC_ENOMEM, "host allocation failed");
+  if (opt) s->opt = *opt; else gc_options_default(&s->opt);
+  if (int rc = validate_options(s->opt, 1.0, 1.0)) { delete s; return rc; }
+  if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return fail(GC_ECUDA, "no CUDA device"); }
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  s->budget = mem_budget_bytes ? mem_budget_bytes : free_b / 2;
+  s->streams.resize(workers);
+  for (int k = 0; k < workers; ++k)
+    if (cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) != cudaSuccess) {
+      for (int j = 0; j < k; ++j) cudaStreamDestroy(s->streams[j]);
+      delete s;
+      return fail(GC_ECUDA, "cudaStreamCreate failed");
+    }
+  for (int k = 0; k < workers; ++k) s->workers.emplace_back(&gc_server_s::worker, s, k);
+  *out = s;
+  return GC_OK;
+}
+
+extern "C" int gc_server_submit(gc_server s, int dim, int L, const double* link_angles, uint64_t orbit_id,
+                                uint64_t n_starts, double omega, double eps, uint64_t* ticket) {
+  if (!s || !link_angles || !ticket) return fail(GC_EINVAL, "gc_server_submit: NULL argument");
+  if (dim < 1 || dim > gc::kMaxDim || L < 2) return fail(GC_EINVAL, "bad lattice %d^%d", L, dim);
+  if (!(omega > 0.0 && omega < 2.0) || !(eps > 0.0)) return fail(GC_EINVAL, "bad omega or eps");
+  const double Vd = std::pow((double)L, dim);
+  if (Vd > gc::kMaxSites) return fail(GC_EINVAL, "lattice of %.0f sites exceeds %d", Vd, gc::kMaxSites);
+  auto r = std::make_shared<Request>();
+  r->dim = dim; r->L = L; r->orbit_id = orbit_id; r->n = n_starts; r->omega = omega; r->eps = eps;
+  r->phi.assign(link_angles, link_angles + (size_t)Vd * dim);
+  r->bytes = request_bytes(dim, L, n_starts, s->opt.precision);
+  if (r->bytes > s->budget)
+    return fail(GC_ENOMEM, "request needs ~%.1f MiB, above the %.1f MiB budget", r->bytes / 1048576.0,
+                s->budget / 1048576.0);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stopping) return fail(GC_ESTATE, "server is shutting down");
+    r->ticket = s->next_ticket++;
+    r->submitted = Clock::now();
+    s->queue.push_back(r);
+    s->all[r->ticket] = r;
+    *ticket = r->ticket;
+  }
+  s->cv_work.notify_all();
+  return GC_OK;
+}
+
+extern "C" int gc_server_wait(gc_server s, uint64_t ticket, double timeout_s, int* status, double* latency_s,
+                              gc_orbit* orbit) {
+  if (!s) return fail(GC_EINVAL, "gc_server_wait: NULL server");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return fail(GC_EINVAL, "unknown or already collected ticket %llu", (unsigned long long)ticket);
+  std::shared_ptr<Request> r = it->second;
+  const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                           std::chrono::duration<double>(timeout_s < 0 ? 1e9 : timeout_s));
+  if (!s->cv_done.wait_until(lk, deadline, [&] { return r->done; }))
+    return fail(GC_ETIMEDOUT, "request %llu not finished within %g s", (unsigned long long)ticket, timeout_s);
+  if (status) *status = r->status;
+  if (latency_s) *latency_s = std::chrono::duration<double>(r->finished - r->submitted).count();
+  if (orbit) *orbit = r->orbit;
+  else if (r->orbit) gc_destroy_orbit(r->orbit);
+  r->orbit = nullptr;
+  s->all.erase(it);
+  if (r->status != GC_OK) g_err = r->message;
+  return GC_OK;
+}
+
+extern "C" int gc_server_destroy(gc_server s) {
+  if (!s) return fail(GC_EINVAL, "gc_server_destroy: NULL server");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stopping = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& t : s->workers) t.join();
+  for (auto& kv : s->all)
+    if (kv.second->orbit) gc_destroy_orbit(kv.second->orbit);
+  for (auto st : s->streams) cudaStreamDestroy(st);
+  delete s;
   return GC_OK;
 }

@@ -149,30 +149,42 @@ __global__ void __launch_bounds__(256) dedup_kernel(const DedupArgs a) {
     bool locked = false;
     unsigned l0 = 0, l1 = 0, l2 = 0;
     if (e < 0) {
-      // slow path: hold the three F-neighbour locks (ascending, distinct), search again, insert
+      // slow path: take the three F-neighbour locks (ascending, distinct) with
+      // non-blocking tries; between tries search again without locks, so that
+      // starts waiting on a copy another warp is inserting take the hit path as
+      // soon as it is published instead of queueing on the lock
       unsigned tmp;
       l0 = lock_of(T, q - 1); l1 = lock_of(T, q); l2 = lock_of(T, q + 1);
       if (l0 > l1) { tmp = l0; l0 = l1; l1 = tmp; }
       if (l1 > l2) { tmp = l1; l1 = l2; l2 = tmp; }
       if (l0 > l1) { tmp = l0; l0 = l1; l1 = tmp; }
-      int ok = 1;
-      if (lane == 0) {
-        const bool got0 = acquire(&T.lock[l0]);
-        const bool got1 = got0 && (l1 == l0 || acquire(&T.lock[l1]));
-        const bool got2 = got1 && (l2 == l1 || acquire(&T.lock[l2]));
-        ok = got2;
-        if (!ok) {
-          if (got1 && l1 != l0) release(&T.lock[l1]);
-          if (got0) release(&T.lock[l0]);
-          atomicExch(&T.err[0], 1);
+      int ok = 0;
+      unsigned ns = 64;
+      for (long long tries = 0; tries < kLockSpins; ++tries) {
+        if (lane == 0) {
+          ok = atomicCAS(&T.lock[l0], 0, 1) == 0;
+          if (ok && l1 != l0 && atomicCAS(&T.lock[l1], 0, 1) != 0) { atomicExch(&T.lock[l0], 0); ok = 0; }
+          if (ok && l2 != l1 && atomicCAS(&T.lock[l2], 0, 1) != 0) {
+            if (l1 != l0) atomicExch(&T.lock[l1], 0);
+            atomicExch(&T.lock[l0], 0);
+            ok = 0;
+          }
+          if (ok) __threadfence();
         }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (ok) break;
+        __nanosleep(ns);
+        if (ns < 2048) ns <<= 1;
+        e = table_search(T, q, t, F, mine, V, lane);
+        if (e >= 0) break;
       }
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) {
-        if (lane == 0) { a.status[i] = kDedupFailed; a.copy_of[i] = -1; }
+      if (!ok && e < 0) {
+        if (lane == 0) { atomicExch(&T.err[0], 1); a.status[i] = kDedupFailed; a.copy_of[i] = -1; }
         ++c_fail;
         continue;
       }
+    }
+    if (e < 0) {
       locked = true;
       __syncwarp();
       e = table_search(T, q, t, F, mine, V, lane);

@@ -1,0 +1,66 @@
+"""Serving with continuous batching: requests admitted while others run give the
+same result as when run alone; admission and waits are bounded."""
+import time
+
+import numpy as np
+import pytest
+
+import orbit_inputs as oi
+from gpu_helpers import run_gpu
+
+pytestmark = pytest.mark.gpu
+
+MIX = [(2, 4, 3000), (2, 8, 5000), (3, 4, 4000), (3, 5, 2000), (4, 3, 3000), (4, 4, 6000),
+       (3, 6, 2000), (2, 6, 8000), (4, 4, 2000), (2, 12, 1000), (3, 8, 2000), (4, 5, 1000)]
+
+
+def test_each_result_same_alone_and_in_the_mix():
+    import paper_1403_0555_b300 as gb
+    opt = gb.gc_options_default(precision=1, check_every=4)
+    srv = gb.gc_server_create(4, 0, opt)
+    tickets = []
+    rng = np.random.default_rng(3)
+    try:
+        for i, (d, L, n) in enumerate(MIX):
+            phi = oi.von_mises_orbit(d, L, 1.0, 50 + i)
+            tickets.append((gb.gc_server_submit(srv, d, L, phi, 50 + i, n), d, L, n, phi, i))
+            time.sleep(rng.exponential(0.002))         # arrivals while others run
+        lat = []
+        for t, d, L, n, phi, i in tickets:
+            status, latency, orb = gb.gc_server_wait(srv, t, 120.0)
+            assert status == gb.GC_OK and orb is not None
+            lat.append(latency)
+            mixed = gb.gc_fetch_copies(orb, L ** d)
+            mst = gb.gc_orbit_stats(orb)
+            gb.gc_destroy_orbit(orb)
+            _, alone, ast = run_gpu(d, L, phi, 50 + i, n, keep_per_start=0, precision=1, check_every=4)
+            assert mixed["n_distinct"] == alone["n_distinct"]
+            for k in ("F", "first_start", "count", "region", "lambda2", "theta"):
+                assert np.array_equal(mixed[k], alone[k]), (d, L, k)
+            assert mst["n_converged"] == ast["n_converged"]
+        assert all(x > 0 for x in lat)
+    finally:
+        gb.gc_server_destroy(srv)
+
+
+def test_budget_and_bounded_wait():
+    import paper_1403_0555_b300 as gb
+    srv = gb.gc_server_create(2, 2 << 30, gb.gc_options_default(precision=1, check_every=4))
+    try:
+        big = oi.von_mises_orbit(4, 6, 1.0, 1)
+        with pytest.raises(gb.GribovError) as e:
+            gb.gc_server_submit(srv, 4, 6, big, 1, 1_000_000)
+        assert e.value.code == gb.GC_ENOMEM
+        phi = oi.von_mises_orbit(4, 4, 1.0, 2)
+        t = gb.gc_server_submit(srv, 4, 4, phi, 2, 200_000)
+        with pytest.raises(gb.GribovError) as e:
+            gb.gc_server_wait(srv, t, 1e-5)
+        assert e.value.code == gb.GC_ETIMEDOUT
+        status, latency, orb = gb.gc_server_wait(srv, t, 120.0)
+        assert status == gb.GC_OK and latency > 0
+        assert gb.gc_orbit_stats(orb)["n_converged"] == 200_000
+        gb.gc_destroy_orbit(orb)
+        with pytest.raises(gb.GribovError):
+            gb.gc_server_wait(srv, t, 1.0)          # ticket retired
+    finally:
+        gb.gc_server_destroy(srv)
