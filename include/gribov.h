@@ -106,6 +106,7 @@ typedef struct {
   uint64_t fp_tests, fp_tests_fp64, lanczos_steps;
   double ms_relax, ms_polish, ms_dedup, ms_fptest; /* device ms, all calls      */
   uint64_t kernel_launches;      /* kernels the library launched for this orbit */
+  uint64_t df_residual_passes;   /* double-float residual passes of the polish   */
 } gc_stats;
 
 /* Device memory hooks (e.g. a framework's caching allocator).  alloc returns
@@ -152,9 +153,10 @@ int gc_enumerate_batch(gc_orbit* orbits, int n_orbits, const uint64_t* n_starts,
                        double eps, const gc_options* opt);
 
 /* Autotuner: picks warps per CTA of the relaxation, polish and FP-test
- * kernels for o's (d, L) and precision from three pilot runs on a throw-away
- * copy of the orbit; cached per process and used by every later call.  The
- * knobs do not change results. */
+ * kernels for o's (d, L) and precision from four pilot runs on a throw-away
+ * copy of the orbit; cached per process and used by every later call.  A
+ * value is a cap on warps per CTA (16: no cap, the largest shape that fits).
+ * The knobs do not change results. */
 int gc_autotune(gc_orbit o, int precision, int* r_warps, int* p_warps, int* f_warps);
 
 /* Serving with continuous batching.  Requests (an orbit and a start count)

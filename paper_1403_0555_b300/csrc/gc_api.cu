@@ -94,7 +94,7 @@ enum StatSlot {
   kSweeps = 0, kUpdates = 1, kConv = 2, kNConv = 3, kNewton = 4, kFallback = 5, kUpd64 = 6,
   kPass = 7, kPConv = 8, kPNConv = 9, kNew = 10, kHit = 11, kDFail = 12, kTests = 13,
   kTests64 = 14, kLanczos = 15, kSweeps32 = 16, kUpdates32 = 17, kConv32 = 18, kNConv32 = 19, kInner = 20, kUpd32Fallback = 21,
-  kNumStats = 24
+  kPassDF = 22, kNumStats = 24
 };
 
 struct gc_orbit_s {
@@ -107,8 +107,8 @@ struct gc_orbit_s {
   // copy table
   unsigned cap = 0, nb = 0, nl = 0, f8cap = 0;
   Buf t_cfg, t_F, t_q, t_t, t_first, t_count, t_next, t_lam, t_region, t_head, t_lock, t_f8;
-  Buf t_counters;    // n_entries, n_new (u32) | n_f8 (u64) | err[4] (i32)
-  Buf t_newlist;
+  Buf t_counters;    // n_entries, n_new (u32) | n_f8 (u64) | err[4] (i32) | n_redo (u32)
+  Buf t_newlist;     // new entries of a batch [cap], then those left to FP64 [cap]
   // batch staging
   Buf s_status, s_sweeps, s_resid, s_F, s_fprint, s_config, s_state32, s_copy;
   Buf work, stats, scratch, theta_tmp;
@@ -136,6 +136,7 @@ struct gc_orbit_s {
   unsigned* n_new() const { return t_counters.as<unsigned>() + 1; }
   unsigned long long* n_f8() const { return reinterpret_cast<unsigned long long*>(t_counters.as<char>() + 8); }
   int* err() const { return reinterpret_cast<int*>(t_counters.as<char>() + 16); }
+  unsigned* n_redo() const { return reinterpret_cast<unsigned*>(t_counters.as<char>() + 32); }
 
   gc::TableView view() const {
     gc::TableView T{};
@@ -206,7 +207,7 @@ int table_reserve(gc_orbit o, unsigned long long need, unsigned cur, cudaStream_
             count.ensure(ncap * 8ull, s) && next.ensure(ncap * 4ull, s) && lam.ensure(ncap * 8ull, s) &&
             region.ensure(ncap * 4ull, s);
   Buf newlist;
-  ok = ok && newlist.ensure(ncap * 4ull, s);
+  ok = ok && newlist.ensure(ncap * 8ull, s);
   const unsigned nnb = next_pow2(2ull * ncap);
   Buf head;
   ok = ok && head.ensure(nnb * 4ull, s);
@@ -251,6 +252,24 @@ int table_reserve(gc_orbit o, unsigned long long need, unsigned cur, cudaStream_
   }
   GC_CUDA(cudaGetLastError());
   return GC_OK;
+}
+
+using FpKernel = void (*)(const gc::FpArgs);
+FpKernel fp_test_for(int d) {
+  switch (d) {
+    case 1: return gc::fp_test_kernel<1>;
+    case 2: return gc::fp_test_kernel<2>;
+    case 3: return gc::fp_test_kernel<3>;
+    default: return gc::fp_test_kernel<4>;
+  }
+}
+FpKernel fp_screen_for(int d) {
+  switch (d) {
+    case 1: return gc::fp_screen_kernel<1>;
+    case 2: return gc::fp_screen_kernel<2>;
+    case 3: return gc::fp_screen_kernel<3>;
+    default: return gc::fp_screen_kernel<4>;
+  }
 }
 
 int team_size(const gc::Geom& G) {
@@ -523,27 +542,47 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
   if (!r_warps) return fail(GC_EINVAL, "relaxation does not fit shared memory");
   if (tune.r_warps > 0 && tune.r_warps < r_warps) r_warps = tune.r_warps;
   const size_t r_smem = relax_bytes(r_warps, site_bytes);
+  // polish: the most warps per SM, over two CTAs (links held twice) or one CTA
+  // of up to 16 warps, with or without the FP64 links in shared memory (ties:
+  // with them)
+  bool u64_smem = true;
   auto polish_bytes = [&](int warps) {
-    return gc::Smem(V, d, sizeof(double2), gc::polish_team_bytes(V, d), warps * tpw).total;
+    return gc::Smem(V, d, gc::polish_link_bytes(u64_smem), gc::polish_team_bytes(V, d), warps * tpw).total;
   };
-  // two CTAs per SM when that fits: the polish is latency bound at low occupancy
-  int p_warps = mixed ? fit_warps(8, [&](int w) { return 2 * polish_bytes(w) + 2048; }) : 0;
-  if (mixed && !p_warps) p_warps = fit_warps(8, polish_bytes);
+  auto polish_shape = [&](int* per_sm) {
+    const int p2 = fit_warps(8, [&](int w) { return 2 * polish_bytes(w) + 2048; });
+    const int p1 = fit_warps(16, polish_bytes);
+    *per_sm = std::max(2 * p2, p1);
+    return 2 * p2 >= p1 ? p2 : p1;
+  };
+  int p_warps = 0;
+  if (mixed) {
+    int per_sm_s = 0, per_sm_g = 0;
+    const int ws = polish_shape(&per_sm_s);
+    u64_smem = false;
+    const int wg = polish_shape(&per_sm_g);
+    u64_smem = per_sm_s >= per_sm_g && ws > 0;
+    p_warps = u64_smem ? ws : wg;
+  }
   if (mixed && !p_warps) return fail(GC_EINVAL, "polish does not fit shared memory");
   if (mixed && tune.p_warps > 0 && tune.p_warps < p_warps) p_warps = tune.p_warps;
   const size_t p_smem = mixed ? polish_bytes(p_warps) : 0;
   const int kmax64 = std::min(opt.lanczos_k, std::max(1, V - 1));
   const int kmax32 = std::min(160, kmax64);
-  const int kmax_sm = std::max(kmax64, kmax32);
-  int f_warps = fit_warps(4, [&](int w) { return gc::FpSmem(V, d, kmax_sm, w).total; });
+  const FpKernel fp64_kern = fp_test_for(d), fp32_kern = fp_screen_for(d);
+  int f_warps = fit_warps(4, [&](int w) { return gc::FpSmem<double>(V, d, kmax64, w).total; });
   if (!f_warps) return fail(GC_EINVAL, "Faddeev-Popov test does not fit shared memory");
   if (tune.f_warps > 0 && tune.f_warps < f_warps) f_warps = tune.f_warps;
-  const size_t f_smem = gc::FpSmem(V, d, kmax_sm, f_warps).total;
+  const size_t f_smem = gc::FpSmem<double>(V, d, kmax64, f_warps).total;
+  // the FP32 screen: twice the FP64 kernel's warps per CTA where they fit
+  int s_warps = fit_warps(2 * f_warps, [&](int w) { return gc::FpSmem<float>(V, d, kmax32, w).total; });
+  if (!s_warps) return fail(GC_EINVAL, "Faddeev-Popov screen does not fit shared memory");
+  const size_t s_smem = gc::FpSmem<float>(V, d, kmax32, s_warps).total;
 
   // dense-mode Lanczos bases: one V x V slot per warp, sized for the largest batch
   int dense_grid = 0;
   if (opt.fp_mode == GC_FP_DENSE) {
-    if (int rc = launch_grid(gc::fp_test_kernel, f_warps * 32, f_smem, f_warps, (long long)B, &dense_grid)) return rc;
+    if (int rc = launch_grid(fp64_kern, f_warps * 32, f_smem, f_warps, (long long)B, &dense_grid)) return rc;
     const size_t slot = (size_t)V * V * 8;
     const size_t max_slots = std::max<size_t>(1, (1ull << 30) / slot);
     dense_grid = (int)std::min<size_t>(dense_grid, std::max<size_t>(1, max_slots / f_warps));
@@ -586,6 +625,7 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     }
     GC_CUDA(cudaMemsetAsync(wctr, 0, 16, s));
     GC_CUDA(cudaMemsetAsync(o->n_new(), 0, 4, s));
+    GC_CUDA(cudaMemsetAsync(o->n_redo(), 0, 4, s));
 
     // relaxation
     gc::RelaxArgs ra{};
@@ -669,12 +709,13 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       pa.om1 = 1.0 - omega;
       pa.eps = eps;
       pa.omega_in = (float)omega;
-      pa.lin_tol = 4e-5f;
+      pa.lin_tol = 4e-4f;
       pa.inner_max = opt.newton_inner;
       pa.newton_max = opt.newton_max;
       pa.max_sweeps = max_sweeps;
       pa.check_every = opt.check_every;
       pa.team = T;
+      pa.u64_smem = u64_smem ? 1 : 0;
       pa.status = ra.status;
       pa.sweeps = ra.sweeps;
       pa.resid = ra.resid;
@@ -734,11 +775,14 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       fa.links32 = ra.links32;
       fa.list = o->t_newlist.as<unsigned>();
       fa.n_list = o->n_new();
+      fa.redo = o->t_newlist.as<unsigned>() + o->cap;
+      fa.n_redo = o->n_redo();
       fa.lambda2 = o->t_lam.as<double>();
       fa.region = o->t_region.as<int>();
       fa.mode = opt.fp_mode;
       fa.kmax32 = kmax32;
       fa.kmax64 = kmax64;
+      fa.count_tests = 1;
       fa.tau = opt.fp_tau;
       fa.margin32 = 1e-3;
       fa.tol32 = 1e-5;
@@ -746,12 +790,24 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       fa.seed = opt.seed;
       fa.stats = stats;
       int fgrid = 0;
-      if (int rc = launch_grid(gc::fp_test_kernel, f_warps * 32, f_smem, f_warps, b, &fgrid)) return rc;
+      if (opt.fp_mode == GC_FP_AUTO) {
+        // FP32 screen of every new copy, then FP64 Lanczos for those it leaves
+        int sgrid = 0;
+        if (int rc = launch_grid(fp32_kern, s_warps * 32, s_smem, s_warps, b, &sgrid)) return rc;
+        fp32_kern<<<sgrid, s_warps * 32, s_smem, s>>>(fa);
+        ++o->launches;
+        GC_CUDA(cudaGetLastError());
+        fa.list = fa.redo;
+        fa.n_list = fa.n_redo;
+        fa.mode = gc::kFpLanczos;
+        fa.count_tests = 0;
+      }
+      if (int rc = launch_grid(fp64_kern, f_warps * 32, f_smem, f_warps, b, &fgrid)) return rc;
       if (opt.fp_mode == GC_FP_DENSE) {
         fgrid = std::min(fgrid, dense_grid);
         fa.scratch = o->scratch.as<double>();
       }
-      gc::fp_test_kernel<<<fgrid, f_warps * 32, f_smem, s>>>(fa);
+      fp64_kern<<<fgrid, f_warps * 32, f_smem, s>>>(fa);
       ++o->launches;
       GC_CUDA(cudaGetLastError());
     }
@@ -930,6 +986,7 @@ int gc_orbit_stats(gc_orbit o, gc_stats* out) {
   out->ms_dedup = o->ms[2];
   out->ms_fptest = o->ms[3];
   out->kernel_launches = o->launches;
+  out->df_residual_passes = st[kPassDF];
   return GC_OK;
 }
 
@@ -1047,14 +1104,15 @@ extern "C" int gc_fp_test_static(int dim, int L, const double* d_links, const do
   G.pos_last = G.color_off[gc::site_color(V - 1, d, L) + 1] - 1;
 
   const int kmax64 = std::max(1, V - 1);
-  const int f_warps = fit_warps(4, [&](int w) { return gc::FpSmem(V, d, kmax64, w).total; });
+  const FpKernel fkern = fp_test_for(d);
+  const int f_warps = fit_warps(4, [&](int w) { return gc::FpSmem<double>(V, d, kmax64, w).total; });
   if (!f_warps) return fail(GC_EINVAL, "Faddeev-Popov test does not fit shared memory");
-  const size_t f_smem = gc::FpSmem(V, d, kmax64, f_warps).total;
+  const size_t f_smem = gc::FpSmem<double>(V, d, kmax64, f_warps).total;
   int fgrid = 0;
-  if (int rc = launch_grid(gc::fp_test_kernel, f_warps * 32, f_smem, f_warps, (long long)n, &fgrid)) return rc;
+  if (int rc = launch_grid(fkern, f_warps * 32, f_smem, f_warps, (long long)n, &fgrid)) return rc;
   fgrid = (int)std::max(1u, std::min<unsigned>((unsigned)fgrid, lay.slots / (unsigned)f_warps));
   const int fwarps_used = lay.slots < (unsigned)f_warps ? (int)lay.slots : f_warps;
-  const size_t fsm = gc::FpSmem(V, d, kmax64, fwarps_used).total;
+  const size_t fsm = gc::FpSmem<double>(V, d, kmax64, fwarps_used).total;
 
   static_fp_setup_kernel<<<64, 256, 0, st>>>(s, lay, (unsigned)n, reinterpret_cast<const double2*>(d_links), V * d);
   GC_CUDA(cudaGetLastError());
@@ -1072,6 +1130,7 @@ extern "C" int gc_fp_test_static(int dim, int L, const double* d_links, const do
   fa.mode = gc::kFpDense;
   fa.kmax32 = std::min(160, kmax64);
   fa.kmax64 = kmax64;
+  fa.count_tests = 1;
   fa.tau = fp_tau;
   fa.margin32 = 1e-3;
   fa.tol32 = 1e-5;
@@ -1079,7 +1138,7 @@ extern "C" int gc_fp_test_static(int dim, int L, const double* d_links, const do
   fa.scratch = reinterpret_cast<double*>(s + lay.q0);
   fa.seed = 1;
   fa.stats = reinterpret_cast<unsigned long long*>(s + lay.stats);
-  gc::fp_test_kernel<<<fgrid, fwarps_used * 32, fsm, st>>>(fa);
+  fkern<<<fgrid, fwarps_used * 32, fsm, st>>>(fa);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
 }
@@ -1133,11 +1192,12 @@ int autotune_shape(gc_orbit like, const gc_options& base, double omega, double e
   opt.use_graph = 0;
   opt.stream = nullptr;
   const uint64_t pilot = std::max<uint64_t>(2048, 262144 / (uint64_t)like->V * 4);
-  const int cand[3][3] = {{2, 2, 1}, {4, 4, 2}, {8, 8, 4}};
+  // caps on warps per CTA; 16 leaves the largest shape that fits
+  const int cand[4][3] = {{2, 2, 1}, {4, 4, 2}, {8, 8, 4}, {8, 16, 4}};
   double best[3] = {1e300, 1e300, 1e300};
   Tuning t;
   int rc = GC_OK;
-  for (int c = 0; c < 3 && rc == GC_OK; ++c) {
+  for (int c = 0; c < 4 && rc == GC_OK; ++c) {
     Tuning cand_t;
     cand_t.r_warps = cand[c][0];
     cand_t.p_warps = cand[c][1];

@@ -298,21 +298,23 @@ __global__ void __launch_bounds__(256) relax_kernel(const RelaxArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// FP64 polish of FP32-relaxed starts (mixed path)
+// Polish of FP32-relaxed starts (mixed path)
 // ---------------------------------------------------------------------------
-// Inexact Newton with FP32 inner solves (mixed-precision iterative refinement):
-//   0. once: link weights w = cos(phi^theta) in FP32 from the FP32 state;
-//   1. FP64: S_x and div_x = Im[conj(g_x) S_x]; stop if max div^2 < eps;
-//   2. FP32: solve M delta = div (M = the Faddeev-Popov Laplacian with weights
-//      w, the Hessian of Eq. 3) by checkerboard SOR until the correction
-//      stalls below lin_tol;
-//   3. FP64: g_x <- g_x exp(i delta_x)   (theta <- theta + delta).
-// The residual and the state stay FP64; only the correction is FP32, so each
-// Newton step shrinks the FP64 residual by the inner solve's relative accuracy
-// (stale FP32 weights only make the steps inexact).  If Newton stalls (an
-// indefinite M near a saddle), the start falls back to FP64 relaxation sweeps.
-// FP64 work per site and Newton step: 8d DFMA for S, 3 for the divergence,
-// 9 for the rotation; every float<->double move uses the integer pipe.
+// Inexact Newton on the gauge angles.  The Jacobian is the Faddeev-Popov
+// operator M, the Hessian of Eq. 3 (a lattice Laplacian with weights
+// cos(phi^theta)):
+//   1. div_x = Im[conj(g_x) S_x] in double-float arithmetic (about 48
+//      significant bits, 1e-13 absolute for d = 4); stop below eps / 4;
+//   2. FP32: weights w from the state's high parts, then checkerboard SOR on
+//      M delta = div until the correction stalls below lin_tol;
+//   3. double-float rotation g_x <- g_x exp(i delta_x), back to |g_x| = 1.
+// One FP64 pass over the FP64 image of the final state then gives the
+// residual that decides convergence (max_x div^2 < eps), the functional
+// (Eq. 3), the fingerprint and the canonical copy together.  That pass is the
+// only FP64 work of a typical start: on this part the FP64 pipe has about
+// 1/64 of the FP32 rate.  Starts the double-float Newton cannot finish (a
+// near-singular or indefinite M) get FP64 Newton rounds, FP32 relaxation
+// sweeps and, last, FP64 relaxation sweeps, all out of line.
 struct PolishArgs {
   Geom geom;
   const double2* links64;
@@ -324,6 +326,7 @@ struct PolishArgs {
                                  // max|t - delta| <= lin_tol max|b / D|
   int inner_max, newton_max, max_sweeps, check_every;
   int team;
+  int u64_smem;                  // FP64 links also in shared memory (else read from links64)
   int8_t* status;                // in: FP32 phase outcome; out: final outcome
   int32_t* sweeps;               // in: FP32 sweeps; out: + FP64 fallback sweeps
   double* resid;
@@ -331,302 +334,576 @@ struct PolishArgs {
   double* F;
   double* fprint;
   double2* config;
-  unsigned long long* stats;     // [4] newton steps, [5] fallbacks, [6] fp64 fallback site
+  unsigned long long* stats;     // [4] newton steps, [5] fallbacks, [6] fp64 relaxation site
                                  // updates, [7] fp64 residual passes, [8] / [9] final
                                  // converged / not converged, [20] inner FP32 SOR sweeps,
-                                 // [21] FP32 relaxation site updates of the fallback
+                                 // [21] FP32 relaxation site updates of the fallback,
+                                 // [22] double-float residual passes
 };
 
-// per team: g (FP64), w (FP32, [mu][p]), b, delta, 1/D (FP32)
+// per team: g (16 B per site: double-float float4 or FP64 double2), w (FP32,
+// [mu][p]), b, delta, 1/D (FP32)
 __host__ __device__ inline size_t polish_team_bytes(int V, int d) {
   return align16((size_t)V * sizeof(double2)) + align16((size_t)V * d * sizeof(float)) +
          3 * align16((size_t)V * sizeof(float));
 }
+// per CTA and link: the double-float copy [mu][p], preceded by the FP64 (cos, sin)
+// [mu][p] when those fit too
+__host__ __device__ inline size_t polish_link_bytes(bool u64_smem) {
+  return sizeof(float4) + (u64_smem ? sizeof(double2) : 0);
+}
+
+// FP64 links of the polish: colour-major in shared memory, or site-major in
+// global memory through the position -> site table (large lattices)
+struct Links64 {
+  const double2* cm;     // [mu][p] shared, or nullptr
+  const double2* sm;     // [x d + mu] global
+  const uint16_t* site;
+  int V, d;
+  __device__ __forceinline__ double2 operator()(int mu, int p) const {
+    return cm ? cm[mu * V + p] : __ldg(sm + (size_t)site[p] * d + mu);
+  }
+};
+
+// ---- double-float arithmetic -------------------------------------------------
+// A value is the unevaluated sum hi + lo of two floats (Dekker 1971).  A site
+// of a double-float state is the float4 (x_hi, y_hi, x_lo, y_lo).  two_sum is
+// Knuth's error-free sum; an FMA gives the exact error of a product.  The _rn
+// intrinsics keep the compiler from contracting or reassociating these steps.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (sh, sl) += (ah + al)(bh + bl), the al * bl term dropped
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float& sh,
+                                       float& sl) {
+  const float p = __fmul_rn(ah, bh);
+  const float c = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, __fmaf_rn(ah, bh, -p)));
+  float s, t;
+  two_sum(sh, p, s, t);
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(t, c));
+}
+
+// div_x = Im[conj(g_x) S_x] of a double-float state
+template <int DD>
+__device__ __forceinline__ float df_divergence(const float4* __restrict__ ud,
+                                               const float4* __restrict__ gd, const uint4 nb,
+                                               int p, int V) {
+  float sxh = 0.f, sxl = 0.f, syh = 0.f, syl = 0.f;
+#pragma unroll
+  for (int mu = 0; mu < DD; ++mu) {
+    const unsigned wd = nb_word(nb, mu);
+    const int xp = wd & 0xffffu, xm = wd >> 16;
+    const float4 a = ud[mu * V + p], h = gd[xp];      // u_{x,mu} g_{x+mu}
+    df_mac(a.x, a.z, h.x, h.z, sxh, sxl);
+    df_mac(-a.y, -a.w, h.y, h.w, sxh, sxl);
+    df_mac(a.x, a.z, h.y, h.w, syh, syl);
+    df_mac(a.y, a.w, h.x, h.z, syh, syl);
+    const float4 b = ud[mu * V + xm], k = gd[xm];     // conj(u_{x-mu,mu}) g_{x-mu}
+    df_mac(b.x, b.z, k.x, k.z, sxh, sxl);
+    df_mac(b.y, b.w, k.y, k.w, sxh, sxl);
+    df_mac(b.x, b.z, k.y, k.w, syh, syl);
+    df_mac(-b.y, -b.w, k.x, k.z, syh, syl);
+  }
+  const float4 gx = gd[p];
+  float dh = 0.f, dl = 0.f;
+  df_mac(gx.x, gx.z, syh, syl, dh, dl);
+  df_mac(-gx.y, -gx.w, sxh, sxl, dh, dl);
+  return __fadd_rn(dh, dl);
+}
+
+// (x, y) / |(x, y)| for a double-float pair with |(x, y)|^2 = 1 + eta, |eta| < 1e-6
+__device__ __forceinline__ float4 df_unit(float xh, float xl, float yh, float yl) {
+  const float px = __fmul_rn(xh, xh), py = __fmul_rn(yh, yh);
+  const float ex = __fmaf_rn(xh, xh, -px), ey = __fmaf_rn(yh, yh, -py);
+  float s, e;
+  two_sum(px, py, s, e);
+  // s - 1 is exact for s in [0.5, 2]
+  const float rest = __fadd_rn(__fadd_rn(ex, ey),
+                               __fmaf_rn(2.f * xh, xl, __fmaf_rn(2.f * yh, yl, e)));
+  const float eta = __fadd_rn(__fsub_rn(s, 1.f), rest);
+  const float q = __fmul_rn(eta, __fmaf_rn(0.375f, eta, -0.5f));  // (1 + eta)^(-1/2) - 1
+  float4 r;
+  two_sum(xh, __fmaf_rn(xh, q, xl), r.x, r.z);
+  two_sum(yh, __fmaf_rn(yh, q, yl), r.y, r.w);
+  return r;
+}
+
+// g exp(i t) in double-float, back to |g| = 1 (|t| <= 0.2).  The FP32 factor's
+// rounding (about 1e-7 of t) is removed by the next Newton round.
+__device__ __forceinline__ float4 df_rotate(const float4 g, float t) {
+  const float t2 = t * t;
+  const float cm = t2 * fmaf(t2, fmaf(t2, -1.f / 720.f, 1.f / 24.f), -0.5f);  // cos t - 1
+  const float sn = t * fmaf(t2, fmaf(t2, 1.f / 120.f, -1.f / 6.f), 1.f);      // sin t
+  const float cx = fmaf(g.x, cm, -g.y * sn), cy = fmaf(g.x, sn, g.y * cm);
+  float xh, xe, yh, ye;
+  two_sum(g.x, cx, xh, xe);
+  two_sum(g.y, cy, yh, ye);
+  return df_unit(xh, __fadd_rn(g.z, xe), yh, __fadd_rn(g.w, ye));
+}
+
+// FP64 image of a double-float state, in place (the same 16 bytes per site)
+__device__ __forceinline__ void df_to_fp64(unsigned char* slot, int tl, int T, int V) {
+  const float4* gd = reinterpret_cast<const float4*>(slot);
+  double2* g = reinterpret_cast<double2*>(slot);
+  for (int p = tl; p < V; p += T) {
+    const float4 v = gd[p];
+    g[p] = make_double2(f2d_bits(v.x) + f2d_bits(v.z), f2d_bits(v.y) + f2d_bits(v.w));
+  }
+}
+
+// One FP64 pass over an FP64 state in colour-position order: returns the
+// team's max_x div(x)^2 and writes record i: the functional (Eq. 3) as
+// sum_x [d - Re(conj(g_x) S+_x)] with S+ the forward half of the staple, the
+// fingerprint cos(phi^theta) of link (site 0, mu 0) and the canonical copy
+// g'_x = g_x conj(g_{V-1}) in site order.
+template <int DD>
+__device__ __forceinline__ double final_pass64(const Links64& u,
+                                               const double2* __restrict__ g, const uint4* nbp,
+                                               const uint16_t* site, const Geom& G, int tl, int T,
+                                               unsigned mask, long long i, double2* config,
+                                               double* Fout, double* fprint) {
+  const int V = G.V;
+  const double2 gc = g[G.pos_last];
+  double r = 0.0, Fp = 0.0;
+  for (int p = tl; p < V; p += T) {
+    const uint4 nb = nbp[p];
+    double fx = 0.0, fy = 0.0, bx = 0.0, by = 0.0;
+#pragma unroll
+    for (int mu = 0; mu < DD; ++mu) {
+      const unsigned wd = nb_word(nb, mu);
+      const int xp = wd & 0xffffu, xm = wd >> 16;
+      const double2 a = u(mu, p), h = g[xp];
+      fx = fma(a.x, h.x, fx); fx = fma(-a.y, h.y, fx);
+      fy = fma(a.x, h.y, fy); fy = fma(a.y, h.x, fy);
+      const double2 b = u(mu, xm), k = g[xm];
+      bx = fma(b.x, k.x, bx); bx = fma(b.y, k.y, bx);
+      by = fma(b.x, k.y, by); by = fma(-b.y, k.x, by);
+    }
+    const double2 gx = g[p];
+    const double dv = fma(gx.x, fy + by, -gx.y * (fx + bx));
+    r = dmax_pos(r, dv * dv);
+    Fp += (double)DD - fma(gx.x, fx, gx.y * fy);
+    config[(size_t)i * V + site[p]] =
+        make_double2(fma(gx.x, gc.x, gx.y * gc.y), fma(gx.y, gc.x, -gx.x * gc.y));
+    if (p == 0) {   // site 0 sits at position 0
+      const double2 a = u(0, 0), h = g[nb.x & 0xffffu];
+      const double tx = fma(a.x, h.x, -a.y * h.y), ty = fma(a.x, h.y, a.y * h.x);
+      fprint[i] = fma(gx.x, tx, gx.y * ty);
+    }
+  }
+  for (int o = T >> 1; o > 0; o >>= 1) r = dmax_pos(r, __shfl_xor_sync(mask, r, o));
+  Fp = team_sum(Fp, T, mask);
+  if (tl == 0) Fout[i] = Fp;
+  return r;
+}
 
 // S_x with DFMA chains (4 per complex term)
-__device__ __forceinline__ double2 staple_dfma(const double2* __restrict__ u,
-                                               const double2* __restrict__ g, const uint4 nb, int p,
-                                               int d, int V) {
+__device__ __forceinline__ double2 staple_dfma(const Links64& u, const double2* __restrict__ g,
+                                               const uint4 nb, int p, int d) {
   double sx = 0.0, sy = 0.0;
   for (int mu = 0; mu < d; ++mu) {
     const unsigned wd = nb_word(nb, mu);
     const int xp = wd & 0xffffu, xm = wd >> 16;
-    const double2 a = u[mu * V + p], h = g[xp];
+    const double2 a = u(mu, p), h = g[xp];
     sx = fma(a.x, h.x, sx); sx = fma(-a.y, h.y, sx);
     sy = fma(a.x, h.y, sy); sy = fma(a.y, h.x, sy);
-    const double2 b = u[mu * V + xm], k = g[xm];
+    const double2 b = u(mu, xm), k = g[xm];
     sx = fma(b.x, k.x, sx); sx = fma(b.y, k.y, sx);
     sy = fma(b.x, k.y, sy); sy = fma(-b.y, k.x, sy);
   }
   return make_double2(sx, sy);
 }
 
+// Per-team shared-memory views of the polish
+struct PolishTeam {
+  unsigned char* slot;   // g: double-float float4 or FP64 double2 per position
+  float *w, *b, *dl, *Dinv;
+  int tl, T;
+  unsigned mask;
+};
+
+// FP32 link weights w = cos(phi^theta) of the state given by (x, y) per
+// position (high parts of a double-float state, or an FP32 state) and 1/D;
+// returns max |b / D| over the team
+template <class GET>
+__device__ __forceinline__ float newton_weights(const PolishTeam& t, const float4* ud,
+                                                const uint4* nbp, int d, int V, GET gxy) {
+  for (int p = t.tl; p < V; p += t.T) {
+    const float2 gx = gxy(p);
+    const uint4 nb = nbp[p];
+    for (int mu = 0; mu < d; ++mu) {
+      const float2 h = gxy(nb_word(nb, mu) & 0xffffu);
+      const float4 a = ud[mu * V + p];
+      const float tx = fmaf(a.x, h.x, -a.y * h.y), ty = fmaf(a.x, h.y, a.y * h.x);
+      t.w[mu * V + p] = fmaf(gx.x, tx, gx.y * ty);
+    }
+    t.dl[p] = 0.f;
+  }
+  __syncwarp(t.mask);
+  float bd = 0.f;
+  for (int p = t.tl; p < V; p += t.T) {
+    const uint4 nb = nbp[p];
+    float D = 0.f;
+    for (int mu = 0; mu < d; ++mu) D += t.w[mu * V + p] + t.w[mu * V + (nb_word(nb, mu) >> 16)];
+    const float di = D > 1e-6f ? __frcp_rn(D) : 0.f;
+    t.Dinv[p] = di;
+    bd = fmaxf(bd, fabsf(t.b[p] * di));
+  }
+  bd = team_max(bd, t.T, t.mask);
+  __syncwarp(t.mask);
+  return bd;
+}
+
+// FP32 checkerboard SOR on M delta = b until the corrections stall; returns sweeps
+__device__ __forceinline__ int newton_solve(const PolishTeam& t, const uint4* nbp, const Geom& G,
+                                            int d, float om, float lin_tol, float bd, int cap) {
+  const int V = G.V;
+  const float om1 = 1.f - om;
+  int k = 0;
+  while (k < cap) {
+    float corr = 0.f;
+    for (int kk = 0; kk < 8; ++kk, ++k) {
+      for (int c = 0; c < G.ncolor; ++c) {
+        const int beg = G.color_off[c], end = G.color_off[c + 1];
+        for (int p = beg + t.tl; p < end; p += t.T) {
+          const uint4 nb = nbp[p];
+          float acc = t.b[p];
+          for (int mu = 0; mu < d; ++mu) {
+            const unsigned wd = nb_word(nb, mu);
+            const int xp = wd & 0xffffu, xm = wd >> 16;
+            acc = fmaf(t.w[mu * V + p], t.dl[xp], acc);
+            acc = fmaf(t.w[mu * V + xm], t.dl[xm], acc);
+          }
+          const float tt = acc * t.Dinv[p], old = t.dl[p];
+          if (kk == 7) corr = fmaxf(corr, fabsf(tt - old));
+          t.dl[p] = fmaf(om, tt, om1 * old);
+        }
+        __syncwarp(t.mask);
+      }
+    }
+    corr = team_max(corr, t.T, t.mask);
+    if (corr <= lin_tol * bd) break;
+  }
+  return k;
+}
+
+struct NewtonOut {
+  double r;
+  int steps, passes, inner;
+  bool conv;
+};
+
+// Rare path: FP64 Newton rounds on an FP64 state (FP64 residual, FP32 inner
+// solve, FP64 rotation).  Stops when max div^2 < eps, after newton_max steps,
+// or when the residual rises (M not positive definite here).
 template <int DD>
-__global__ void __launch_bounds__(256) polish_kernel(const PolishArgs a) {
+__device__ __noinline__ NewtonOut fp64_newton(const PolishTeam t, const Links64 u,
+                                              const float4* ud, const uint4* nbp, const Geom G,
+                                              double eps, int newton_max, int inner_max,
+                                              float om_in, float lin_tol) {
+  constexpr int d = DD;
+  const int V = G.V;
+  double2* g = reinterpret_cast<double2*>(t.slot);
+  NewtonOut o{0.0, 0, 0, 0, false};
+  double r_prev = 1e300;
+  int inner_cap = inner_max;
+  for (int it = 0;; ++it) {
+    double r = 0.0;
+    for (int p = t.tl; p < V; p += t.T) {
+      const double2 S = staple_dfma(u, g, nbp[p], p, d);
+      const double2 gx = g[p];
+      const double dv = fma(gx.x, S.y, -gx.y * S.x);
+      t.b[p] = d2f_bits(dv);
+      r = dmax_pos(r, dv * dv);
+    }
+    ++o.passes;
+    for (int k = t.T >> 1; k > 0; k >>= 1) r = dmax_pos(r, __shfl_xor_sync(t.mask, r, k));
+    o.r = r;
+    if (dless_pos(r, eps)) { o.conv = true; break; }
+    if (it >= newton_max) break;
+    if (it > 0 && !dless_pos(r, r_prev)) break;
+    if (!dless_pos(r, 0.25 * r_prev)) inner_cap = min(4 * inner_cap, 8192);
+    r_prev = r;
+    ++o.steps;
+    const float bd = newton_weights(t, ud, nbp, d, V, [&](int q) {
+      const double2 v = g[q];
+      return make_float2(d2f_bits(v.x), d2f_bits(v.y));
+    });
+    o.inner += newton_solve(t, nbp, G, d, om_in, lin_tol, bd, inner_cap);
+    for (int p = t.tl; p < V; p += t.T) {
+      const float tf = fminf(fmaxf(t.dl[p], -0.2f), 0.2f);
+      const double tt = f2d_bits(tf);
+      const double t2 = tt * tt;
+      double c = 1.0 - t2 * (0.5 - t2 * (1.0 / 24.0 - t2 * (1.0 / 720.0)));
+      double sn = tt * (1.0 - t2 * (1.0 / 6.0 - t2 * (1.0 / 120.0 - t2 * (1.0 / 5040.0))));
+      const double q2 = rsqrt(c * c + sn * sn);
+      c *= q2; sn *= q2;
+      const double2 gx = g[p];
+      g[p] = make_double2(fma(gx.x, c, -gx.y * sn), fma(gx.x, sn, gx.y * c));
+    }
+    __syncwarp(t.mask);
+  }
+  return o;
+}
+
+// Rare path: FP32 relaxation sweeps from an FP64 state (a descent method: it
+// moves a start that Newton could not finish, e.g. one near a saddle, towards
+// its minimum).  The FP32 lattice lives in w (V d floats >= 2V for d >= 2).
+// A fixed budget: the residual may rise for a while, so only the FP32 floor
+// (max div^2 ~ 1e-11) ends it early.  Returns the sweeps done.
+template <int DD>
+__device__ __noinline__ int relax32_fallback(const PolishTeam t, const float4* ud,
+                                             const uint4* nbp, const Geom G, float om, float om1,
+                                             int cap) {
+  constexpr int d = DD;
+  const int V = G.V;
+  const double2* g = reinterpret_cast<const double2*>(t.slot);
+  float2* g32 = reinterpret_cast<float2*>(t.w);
+  for (int p = t.tl; p < V; p += t.T) g32[p] = make_float2(d2f_bits(g[p].x), d2f_bits(g[p].y));
+  __syncwarp(t.mask);
+  auto staple32 = [&](int p) {
+    const uint4 nb = nbp[p];
+    float sx = 0.f, sy = 0.f;
+    for (int mu = 0; mu < d; ++mu) {
+      const unsigned wd = nb_word(nb, mu);
+      const int xp = wd & 0xffffu, xm = wd >> 16;
+      const float4 aa = ud[mu * V + p], bb = ud[mu * V + xm];
+      const float2 h = g32[xp], k = g32[xm];
+      sx = fmaf(aa.x, h.x, sx); sx = fmaf(-aa.y, h.y, sx);
+      sy = fmaf(aa.x, h.y, sy); sy = fmaf(aa.y, h.x, sy);
+      sx = fmaf(bb.x, k.x, sx); sx = fmaf(bb.y, k.y, sx);
+      sy = fmaf(bb.x, k.y, sy); sy = fmaf(-bb.y, k.x, sy);
+    }
+    return make_float2(sx, sy);
+  };
+  int sweeps = 0;
+  for (int sw = 0; sw < cap; ++sw) {
+    for (int c = 0; c < G.ncolor; ++c) {
+      const int beg = G.color_off[c], end = G.color_off[c + 1];
+      for (int p = beg + t.tl; p < end; p += t.T) {
+        const float2 S = staple32(p);
+        const float n2 = fmaf(S.x, S.x, S.y * S.y);
+        if (!(n2 > 0.f)) continue;
+        const float rr = rsqrtf(n2) * om;
+        const float2 gx = g32[p];
+        const float vx = fmaf(S.x, rr, om1 * gx.x), vy = fmaf(S.y, rr, om1 * gx.y);
+        const float q = rsqrtf(fmaf(vx, vx, vy * vy));
+        g32[p] = make_float2(vx * q, vy * q);
+      }
+      __syncwarp(t.mask);
+    }
+    ++sweeps;
+    if (sw % 16 == 15) {
+      float r32 = 0.f;
+      for (int p = t.tl; p < V; p += t.T) {
+        const float2 S = staple32(p), gx = g32[p];
+        const float dv = fmaf(gx.x, S.y, -gx.y * S.x);
+        r32 = fmaxf(r32, dv * dv);
+      }
+      r32 = team_max(r32, t.T, t.mask);
+      if (r32 < 1e-11f) break;
+    }
+  }
+  return sweeps;
+}
+
+struct RelaxOut {
+  double r;
+  int sweeps;
+  bool conv;
+};
+
+// Last resort: FP64 relaxation sweeps on an FP64 state until max div^2 < eps
+template <int DD>
+__device__ __noinline__ RelaxOut relax64_last_resort(const PolishTeam t, const Links64 u,
+                                                     const uint4* nbp, const Geom G, double om,
+                                                     double om1, double eps, int max_sweeps,
+                                                     int check_every) {
+  constexpr int d = DD;
+  const int V = G.V;
+  double2* g = reinterpret_cast<double2*>(t.slot);
+  RelaxOut o{0.0, 0, false};
+  while (o.sweeps < max_sweeps) {
+    for (int c = 0; c < G.ncolor; ++c) {
+      const int beg = G.color_off[c], end = G.color_off[c + 1];
+      for (int p = beg + t.tl; p < end; p += t.T) {
+        const double2 S = staple_dfma(u, g, nbp[p], p, d);
+        const double n2 = S.x * S.x + S.y * S.y;
+        if (!(n2 > 0.0)) continue;
+        const double rr = om * rsqrt(n2);
+        const double2 gx = g[p];
+        const double vx = fma(S.x, rr, om1 * gx.x), vy = fma(S.y, rr, om1 * gx.y);
+        const double q2 = rsqrt(vx * vx + vy * vy);
+        g[p] = make_double2(vx * q2, vy * q2);
+      }
+      __syncwarp(t.mask);
+    }
+    ++o.sweeps;
+    if (o.sweeps % check_every == 0) {
+      double r = 0.0;
+      for (int p = t.tl; p < V; p += t.T) {
+        const double2 S = staple_dfma(u, g, nbp[p], p, d);
+        const double2 gx = g[p];
+        const double dv = fma(gx.x, S.y, -gx.y * S.x);
+        r = dmax_pos(r, dv * dv);
+      }
+      for (int k = t.T >> 1; k > 0; k >>= 1) r = dmax_pos(r, __shfl_xor_sync(t.mask, r, k));
+      o.r = r;
+      if (dless_pos(r, eps)) { o.conv = true; break; }
+    }
+  }
+  return o;
+}
+
+template <int DD>
+__global__ void __launch_bounds__(512, 1) polish_kernel(const PolishArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Geom G = a.geom;
   constexpr int d = DD;
   const int V = G.V, T = a.team;
   const int teams_per_warp = 32 / T, warps = blockDim.x >> 5;
-  const Smem lay(V, d, sizeof(double2), polish_team_bytes(V, d), warps * teams_per_warp);
-  double2* u = reinterpret_cast<double2*>(smem + lay.links);
+  const Smem lay(V, d, polish_link_bytes(a.u64_smem), polish_team_bytes(V, d),
+                 warps * teams_per_warp);
+  double2* u64s = a.u64_smem ? reinterpret_cast<double2*>(smem + lay.links) : nullptr;
+  float4* ud = reinterpret_cast<float4*>(smem + lay.links +
+                                         (a.u64_smem ? (size_t)V * d * sizeof(double2) : 0));
   uint4* nbp = reinterpret_cast<uint4*>(smem + lay.nbp);
   uint16_t* site = reinterpret_cast<uint16_t*>(smem + lay.site);
   build_colour_geometry(G, site, nbp, reinterpret_cast<uint16_t*>(smem + lay.pos));
-  load_links(u, a.links64, site, V, d);
+  if (u64s) load_links(u64s, a.links64, site, V, d);
+  for (int k = threadIdx.x; k < V * d; k += blockDim.x) {   // double-float split, once per CTA
+    const int mu = k / V, p = k - mu * V;
+    const double2 v = a.links64[(size_t)site[p] * d + mu];
+    const float xh = __double2float_rn(v.x), yh = __double2float_rn(v.y);
+    ud[k] = make_float4(xh, yh, __double2float_rn(v.x - (double)xh),
+                        __double2float_rn(v.y - (double)yh));
+  }
   __syncthreads();
+  const Links64 u{u64s, a.links64, site, V, d};
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tw = lane / T, tl = lane & (T - 1);
-  const unsigned tmask = team_mask(T, tw);
-  unsigned char* base = smem + lay.team0 + (size_t)(warp * teams_per_warp + tw) * lay.per_team;
-  double2* g = reinterpret_cast<double2*>(base);
-  float* w = reinterpret_cast<float*>(base + align16((size_t)V * sizeof(double2)));
-  float* b = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(w) + align16((size_t)V * d * sizeof(float)));
-  float* dl = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(b) + align16((size_t)V * sizeof(float)));
-  float* Dinv = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(dl) + align16((size_t)V * sizeof(float)));
+  PolishTeam t;
+  t.mask = team_mask(T, tw);
+  t.tl = tl;
+  t.T = T;
+  t.slot = smem + lay.team0 + (size_t)(warp * teams_per_warp + tw) * lay.per_team;
+  t.w = reinterpret_cast<float*>(t.slot + align16((size_t)V * sizeof(double2)));
+  t.b = t.w + align16((size_t)V * d * sizeof(float)) / sizeof(float);
+  t.dl = t.b + align16((size_t)V * sizeof(float)) / sizeof(float);
+  t.Dinv = t.dl + align16((size_t)V * sizeof(float)) / sizeof(float);
+  float4* gd = reinterpret_cast<float4*>(t.slot);
+  const double2* g64 = reinterpret_cast<const double2*>(t.slot);
+  // double-float Newton runs while eps / 4 is above its noise floor (|div| ~ 1e-13)
+  const bool use_df = a.eps >= 1e-25;
+  const float eps_df = (float)(0.25 * a.eps);
 
-  unsigned long long c_newton = 0, c_fallback = 0, c_upd64 = 0, c_pass = 0, c_conv = 0, c_nconv = 0;
-  unsigned long long c_inner = 0, c_upd32 = 0;
-  // Teams are independent here (no lock step needed): each loops over starts.
+  unsigned long long c_newton = 0, c_fallback = 0, c_upd64 = 0, c_pass = 0, c_conv = 0,
+                     c_nconv = 0, c_inner = 0, c_upd32 = 0, c_df = 0;
   for (;;) {
     long long idx = 0;
     if (tl == 0) idx = (long long)atomicAdd(a.work_ctr, 1ULL);
-    idx = __shfl_sync(tmask, idx, tw * T);
+    idx = __shfl_sync(t.mask, idx, tw * T);
     if (idx >= a.n) break;
     const int8_t st32 = a.status[idx];
     const float2* s32 = a.state32 + (size_t)idx * V;
-    // promote: exact float -> double, then renormalise with two Newton steps
-    // for 1/sqrt (|g32| = 1 to FP32 precision)
     for (int p = tl; p < V; p += T) {
-      const float2 gx = s32[p];
-      const double px = f2d_bits(gx.x), py = f2d_bits(gx.y);
-      const double n2 = fma(px, px, py * py);
-      double q = fma(-0.5, n2, 1.5);
-      q = q * fma(-0.5 * n2, q * q, 1.5);
-      g[p] = make_double2(px * q, py * q);
+      const float2 v = s32[p];
+      gd[p] = df_unit(v.x, 0.f, v.y, 0.f);
     }
-    __syncwarp(tmask);
-    bool conv = false;
+    __syncwarp(t.mask);
+    bool conv = false, written = false;
     double r = 0.0;
     int extra_sweeps = 0;
-    int relax32_sweeps = 0;
     if (st32 == kConverged) {
-      // up to two Newton rounds; between them, FP32 relaxation sweeps from the
-      // current state (a descent method, cheap) move a start that Newton could
-      // not finish (near-singular or indefinite Hessian) closer to its minimum
       for (int round = 0; round < 2 && !conv; ++round) {
         if (round == 1) {
-          if (d < 2) break;  // the FP32 scratch lattice reuses w (V d floats >= 2V)
+          if (d < 2) break;
           ++c_fallback;
-          float2* g32 = reinterpret_cast<float2*>(w);
-          for (int p = tl; p < V; p += T) g32[p] = make_float2(d2f_bits(g[p].x), d2f_bits(g[p].y));
-          __syncwarp(tmask);
-          const float om = (float)a.omega, om1 = (float)a.om1;
-          // A fixed budget of FP32 sweeps: the residual may rise for a while
-          // (a start leaving the neighbourhood of a saddle), so only reaching
-          // the FP32 floor (~1e-11 for max div^2) ends it early.
           const int cap32 = a.max_sweeps < 2048 ? a.max_sweeps : 2048;
-          for (int sw = 0; sw < cap32; ++sw) {
-            for (int c = 0; c < G.ncolor; ++c) {
-              const int beg = G.color_off[c], end = G.color_off[c + 1];
-              for (int p = beg + tl; p < end; p += T) {
-                const uint4 nb = nbp[p];
-                float sx = 0.f, sy = 0.f;
-                for (int mu = 0; mu < d; ++mu) {
-                  const unsigned wd = nb_word(nb, mu);
-                  const int xp = wd & 0xffffu, xm = wd >> 16;
-                  const float2 aa = a.links32[site[p] * d + mu], h = g32[xp];
-                  sx = fmaf(aa.x, h.x, sx); sx = fmaf(-aa.y, h.y, sx);
-                  sy = fmaf(aa.x, h.y, sy); sy = fmaf(aa.y, h.x, sy);
-                  const float2 bb = a.links32[site[xm] * d + mu], k = g32[xm];
-                  sx = fmaf(bb.x, k.x, sx); sx = fmaf(bb.y, k.y, sx);
-                  sy = fmaf(bb.x, k.y, sy); sy = fmaf(-bb.y, k.x, sy);
-                }
-                const float n2 = fmaf(sx, sx, sy * sy);
-                if (!(n2 > 0.f)) continue;
-                const float rr = rsqrtf(n2) * om;
-                const float2 gx = g32[p];
-                const float vx = fmaf(sx, rr, om1 * gx.x), vy = fmaf(sy, rr, om1 * gx.y);
-                const float q = rsqrtf(fmaf(vx, vx, vy * vy));
-                g32[p] = make_float2(vx * q, vy * q);
-              }
-              __syncwarp(tmask);
-            }
-            ++relax32_sweeps;
-            if (sw % 16 == 15) {
-              // FP32 residual; stop near the FP32 floor
-              float r32 = 0.f;
-              for (int p = tl; p < V; p += T) {
-                const uint4 nb = nbp[p];
-                float sx = 0.f, sy = 0.f;
-                for (int mu = 0; mu < d; ++mu) {
-                  const unsigned wd = nb_word(nb, mu);
-                  const int xp = wd & 0xffffu, xm = wd >> 16;
-                  const float2 aa = a.links32[site[p] * d + mu], h = g32[xp];
-                  sx = fmaf(aa.x, h.x, sx); sx = fmaf(-aa.y, h.y, sx);
-                  sy = fmaf(aa.x, h.y, sy); sy = fmaf(aa.y, h.x, sy);
-                  const float2 bb = a.links32[site[xm] * d + mu], k = g32[xm];
-                  sx = fmaf(bb.x, k.x, sx); sx = fmaf(bb.y, k.y, sx);
-                  sy = fmaf(bb.x, k.y, sy); sy = fmaf(-bb.y, k.x, sy);
-                }
-                const float2 gx = g32[p];
-                const float dv = fmaf(gx.x, sy, -gx.y * sx);
-                r32 = fmaxf(r32, dv * dv);
-              }
-              r32 = team_max(r32, T, tmask);
-              if (r32 < 1e-11f) break;
-            }
-          }
+          const int sw = relax32_fallback<DD>(t, ud, nbp, G, (float)a.omega, (float)a.om1, cap32);
+          c_upd32 += (unsigned long long)sw * V;
+          const float2* g32 = reinterpret_cast<const float2*>(t.w);
           for (int p = tl; p < V; p += T) {
-            const float2 gx = g32[p];
-            const double px = f2d_bits(gx.x), py = f2d_bits(gx.y);
-            const double n2 = fma(px, px, py * py);
-            double q = fma(-0.5, n2, 1.5);
-            q = q * fma(-0.5 * n2, q * q, 1.5);
-            g[p] = make_double2(px * q, py * q);
+            const float2 v = g32[p];
+            gd[p] = df_unit(v.x, 0.f, v.y, 0.f);
           }
-          __syncwarp(tmask);
+          __syncwarp(t.mask);
         }
-        double r_prev = 1e300;
-        int inner_cap = a.inner_max;
-        for (int it = 0;; ++it) {
-          // (1) FP64 divergence; the FP32 copy feeds the inner solve
-          r = 0.0;
-          for (int p = tl; p < V; p += T) {
-            const double2 S = staple_dfma(u, g, nbp[p], p, d, V);
-            const double2 gx = g[p];
-            const double dv = fma(gx.x, S.y, -gx.y * S.x);
-            b[p] = d2f_bits(dv);
-            r = dmax_pos(r, dv * dv);
-          }
-          ++c_pass;
-          for (int o = T >> 1; o > 0; o >>= 1) r = dmax_pos(r, __shfl_xor_sync(tmask, r, o));
-          if (dless_pos(r, a.eps)) { conv = true; break; }
-          if (it >= a.newton_max) break;
-          if (it > 0 && !dless_pos(r, r_prev)) break;   // rising: Hessian not positive here
-          if (!dless_pos(r, 0.25 * r_prev)) inner_cap = min(4 * inner_cap, 8192);  // poor step
-          r_prev = r;
-          ++c_newton;
-          // (2) Jacobian (FP32 link weights of the current state) and 1/D
-          for (int p = tl; p < V; p += T) {
-            const double2 gx = g[p];
-            const float gxx = d2f_bits(gx.x), gxy = d2f_bits(gx.y);
-            const uint4 nb = nbp[p];
-            for (int mu = 0; mu < d; ++mu) {
-              const double2 hd = g[nb_word(nb, mu) & 0xffffu];
-              const float hx = d2f_bits(hd.x), hy = d2f_bits(hd.y);
-              const double2 ud = u[mu * V + p];
-              const float ux = d2f_bits(ud.x), uy = d2f_bits(ud.y);
-              const float tx = fmaf(ux, hx, -uy * hy), ty = fmaf(ux, hy, uy * hx);
-              w[mu * V + p] = fmaf(gxx, tx, gxy * ty);
+        if (use_df) {
+          float r_prev = 3.4e38f;
+          int inner_cap = a.inner_max;
+          for (int it = 0;; ++it) {
+            // (1) double-float divergence; its FP32 rounding feeds the inner solve
+            float rf = 0.f;
+            for (int p = tl; p < V; p += T) {
+              const float dv = df_divergence<DD>(ud, gd, nbp[p], p, V);
+              t.b[p] = dv;
+              rf = fmaxf(rf, dv * dv);
             }
-            dl[p] = 0.f;
+            ++c_df;
+            rf = team_max(rf, T, t.mask);
+            if (rf < eps_df) break;
+            if (it >= a.newton_max) break;
+            if (it > 0 && !(rf < r_prev)) break;   // rising: M not positive definite here
+            if (!(rf < 0.25f * r_prev)) inner_cap = min(4 * inner_cap, 8192);  // poor step
+            r_prev = rf;
+            ++c_newton;
+            // (2) Jacobian weights from the high parts, (3) FP32 SOR solve
+            const float bd = newton_weights(t, ud, nbp, d, V, [&](int q) {
+              const float4 v = gd[q];
+              return make_float2(v.x, v.y);
+            });
+            c_inner += (unsigned long long)newton_solve(t, nbp, G, d, a.omega_in, a.lin_tol, bd,
+                                                        inner_cap);
+            // (4) g_x <- g_x exp(i delta_x), |delta| capped at 0.2
+            for (int p = tl; p < V; p += T)
+              gd[p] = df_rotate(gd[p], fminf(fmaxf(t.dl[p], -0.2f), 0.2f));
+            __syncwarp(t.mask);
           }
-          __syncwarp(tmask);
-          float bd = 0.f;
-          for (int p = tl; p < V; p += T) {
-            const uint4 nb = nbp[p];
-            float D = 0.f;
-            for (int mu = 0; mu < d; ++mu) D += w[mu * V + p] + w[mu * V + (nb_word(nb, mu) >> 16)];
-            const float di = D > 1e-6f ? __frcp_rn(D) : 0.f;
-            Dinv[p] = di;
-            bd = fmaxf(bd, fabsf(b[p] * di));
-          }
-          bd = team_max(bd, T, tmask);
-          __syncwarp(tmask);
-          // (3) FP32 SOR on M delta = div until the corrections stall
-          const float om = a.omega_in, om1 = 1.f - a.omega_in;
-          int k = 0;
-          while (k < inner_cap) {
-            float corr = 0.f;
-            for (int kk = 0; kk < 8; ++kk, ++k) {
-              for (int c = 0; c < G.ncolor; ++c) {
-                const int beg = G.color_off[c], end = G.color_off[c + 1];
-                for (int p = beg + tl; p < end; p += T) {
-                  const uint4 nb = nbp[p];
-                  float acc = b[p];
-                  for (int mu = 0; mu < d; ++mu) {
-                    const unsigned wd = nb_word(nb, mu);
-                    const int xp = wd & 0xffffu, xm = wd >> 16;
-                    acc = fmaf(w[mu * V + p], dl[xp], acc);
-                    acc = fmaf(w[mu * V + xm], dl[xm], acc);
-                  }
-                  const float t = acc * Dinv[p], old = dl[p];
-                  if (kk == 7) corr = fmaxf(corr, fabsf(t - old));
-                  dl[p] = fmaf(om, t, om1 * old);
-                }
-                __syncwarp(tmask);
-              }
-            }
-            corr = team_max(corr, T, tmask);
-            if (corr <= a.lin_tol * bd) break;
-          }
-          c_inner += (unsigned long long)k;
-          // (4) FP64 rotation g_x <- g_x exp(i delta_x), |delta| capped at 0.2
-          for (int p = tl; p < V; p += T) {
-            const float tf = fminf(fmaxf(dl[p], -0.2f), 0.2f);
-            const double t = f2d_bits(tf);
-            const double t2 = t * t;
-            double c, sn;
-            if (fabsf(tf) < 1e-3f) {
-              c = fma(t2, fma(t2, 1.0 / 24.0, -0.5), 1.0);
-              sn = t * fma(t2, -1.0 / 6.0, 1.0);
-            } else {
-              c = 1.0 - t2 * (0.5 - t2 * (1.0 / 24.0 - t2 * (1.0 / 720.0)));
-              sn = t * (1.0 - t2 * (1.0 / 6.0 - t2 * (1.0 / 120.0 - t2 * (1.0 / 5040.0))));
-              const double q2 = rsqrt(c * c + sn * sn);
-              c *= q2; sn *= q2;
-            }
-            const double2 gx = g[p];
-            g[p] = make_double2(fma(gx.x, c, -gx.y * sn), fma(gx.x, sn, gx.y * c));
-          }
-          __syncwarp(tmask);
+        }
+        df_to_fp64(t.slot, tl, T, V);
+        __syncwarp(t.mask);
+        r = final_pass64<DD>(u, g64, nbp, site, G, tl, T, t.mask, idx, a.config, a.F, a.fprint);
+        ++c_pass;
+        written = true;
+        conv = dless_pos(r, a.eps);
+        if (!conv) {
+          const NewtonOut o = fp64_newton<DD>(t, u, ud, nbp, G, a.eps, a.newton_max, a.inner_max,
+                                              a.omega_in, a.lin_tol);
+          c_newton += o.steps;
+          c_pass += o.passes;
+          c_inner += o.inner;
+          r = o.r;
+          conv = o.conv;
+          if (o.steps) written = false;
         }
       }
       if (!conv) {
-        // last resort: FP64 relaxation sweeps (descent method; slow on this part)
-        const double om1 = a.om1, om = a.omega;
-        while (extra_sweeps < a.max_sweeps) {
-          for (int c = 0; c < G.ncolor; ++c) {
-            const int beg = G.color_off[c], end = G.color_off[c + 1];
-            for (int p = beg + tl; p < end; p += T) {
-              const double2 S = staple_dfma(u, g, nbp[p], p, d, V);
-              const double n2 = S.x * S.x + S.y * S.y;
-              if (!(n2 > 0.0)) continue;
-              const double rr = om * rsqrt(n2);
-              const double2 gx = g[p];
-              const double vx = fma(S.x, rr, om1 * gx.x), vy = fma(S.y, rr, om1 * gx.y);
-              const double q2 = rsqrt(vx * vx + vy * vy);
-              g[p] = make_double2(vx * q2, vy * q2);
-            }
-            __syncwarp(tmask);
-          }
-          ++extra_sweeps;
-          if (extra_sweeps % a.check_every == 0) {
-            r = 0.0;
-            for (int p = tl; p < V; p += T) {
-              const double2 S = staple_dfma(u, g, nbp[p], p, d, V);
-              const double2 gx = g[p];
-              const double dv = fma(gx.x, S.y, -gx.y * S.x);
-              r = dmax_pos(r, dv * dv);
-            }
-            for (int o = T >> 1; o > 0; o >>= 1) r = dmax_pos(r, __shfl_xor_sync(tmask, r, o));
-            if (dless_pos(r, a.eps)) { conv = true; break; }
-          }
-        }
-        c_upd64 += (unsigned long long)extra_sweeps * V;
+        const RelaxOut o = relax64_last_resort<DD>(t, u, nbp, G, a.omega, a.om1, a.eps,
+                                                   a.max_sweeps, a.check_every);
+        extra_sweeps = o.sweeps;
+        c_upd64 += (unsigned long long)o.sweeps * V;
+        if (o.sweeps >= a.check_every) r = o.r;
+        conv = o.conv;
+        if (o.sweeps) written = false;
       }
+    } else {
+      df_to_fp64(t.slot, tl, T, V);
+      __syncwarp(t.mask);
     }
-    c_upd32 += (unsigned long long)relax32_sweeps * V;
+    if (!written)
+      final_pass64<DD>(u, g64, nbp, site, G, tl, T, t.mask, idx, a.config, a.F, a.fprint);
     if (tl == 0) {
       a.status[idx] = conv ? kConverged : kNotConverged;
       a.sweeps[idx] += extra_sweeps;
       a.resid[idx] = r;
       if (conv) ++c_conv; else ++c_nconv;
     }
-    write_copy64(g, u, nbp, site, G, tl, T, tmask, idx, a.config, a.F, a.fprint);
-    __syncwarp(tmask);
+    __syncwarp(t.mask);
   }
   if (tl == 0) {
     atomicAdd(&a.stats[4], c_newton);
@@ -637,6 +914,7 @@ __global__ void __launch_bounds__(256) polish_kernel(const PolishArgs a) {
     atomicAdd(&a.stats[9], c_nconv);
     atomicAdd(&a.stats[20], c_inner);
     atomicAdd(&a.stats[21], c_upd32);
+    atomicAdd(&a.stats[22], c_df);
   }
 }
 
