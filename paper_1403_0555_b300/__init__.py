@@ -254,17 +254,33 @@ def gc_autotune(orbit, precision: int) -> dict:
     return {"r_warps": r.value, "p_warps": p.value, "f_warps": f.value}
 
 
-def gc_fetch_copies(orbit, V: int, capacity: int | None = None, theta: bool = True) -> dict:
+def gc_fetch_copies(orbit, V: int, capacity: int | None = None, theta: bool = True,
+                    out: dict | None = None) -> dict:
+    """Distinct copies sorted by (F, first start).  `out` may hold preallocated
+    arrays (for example in pinned host memory) named like the result's keys,
+    each with at least as many rows as are fetched; the result then holds views
+    of them."""
     lib = load()
     n = ctypes.c_size_t()
     _check(lib.gc_fetch_copies(orbit, 0, ctypes.byref(n), None, None, None, None, None, None))
     m = n.value if capacity is None else min(capacity, n.value)
-    F = np.zeros(m)
-    th = np.zeros((m, V)) if theta else None
-    first = np.zeros(m, np.uint64)
-    count = np.zeros(m, np.uint64)
-    lam = np.zeros(m)
-    reg = np.zeros(m, np.int32)
+    if out is not None:
+        for k_, a_ in out.items():
+            if a_ is not None and len(a_) < m:
+                raise ValueError(f"out[{k_!r}] holds {len(a_)} rows, {m} needed")
+        F = out["F"][:m]
+        th = out["theta"][:m] if theta else None
+        first = out["first_start"][:m]
+        count = out["count"][:m]
+        lam = out["lambda2"][:m]
+        reg = out["region"][:m]
+    else:
+        F = np.empty(m)
+        th = np.empty((m, V)) if theta else None
+        first = np.empty(m, np.uint64)
+        count = np.empty(m, np.uint64)
+        lam = np.empty(m)
+        reg = np.empty(m, np.int32)
     if m:
         _check(lib.gc_fetch_copies(orbit, m, ctypes.byref(n), _ptr(F, ctypes.c_double),
                                    _ptr(th, ctypes.c_double), _ptr(first, ctypes.c_uint64),

@@ -2,6 +2,8 @@
 // admission, batch planning and kernel launches (declarations: gribov.h).
 #include "gribov.h"
 
+#include <cub/device/device_radix_sort.cuh>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -112,6 +114,7 @@ struct gc_orbit_s {
   // batch staging
   Buf s_status, s_sweeps, s_resid, s_F, s_fprint, s_config, s_state32, s_copy;
   Buf work, stats, scratch, theta_tmp;
+  Buf sort_keys, sort_idx, sort_tmp;  // fetch ordering: keys [2n], indices [2n], CUB scratch
   size_t batch_cap = 0;
   uint64_t next_start = 0;
   // per-start records of the last call
@@ -420,7 +423,8 @@ int gc_destroy_orbit(gc_orbit o) {
   for (Buf* b : {&o->links64, &o->links32, &o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_count,
                  &o->t_next, &o->t_lam, &o->t_region, &o->t_head, &o->t_lock, &o->t_f8, &o->t_counters,
                  &o->t_newlist, &o->s_status, &o->s_sweeps, &o->s_resid, &o->s_F, &o->s_fprint,
-                 &o->s_config, &o->s_state32, &o->s_copy, &o->work, &o->stats, &o->scratch, &o->theta_tmp})
+                 &o->s_config, &o->s_state32, &o->s_copy, &o->work, &o->stats, &o->scratch, &o->theta_tmp,
+                 &o->sort_keys, &o->sort_idx, &o->sort_tmp})
     b->release(s);
   for (auto& e : o->ev)
     if (e) cudaEventDestroy(e);
@@ -847,35 +851,44 @@ int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
 
 namespace {
 
-struct Meta {
-  std::vector<double> F, lam;
-  std::vector<unsigned long long> first, count;
-  std::vector<int> region;
-  std::vector<unsigned> order;  // sorted position -> entry
-};
-
-int read_meta(gc_orbit o, Meta& m, unsigned* n_out) {
+// Entries in the pool after the last call (synchronises its stream and reports
+// device-side errors).
+int read_count(gc_orbit o, unsigned* n_out) {
   GC_CUDA(cudaStreamSynchronize(o->last_stream));
   harvest_timing(o);
   if (int rc = check_errors(o)) return rc;
   unsigned n = 0;
   GC_CUDA(cudaMemcpy(&n, o->n_entries(), 4, cudaMemcpyDeviceToHost));
-  n = std::min(n, o->cap);
-  m.F.resize(n); m.lam.resize(n); m.first.resize(n); m.count.resize(n); m.region.resize(n);
-  if (n) {
-    GC_CUDA(cudaMemcpy(m.F.data(), o->t_F.p, n * 8ull, cudaMemcpyDeviceToHost));
-    GC_CUDA(cudaMemcpy(m.lam.data(), o->t_lam.p, n * 8ull, cudaMemcpyDeviceToHost));
-    GC_CUDA(cudaMemcpy(m.first.data(), o->t_first.p, n * 8ull, cudaMemcpyDeviceToHost));
-    GC_CUDA(cudaMemcpy(m.count.data(), o->t_count.p, n * 8ull, cudaMemcpyDeviceToHost));
-    GC_CUDA(cudaMemcpy(m.region.data(), o->t_region.p, n * 4ull, cudaMemcpyDeviceToHost));
-  }
-  m.order.resize(n);
-  std::iota(m.order.begin(), m.order.end(), 0u);
-  std::sort(m.order.begin(), m.order.end(), [&](unsigned a, unsigned b) {
-    if (m.F[a] != m.F[b]) return m.F[a] < m.F[b];
-    return m.first[a] < m.first[b];
-  });
-  *n_out = n;
+  *n_out = std::min(n, o->cap);
+  return GC_OK;
+}
+
+// Device array of pool entries in (F, first start) order: two stable radix
+// sorts, by first start and then by F.  Returns nullptr for n = 0.
+int device_order(gc_orbit o, unsigned n, const unsigned** order) {
+  *order = nullptr;
+  if (n == 0) return GC_OK;
+  cudaStream_t s = o->last_stream;
+  if (!o->sort_keys.ensure((size_t)n * 16, s) || !o->sort_idx.ensure((size_t)n * 8, s))
+    return fail(GC_ENOMEM, "cannot admit %u sort records", n);
+  unsigned long long* k0 = o->sort_keys.as<unsigned long long>();
+  unsigned long long* k1 = k0 + n;
+  unsigned* i0 = o->sort_idx.as<unsigned>();
+  unsigned* i1 = i0 + n;
+  size_t tmp = 0, tmp2 = 0;
+  GC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, k0, k1, i0, i1, (int)n, 0, 64, s));
+  GC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp2, k1, k0, i1, i0, (int)n, 0, 64, s));
+  tmp = std::max(tmp, tmp2);
+  if (!o->sort_tmp.ensure(tmp, s)) return fail(GC_ENOMEM, "cannot admit sort scratch");
+  const int blocks = (int)std::min<unsigned>((n + 255) / 256, 4096);
+  GC_CUDA(cudaMemcpyAsync(k0, o->t_first.p, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+  gc::iota_kernel<<<blocks, 256, 0, s>>>(i0, n);
+  GC_CUDA(cub::DeviceRadixSort::SortPairs(o->sort_tmp.p, tmp, k0, k1, i0, i1, (int)n, 0, 64, s));
+  gc::f_keys_kernel<<<blocks, 256, 0, s>>>(o->t_F.as<double>(), i1, k0, n);
+  GC_CUDA(cub::DeviceRadixSort::SortPairs(o->sort_tmp.p, tmp, k0, k1, i1, i0, (int)n, 0, 64, s));
+  o->launches += 2;
+  GC_CUDA(cudaGetLastError());
+  *order = i0;
   return GC_OK;
 }
 
@@ -885,33 +898,45 @@ int gc_fetch_copies(gc_orbit o, size_t capacity, size_t* n_distinct, double* F, 
                     uint64_t* first_start, uint64_t* count, double* lambda2, int* region) {
   if (!o) return fail(GC_EINVAL, "gc_fetch_copies: NULL orbit");
   if (!n_distinct) return fail(GC_EINVAL, "gc_fetch_copies: n_distinct is NULL");
-  Meta m;
   unsigned n = 0;
-  if (int rc = read_meta(o, m, &n)) return rc;
+  if (int rc = read_count(o, &n)) return rc;
   *n_distinct = n;
-  if (capacity == 0) return GC_OK;
-  const size_t k = std::min<size_t>(capacity, n);
+  if (capacity == 0 || n == 0) return GC_OK;
+  const unsigned k = (unsigned)std::min<size_t>(capacity, n);
   const size_t V = o->V;
-  for (size_t i = 0; i < k; ++i) {
-    const unsigned e = m.order[i];
-    if (F) F[i] = m.F[e];
-    if (first_start) first_start[i] = m.first[e];
-    if (count) count[i] = m.count[e];
-    if (lambda2) lambda2[i] = m.lam[e];
-    if (region) region[i] = m.region[e];
-  }
-  if (theta && k) {
-    if (!o->theta_tmp.ensure((size_t)n * V * 8, o->last_stream)) return fail(GC_ENOMEM, "cannot admit fetch buffer");
-    const size_t tot = (size_t)n * V;
-    const int blocks = (int)std::min<size_t>((tot + 255) / 256, 8192);
-    gc::angles_kernel<<<blocks, 256, 0, o->last_stream>>>(o->t_cfg.as<double2>(), o->theta_tmp.as<double>(), tot);
+  cudaStream_t s = o->last_stream;
+  const unsigned* order = nullptr;
+  if (int rc = device_order(o, n, &order)) return rc;
+  // staging in sorted order: F, first, count, lambda_2 (8 B each), region (4 B), theta (V doubles)
+  const size_t meta = (size_t)k * 36 + 16, th = theta ? (size_t)k * V * 8 : 0;
+  if (!o->theta_tmp.ensure(meta + th, s)) return fail(GC_ENOMEM, "cannot admit fetch buffer");
+  unsigned char* st = o->theta_tmp.as<unsigned char>();
+  double* sF = reinterpret_cast<double*>(st);
+  unsigned long long* sfirst = reinterpret_cast<unsigned long long*>(st + (size_t)k * 8);
+  unsigned long long* scount = sfirst + k;
+  double* slam = reinterpret_cast<double*>(scount + k);
+  int* sreg = reinterpret_cast<int*>(slam + k);
+  double* sth = reinterpret_cast<double*>(st + (((size_t)k * 36 + 15) & ~size_t(15)));
+  {
+    const int blocks = (int)std::min<unsigned>((k + 255) / 256, 4096);
+    gc::gather_meta_kernel<<<blocks, 256, 0, s>>>(order, k, o->t_F.as<double>(), o->t_first.as<unsigned long long>(),
+                                                  o->t_count.as<unsigned long long>(), o->t_lam.as<double>(),
+                                                  o->t_region.as<int>(), sF, sfirst, scount, slam, sreg);
     ++o->launches;
-    GC_CUDA(cudaGetLastError());
-    std::vector<double> all(tot);
-    GC_CUDA(cudaMemcpyAsync(all.data(), o->theta_tmp.p, tot * 8, cudaMemcpyDeviceToHost, o->last_stream));
-    GC_CUDA(cudaStreamSynchronize(o->last_stream));
-    for (size_t i = 0; i < k; ++i) std::memcpy(theta + i * V, all.data() + (size_t)m.order[i] * V, V * 8);
   }
+  if (theta) {
+    const int blocks = (int)std::min<size_t>(((size_t)k * V + 255) / 256, 8192);
+    gc::gather_angles_kernel<<<blocks, 256, 0, s>>>(order, k, (int)V, o->t_cfg.as<double2>(), sth);
+    ++o->launches;
+  }
+  GC_CUDA(cudaGetLastError());
+  if (F) GC_CUDA(cudaMemcpyAsync(F, sF, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+  if (first_start) GC_CUDA(cudaMemcpyAsync(first_start, sfirst, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+  if (count) GC_CUDA(cudaMemcpyAsync(count, scount, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+  if (lambda2) GC_CUDA(cudaMemcpyAsync(lambda2, slam, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+  if (region) GC_CUDA(cudaMemcpyAsync(region, sreg, (size_t)k * 4, cudaMemcpyDeviceToHost, s));
+  if (theta) GC_CUDA(cudaMemcpyAsync(theta, sth, (size_t)k * V * 8, cudaMemcpyDeviceToHost, s));
+  GC_CUDA(cudaStreamSynchronize(s));
   return GC_OK;
 }
 
@@ -925,11 +950,15 @@ int gc_fetch_starts(gc_orbit o, uint64_t first, uint64_t n, int* status, int* sw
                 (unsigned long long)o->rec_first, (unsigned long long)(o->rec_first + o->rec_n));
   std::vector<int64_t> pos;
   if (copy_idx) {
-    Meta m;
     unsigned ne = 0;
-    if (int rc = read_meta(o, m, &ne)) return rc;
+    if (int rc = read_count(o, &ne)) return rc;
+    const unsigned* order = nullptr;
+    if (int rc = device_order(o, ne, &order)) return rc;
+    std::vector<unsigned> ord(ne);
+    if (ne) GC_CUDA(cudaMemcpyAsync(ord.data(), order, (size_t)ne * 4, cudaMemcpyDeviceToHost, o->last_stream));
+    GC_CUDA(cudaStreamSynchronize(o->last_stream));
     pos.assign(ne, -1);
-    for (unsigned i = 0; i < ne; ++i) pos[m.order[i]] = i;
+    for (unsigned i = 0; i < ne; ++i) pos[ord[i]] = i;
   }
   for (uint64_t i = 0; i < n; ++i) {
     const size_t r = (size_t)(first - o->rec_first + i);
@@ -953,9 +982,10 @@ int gc_orbit_stats(gc_orbit o, gc_stats* out) {
   GC_CUDA(cudaMemcpy(st, o->stats.p, sizeof st, cudaMemcpyDeviceToHost));
   unsigned long long nf8 = 0;
   GC_CUDA(cudaMemcpy(&nf8, o->n_f8(), 8, cudaMemcpyDeviceToHost));
-  Meta m;
   unsigned n = 0;
-  if (int rc = read_meta(o, m, &n)) return rc;
+  if (int rc = read_count(o, &n)) return rc;
+  std::vector<int> reg(n);
+  if (n) GC_CUDA(cudaMemcpy(reg.data(), o->t_region.p, (size_t)n * 4, cudaMemcpyDeviceToHost));
   out->n_starts = o->n_starts;
   out->n_converged = st[kConv] + st[kPConv];
   out->n_not_converged = st[kNConv] + st[kPNConv];
@@ -963,7 +993,7 @@ int gc_orbit_stats(gc_orbit o, gc_stats* out) {
   out->n_distinct = n;
   out->n_distinct_F8 = nf8;
   for (unsigned i = 0; i < n; ++i) {
-    switch (m.region[i]) {
+    switch (reg[i]) {
       case GC_REGION_IN: out->n_in++; break;
       case GC_REGION_OUT: out->n_out++; break;
       case GC_REGION_MARGINAL: out->n_marginal++; break;
@@ -1191,7 +1221,9 @@ int autotune_shape(gc_orbit like, const gc_options& base, double omega, double e
   opt.async = 0;
   opt.use_graph = 0;
   opt.stream = nullptr;
-  const uint64_t pilot = std::max<uint64_t>(2048, 262144 / (uint64_t)like->V * 4);
+  // pilots long enough to time throughput, not one start's tail: about 2^25
+  // site-starts (2^17 starts of a 4^4 lattice)
+  const uint64_t pilot = std::min<uint64_t>(1u << 17, std::max<uint64_t>(8192, (1ull << 25) / (uint64_t)like->V));
   // caps on warps per CTA; 16 leaves the largest shape that fits
   const int cand[4][3] = {{2, 2, 1}, {4, 4, 2}, {8, 8, 4}, {8, 16, 4}};
   double best[3] = {1e300, 1e300, 1e300};

@@ -284,9 +284,46 @@ __global__ void fill_u64_kernel(unsigned long long* p, unsigned long long v, siz
 }
 
 // theta'_x = arg g'_x for the first n entries (fetch)
-__global__ void angles_kernel(const double2* __restrict__ cfg, double* __restrict__ theta, size_t n) {
+// ---------------------------------------------------------------------------
+// Fetch: distinct copies in (F, first start) order
+// ---------------------------------------------------------------------------
+// ascending order of doubles as unsigned 64-bit keys (negative values too)
+__device__ __forceinline__ unsigned long long f64_order_key(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+
+__global__ void iota_kernel(unsigned* idx, unsigned n) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) idx[i] = i;
+}
+
+// keys of the second sort pass: F of the entries in first-start order
+__global__ void f_keys_kernel(const double* __restrict__ F, const unsigned* __restrict__ idx,
+                              unsigned long long* __restrict__ key, unsigned n) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    key[i] = f64_order_key(F[idx[i]]);
+}
+
+// per-copy records in sorted order
+__global__ void gather_meta_kernel(const unsigned* __restrict__ order, unsigned k,
+                                   const double* __restrict__ F, const unsigned long long* __restrict__ first,
+                                   const unsigned long long* __restrict__ count,
+                                   const double* __restrict__ lam, const int* __restrict__ region,
+                                   double* oF, unsigned long long* ofirst, unsigned long long* ocount,
+                                   double* olam, int* oregion) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+    const unsigned e = order[i];
+    oF[i] = F[e]; ofirst[i] = first[e]; ocount[i] = count[e]; olam[i] = lam[e]; oregion[i] = region[e];
+  }
+}
+
+// canonical angles theta'_x = arg g'_x of the copies in sorted order
+__global__ void gather_angles_kernel(const unsigned* __restrict__ order, unsigned k, int V,
+                                     const double2* __restrict__ cfg, double* __restrict__ theta) {
+  const size_t n = (size_t)k * V;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double2 z = cfg[i];
+    const size_t c = i / (unsigned)V, x = i - c * (unsigned)V;
+    const double2 z = cfg[(size_t)order[c] * V + x];
     theta[i] = atan2(z.y, z.x);
   }
 }
