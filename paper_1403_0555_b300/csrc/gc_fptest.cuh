@@ -255,6 +255,8 @@ __global__ void __launch_bounds__(256) fp_screen_kernel(const FpArgs a) {
   const int V = G.V;
   const int warps = blockDim.x >> 5;
   const int kmax = a.kmax32;
+  const unsigned n = *a.n_list;
+  if ((unsigned long long)blockIdx.x * warps >= n) return;   // no copy for this CTA (uniform)
   const FpSmem<float> lay(V, DD, kmax, warps);
   uint4* nbr = reinterpret_cast<uint4*>(smem + lay.nbr);
   build_site_neighbours(G, nbr);
@@ -268,7 +270,6 @@ __global__ void __launch_bounds__(256) fp_screen_kernel(const FpArgs a) {
 
   const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const unsigned n = *a.n_list;
   unsigned long long c_tests = 0;
   int steps = 0;
   for (long long li = gwarp; li < (long long)n; li += nwarps) {
@@ -326,6 +327,8 @@ __global__ void __launch_bounds__(128) fp_test_kernel(const FpArgs a) {
   const int V = G.V;
   const int warps = blockDim.x >> 5;
   const int kmax = a.kmax64;
+  const unsigned n = *a.n_list;
+  if ((unsigned long long)blockIdx.x * warps >= n) return;   // no copy for this CTA (uniform)
   const FpSmem<double> lay(V, DD, kmax, warps);
   uint4* nbr = reinterpret_cast<uint4*>(smem + lay.nbr);
   build_site_neighbours(G, nbr);
@@ -341,7 +344,6 @@ __global__ void __launch_bounds__(128) fp_test_kernel(const FpArgs a) {
   const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   double* Q = a.mode == kFpDense ? a.scratch + (size_t)gwarp * V * V : nullptr;
-  const unsigned n = *a.n_list;
   unsigned long long c_tests = 0, c64 = 0;
   int steps = 0;
   for (long long li = gwarp; li < (long long)n; li += nwarps) {
