@@ -1,0 +1,124 @@
+"""Full-size workloads in the launch configurations the benchmark times, checked
+on sampled outputs the oracle computes one by one, plus invariants that hold at
+any size.
+
+* 4D 4^4, eight von Mises orbits, 2^20 starts each, mixed precision, one
+  gc_enumerate_batch call captured as one CUDA graph on a side stream with the
+  autotuner on (the bench step).
+* 3D 6^3, 10^5 starts of a von Mises orbit and of the gauge-hidden cold orbit,
+  plain FP64 (bit-exact to the oracle start by start).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import orbit_inputs as oi
+from gpu_helpers import wrap
+
+pytestmark = pytest.mark.gpu
+
+
+def _table_invariants(c, st, V):
+    n = c["n_distinct"]
+    assert n == st["n_distinct"] > 0
+    assert int(c["count"].sum()) == st["n_converged"]           # every converged start counted once
+    assert len(np.unique(c["first_start"])) == n                 # one representative per copy
+    assert np.all(np.diff(c["F"]) >= 0)                          # fetched in F order
+    assert np.all(np.abs(c["theta"][:, V - 1]) <= 1e-15)         # global phase fixed at site V-1
+    assert np.all(c["F"] >= -1e-9)
+
+
+def _find(c, F, theta, delta=1e-6):
+    """Index of the copy within delta of (F, theta) in the fetched table, or -1."""
+    cand = np.flatnonzero(np.abs(c["F"] - F) <= 1e-7 * max(1.0, abs(F)))
+    for j in cand:
+        if np.max(np.abs(wrap(c["theta"][j] - theta))) <= delta:
+            return int(j)
+    return -1
+
+
+def test_bench_shape_4d_l4_x8_sampled():
+    import torch
+    import paper_1403_0555_b300 as gb
+    d, L, V = 4, 4, 256
+    n = 1 << 20
+    w = oi.workload_4d_4to4(n)
+    side = torch.cuda.Stream()
+    opt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=4, fp_mode=gb.GC_FP_AUTO,
+                                stream=side, use_graph=1, autotune=1)
+    with torch.cuda.stream(side):
+        hs = [gb.gc_create_orbit(d, L, o.phi, o.orbit_id, n) for o in w.orbits]
+        gb.gc_enumerate_batch(hs, [n] * len(hs), w.omega, w.eps, opt)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    try:
+        for j in (0, 7):                       # kappa = 0.5 (most copies) and 2.0
+            o, h = w.orbits[j], hs[j]
+            st = gb.gc_orbit_stats(h)
+            assert st["n_converged"] == n and st["n_dedup_failed"] == 0
+            c = gb.gc_fetch_copies(h, V)
+            _table_invariants(c, st, V)
+            # (a) the oracle's FP64 relaxation of sampled start indices reaches a
+            # copy of the table (the same minimum, within the dedup distance)
+            idx = np.sort(rng.choice(n, 24, replace=False))
+            rel = oracle.relax_indices(d, L, o.phi, 1, o.orbit_id, idx)
+            assert np.all(rel.status == oracle.CONVERGED)
+            _, th = oracle.canonical(rel.g)
+            F_or = oracle.functional(d, L, o.phi, th)
+            found = [_find(c, F_or[k], th[k]) for k in range(len(idx))]
+            # a start may rarely settle in a neighbouring basin on the FP32 path
+            # (agreement with the FP64 path is >= 99.9 %), hence one allowed miss
+            hits = [k for k, f in enumerate(found) if f >= 0 and c["first_start"][f] <= idx[k]]
+            assert len(hits) >= len(idx) - 1, found
+            for k in hits:
+                assert abs(c["F"][found[k]] - F_or[k]) <= 1e-10 * max(1.0, F_or[k])
+            # (b) sampled copies: their first start relaxes (oracle) to them, and
+            # lambda_2 / region agree with the oracle's dense eigensolve
+            pick = np.sort(rng.choice(c["n_distinct"], min(8, c["n_distinct"]), replace=False))
+            rel = oracle.relax_indices(d, L, o.phi, 1, o.orbit_id, c["first_start"][pick])
+            _, th = oracle.canonical(rel.g)
+            same = [np.max(np.abs(wrap(th[k] - c["theta"][p]))) <= 1e-6 for k, p in enumerate(pick)]
+            assert sum(same) >= len(pick) - 1
+            for p in pick:
+                lam = oracle.lambda2(d, L, oracle.fp_weights(d, L, o.phi, c["theta"][p]))
+                assert abs(c["lambda2"][p] - lam) <= 1e-3 * max(abs(lam), 1e-2), (p, c["lambda2"][p], lam)
+                assert c["region"][p] == oracle.region_flag(lam, 1e-9)
+    finally:
+        for h in hs:
+            gb.gc_destroy_orbit(h)
+
+
+@pytest.mark.parametrize("which", [0, 4])
+def test_config2_3d_l6_plain_full_size_sampled(which):
+    import paper_1403_0555_b300 as gb
+    w = oi.workload_3d_6cubed()
+    o = w.orbits[which]                        # von Mises seed 1, and the cold orbit
+    d, L, n = o.d, o.L, w.n_starts
+    V = L ** d
+    opt = gb.gc_options_default(precision=gb.GC_FP64, check_every=1, keep_per_start=1)
+    h = gb.gc_create_orbit(d, L, o.phi, o.orbit_id)
+    try:
+        gb.gc_enumerate_copies(h, n, w.omega, w.eps, opt)
+        st = gb.gc_orbit_stats(h)
+        s = gb.gc_fetch_starts(h, 0, n)
+        c = gb.gc_fetch_copies(h, V)
+    finally:
+        gb.gc_destroy_orbit(h)
+    assert st["n_starts"] == n
+    _table_invariants(c, st, V)
+    rng = np.random.default_rng(5 + which)
+    idx = np.sort(rng.choice(n, 48, replace=False))
+    rel = oracle.relax_indices(d, L, o.phi, 1, o.orbit_id, idx, w.omega, w.eps)
+    # the plain path follows the oracle's trajectory exactly: status, sweeps, F
+    assert np.array_equal(s["status"][idx], rel.status.astype(np.int32))
+    assert np.array_equal(s["sweeps"][idx], rel.sweeps)
+    conv = rel.status == oracle.CONVERGED
+    _, th = oracle.canonical(rel.g)
+    F_or = oracle.functional(d, L, o.phi, th)
+    assert np.all(np.abs(s["F"][idx][conv] - F_or[conv]) <= 1e-12 * np.maximum(1.0, F_or[conv]))
+    # each sampled start's copy holds its configuration (within the dedup distance;
+    # the copy's angles are those of its lowest start)
+    for k in np.flatnonzero(conv):
+        ci = s["copy_idx"][idx[k]]
+        assert ci >= 0 and c["first_start"][ci] <= idx[k]
+        assert np.max(np.abs(wrap(c["theta"][ci] - th[k]))) <= 1e-6
