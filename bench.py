@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--cpu-starts", type=int, default=1536)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--check-every", type=int, default=4)
+    p.add_argument("--no-uneven", dest="uneven", action="store_false",
+                   help="skip the uneven-batch leg (26 orbits of 13 lattice sizes in one graph)")
     p.add_argument("--serve-requests", type=int, default=100,
                    help="requests of the Poisson serving leg (0 skips it)")
     return p.parse_args()
@@ -156,6 +158,41 @@ def run_reference(args):
         "e2e": {"value": v, "unit": "copies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
+
+
+# ----------------------------------------------------------------------------
+# uneven batch: every (d, L) of the uneven sizes, two orbits each, in one graph
+# ----------------------------------------------------------------------------
+
+def uneven_leg(gb, torch, check_every, steps=2):
+    w = oi.workload_uneven()
+    n_list = w.extra["n_starts"]
+    side = torch.cuda.Stream()
+    opt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=check_every,
+                                fp_mode=gb.GC_FP_AUTO, stream=side, use_graph=1, autotune=1)
+    ms, conv, upd = 0.0, 0, 0
+    with torch.cuda.stream(side):
+        for k in range(1 + steps):          # one untimed step: allocations, autotuning
+            hs = [gb.gc_create_orbit(o.d, o.L, o.phi, o.orbit_id, n) for o, n in zip(w.orbits, n_list)]
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(side)
+            gb.gc_enumerate_batch(hs, n_list, w.omega, w.eps, opt)
+            e1.record(side)
+            e1.synchronize()
+            sts = [gb.gc_orbit_stats(h) for h in hs]
+            for h in hs:
+                gb.gc_destroy_orbit(h)
+            if k == 0:
+                continue
+            ms += e0.elapsed_time(e1)
+            conv += sum(st["n_converged"] for st in sts)
+            upd += sum(st["site_updates_fp32"] + st["site_updates_fp64"] for st in sts)
+    return {"orbits": len(w.orbits), "starts_per_step": int(sum(n_list)),
+            "shapes": {f"{o.d}D L{o.L}": n for o, n in list(zip(w.orbits, n_list))[::2]},
+            "value": conv / (ms / 1e3), "unit": "copies/s",
+            "site_updates_per_s": upd / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
+            "launch": "one gc_enumerate_batch per step as one CUDA graph, autotuned shapes"}
 
 
 # ----------------------------------------------------------------------------
@@ -451,6 +488,8 @@ def run_ours(args):
     roof["stage_ms_isolated"] = stage_ms
     roof["launch_starts"] = n_launch_starts
 
+    uneven = uneven_leg(gb, torch, args.check_every) if args.uneven else None
+
     serving = None
     if args.serve_requests > 0:
         sopt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=args.check_every,
@@ -481,6 +520,7 @@ def run_ours(args):
         "site_updates_fp32": tot["site_updates_fp32"], "site_updates_fp64": tot["site_updates_fp64"],
         "distinct_copies_per_orbit": n_distinct,
         "plain_fp64": plain,
+        "batch_uneven": uneven,
         "serving": serving,
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -139,15 +139,24 @@ def workload_4d_4to4(n_starts: int = 1 << 20) -> Workload:
 UNEVEN_SIZES = {2: (4, 6, 8, 12, 16), 3: (4, 5, 6, 8), 4: (3, 4, 5, 6)}
 
 
-def workload_uneven() -> Workload:
-    """Uneven batch: every (d, L) of UNEVEN_SIZES, two von Mises(1.0) orbits each."""
-    orbits = []
+def uneven_starts(d: int, L: int, site_updates: float = 1e9, sweeps: float = 100.0) -> int:
+    """Starts per orbit so that a size's two orbits do about `site_updates`
+    site updates at `sweeps` sweeps per start (a multiple of 256)."""
+    n = site_updates / (2.0 * volume(d, L) * sweeps)
+    return max(256, int(round(n / 256.0)) * 256)
+
+
+def workload_uneven(scale: float = 1.0) -> Workload:
+    """Uneven batch: every (d, L) of UNEVEN_SIZES, two von Mises(1.0) orbits each,
+    start counts from uneven_starts (times `scale`) in extra["n_starts"]."""
+    orbits, n = [], []
     for d, Ls in UNEVEN_SIZES.items():
         for L in Ls:
             for s in (1, 2):
                 orbits.append(Orbit(f"d{d}L{L}s{s}", d, L, von_mises_orbit(d, L, 1.0, s),
                                     1000 * d + 10 * L + s))
-    return Workload("uneven_batch", orbits, 0)
+                n.append(max(256, int(uneven_starts(d, L) * scale) // 256 * 256))
+    return Workload("uneven_batch", orbits, 0, extra={"n_starts": n})
 
 
 @dataclass

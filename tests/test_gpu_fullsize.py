@@ -122,3 +122,42 @@ def test_config2_3d_l6_plain_full_size_sampled(which):
         ci = s["copy_idx"][idx[k]]
         assert ci >= 0 and c["first_start"][ci] <= idx[k]
         assert np.max(np.abs(wrap(c["theta"][ci] - th[k]))) <= 1e-6
+
+
+def test_uneven_batch_full_size_sampled():
+    """The uneven batch (13 sizes x 2 orbits, about 10^9 site updates per size)
+    in one captured graph: every start accounted for, table invariants, and
+    sampled starts of four shapes (odd L included) reach table copies."""
+    import torch
+    import paper_1403_0555_b300 as gb
+    w = oi.workload_uneven()
+    n_list = w.extra["n_starts"]
+    side = torch.cuda.Stream()
+    opt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=4, fp_mode=gb.GC_FP_AUTO,
+                                stream=side, use_graph=1, autotune=1)
+    with torch.cuda.stream(side):
+        hs = [gb.gc_create_orbit(o.d, o.L, o.phi, o.orbit_id, n) for o, n in zip(w.orbits, n_list)]
+        gb.gc_enumerate_batch(hs, n_list, w.omega, w.eps, opt)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(23)
+    try:
+        for o, h, n in zip(w.orbits, hs, n_list):
+            st = gb.gc_orbit_stats(h)
+            assert st["n_starts"] == n
+            assert st["n_converged"] + st["n_not_converged"] == n
+            assert st["n_not_converged"] <= n // 1000 and st["n_dedup_failed"] == 0
+            if (o.d, o.L) not in ((2, 16), (3, 5), (4, 3), (4, 6)) or o.orbit_id % 10 != 1:
+                continue
+            V = o.L ** o.d
+            c = gb.gc_fetch_copies(h, V)
+            _table_invariants(c, st, V)
+            idx = np.sort(rng.choice(n, 12, replace=False))
+            rel = oracle.relax_indices(o.d, o.L, o.phi, 1, o.orbit_id, idx)
+            conv = np.flatnonzero(rel.status == oracle.CONVERGED)
+            _, th = oracle.canonical(rel.g)
+            F_or = oracle.functional(o.d, o.L, o.phi, th)
+            found = [_find(c, F_or[k], th[k]) for k in conv]
+            assert sum(f >= 0 for f in found) >= len(conv) - 1, (o.name, found)
+    finally:
+        for h in hs:
+            gb.gc_destroy_orbit(h)
