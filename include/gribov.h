@@ -107,6 +107,9 @@ typedef struct {
   double ms_relax, ms_polish, ms_dedup, ms_fptest; /* device ms, all calls      */
   uint64_t kernel_launches;      /* kernels the library launched for this orbit */
   uint64_t df_residual_passes;   /* double-float residual passes of the polish   */
+  double ms_polish_redo;         /* part of ms_polish: polish_kernel rerunning the
+                                    starts the line polish left (4^4)          */
+  uint64_t polish_redo_starts;   /* starts it reran                              */
 } gc_stats;
 
 /* Device memory hooks (e.g. a framework's caching allocator).  alloc returns

@@ -81,7 +81,8 @@ class gc_stats(ctypes.Structure):
         "newton_inner_sweeps", "polish_fallbacks", "fp64_residual_passes", "fp_tests", "fp_tests_fp64",
         "lanczos_steps")] + [(n, ctypes.c_double) for n in (
         "ms_relax", "ms_polish", "ms_dedup", "ms_fptest")] + [
-        ("kernel_launches", ctypes.c_uint64), ("df_residual_passes", ctypes.c_uint64)]
+        ("kernel_launches", ctypes.c_uint64), ("df_residual_passes", ctypes.c_uint64),
+        ("ms_polish_redo", ctypes.c_double), ("polish_redo_starts", ctypes.c_uint64)]
 
 
 EXPORTED = ("gc_set_allocator", "gc_options_default", "gc_create_orbit", "gc_enumerate_copies",

@@ -96,7 +96,7 @@ enum StatSlot {
   kSweeps = 0, kUpdates = 1, kConv = 2, kNConv = 3, kNewton = 4, kFallback = 5, kUpd64 = 6,
   kPass = 7, kPConv = 8, kPNConv = 9, kNew = 10, kHit = 11, kDFail = 12, kTests = 13,
   kTests64 = 14, kLanczos = 15, kSweeps32 = 16, kUpdates32 = 17, kConv32 = 18, kNConv32 = 19, kInner = 20, kUpd32Fallback = 21,
-  kPassDF = 22, kNumStats = 24
+  kPassDF = 22, kRedo = 23, kNumStats = 24
 };
 
 struct gc_orbit_s {
@@ -125,7 +125,7 @@ struct gc_orbit_s {
   std::vector<int32_t> rec_copy;
   // host-side accumulators
   uint64_t n_starts = 0;
-  double ms[4] = {0, 0, 0, 0};
+  double ms[5] = {0, 0, 0, 0, 0};   // relax, polish (all launches), dedup, FP test, polish redo
   uint64_t launches = 0;   // kernels this orbit launched
   uint64_t enqueued = 0;   // starts enqueued so far (bounds the copy count without a sync)
   std::vector<cudaEvent_t> ev_pool;      // timing events of enqueued batches (5 per batch)
@@ -463,13 +463,12 @@ int validate_options(const gc_options& opt, double omega, double eps) {
 // Add up the stage times of every batch enqueued since the last harvest
 // (the orbit's work must be complete).
 void harvest_timing(gc_orbit o) {
-  for (size_t k = 0; k + 4 < o->ev_used; k += 5) {
-    float t01 = 0, t12 = 0, t23 = 0, t34 = 0;
-    cudaEventElapsedTime(&t01, o->ev_pool[k], o->ev_pool[k + 1]);
-    cudaEventElapsedTime(&t12, o->ev_pool[k + 1], o->ev_pool[k + 2]);
-    cudaEventElapsedTime(&t23, o->ev_pool[k + 2], o->ev_pool[k + 3]);
-    cudaEventElapsedTime(&t34, o->ev_pool[k + 3], o->ev_pool[k + 4]);
-    o->ms[0] += t01; o->ms[1] += t12; o->ms[2] += t23; o->ms[3] += t34;
+  // per batch: before relax | after relax | after the first polish launch |
+  // after the redo polish launch | after dedup | after the FP test
+  for (size_t k = 0; k + 5 < o->ev_used; k += 6) {
+    float t[5] = {0, 0, 0, 0, 0};
+    for (int j = 0; j < 5; ++j) cudaEventElapsedTime(&t[j], o->ev_pool[k + j], o->ev_pool[k + j + 1]);
+    o->ms[0] += t[0]; o->ms[1] += t[1] + t[2]; o->ms[2] += t[3]; o->ms[3] += t[4]; o->ms[4] += t[2];
   }
   cudaGetLastError();
   o->ev_used = 0;
@@ -619,15 +618,15 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     // timing events of this batch
     cudaEvent_t* ev = nullptr;
     if (timing) {
-      while (o->ev_pool.size() < o->ev_used + 5) {
+      while (o->ev_pool.size() < o->ev_used + 6) {
         cudaEvent_t e;
         GC_CUDA(cudaEventCreate(&e));
         o->ev_pool.push_back(e);
       }
       ev = o->ev_pool.data() + o->ev_used;
-      o->ev_used += 5;
+      o->ev_used += 6;
     }
-    GC_CUDA(cudaMemsetAsync(wctr, 0, 16, s));
+    GC_CUDA(cudaMemsetAsync(wctr, 0, 32, s));   // relax, polish, redo polish counters; redo count
     GC_CUDA(cudaMemsetAsync(o->n_new(), 0, 4, s));
     GC_CUDA(cudaMemsetAsync(o->n_redo(), 0, 4, s));
 
@@ -661,7 +660,8 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     ra.stats = stats;
     int grid = 0;
     if (ev) GC_CUDA(cudaEventRecord(ev[0], s));
-    if (mixed && opt.relax_variant != GC_RELAX_GENERIC && d == 4 && o->L == 4) {
+    const bool line_variant = mixed && opt.relax_variant != GC_RELAX_GENERIC;
+    if (line_variant && d == 4 && o->L == 4) {
       constexpr int kTeams = 4;
       auto k = gc::relax32_lines_kernel<4, 4, kTeams>;
       const size_t sm = gc::relax32_lines_smem<4, 4, kTeams>();
@@ -728,6 +728,25 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       pa.fprint = ra.fprint;
       pa.config = ra.config;
       pa.stats = stats;
+      if (line_variant && d == 4 && o->L == 4) {
+        // two-line-per-lane polish; the starts it leaves are rerun by
+        // polish_kernel from the redo list (staged in the copy-index buffer,
+        // which dedup fills only afterwards)
+        constexpr int kTeams = 16;
+        auto k = gc::polish_pairs_kernel<4, 4, kTeams>;
+        const size_t sm = gc::PolishPairSmem<4, 4>::bytes(kTeams);
+        gc::PolishArgs pl = pa;
+        pl.redo = reinterpret_cast<unsigned*>(o->s_copy.as<int>());
+        pl.n_redo = wctr + 3;
+        if (int rc = launch_grid(k, 32 * kTeams, sm, kTeams, b, &grid)) return rc;
+        k<<<grid, 32 * kTeams, sm, s>>>(pl);
+        ++o->launches;
+        GC_CUDA(cudaGetLastError());
+        pa.list = pl.redo;
+        pa.n_list = wctr + 3;
+        pa.work_ctr = wctr + 2;
+        if (ev) GC_CUDA(cudaEventRecord(ev[2], s));
+      }
       auto plaunch = [&](auto kern) -> int {
         if (int rc = launch_grid(kern, p_warps * 32, p_smem, (long long)p_warps * tpw, b, &grid)) return rc;
         kern<<<grid, p_warps * 32, p_smem, s>>>(pa);
@@ -743,8 +762,11 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       }
       if (prc) return prc;
       GC_CUDA(cudaGetLastError());
+      if (ev && !pa.list) GC_CUDA(cudaEventRecord(ev[2], s));   // no redo launch: its time is 0
+    } else if (ev) {
+      GC_CUDA(cudaEventRecord(ev[2], s));
     }
-    if (ev) GC_CUDA(cudaEventRecord(ev[2], s));
+    if (ev) GC_CUDA(cudaEventRecord(ev[3], s));
     // deduplication
     gc::DedupArgs da{};
     da.tab = o->view();
@@ -768,7 +790,7 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       ++o->launches;
       GC_CUDA(cudaGetLastError());
     }
-    if (ev) GC_CUDA(cudaEventRecord(ev[3], s));
+    if (ev) GC_CUDA(cudaEventRecord(ev[4], s));
     // Faddeev-Popov test of the copies this batch created
     if (opt.fp_mode != GC_FP_NONE) {
       gc::FpArgs fa{};
@@ -815,7 +837,7 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       ++o->launches;
       GC_CUDA(cudaGetLastError());
     }
-    if (ev) GC_CUDA(cudaEventRecord(ev[4], s));
+    if (ev) GC_CUDA(cudaEventRecord(ev[5], s));
     if (opt.keep_per_start) {
       const size_t off = done;
       GC_CUDA(cudaMemcpyAsync(o->rec_status.data() + off, ra.status, b, cudaMemcpyDeviceToHost, s));
@@ -1015,6 +1037,8 @@ int gc_orbit_stats(gc_orbit o, gc_stats* out) {
   out->ms_polish = o->ms[1];
   out->ms_dedup = o->ms[2];
   out->ms_fptest = o->ms[3];
+  out->ms_polish_redo = o->ms[4];
+  out->polish_redo_starts = st[kRedo];
   out->kernel_launches = o->launches;
   out->df_residual_passes = st[kPassDF];
   return GC_OK;

@@ -334,11 +334,16 @@ struct PolishArgs {
   double* F;
   double* fprint;
   double2* config;
+  unsigned* redo;                // polish_pairs_kernel: starts left to polish_kernel
+  unsigned long long* n_redo;
+  const unsigned* list;          // polish_kernel: only these batch entries, when set
+  const unsigned long long* n_list;
   unsigned long long* stats;     // [4] newton steps, [5] fallbacks, [6] fp64 relaxation site
                                  // updates, [7] fp64 residual passes, [8] / [9] final
                                  // converged / not converged, [20] inner FP32 SOR sweeps,
                                  // [21] FP32 relaxation site updates of the fallback,
-                                 // [22] double-float residual passes
+                                 // [22] double-float residual passes, [23] starts rerun
+                                 // from the redo list
 };
 
 // per team: g (16 B per site: double-float float4 or FP64 double2), w (FP32,
@@ -761,6 +766,9 @@ __device__ __noinline__ RelaxOut relax64_last_resort(const PolishTeam t, const L
 template <int DD>
 __global__ void __launch_bounds__(512, 1) polish_kernel(const PolishArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  const long long n_items = a.list ? (long long)*a.n_list : a.n;
+  if (n_items == 0) return;   // uniform: an empty redo list
+  if (a.list && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.stats[23], (unsigned long long)n_items);
   const Geom G = a.geom;
   constexpr int d = DD;
   const int V = G.V, T = a.team;
@@ -807,7 +815,8 @@ __global__ void __launch_bounds__(512, 1) polish_kernel(const PolishArgs a) {
     long long idx = 0;
     if (tl == 0) idx = (long long)atomicAdd(a.work_ctr, 1ULL);
     idx = __shfl_sync(t.mask, idx, tw * T);
-    if (idx >= a.n) break;
+    if (idx >= n_items) break;
+    if (a.list) idx = a.list[idx];
     const int8_t st32 = a.status[idx];
     const float2* s32 = a.state32 + (size_t)idx * V;
     for (int p = tl; p < V; p += T) {
@@ -1250,6 +1259,384 @@ __global__ void __launch_bounds__(LineGeom<D, L>::NL * TEAMS, (D == 4 ? 2 : 1)) 
 template <int D, int L, int TEAMS>
 __host__ inline size_t relax32_lines_smem() {
   return (size_t)TEAMS * LineGeom<D, L>::V * sizeof(float2) + (size_t)TEAMS * 32 * sizeof(float);
+}
+
+// ---------------------------------------------------------------------------
+// Polish for lattices whose lines of each parity fill one warp (4^4, 8^3 ...):
+// one warp per start, lane h owns the h-th line of each parity
+// ---------------------------------------------------------------------------
+// The double-float Newton polish of polish_kernel, with every step's
+// arithmetic in the same order.  During the inner solve lane h keeps, for the
+// 2L sites of its two lines, the Newton weights (forward and, off axis 0,
+// backward), the right-hand side, 1/D and the correction in registers:
+// axis-0 neighbours are the lane's own sites, the other neighbours' corrections
+// are read from the team's shared copy [x_0][parity][h], so an inner SOR site
+// update reads 2(D-1) shared words, and the warp synchronises with __syncwarp
+// only.  The residual, rotation and FP64 passes run as loops over the lane's
+// sites on the shared state (compact code: the whole kernel stays in the
+// instruction cache).  The links, double-float and FP64, sit in shared memory
+// as [x_0][mu][parity][h].  A start this common path does not finish (FP32
+// phase not converged, the double-float Newton stalls, or the FP64 pass
+// rejects it) goes to a redo list that polish_kernel reruns from its FP32
+// state.
+template <int D, int L>
+struct PolishPairSmem {
+  using LG = LineGeom<D, L>;
+  static constexpr size_t u_df = 0;                                         // float4 [L][D][2][NLH]
+  static constexpr size_t u_64 = u_df + (size_t)LG::V * D * sizeof(float4);  // double2, same order
+  static constexpr size_t team0 = u_64 + (size_t)LG::V * D * sizeof(double2);
+  // per team [x0][parity][h]: state (16 B), correction (4 B), divergence (4 B)
+  static constexpr size_t per_team = (size_t)LG::V * 24;
+  static constexpr size_t bytes(int teams) { return team0 + (size_t)teams * per_team; }
+};
+
+template <int OFF>
+__device__ __forceinline__ float4 lds_f4(unsigned base) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+%5];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(base), "n"(OFF));
+  return v;
+}
+template <int OFF>
+__device__ __forceinline__ void sts_f4(unsigned base, float4 v) {
+  asm volatile("st.shared.v4.f32 [%0+%1], {%2, %3, %4, %5};" ::"r"(base), "n"(OFF), "f"(v.x),
+               "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
+}
+template <int OFF>
+__device__ __forceinline__ float lds_f1(unsigned base) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(base), "n"(OFF));
+  return v;
+}
+template <int OFF>
+__device__ __forceinline__ void sts_f1(unsigned base, float v) {
+  asm volatile("st.shared.f32 [%0+%1], %2;" ::"r"(base), "n"(OFF), "f"(v) : "memory");
+}
+template <int OFF>
+__device__ __forceinline__ double2 lds_d2(unsigned base) {
+  double2 v;
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2+%3];" : "=d"(v.x), "=d"(v.y) : "r"(base), "n"(OFF));
+  return v;
+}
+template <int OFF>
+__device__ __forceinline__ void sts_d2(unsigned base, double2 v) {
+  asm volatile("st.shared.v2.f64 [%0+%1], {%2, %3};" ::"r"(base), "n"(OFF), "d"(v.x), "d"(v.y) : "memory");
+}
+
+template <int D, int L, int TEAMS>
+__global__ void __launch_bounds__(32 * TEAMS, 1) polish_pairs_kernel(const PolishArgs a) {
+  using LG = LineGeom<D, L>;
+  using SM = PolishPairSmem<D, L>;
+  constexpr int NLH = LG::NLH, V = LG::V;
+  static_assert(NLH == 32, "one warp holds one line of each parity per lane");
+  constexpr int SS = 2 * NLH * 16;   // bytes from site x0 to x0 + 1 of a line: state, links
+  constexpr int SD = 2 * NLH * 4;    //                                          correction
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int h = threadIdx.x & 31, team = threadIdx.x >> 5;
+  unsigned char* tb = smem + SM::team0 + (size_t)team * SM::per_team;
+
+  // links into shared memory, [x0][mu][parity][h]
+  for (int e = threadIdx.x; e < 2 * NLH * L * D; e += blockDim.x) {
+    const int lq = e % (2 * NLH), rest = e / (2 * NLH), mu = rest % D, k = rest / D;
+    const int ql = lq / NLH, hl = lq % NLH;
+    const int ll = line_of<D, L>(ql, hl);
+    const double2 v = a.links64[(size_t)(k + L * ll) * D + mu];
+    const int i = ((k * D + mu) * 2 + ql) * NLH + hl;
+    reinterpret_cast<double2*>(smem + SM::u_64)[i] = v;
+    const float xh = __double2float_rn(v.x), yh = __double2float_rn(v.y);
+    reinterpret_cast<float4*>(smem + SM::u_df)[i] =
+        make_float4(xh, yh, __double2float_rn(v.x - (double)xh), __double2float_rn(v.y - (double)yh));
+  }
+  __syncthreads();
+
+  const unsigned s_st = (unsigned)__cvta_generic_to_shared(tb);
+  const unsigned s_dl = s_st + (unsigned)V * 16u;
+  const unsigned s_dv = s_dl + (unsigned)V * 4u;
+  const unsigned s_udf = (unsigned)__cvta_generic_to_shared(smem + SM::u_df);
+  const unsigned s_u64 = (unsigned)__cvta_generic_to_shared(smem + SM::u_64);
+  // per parity P: the line, and the correction addresses of its neighbour lines
+  // (parity 1 - P) along mu >= 1; element e sits at e*16 past the state and
+  // link bases, e*4 past the correction and divergence bases
+  int line[2];
+  unsigned dlp[2][D], dlm[2][D];
+#pragma unroll
+  for (int P = 0; P < 2; ++P) {
+    const int l = line_of<D, L>(P, h);
+    line[P] = l;
+    int t = l, stride = 1;
+    dlp[P][0] = dlm[P][0] = 0;
+#pragma unroll
+    for (int mu = 1; mu < D; ++mu) {
+      const int c = t % L;
+      t /= L;
+      const int lp = l + (((c + 1) % L) - c) * stride;
+      const int lm = l + (((c + L - 1) % L) - c) * stride;
+      dlp[P][mu] = s_dl + 4u * ((1 - P) * NLH + half_of<D, L>(lp));
+      dlm[P][mu] = s_dl + 4u * ((1 - P) * NLH + half_of<D, L>(lm));
+      stride *= L;
+    }
+  }
+  const bool use_df = a.eps >= 1e-25;
+  const float eps_df = (float)(0.25 * a.eps);
+  const float om = a.omega_in, om1 = 1.f - a.omega_in;
+  // site V-1 (all coordinates L-1): x0 = L-1 of the last line, parity (D-1)(L-1)
+  const unsigned st_last = s_st + 16u * ((L - 1) * 2 * NLH + (((D - 1) * (L - 1)) & 1) * NLH + NLH - 1);
+  auto warp_max = [&](float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+  };
+  // the lane's site i = P L + K: own element and the neighbour correction addresses
+  auto own_el = [&](int P) { return (unsigned)(P * NLH + h); };
+  auto nbp_dl = [&](int P, int mu) { return P ? dlp[1][mu] : dlp[0][mu]; };
+  auto nbm_dl = [&](int P, int mu) { return P ? dlm[1][mu] : dlm[0][mu]; };
+
+  float b[2][L], Dv[2][L], dl[2][L];
+  float wf[2][L][D], wb[2][L][D];   // w_{x,mu}; w_{x-mu,mu} for mu >= 1
+  unsigned c_newton = 0, c_inner = 0, c_df = 0, c_pass = 0, c_conv = 0;   // lane 0's
+
+  // Newton weights of the parity-P line from the high parts, 1/D, zero correction
+  auto weights = [&](auto PC, float& bd) {
+    constexpr int P = decltype(PC)::value;
+    const unsigned e = P * NLH + h;
+    const unsigned so = s_st + 16u * e, uo = s_udf + 16u * e, dlo = s_dl + 4u * e, dvo = s_dv + 4u * e;
+    static_for<L>([&](auto KC) {
+      constexpr int K = decltype(KC)::value;
+      b[P][K] = lds_f1<K * SD>(dvo);
+      const float4 gv = lds_f4<K * SS>(so);
+      static_for<D>([&](auto MC) {
+        constexpr int mu = decltype(MC)::value;
+        const float4 A = lds_f4<(K * D + mu) * SS>(uo);
+        float4 H;
+        if constexpr (mu == 0) H = lds_f4<((K + 1) % L) * SS>(so);
+        else H = lds_f4<K * SS>(s_st + 4u * (dlp[P][mu] - s_dl));
+        const float tx = fmaf(A.x, H.x, -A.y * H.y), ty = fmaf(A.x, H.y, A.y * H.x);
+        wf[P][K][mu] = fmaf(gv.x, tx, gv.y * ty);
+        if constexpr (mu > 0) {   // w_{x-mu,mu} = Re[conj(g_{x-mu}) u_{x-mu,mu} g_x]
+          const unsigned em16 = 4u * (dlm[P][mu] - s_dl);
+          const float4 B = lds_f4<(K * D + mu) * SS>(s_udf + em16);
+          const float4 G = lds_f4<K * SS>(s_st + em16);
+          const float sx = fmaf(B.x, gv.x, -B.y * gv.y), sy = fmaf(B.x, gv.y, B.y * gv.x);
+          wb[P][K][mu] = fmaf(G.x, sx, G.y * sy);
+        }
+      });
+    });
+    static_for<L>([&](auto KC) {
+      constexpr int K = decltype(KC)::value;
+      float Dd = 0.f;
+      static_for<D>([&](auto MC) {
+        constexpr int mu = decltype(MC)::value;
+        if constexpr (mu == 0) Dd += wf[P][K][0] + wf[P][(K + L - 1) % L][0];
+        else Dd += wf[P][K][mu] + wb[P][K][mu];
+      });
+      Dv[P][K] = Dd > 1e-6f ? __frcp_rn(Dd) : 0.f;
+      bd = fmaxf(bd, fabsf(b[P][K] * Dv[P][K]));
+      dl[P][K] = 0.f;
+      sts_f1<K * SD>(dlo, 0.f);
+    });
+  };
+  // one SOR site update of the parity-P line at x0 = K; returns |t - old|
+  auto sor = [&](auto PC, auto KC) -> float {
+    constexpr int P = decltype(PC)::value, K = decltype(KC)::value;
+    float acc = b[P][K];
+    static_for<D>([&](auto MC) {
+      constexpr int mu = decltype(MC)::value;
+      if constexpr (mu == 0) {
+        acc = fmaf(wf[P][K][0], dl[P][(K + 1) % L], acc);
+        acc = fmaf(wf[P][(K + L - 1) % L][0], dl[P][(K + L - 1) % L], acc);
+      } else {
+        acc = fmaf(wf[P][K][mu], lds_f1<K * SD>(dlp[P][mu]), acc);
+        acc = fmaf(wb[P][K][mu], lds_f1<K * SD>(dlm[P][mu]), acc);
+      }
+    });
+    const float t = acc * Dv[P][K], old = dl[P][K];
+    dl[P][K] = fmaf(om, t, om1 * old);
+    sts_f1<K * SD>(s_dl + 4u * (P * NLH + h), dl[P][K]);
+    return fabsf(t - old);
+  };
+  // colour C (0 or 1) of both lines: x0 = 2j + (C xor P)
+  auto colour = [&](auto CC, bool last, float& corr) {
+    constexpr int C = decltype(CC)::value;
+    static_for<2>([&](auto PC) {
+      constexpr int P = decltype(PC)::value;
+      static_for<L / 2>([&](auto JC) {
+        const float c = sor(PC, std::integral_constant<int, 2 * decltype(JC)::value + (C ^ P)>{});
+        if (last) corr = fmaxf(corr, c);
+      });
+    });
+    __syncwarp();
+  };
+
+  for (;;) {
+    long long idx = 0;
+    if (h == 0) idx = (long long)atomicAdd(a.work_ctr, 1ULL);
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    if (idx >= a.n) break;
+    const int8_t st32 = a.status[idx];
+#pragma unroll 1
+    for (int i = 0; i < 2 * L; ++i) {   // promote the FP32 state
+      const int P = i / L, K = i % L;
+      const int x = K + L * (P ? line[1] : line[0]);
+      const float2 v = a.state32[(size_t)idx * V + ((K + P) & 1) * (V / 2) + (x >> 1)];
+      sts_f4<0>(s_st + 16u * own_el(P) + (unsigned)K * SS, df_unit(v.x, 0.f, v.y, 0.f));
+    }
+    __syncwarp();
+    bool ok = false;
+    if (st32 == kConverged && use_df) {
+      float r_prev = 3.4e38f;
+      const int inner_cap = a.inner_max;
+      bool dconv = false;
+      for (int it = 0;; ++it) {
+        // double-float divergence of the lane's sites (order of df_divergence)
+        float rf = 0.f;
+#pragma unroll 1
+        for (int i = 0; i < 2 * L; ++i) {
+          const int P = i / L, K = i % L;
+          const unsigned e = own_el(P);
+          const unsigned so = s_st + 16u * e, uo = s_udf + 16u * e + (unsigned)(K * D) * SS;
+          float sxh = 0.f, sxl = 0.f, syh = 0.f, syl = 0.f;
+#pragma unroll
+          for (int mu = 0; mu < D; ++mu) {
+            float4 A, H, B, G;
+            if (mu == 0) {
+              A = lds_f4<0>(uo);
+              H = lds_f4<0>(so + (unsigned)((K + 1) % L) * SS);
+              B = lds_f4<0>(s_udf + 16u * e + (unsigned)(((K + L - 1) % L) * D) * SS);
+              G = lds_f4<0>(so + (unsigned)((K + L - 1) % L) * SS);
+            } else {
+              const unsigned ep16 = 4u * (nbp_dl(P, mu) - s_dl), em16 = 4u * (nbm_dl(P, mu) - s_dl);
+              A = lds_f4<0>(uo + (unsigned)mu * SS);
+              H = lds_f4<0>(s_st + ep16 + (unsigned)K * SS);
+              B = lds_f4<0>(s_udf + em16 + (unsigned)(K * D + mu) * SS);
+              G = lds_f4<0>(s_st + em16 + (unsigned)K * SS);
+            }
+            df_mac(A.x, A.z, H.x, H.z, sxh, sxl);
+            df_mac(-A.y, -A.w, H.y, H.w, sxh, sxl);
+            df_mac(A.x, A.z, H.y, H.w, syh, syl);
+            df_mac(A.y, A.w, H.x, H.z, syh, syl);
+            df_mac(B.x, B.z, G.x, G.z, sxh, sxl);
+            df_mac(B.y, B.w, G.y, G.w, sxh, sxl);
+            df_mac(B.x, B.z, G.y, G.w, syh, syl);
+            df_mac(-B.y, -B.w, G.x, G.z, syh, syl);
+          }
+          const float4 gx = lds_f4<0>(so + (unsigned)K * SS);
+          float dh = 0.f, dlo = 0.f;
+          df_mac(gx.x, gx.z, syh, syl, dh, dlo);
+          df_mac(-gx.y, -gx.w, sxh, sxl, dh, dlo);
+          const float dv = __fadd_rn(dh, dlo);
+          sts_f1<0>(s_dv + 4u * e + (unsigned)K * SD, dv);
+          rf = fmaxf(rf, dv * dv);
+        }
+        ++c_df;
+        rf = warp_max(rf);
+        if (rf < eps_df) { dconv = true; break; }
+        // a start Newton does not contract quickly (near-singular or
+        // indefinite M) leaves this kernel at once, for polish_kernel's
+        // escalating inner solves and fallbacks
+        if (it >= (a.newton_max < 4 ? a.newton_max : 4)) break;
+        if (it > 0 && !(rf < 0.25f * r_prev)) break;
+        r_prev = rf;
+        ++c_newton;
+        float bd = 0.f;
+        weights(std::integral_constant<int, 0>{}, bd);
+        weights(std::integral_constant<int, 1>{}, bd);
+        bd = warp_max(bd);   // also orders the zeroed corrections before the sweeps
+        int k = 0;
+        while (k < inner_cap) {
+          float corr = 0.f;
+          for (int kk = 0; kk < 8; ++kk, ++k) {
+            colour(std::integral_constant<int, 0>{}, kk == 7, corr);
+            colour(std::integral_constant<int, 1>{}, kk == 7, corr);
+          }
+          corr = warp_max(corr);
+          if (corr <= a.lin_tol * bd) break;
+        }
+        c_inner += (unsigned)k;
+#pragma unroll 1
+        for (int i = 0; i < 2 * L; ++i) {   // g_x <- g_x exp(i delta_x), |delta| capped at 0.2
+          const int P = i / L, K = i % L;
+          const unsigned e = own_el(P);
+          const unsigned sa = s_st + 16u * e + (unsigned)K * SS;
+          const float t = lds_f1<0>(s_dl + 4u * e + (unsigned)K * SD);
+          sts_f4<0>(sa, df_rotate(lds_f4<0>(sa), fminf(fmaxf(t, -0.2f), 0.2f)));
+        }
+        __syncwarp();
+      }
+      if (dconv) {
+        // FP64 image in place (the last reduction ended every lane's double-float
+        // reads), then one FP64 pass: residual, functional, fingerprint, copy
+#pragma unroll 1
+        for (int i = 0; i < 2 * L; ++i) {
+          const unsigned sa = s_st + 16u * own_el(i / L) + (unsigned)(i % L) * SS;
+          const float4 v = lds_f4<0>(sa);
+          sts_d2<0>(sa, make_double2(f2d_bits(v.x) + f2d_bits(v.z), f2d_bits(v.y) + f2d_bits(v.w)));
+        }
+        __syncwarp();
+        double2 gc;
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(gc.x), "=d"(gc.y) : "r"(st_last));
+        double r = 0.0, Fp = 0.0;
+#pragma unroll 1
+        for (int i = 0; i < 2 * L; ++i) {
+          const int P = i / L, K = i % L;
+          const unsigned e = own_el(P);
+          const unsigned so = s_st + 16u * e, uo = s_u64 + 16u * e + (unsigned)(K * D) * SS;
+          double fx = 0.0, fy = 0.0, bx = 0.0, by = 0.0;
+#pragma unroll
+          for (int mu = 0; mu < D; ++mu) {
+            double2 A, H, B, G;
+            if (mu == 0) {
+              A = lds_d2<0>(uo);
+              H = lds_d2<0>(so + (unsigned)((K + 1) % L) * SS);
+              B = lds_d2<0>(s_u64 + 16u * e + (unsigned)(((K + L - 1) % L) * D) * SS);
+              G = lds_d2<0>(so + (unsigned)((K + L - 1) % L) * SS);
+            } else {
+              const unsigned ep16 = 4u * (nbp_dl(P, mu) - s_dl), em16 = 4u * (nbm_dl(P, mu) - s_dl);
+              A = lds_d2<0>(uo + (unsigned)mu * SS);
+              H = lds_d2<0>(s_st + ep16 + (unsigned)K * SS);
+              B = lds_d2<0>(s_u64 + em16 + (unsigned)(K * D + mu) * SS);
+              G = lds_d2<0>(s_st + em16 + (unsigned)K * SS);
+            }
+            fx = fma(A.x, H.x, fx); fx = fma(-A.y, H.y, fx);
+            fy = fma(A.x, H.y, fy); fy = fma(A.y, H.x, fy);
+            bx = fma(B.x, G.x, bx); bx = fma(B.y, G.y, bx);
+            by = fma(B.x, G.y, by); by = fma(-B.y, G.x, by);
+          }
+          const double2 gx = lds_d2<0>(so + (unsigned)K * SS);
+          const double dv = fma(gx.x, fy + by, -gx.y * (fx + bx));
+          r = dmax_pos(r, dv * dv);
+          Fp += (double)D - fma(gx.x, fx, gx.y * fy);
+          const int x = K + L * (P ? line[1] : line[0]);
+          a.config[(size_t)idx * V + x] =
+              make_double2(fma(gx.x, gc.x, gx.y * gc.y), fma(gx.y, gc.x, -gx.x * gc.y));
+          if (x == 0) {   // site 0: cos(phi^theta) of its mu = 0 link
+            const double2 A = lds_d2<0>(uo), H = lds_d2<0>(so + (unsigned)SS);
+            const double tx = fma(A.x, H.x, -A.y * H.y), ty = fma(A.x, H.y, A.y * H.x);
+            a.fprint[idx] = fma(gx.x, tx, gx.y * ty);
+          }
+        }
+        ++c_pass;
+        for (int o = 16; o > 0; o >>= 1) {
+          r = dmax_pos(r, __shfl_xor_sync(0xffffffffu, r, o));
+          Fp += __shfl_xor_sync(0xffffffffu, Fp, o);
+        }
+        ok = dless_pos(r, a.eps);
+        if (ok && h == 0) {
+          a.F[idx] = Fp;
+          a.resid[idx] = r;
+          a.status[idx] = kConverged;
+          ++c_conv;
+        }
+      }
+    }
+    if (!ok && h == 0) a.redo[atomicAdd(a.n_redo, 1ULL)] = (unsigned)idx;
+    __syncwarp();
+  }
+  if (h == 0) {
+    atomicAdd(&a.stats[4], (unsigned long long)c_newton);
+    atomicAdd(&a.stats[7], (unsigned long long)c_pass);
+    atomicAdd(&a.stats[8], (unsigned long long)c_conv);
+    atomicAdd(&a.stats[20], (unsigned long long)c_inner);
+    atomicAdd(&a.stats[22], (unsigned long long)c_df);
+  }
 }
 
 }  // namespace gc
