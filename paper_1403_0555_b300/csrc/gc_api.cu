@@ -548,9 +548,9 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
   // polish: the most warps per SM, over two CTAs (links held twice) or one CTA
   // of up to 16 warps, with or without the FP64 links in shared memory (ties:
   // with them)
-  bool u64_smem = true;
+  bool u64_smem = true, cg = false;
   auto polish_bytes = [&](int warps) {
-    return gc::Smem(V, d, gc::polish_link_bytes(u64_smem), gc::polish_team_bytes(V, d), warps * tpw).total;
+    return gc::Smem(V, d, gc::polish_link_bytes(u64_smem), gc::polish_team_bytes(V, d, cg), warps * tpw).total;
   };
   auto polish_shape = [&](int* per_sm) {
     const int p2 = fit_warps(8, [&](int w) { return 2 * polish_bytes(w) + 2048; });
@@ -558,18 +558,33 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     *per_sm = std::max(2 * p2, p1);
     return 2 * p2 >= p1 ? p2 : p1;
   };
-  int p_warps = 0;
-  if (mixed) {
+  auto best_shape = [&](bool* smem_links) {
     int per_sm_s = 0, per_sm_g = 0;
+    u64_smem = true;
     const int ws = polish_shape(&per_sm_s);
     u64_smem = false;
     const int wg = polish_shape(&per_sm_g);
-    u64_smem = per_sm_s >= per_sm_g && ws > 0;
-    p_warps = u64_smem ? ws : wg;
-  }
+    *smem_links = per_sm_s >= per_sm_g && ws > 0;
+    return *smem_links ? ws : wg;
+  };
+  int p_warps = 0;
+  if (mixed) p_warps = best_shape(&u64_smem);
   if (mixed && !p_warps) return fail(GC_EINVAL, "polish does not fit shared memory");
   if (mixed && tune.p_warps > 0 && tune.p_warps < p_warps) p_warps = tune.p_warps;
   const size_t p_smem = mixed ? polish_bytes(p_warps) : 0;
+  const bool p_u64 = u64_smem;
+  // the redo launch (starts the line polish hands back) solves by CG: larger teams
+  bool r_u64 = false;
+  int r_warps_cg = 0;
+  size_t r_smem_cg = 0;
+  if (mixed) {
+    cg = true;
+    r_warps_cg = best_shape(&r_u64);
+    u64_smem = r_u64;
+    r_smem_cg = r_warps_cg ? polish_bytes(r_warps_cg) : 0;
+    cg = false;
+    u64_smem = p_u64;
+  }
   const int kmax64 = std::min(opt.lanczos_k, std::max(1, V - 1));
   const int kmax32 = std::min(160, kmax64);
   const FpKernel fp64_kern = fp_test_for(d), fp32_kern = fp_screen_for(d);
@@ -746,19 +761,56 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
         pa.n_list = wctr + 3;
         pa.work_ctr = wctr + 2;
         if (ev) GC_CUDA(cudaEventRecord(ev[2], s));
+      } else if (r_warps_cg > 0) {
+        // generic polish handing hard starts on to the CG instance
+        gc::PolishArgs pm = pa;
+        pm.redo = reinterpret_cast<unsigned*>(o->s_copy.as<int>());
+        pm.n_redo = wctr + 3;
+        auto mlaunch = [&](auto kern) -> int {
+          if (int rc = launch_grid(kern, p_warps * 32, p_smem, (long long)p_warps * tpw, b, &grid)) return rc;
+          kern<<<grid, p_warps * 32, p_smem, s>>>(pm);
+          ++o->launches;
+          return GC_OK;
+        };
+        int mrc = GC_OK;
+        switch (d) {
+          case 1: mrc = mlaunch(gc::polish_kernel<1, false>); break;
+          case 2: mrc = mlaunch(gc::polish_kernel<2, false>); break;
+          case 3: mrc = mlaunch(gc::polish_kernel<3, false>); break;
+          default: mrc = mlaunch(gc::polish_kernel<4, false>); break;
+        }
+        if (mrc) return mrc;
+        GC_CUDA(cudaGetLastError());
+        pa.list = pm.redo;
+        pa.n_list = wctr + 3;
+        pa.work_ctr = wctr + 2;
+        if (ev) GC_CUDA(cudaEventRecord(ev[2], s));
       }
+      const bool redo_cg = pa.list && r_warps_cg > 0;
+      const int pw = redo_cg ? r_warps_cg : p_warps;
+      const size_t psm = redo_cg ? r_smem_cg : p_smem;
+      if (redo_cg) pa.u64_smem = r_u64 ? 1 : 0;
       auto plaunch = [&](auto kern) -> int {
-        if (int rc = launch_grid(kern, p_warps * 32, p_smem, (long long)p_warps * tpw, b, &grid)) return rc;
-        kern<<<grid, p_warps * 32, p_smem, s>>>(pa);
+        if (int rc = launch_grid(kern, pw * 32, psm, (long long)pw * tpw, b, &grid)) return rc;
+        kern<<<grid, pw * 32, psm, s>>>(pa);
         ++o->launches;
         return GC_OK;
       };
       int prc = GC_OK;
-      switch (d) {
-        case 1: prc = plaunch(gc::polish_kernel<1>); break;
-        case 2: prc = plaunch(gc::polish_kernel<2>); break;
-        case 3: prc = plaunch(gc::polish_kernel<3>); break;
-        default: prc = plaunch(gc::polish_kernel<4>); break;
+      if (redo_cg) {
+        switch (d) {
+          case 1: prc = plaunch(gc::polish_kernel<1, true>); break;
+          case 2: prc = plaunch(gc::polish_kernel<2, true>); break;
+          case 3: prc = plaunch(gc::polish_kernel<3, true>); break;
+          default: prc = plaunch(gc::polish_kernel<4, true>); break;
+        }
+      } else {
+        switch (d) {
+          case 1: prc = plaunch(gc::polish_kernel<1, false>); break;
+          case 2: prc = plaunch(gc::polish_kernel<2, false>); break;
+          case 3: prc = plaunch(gc::polish_kernel<3, false>); break;
+          default: prc = plaunch(gc::polish_kernel<4, false>); break;
+        }
       }
       if (prc) return prc;
       GC_CUDA(cudaGetLastError());

@@ -314,7 +314,11 @@ __global__ void __launch_bounds__(256) relax_kernel(const RelaxArgs a) {
 // only FP64 work of a typical start: on this part the FP64 pipe has about
 // 1/64 of the FP32 rate.  Starts the double-float Newton cannot finish (a
 // near-singular or indefinite M) get FP64 Newton rounds, FP32 relaxation
-// sweeps and, last, FP64 relaxation sweeps, all out of line.
+// sweeps and, last, FP64 relaxation sweeps, all out of line.  With a redo list
+// the main launch hands such starts on instead (after at most four
+// contracting Newton steps, or when the FP64 pass rejects them) and the CG
+// instance (inner solves by conjugate gradients) reruns them from their FP32
+// state.
 struct PolishArgs {
   Geom geom;
   const double2* links64;
@@ -347,10 +351,11 @@ struct PolishArgs {
 };
 
 // per team: g (16 B per site: double-float float4 or FP64 double2), w (FP32,
-// [mu][p]), b, delta, 1/D (FP32)
-__host__ __device__ inline size_t polish_team_bytes(int V, int d) {
+// [mu][p]), b, delta, 1/D (FP32) and, for conjugate-gradient inner solves, the
+// search direction and M times it
+__host__ __device__ inline size_t polish_team_bytes(int V, int d, bool cg = false) {
   return align16((size_t)V * sizeof(double2)) + align16((size_t)V * d * sizeof(float)) +
-         3 * align16((size_t)V * sizeof(float));
+         (cg ? 5 : 3) * align16((size_t)V * sizeof(float));
 }
 // per CTA and link: the double-float copy [mu][p], preceded by the FP64 (cos, sin)
 // [mu][p] when those fit too
@@ -526,6 +531,7 @@ __device__ __forceinline__ double2 staple_dfma(const Links64& u, const double2* 
 struct PolishTeam {
   unsigned char* slot;   // g: double-float float4 or FP64 double2 per position
   float *w, *b, *dl, *Dinv;
+  float *pv, *qv;        // conjugate-gradient vectors, or nullptr (SOR)
   int tl, T;
   unsigned mask;
 };
@@ -562,10 +568,72 @@ __device__ __forceinline__ float newton_weights(const PolishTeam& t, const float
   return bd;
 }
 
-// FP32 checkerboard SOR on M delta = b until the corrections stall; returns sweeps
+// Jacobi-preconditioned conjugate gradients on M delta = b, M = D - A the
+// Faddeev-Popov operator with the weights w.  Iterations grow like the square
+// root of M's condition number, where SOR at a fixed omega needs sweeps in
+// proportion to it: the solver of the starts whose M is nearly singular.
+// Stops when max |D^-1 r| <= lin_tol max |D^-1 b|, at the cap, or when M is not
+// positive along a search direction (indefinite Hessian).  b is overwritten by
+// the residual; delta (dl) starts at 0.  Returns the iterations.
+__device__ __forceinline__ int newton_cg(const PolishTeam& t, const uint4* nbp, int d, int V,
+                                         float lin_tol, float bd, int cap) {
+  float rz = 0.f;
+  for (int p = t.tl; p < V; p += t.T) {
+    const float z = t.b[p] * t.Dinv[p];
+    t.pv[p] = z;
+    rz = fmaf(t.b[p], z, rz);
+  }
+  rz = team_sum(rz, t.T, t.mask);
+  __syncwarp(t.mask);
+  int k = 0;
+  while (k < cap) {
+    ++k;
+    float pq = 0.f;
+    for (int p = t.tl; p < V; p += t.T) {   // q = M p
+      const uint4 nb = nbp[p];
+      const float pp = t.pv[p];
+      float q = 0.f;
+      for (int mu = 0; mu < d; ++mu) {
+        const unsigned wd = nb_word(nb, mu);
+        const int xp = wd & 0xffffu, xm = wd >> 16;
+        q = fmaf(t.w[mu * V + p], pp - t.pv[xp], q);
+        q = fmaf(t.w[mu * V + xm], pp - t.pv[xm], q);
+      }
+      t.qv[p] = q;
+      pq = fmaf(pp, q, pq);
+    }
+    pq = team_sum(pq, t.T, t.mask);
+    if (!(pq > 0.f)) break;
+    const float alpha = rz / pq;
+    float rz1 = 0.f, zmax = 0.f;
+    for (int p = t.tl; p < V; p += t.T) {
+      t.dl[p] = fmaf(alpha, t.pv[p], t.dl[p]);
+      const float r = fmaf(-alpha, t.qv[p], t.b[p]);
+      t.b[p] = r;
+      const float z = r * t.Dinv[p];
+      rz1 = fmaf(r, z, rz1);
+      zmax = fmaxf(zmax, fabsf(z));
+    }
+    rz1 = team_sum(rz1, t.T, t.mask);
+    zmax = team_max(zmax, t.T, t.mask);
+    if (zmax <= lin_tol * bd) break;
+    const float beta = rz1 / rz;
+    rz = rz1;
+    __syncwarp(t.mask);
+    for (int p = t.tl; p < V; p += t.T) t.pv[p] = fmaf(beta, t.pv[p], t.b[p] * t.Dinv[p]);
+    __syncwarp(t.mask);
+  }
+  __syncwarp(t.mask);
+  return k;
+}
+
+// FP32 checkerboard SOR on M delta = b until the corrections stall (CG in the
+// CG instances); returns sweeps / iterations
+template <bool CG>
 __device__ __forceinline__ int newton_solve(const PolishTeam& t, const uint4* nbp, const Geom& G,
                                             int d, float om, float lin_tol, float bd, int cap) {
   const int V = G.V;
+  if constexpr (CG) return newton_cg(t, nbp, d, V, lin_tol, bd, cap);
   const float om1 = 1.f - om;
   int k = 0;
   while (k < cap) {
@@ -604,7 +672,7 @@ struct NewtonOut {
 // Rare path: FP64 Newton rounds on an FP64 state (FP64 residual, FP32 inner
 // solve, FP64 rotation).  Stops when max div^2 < eps, after newton_max steps,
 // or when the residual rises (M not positive definite here).
-template <int DD>
+template <int DD, bool CG>
 __device__ __noinline__ NewtonOut fp64_newton(const PolishTeam t, const Links64 u,
                                               const float4* ud, const uint4* nbp, const Geom G,
                                               double eps, int newton_max, int inner_max,
@@ -637,7 +705,7 @@ __device__ __noinline__ NewtonOut fp64_newton(const PolishTeam t, const Links64 
       const double2 v = g[q];
       return make_float2(d2f_bits(v.x), d2f_bits(v.y));
     });
-    o.inner += newton_solve(t, nbp, G, d, om_in, lin_tol, bd, inner_cap);
+    o.inner += newton_solve<CG>(t, nbp, G, d, om_in, lin_tol, bd, inner_cap);
     for (int p = t.tl; p < V; p += t.T) {
       const float tf = fminf(fmaxf(t.dl[p], -0.2f), 0.2f);
       const double tt = f2d_bits(tf);
@@ -763,7 +831,7 @@ __device__ __noinline__ RelaxOut relax64_last_resort(const PolishTeam t, const L
   return o;
 }
 
-template <int DD>
+template <int DD, bool CG>
 __global__ void __launch_bounds__(512, 1) polish_kernel(const PolishArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const long long n_items = a.list ? (long long)*a.n_list : a.n;
@@ -773,7 +841,7 @@ __global__ void __launch_bounds__(512, 1) polish_kernel(const PolishArgs a) {
   constexpr int d = DD;
   const int V = G.V, T = a.team;
   const int teams_per_warp = 32 / T, warps = blockDim.x >> 5;
-  const Smem lay(V, d, polish_link_bytes(a.u64_smem), polish_team_bytes(V, d),
+  const Smem lay(V, d, polish_link_bytes(a.u64_smem), polish_team_bytes(V, d, CG),
                  warps * teams_per_warp);
   double2* u64s = a.u64_smem ? reinterpret_cast<double2*>(smem + lay.links) : nullptr;
   float4* ud = reinterpret_cast<float4*>(smem + lay.links +
@@ -803,11 +871,16 @@ __global__ void __launch_bounds__(512, 1) polish_kernel(const PolishArgs a) {
   t.b = t.w + align16((size_t)V * d * sizeof(float)) / sizeof(float);
   t.dl = t.b + align16((size_t)V * sizeof(float)) / sizeof(float);
   t.Dinv = t.dl + align16((size_t)V * sizeof(float)) / sizeof(float);
+  t.pv = CG ? t.Dinv + align16((size_t)V * sizeof(float)) / sizeof(float) : nullptr;
+  t.qv = CG ? t.pv + align16((size_t)V * sizeof(float)) / sizeof(float) : nullptr;
   float4* gd = reinterpret_cast<float4*>(t.slot);
   const double2* g64 = reinterpret_cast<const double2*>(t.slot);
   // double-float Newton runs while eps / 4 is above its noise floor (|div| ~ 1e-13)
   const bool use_df = a.eps >= 1e-25;
   const float eps_df = (float)(0.25 * a.eps);
+  // main launch with a redo list: starts Newton does not finish quickly go to
+  // the CG instance instead of this kernel's escalating solves and fallbacks
+  const bool handoff = !CG && a.redo != nullptr;
 
   unsigned long long c_newton = 0, c_fallback = 0, c_upd64 = 0, c_pass = 0, c_conv = 0,
                      c_nconv = 0, c_inner = 0, c_upd32 = 0, c_df = 0;
@@ -824,11 +897,11 @@ __global__ void __launch_bounds__(512, 1) polish_kernel(const PolishArgs a) {
       gd[p] = df_unit(v.x, 0.f, v.y, 0.f);
     }
     __syncwarp(t.mask);
-    bool conv = false, written = false;
+    bool conv = false, written = false, handed = false;
     double r = 0.0;
     int extra_sweeps = 0;
     if (st32 == kConverged) {
-      for (int round = 0; round < 2 && !conv; ++round) {
+      for (int round = 0; round < 2 && !conv && !handed; ++round) {
         if (round == 1) {
           if (d < 2) break;
           ++c_fallback;
@@ -842,6 +915,7 @@ __global__ void __launch_bounds__(512, 1) polish_kernel(const PolishArgs a) {
           }
           __syncwarp(t.mask);
         }
+        bool dconv = false;
         if (use_df) {
           float r_prev = 3.4e38f;
           int inner_cap = a.inner_max;
@@ -855,10 +929,13 @@ __global__ void __launch_bounds__(512, 1) polish_kernel(const PolishArgs a) {
             }
             ++c_df;
             rf = team_max(rf, T, t.mask);
-            if (rf < eps_df) break;
-            if (it >= a.newton_max) break;
+            if (rf < eps_df) { dconv = true; break; }
+            if (it >= (handoff ? min(a.newton_max, 4) : a.newton_max)) break;
             if (it > 0 && !(rf < r_prev)) break;   // rising: M not positive definite here
-            if (!(rf < 0.25f * r_prev)) inner_cap = min(4 * inner_cap, 8192);  // poor step
+            if (!(rf < 0.25f * r_prev)) {          // poor step
+              if (handoff) break;
+              inner_cap = min(4 * inner_cap, 8192);
+            }
             r_prev = rf;
             ++c_newton;
             // (2) Jacobian weights from the high parts, (3) FP32 SOR solve
@@ -866,7 +943,7 @@ __global__ void __launch_bounds__(512, 1) polish_kernel(const PolishArgs a) {
               const float4 v = gd[q];
               return make_float2(v.x, v.y);
             });
-            c_inner += (unsigned long long)newton_solve(t, nbp, G, d, a.omega_in, a.lin_tol, bd,
+            c_inner += (unsigned long long)newton_solve<CG>(t, nbp, G, d, a.omega_in, a.lin_tol, bd,
                                                         inner_cap);
             // (4) g_x <- g_x exp(i delta_x), |delta| capped at 0.2
             for (int p = tl; p < V; p += T)
@@ -874,14 +951,16 @@ __global__ void __launch_bounds__(512, 1) polish_kernel(const PolishArgs a) {
             __syncwarp(t.mask);
           }
         }
+        if (handoff && use_df && !dconv) { handed = true; break; }
         df_to_fp64(t.slot, tl, T, V);
         __syncwarp(t.mask);
         r = final_pass64<DD>(u, g64, nbp, site, G, tl, T, t.mask, idx, a.config, a.F, a.fprint);
         ++c_pass;
         written = true;
         conv = dless_pos(r, a.eps);
+        if (!conv && handoff) { handed = true; break; }
         if (!conv) {
-          const NewtonOut o = fp64_newton<DD>(t, u, ud, nbp, G, a.eps, a.newton_max, a.inner_max,
+          const NewtonOut o = fp64_newton<DD, CG>(t, u, ud, nbp, G, a.eps, a.newton_max, a.inner_max,
                                               a.omega_in, a.lin_tol);
           c_newton += o.steps;
           c_pass += o.passes;
@@ -891,7 +970,7 @@ __global__ void __launch_bounds__(512, 1) polish_kernel(const PolishArgs a) {
           if (o.steps) written = false;
         }
       }
-      if (!conv) {
+      if (!conv && !handed) {
         const RelaxOut o = relax64_last_resort<DD>(t, u, nbp, G, a.omega, a.om1, a.eps,
                                                    a.max_sweeps, a.check_every);
         extra_sweeps = o.sweeps;
@@ -903,6 +982,11 @@ __global__ void __launch_bounds__(512, 1) polish_kernel(const PolishArgs a) {
     } else {
       df_to_fp64(t.slot, tl, T, V);
       __syncwarp(t.mask);
+    }
+    if (handed) {   // left, with its FP32 state, to the CG instance
+      if (tl == 0) a.redo[atomicAdd(a.n_redo, 1ULL)] = (unsigned)idx;
+      __syncwarp(t.mask);
+      continue;
     }
     if (!written)
       final_pass64<DD>(u, g64, nbp, site, G, tl, T, t.mask, idx, a.config, a.F, a.fprint);
