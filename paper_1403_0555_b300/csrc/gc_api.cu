@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -281,10 +282,30 @@ int team_size(const gc::Geom& G) {
   return (int)std::min<unsigned>(32u, next_pow2((unsigned)std::max(1, maxc)));
 }
 
+// A kernel's dynamic shared-memory limit only ever rises (per device and
+// kernel, under a lock): threads launching one kernel for different lattice
+// sizes at the same time (serving) never lower it under each other's launch.
+std::mutex g_smem_mu;
+std::map<std::pair<int, const void*>, size_t> g_smem_set;
+
+template <class K>
+int raise_smem_limit(K kernel, size_t smem) {
+  if (smem <= 48 * 1024) return GC_OK;
+  int dev = 0;
+  GC_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  size_t& cur = g_smem_set[{dev, reinterpret_cast<const void*>(kernel)}];
+  if (smem > cur) {
+    GC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cur = smem;
+  }
+  return GC_OK;
+}
+
 template <class K>
 int launch_grid(K kernel, int threads, size_t smem, long long work_items_per_block, long long items,
                 int* grid) {
-  if (smem > 48 * 1024) GC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (int rc = raise_smem_limit(kernel, smem)) return rc;
   int per_sm = 0;
   GC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
   if (per_sm < 1) return fail(GC_EINVAL, "kernel does not fit an SM (%zu bytes shared memory)", smem);

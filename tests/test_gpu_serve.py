@@ -64,3 +64,24 @@ def test_budget_and_bounded_wait():
             gb.gc_server_wait(srv, t, 1.0)          # ticket retired
     finally:
         gb.gc_server_destroy(srv)
+
+
+def test_concurrent_shapes_of_one_dimension_all_succeed():
+    """Workers launch the same kernels for different lattice sizes at once (one
+    kernel, different shared-memory footprints): every request must succeed."""
+    import paper_1403_0555_b300 as gb
+    srv = gb.gc_server_create(8, 0, gb.gc_options_default(precision=1, check_every=4))
+    tickets = []
+    try:
+        for i in range(48):
+            L = (3, 4, 5, 6)[i % 4]
+            phi = oi.von_mises_orbit(4, L, 1.0, 200 + i)
+            tickets.append(gb.gc_server_submit(srv, 4, L, phi, 200 + i, 600 + 97 * i))
+        for t in tickets:
+            status, latency, orb = gb.gc_server_wait(srv, t, 120.0)
+            assert status == gb.GC_OK and orb is not None
+            st = gb.gc_orbit_stats(orb)
+            assert st["n_converged"] + st["n_not_converged"] == st["n_starts"]
+            gb.gc_destroy_orbit(orb)
+    finally:
+        gb.gc_server_destroy(srv)
