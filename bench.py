@@ -56,7 +56,10 @@ def parse():
     p.add_argument("--plain-starts", type=int, default=1 << 16)
     p.add_argument("--cpu-starts", type=int, default=1536)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--check-every", type=int, default=4)
+    p.add_argument("--check-every", type=int, default=4,
+                   help="sweeps between residual checks when --autotune is 1")
+    p.add_argument("--autotune", type=int, choices=[1, 2], default=2,
+                   help="1: launch shapes only; 2: also the sweep-unroll depth")
     p.add_argument("--no-uneven", dest="uneven", action="store_false",
                    help="skip the uneven-batch leg (26 orbits of 13 lattice sizes in one graph)")
     p.add_argument("--serve-requests", type=int, default=100,
@@ -169,7 +172,7 @@ def uneven_leg(gb, torch, check_every, steps=2):
     n_list = w.extra["n_starts"]
     side = torch.cuda.Stream()
     opt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=check_every,
-                                fp_mode=gb.GC_FP_AUTO, stream=side, use_graph=1, autotune=1)
+                                fp_mode=gb.GC_FP_AUTO, stream=side, use_graph=1, autotune=2)
     ms, conv, upd = 0.0, 0, 0
     with torch.cuda.stream(side):
         for k in range(1 + steps):          # one untimed step: allocations, autotuning
@@ -192,7 +195,7 @@ def uneven_leg(gb, torch, check_every, steps=2):
             "shapes": {f"{o.d}D L{o.L}": n for o, n in list(zip(w.orbits, n_list))[::2]},
             "value": conv / (ms / 1e3), "unit": "copies/s",
             "site_updates_per_s": upd / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
-            "launch": "one gc_enumerate_batch per step as one CUDA graph, autotuned shapes"}
+            "launch": "one gc_enumerate_batch per step as one CUDA graph, autotuned shapes and sweep-unroll depth"}
 
 
 # ----------------------------------------------------------------------------
@@ -287,7 +290,7 @@ def run_ours(args):
     V = L ** d
     side = torch.cuda.Stream()
     opt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=args.check_every,
-                                fp_mode=gb.GC_FP_AUTO, stream=side, use_graph=1, autotune=1)
+                                fp_mode=gb.GC_FP_AUTO, stream=side, use_graph=1, autotune=args.autotune)
 
     def barrier():
         torch.cuda.synchronize()
@@ -306,10 +309,12 @@ def run_ours(args):
         return [gb.gc_create_orbit(d, L, o.phi, o.orbit_id, args.starts) for o in orbs]
 
     n_list = [args.starts] * len(orbits)
-    # launch shapes: tuned once (cached for every later call), recorded in config
+    # launch shapes and sweep-unroll depth: tuned once (cached for every later
+    # call), recorded in config
     h = gb.gc_create_orbit(d, L, orbits[0].phi, orbits[0].orbit_id)
-    tuning = gb.gc_autotune(h, gb.GC_MIXED)
+    tuning = gb.gc_autotune(h, gb.GC_MIXED, mode=args.autotune)
     gb.gc_destroy_orbit(h)
+    ce = tuning["check_every"] or args.check_every
     # warm-up: whole steps (allocations cached, autotuning done)
     with torch.cuda.stream(side):
         for k in range(args.warmup):
@@ -437,7 +442,7 @@ def run_ours(args):
     # kappa = 0.5 orbit), with CUDA events on the launch stream around every
     # kernel (the library's per-stage events).
     o = orbits[0]
-    ropt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=args.check_every,
+    ropt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=ce,
                                  fp_mode=gb.GC_FP_AUTO, stream=stream)
     h = gb.gc_create_orbit(d, L, o.phi, o.orbit_id, args.starts)
     gb.gc_enumerate_copies(h, args.starts, w.omega, w.eps, ropt)
@@ -452,7 +457,7 @@ def run_ours(args):
     # polish hands back (near-singular Faddeev-Popov operators), whose single-
     # warp runs form a latency tail that other orbits' kernels fill in a batch
     dom = max((k for k in stage_ms if k != "polish_redo"), key=stage_ms.get)
-    fp32_per_update = 8 * d + 11 + (8 * d + 3) / args.check_every
+    fp32_per_update = 8 * d + 11 + (8 * d + 3) / ce
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     fp64_peak = FP64_NOMINAL_TFLOPS / 2.0                        # DFMA per second, 1e12
     # DRAM bytes per start from the ncu capture of the small case (65536 starts),
@@ -518,7 +523,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "4d_L4_vonmises_x8", "lattice": "4^4", "orbits": 8,
                    "starts_per_orbit": args.starts, "omega": 1.7, "eps32": 1e-10, "eps": 1e-24,
-                   "check_every": args.check_every, "precision": "fp32 sweeps + fp64 polish",
+                   "check_every": ce, "precision": "fp32 sweeps + fp64 polish",
                    "fp_test": "lanczos fp32 screen + fp64", "parallelism": f"weak x{world}", "launch": "one CUDA graph per step (8 orbits, 16 streams)",
                    "timed": "device events around each step's batch launch; orbit creation outside",
                    "tuning": tuning,

@@ -89,7 +89,10 @@ typedef struct {
                            complete when opt->stream reaches this point)          */
   int use_graph;        /* gc_enumerate_batch: capture the whole batch as one CUDA
                            graph and launch it (needs a non-default stream)       */
-  int autotune;         /* tune launch shapes on first use of a (d, L, precision) */
+  int autotune;         /* 0 off; 1 tune launch shapes on first use of a (d, L,
+                           precision) (results unchanged); 2 also the sweep-unroll
+                           depth (mixed precision: sweeps between residual checks,
+                           replacing check_every; results move within tolerance) */
 } gc_options;
 
 typedef struct {
@@ -161,6 +164,11 @@ int gc_enumerate_batch(gc_orbit* orbits, int n_orbits, const uint64_t* n_starts,
  * value is a cap on warps per CTA (16: no cap, the largest shape that fits).
  * The knobs do not change results. */
 int gc_autotune(gc_orbit o, int precision, int* r_warps, int* p_warps, int* f_warps);
+
+/* The same with the mode of gc_options.autotune (1 or 2); *check_every gets
+ * the tuned sweep-unroll depth in mode 2 with GC_MIXED, else 0. */
+int gc_autotune_ex(gc_orbit o, int precision, int mode, int* r_warps, int* p_warps,
+                   int* f_warps, int* check_every);
 
 /* Serving with continuous batching.  Requests (an orbit and a start count)
  * queue in arrival order; `workers` threads, each on its own stream, start the

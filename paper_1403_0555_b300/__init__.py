@@ -88,8 +88,8 @@ class gc_stats(ctypes.Structure):
 EXPORTED = ("gc_set_allocator", "gc_options_default", "gc_create_orbit", "gc_enumerate_copies",
             "gc_fetch_copies", "gc_fetch_starts", "gc_orbit_stats", "gc_destroy_orbit",
             "gc_last_error", "gc_version", "gc_fp_test_static", "gc_enumerate_batch",
-            "gc_autotune", "gc_server_create", "gc_server_submit", "gc_server_wait",
-            "gc_server_destroy")
+            "gc_autotune", "gc_autotune_ex", "gc_server_create", "gc_server_submit",
+            "gc_server_wait", "gc_server_destroy")
 
 _lib = None
 _lock = threading.Lock()
@@ -138,6 +138,7 @@ def load(build_if_stale: bool = True):
                                          ctypes.POINTER(ctypes.c_uint64), ctypes.c_double,
                                          ctypes.c_double, ctypes.POINTER(gc_options)]
         L.gc_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, p_i, p_i, p_i]
+        L.gc_autotune_ex.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, p_i, p_i, p_i, p_i]
         L.gc_server_create.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(gc_options),
                                        ctypes.POINTER(ctypes.c_void_p)]
         L.gc_server_submit.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, p_d, ctypes.c_uint64,
@@ -249,10 +250,16 @@ def gc_enumerate_batch(orbits, n_starts, omega: float, eps: float, opt: gc_optio
                                      None if opt is None else ctypes.byref(opt)))
 
 
-def gc_autotune(orbit, precision: int) -> dict:
-    r, p, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(load().gc_autotune(orbit, precision, ctypes.byref(r), ctypes.byref(p), ctypes.byref(f)))
-    return {"r_warps": r.value, "p_warps": p.value, "f_warps": f.value}
+def gc_autotune_ex(orbit, precision: int, mode: int) -> dict:
+    """Launch shapes (mode 1) and, in mode 2 with GC_MIXED, the sweep-unroll depth."""
+    r, p, f, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().gc_autotune_ex(orbit, precision, mode, ctypes.byref(r), ctypes.byref(p),
+                                 ctypes.byref(f), ctypes.byref(c)))
+    return {"r_warps": r.value, "p_warps": p.value, "f_warps": f.value, "check_every": c.value}
+
+
+def gc_autotune(orbit, precision: int, mode: int = 1) -> dict:
+    return gc_autotune_ex(orbit, precision, mode)
 
 
 def gc_fetch_copies(orbit, V: int, capacity: int | None = None, theta: bool = True,

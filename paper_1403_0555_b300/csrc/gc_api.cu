@@ -464,6 +464,7 @@ namespace {
 struct Tuning {
   int r_warps = 0, p_warps = 0, f_warps = 0;
   size_t batch = 0;
+  int check_every = 0;   // sweep-unroll depth (autotune mode 2 only; 0: the caller's)
 };
 
 int validate_options(const gc_options& opt, double omega, double eps) {
@@ -507,14 +508,21 @@ int check_errors(gc_orbit o) {
 }
 
 std::mutex g_tune_mu;
-std::vector<std::pair<long long, Tuning>> g_tune_cache;   // key: d | L << 4 | precision << 12
+std::vector<std::pair<long long, Tuning>> g_tune_cache;   // key: tune_key
 
-long long tune_key(int d, int L, int precision) { return (long long)d | ((long long)L << 4) | ((long long)precision << 12); }
+// d | L << 4 | precision << 12 | deep << 16 (deep: sweep-unroll depth tuned too)
+long long tune_key(int d, int L, int precision, bool deep) {
+  return (long long)d | ((long long)L << 4) | ((long long)precision << 12) | ((long long)deep << 16);
+}
 
-Tuning cached_tuning(int d, int L, int precision) {
+int autotune_shape(gc_orbit like, const gc_options& base, double omega, double eps, Tuning* out);
+bool have_tuning(int d, int L, int precision, bool deep = false);
+bool deep_tuning(const gc_options& opt);
+
+Tuning cached_tuning(int d, int L, int precision, bool deep = false) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   for (auto& kv : g_tune_cache)
-    if (kv.first == tune_key(d, L, precision)) return kv.second;
+    if (kv.first == tune_key(d, L, precision, deep)) return kv.second;
   return Tuning{};
 }
 
@@ -526,7 +534,8 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
                    cudaStream_t s, bool async, bool timing, const Tuning& tune,
                    bool prepare_only = false) {
   if (n_starts == 0) return GC_OK;
-  const int max_sweeps = ((opt.max_sweeps + opt.check_every - 1) / opt.check_every) * opt.check_every;
+  const int check_every = (opt.autotune == 2 && tune.check_every > 0) ? tune.check_every : opt.check_every;
+  const int max_sweeps = ((opt.max_sweeps + check_every - 1) / check_every) * check_every;
   const int V = o->V, d = o->d;
   const bool mixed = opt.precision == GC_MIXED;
   o->last_precision = opt.precision;
@@ -682,7 +691,7 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     ra.omega32 = (float)omega;
     ra.om1_32 = (float)(1.0 - omega);
     ra.eps32 = (float)opt.eps32;
-    ra.check_every = opt.check_every;
+    ra.check_every = check_every;
     ra.max_sweeps = max_sweeps;
     ra.team = T;
     ra.stat_base = mixed ? kSweeps32 : kSweeps;
@@ -753,7 +762,7 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       pa.inner_max = opt.newton_inner;
       pa.newton_max = opt.newton_max;
       pa.max_sweeps = max_sweeps;
-      pa.check_every = opt.check_every;
+      pa.check_every = check_every;
       pa.team = T;
       pa.u64_smem = u64_smem ? 1 : 0;
       pa.status = ra.status;
@@ -937,7 +946,11 @@ int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
   if (int rc = validate_options(opt, omega, eps)) return rc;
   if (n_starts == 0) return GC_OK;
   cudaStream_t s = (cudaStream_t)opt.stream;
-  const Tuning tune = cached_tuning(o->d, o->L, opt.precision);
+  if (opt.autotune && !have_tuning(o->d, o->L, opt.precision, deep_tuning(opt))) {
+    Tuning t;
+    if (int rc = autotune_shape(o, opt, omega, eps, &t)) return rc;
+  }
+  const Tuning tune = cached_tuning(o->d, o->L, opt.precision, deep_tuning(opt));
   if (int rc = enumerate_impl(o, n_starts, omega, eps, opt, s, false, true, tune)) return rc;
   GC_CUDA(cudaStreamSynchronize(s));
   harvest_timing(o);
@@ -1302,8 +1315,11 @@ int reserve_for(gc_orbit o, uint64_t n, cudaStream_t s) {
   return table_reserve(o, need, cur, s);
 }
 
-// Pilot runs on a throw-away copy of the orbit: three launch shapes per
-// kernel, the fastest kept per kernel.  Only result-neutral knobs are tuned.
+// Pilot runs on a throw-away copy of the orbit: four launch shapes per kernel,
+// the fastest kept per kernel (result-neutral knobs).  In mode 2 (mixed
+// precision) the sweep-unroll depth -- sweeps between residual checks, 2, 4
+// or 8 -- is then picked by the whole path's pilot time; it changes where a
+// start's FP32 phase stops, so results move within the convergence tolerance.
 int autotune_shape(gc_orbit like, const gc_options& base, double omega, double eps, Tuning* out) {
   std::vector<double> phi((size_t)like->V * like->d);
   {
@@ -1341,20 +1357,45 @@ int autotune_shape(gc_orbit like, const gc_options& base, double omega, double e
     if (dt[1] < best[1]) { best[1] = dt[1]; t.p_warps = cand_t.p_warps; }
     if (dt[2] < best[2]) { best[2] = dt[2]; t.f_warps = cand_t.f_warps; }
   }
+  const bool deep = base.autotune == 2 && base.precision == GC_MIXED;
+  if (rc == GC_OK && deep) {
+    // the depth moves the FP32 sweeps and the polish; the redo launch is a
+    // few starts' latency tail that batches hide, so it is left out, and each
+    // depth is timed twice (the faster counts) on pilots twice as long
+    double best_all = 1e300;
+    for (int ce : {2, 4, 8}) {
+      gc_options o2 = opt;
+      o2.check_every = ce;
+      o2.autotune = 0;
+      double dt_min = 1e300;
+      for (int rep = 0; rep < 2 && rc == GC_OK; ++rep) {
+        const double m0 = tmp->ms[0] + tmp->ms[1] - tmp->ms[4];
+        rc = enumerate_impl(tmp, 2 * pilot, omega, eps, o2, nullptr, false, true, t);
+        if (rc == GC_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) rc = fail(GC_ECUDA, "autotune pilot failed");
+        if (rc != GC_OK) break;
+        harvest_timing(tmp);
+        dt_min = std::min(dt_min, tmp->ms[0] + tmp->ms[1] - tmp->ms[4] - m0);
+      }
+      if (rc != GC_OK) break;
+      if (dt_min < best_all) { best_all = dt_min; t.check_every = ce; }
+    }
+  }
   gc_destroy_orbit(tmp);
   if (rc != GC_OK) return rc;
   *out = t;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune_cache.emplace_back(tune_key(like->d, like->L, base.precision), t);
+  g_tune_cache.emplace_back(tune_key(like->d, like->L, base.precision, deep), t);
   return GC_OK;
 }
 
-bool have_tuning(int d, int L, int precision) {
+bool have_tuning(int d, int L, int precision, bool deep) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   for (auto& kv : g_tune_cache)
-    if (kv.first == tune_key(d, L, precision)) return true;
+    if (kv.first == tune_key(d, L, precision, deep)) return true;
   return false;
 }
+
+bool deep_tuning(const gc_options& opt) { return opt.autotune == 2 && opt.precision == GC_MIXED; }
 
 }  // namespace
 
@@ -1376,13 +1417,13 @@ extern "C" int gc_enumerate_batch(gc_orbit* orbits, int n_orbits, const uint64_t
   // set-up that needs the host: tuning, copy pools, staging buffers
   for (int i = 0; i < n_orbits; ++i) {
     gc_orbit o = orbits[i];
-    if (opt.autotune && !have_tuning(o->d, o->L, opt.precision)) {
+    if (opt.autotune && !have_tuning(o->d, o->L, opt.precision, deep_tuning(opt))) {
       Tuning t;
       if (int rc = autotune_shape(o, opt, omega, eps, &t)) return rc;
     }
     if (int rc = reserve_for(o, n_starts[i], origin)) return rc;
     if (int rc = enumerate_impl(o, n_starts[i], omega, eps, opt, origin, true, false,
-                                cached_tuning(o->d, o->L, opt.precision), true))
+                                cached_tuning(o->d, o->L, opt.precision, deep_tuning(opt)), true))
       return rc;
   }
   GC_CUDA(cudaStreamSynchronize(origin));
@@ -1403,7 +1444,7 @@ extern "C" int gc_enumerate_batch(gc_orbit* orbits, int n_orbits, const uint64_t
     if (cudaStreamWaitEvent(pool[k], fork, 0) != cudaSuccess) rc = fail(GC_ECUDA, "fork wait failed");
   for (int i = 0; rc == GC_OK && i < n_orbits; ++i)
     rc = enumerate_impl(orbits[i], n_starts[i], omega, eps, opt, pool[i % kPoolStreams], true, true,
-                        cached_tuning(orbits[i]->d, orbits[i]->L, opt.precision));
+                        cached_tuning(orbits[i]->d, orbits[i]->L, opt.precision, deep_tuning(opt)));
   for (int k = 0; k < used; ++k) {
     if (cudaEventRecord(join[k], pool[k]) != cudaSuccess && rc == GC_OK) rc = fail(GC_ECUDA, "join record failed");
     if (cudaStreamWaitEvent(origin, join[k], 0) != cudaSuccess && rc == GC_OK) rc = fail(GC_ECUDA, "join wait failed");
@@ -1429,20 +1470,29 @@ extern "C" int gc_enumerate_batch(gc_orbit* orbits, int n_orbits, const uint64_t
   return GC_OK;
 }
 
-extern "C" int gc_autotune(gc_orbit o, int precision, int* r_warps, int* p_warps, int* f_warps) {
+extern "C" int gc_autotune_ex(gc_orbit o, int precision, int mode, int* r_warps, int* p_warps,
+                              int* f_warps, int* check_every) {
   if (!o) return fail(GC_EINVAL, "gc_autotune: NULL orbit");
   if (precision != GC_FP64 && precision != GC_MIXED) return fail(GC_EINVAL, "unknown precision %d", precision);
+  if (mode != 1 && mode != 2) return fail(GC_EINVAL, "autotune mode %d not 1 or 2", mode);
   gc_options opt;
   gc_options_default(&opt);
   opt.precision = precision;
   opt.check_every = precision == GC_MIXED ? 4 : 1;
+  opt.autotune = mode;
+  const bool deep = deep_tuning(opt);
   Tuning t;
-  if (have_tuning(o->d, o->L, precision)) t = cached_tuning(o->d, o->L, precision);
+  if (have_tuning(o->d, o->L, precision, deep)) t = cached_tuning(o->d, o->L, precision, deep);
   else if (int rc = autotune_shape(o, opt, 1.7, 1e-24, &t)) return rc;
   if (r_warps) *r_warps = t.r_warps;
   if (p_warps) *p_warps = t.p_warps;
   if (f_warps) *f_warps = t.f_warps;
+  if (check_every) *check_every = deep ? t.check_every : 0;
   return GC_OK;
+}
+
+extern "C" int gc_autotune(gc_orbit o, int precision, int* r_warps, int* p_warps, int* f_warps) {
+  return gc_autotune_ex(o, precision, 1, r_warps, p_warps, f_warps, nullptr);
 }
 
 // ---------------------------------------------------------------------------

@@ -82,3 +82,19 @@ def test_autotune_is_result_neutral():
     assert t["r_warps"] in (2, 4, 8) and t["p_warps"] in (2, 4, 8, 16) and t["f_warps"] in (1, 2, 4)
     opt.autotune = 1
     _same(ref, _batch(gb, orbits, 2000, opt))
+
+
+def test_autotune_mode2_equals_fixed_depth():
+    """Mode 2 also tunes the sweep-unroll depth; its results are exactly those of
+    an untuned run with that check_every (launch shapes are result-neutral)."""
+    import paper_1403_0555_b300 as gb
+    orbits = _orbits()[-2:]
+    h = gb.gc_create_orbit(*orbits[1][:3], orbits[1][3])
+    t = gb.gc_autotune(h, 1, mode=2)
+    gb.gc_destroy_orbit(h)
+    assert t["check_every"] in (2, 4, 8)
+    tuned = gb.gc_options_default(precision=1, check_every=4)
+    tuned.autotune = 2
+    fixed = gb.gc_options_default(precision=1, check_every=t["check_every"])
+    d, L, phi, oid = orbits[1]
+    _same(_single(gb, [orbits[1]], 3000, fixed), _batch(gb, [orbits[1]], 3000, tuned))
