@@ -18,6 +18,7 @@
 #include "gc_common.cuh"
 #include "gc_fptest.cuh"
 #include "gc_relax.cuh"
+#include "gc_fptest_lines.cuh"
 #include "gc_table.cuh"
 
 namespace {
@@ -901,8 +902,15 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       if (opt.fp_mode == GC_FP_AUTO) {
         // FP32 screen of every new copy, then FP64 Lanczos for those it leaves
         int sgrid = 0;
-        if (int rc = launch_grid(fp32_kern, s_warps * 32, s_smem, s_warps, b, &sgrid)) return rc;
-        fp32_kern<<<sgrid, s_warps * 32, s_smem, s>>>(fa);
+        if (d == 4 && o->L == 4) {   // lines of each parity fill a warp: two lines per lane
+          auto k = gc::fp_screen_pairs_kernel<4, 4>;
+          const size_t sm = gc::FpPairSmem<4, 4>::bytes(8, kmax32);
+          if (int rc = launch_grid(k, 256, sm, 8, b, &sgrid)) return rc;
+          k<<<sgrid, 256, sm, s>>>(fa);
+        } else {
+          if (int rc = launch_grid(fp32_kern, s_warps * 32, s_smem, s_warps, b, &sgrid)) return rc;
+          fp32_kern<<<sgrid, s_warps * 32, s_smem, s>>>(fa);
+        }
         ++o->launches;
         GC_CUDA(cudaGetLastError());
         fa.list = fa.redo;
