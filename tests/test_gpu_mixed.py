@@ -68,3 +68,22 @@ def test_mixed_sampled_against_oracle():
     assert same.mean() >= 0.9
     F_or = oracle.functional(d, L, o.phi, th)
     assert np.all(np.abs(F_or[same] - ms["F"][idx][same]) < 1e-10 * np.maximum(1, F_or[same]))
+
+
+def test_hard_start_through_the_cg_redo_matches_oracle():
+    """A start whose Faddeev-Popov operator is nearly singular at its minimum
+    (4D 5^4, lambda_2 ~ 1e-4; the oracle's FP64 relaxation needs ~5e4 sweeps):
+    the main polish hands it on, the conjugate-gradient instance finishes it,
+    and it lands on the oracle's copy."""
+    d, L = 4, 5
+    phi = oi.von_mises_orbit(d, L, 1.0, 3)
+    ms, mc, st = run_gpu(d, L, phi, 3, 8, check_every=4, fp_mode=0, precision=1)
+    assert st["polish_redo_starts"] >= 1
+    assert ms["status"][2] == oracle.CONVERGED
+    rel = oracle.relax_indices(d, L, phi, 1, 3, [2])
+    assert rel.status[0] == oracle.CONVERGED
+    _, th = oracle.canonical(rel.g)
+    th_m = mc["theta"][ms["copy_idx"][2]]
+    assert np.max(np.abs(wrap(th[0] - th_m))) < 1e-6
+    lam = oracle.lambda2(d, L, oracle.fp_weights(d, L, phi, th[0]))
+    assert 0 < lam < 1e-3
