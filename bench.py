@@ -42,8 +42,8 @@ FP64_NOMINAL_TFLOPS = 1.25          # B300 dense FP64 (DFMA = 2 flops)
 # DRAM traffic per start (read + write) of the two heavy kernels, from the ncu
 # capture of the 65536-start 4^4 case recorded under profiles/ (None = not
 # captured for the current kernel)
-TRAFFIC_POLISH_PER_START = (1.371e8 + 2.194e8) / 65536      # profiles/polish_kernel_4d_L4.md
-TRAFFIC_RELAX_PER_START = (2.26e5 + 8.22e7) / 65536         # profiles/relax32_lines_4d_L4.md
+TRAFFIC_POLISH_PER_START = (1.345e8 + 2.173e8) / 65536      # profiles/polish_kernel_4d_L4.md (line polish)
+TRAFFIC_RELAX_PER_START = (6.73e5 + 8.264e7) / 65536        # profiles/relax32_lines_4d_L4.md
 
 
 def parse():
