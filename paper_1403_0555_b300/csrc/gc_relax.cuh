@@ -1168,7 +1168,7 @@ __global__ void __launch_bounds__(LineGeom<D, L>::NL * TEAMS, (D == 4 ? 2 : 1)) 
   const float om = a.omega32, om1 = a.om1_32;
 
   float2 g[L];
-  unsigned long long my_sweeps = 0, my_updates = 0, my_conv = 0, my_nconv = 0;
+  unsigned my_sweeps = 0, my_conv = 0, my_nconv = 0;   // thread 0's, per kernel
   auto fetch = [&]() -> long long {
     if (tt == 0) *tidx = (long long)atomicAdd(a.work_ctr, 1ULL);
     team_bar(bar_id, NL);
@@ -1308,7 +1308,6 @@ __global__ void __launch_bounds__(LineGeom<D, L>::NL * TEAMS, (D == 4 ? 2 : 1)) 
             a.status[idx] = conv ? kConverged : kNotConverged;
             a.sweeps[idx] = sweeps;
             my_sweeps += sweeps;
-            my_updates += (unsigned long long)sweeps * V;
             if (conv) ++my_conv; else ++my_nconv;
           }
           idx = fetch();
@@ -1333,10 +1332,10 @@ __global__ void __launch_bounds__(LineGeom<D, L>::NL * TEAMS, (D == 4 ? 2 : 1)) 
   };
   if (q) run(std::integral_constant<int, 1>{}); else run(std::integral_constant<int, 0>{});
   if (tt == 0 && (my_sweeps | my_conv | my_nconv)) {
-    atomicAdd(&a.stats[a.stat_base + 0], my_sweeps);
-    atomicAdd(&a.stats[a.stat_base + 1], my_updates);
-    atomicAdd(&a.stats[a.stat_base + 2], my_conv);
-    atomicAdd(&a.stats[a.stat_base + 3], my_nconv);
+    atomicAdd(&a.stats[a.stat_base + 0], (unsigned long long)my_sweeps);
+    atomicAdd(&a.stats[a.stat_base + 1], (unsigned long long)my_sweeps * V);
+    atomicAdd(&a.stats[a.stat_base + 2], (unsigned long long)my_conv);
+    atomicAdd(&a.stats[a.stat_base + 3], (unsigned long long)my_nconv);
   }
 }
 
