@@ -168,7 +168,16 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 
 def uneven_leg(gb, torch, check_every, steps=2):
-    w = oi.workload_uneven()
+    # start counts: about 1e9 site updates per size, from the mean FP32 sweeps
+    # per start of a 1000-start pilot of each size's first orbit
+    mean_sweeps = {}
+    for o in oi.workload_uneven().orbits[::2]:
+        h = gb.gc_create_orbit(o.d, o.L, o.phi, o.orbit_id)
+        gb.gc_enumerate_copies(h, 1000, 1.7, 1e-24,
+                               gb.gc_options_default(precision=gb.GC_MIXED, check_every=check_every))
+        mean_sweeps[(o.d, o.L)] = gb.gc_orbit_stats(h)["sweeps_fp32"] / 1000.0
+        gb.gc_destroy_orbit(h)
+    w = oi.workload_uneven(mean_sweeps=mean_sweeps)
     n_list = w.extra["n_starts"]
     side = torch.cuda.Stream()
     opt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=check_every,
@@ -193,6 +202,8 @@ def uneven_leg(gb, torch, check_every, steps=2):
             upd += sum(st["site_updates_fp32"] + st["site_updates_fp64"] for st in sts)
     return {"orbits": len(w.orbits), "starts_per_step": int(sum(n_list)),
             "shapes": {f"{o.d}D L{o.L}": n for o, n in list(zip(w.orbits, n_list))[::2]},
+            "pilot_mean_sweeps": {f"{d_}D L{L_}": round(v, 1) for (d_, L_), v in mean_sweeps.items()},
+            "site_updates_per_step": upd / steps,
             "value": conv / (ms / 1e3), "unit": "copies/s",
             "site_updates_per_s": upd / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
             "launch": "one gc_enumerate_batch per step as one CUDA graph, autotuned shapes and sweep-unroll depth"}

@@ -146,16 +146,19 @@ def uneven_starts(d: int, L: int, site_updates: float = 1e9, sweeps: float = 100
     return max(256, int(round(n / 256.0)) * 256)
 
 
-def workload_uneven(scale: float = 1.0) -> Workload:
+def workload_uneven(scale: float = 1.0, mean_sweeps: dict | None = None) -> Workload:
     """Uneven batch: every (d, L) of UNEVEN_SIZES, two von Mises(1.0) orbits each,
-    start counts from uneven_starts (times `scale`) in extra["n_starts"]."""
+    start counts in extra["n_starts"] (times `scale`): about 1e9 site updates
+    per size, from `mean_sweeps[(d, L)]` (sweeps per start measured on a
+    pilot) where given, else at 100 sweeps per start."""
     orbits, n = [], []
     for d, Ls in UNEVEN_SIZES.items():
         for L in Ls:
+            sw = (mean_sweeps or {}).get((d, L), 100.0)
             for s in (1, 2):
                 orbits.append(Orbit(f"d{d}L{L}s{s}", d, L, von_mises_orbit(d, L, 1.0, s),
                                     1000 * d + 10 * L + s))
-                n.append(max(256, int(uneven_starts(d, L) * scale) // 256 * 256))
+                n.append(max(256, int(uneven_starts(d, L, sweeps=sw) * scale) // 256 * 256))
     return Workload("uneven_batch", orbits, 0, extra={"n_starts": n})
 
 

@@ -2,8 +2,12 @@
 
     python -m paper_1403_0555_b300 enumerate --dim 4 --L 4 --kappa 0.714 --seed 2 \\
         --starts 65536 --precision mixed
+    python -m paper_1403_0555_b300 tables --entries 2:4,4:2 --orbits 100 --mebisamples 4
 
-Prints the orbit's statistics as one JSON line.  Orbits are seeded synthetic
+`enumerate` prints the orbit's statistics as one JSON line; `tables` one line
+per lattice of paper-style statistics over random uniform orbits (the number
+of minima of Table I, the global-minimum functional of Table III and the
+discovery curve of Figs. 1-3).  Orbits are seeded synthetic
 inputs (orbit_inputs): von Mises(kappa) link angles, or uniform with --kappa 0.
 """
 from __future__ import annotations
@@ -35,7 +39,23 @@ def main(argv=None):
     e.add_argument("--eps", type=float, default=1e-24)
     e.add_argument("--check-every", type=int, default=None)
     e.add_argument("--fp-mode", choices=["auto", "lanczos", "dense", "none"], default="auto")
+    t = sub.add_parser("tables", help="paper-style statistics over random uniform orbits "
+                                      "(number of minima, global-minimum F/(dV), discovery curve)")
+    t.add_argument("--entries", default="2:2,2:4,3:2,4:2", help="comma list of d:N")
+    t.add_argument("--orbits", type=int, default=100)
+    t.add_argument("--mebisamples", type=float, default=4.0, help="starts per orbit / 1024^2")
+    t.add_argument("--omega", type=float, default=1.0)
+    t.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     a = p.parse_args(argv)
+    if a.cmd == "tables":
+        from paper_1403_0555_b300.analysis import table_statistics
+        for ent in a.entries.split(","):
+            d, N = (int(x) for x in ent.split(":"))
+            st = table_statistics(d, N, a.orbits, int(a.mebisamples * (1 << 20)), a.omega,
+                                  gb.GC_MIXED if a.precision == "mixed" else gb.GC_FP64,
+                                  check_every=4 if a.precision == "mixed" else 1, curve=True)
+            print(json.dumps(st), flush=True)
+        return
 
     d, L = a.dim, a.L
     phi = (oi.uniform_orbit(d, L, a.seed) if a.kappa == 0
