@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--plain-starts", type=int, default=1 << 16)
     p.add_argument("--cpu-starts", type=int, default=1536)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-configs", action="store_true",
+                   help="also time the oracle on configs 1 and 2 (a few minutes of host time)")
     p.add_argument("--check-every", type=int, default=4,
                    help="sweeps between residual checks when --autotune is 1")
     p.add_argument("--autotune", type=int, choices=[1, 2], default=2,
@@ -130,6 +132,41 @@ def oracle_sample(orbit, n_starts, start0=0):
                                           n_starts, omega=1.7, eps=1e-24, start0=start0)
     dt = time.perf_counter() - t
     return int((relaxed.status == oracle.CONVERGED).sum()), dt, oracle.max_threads()
+
+
+def oracle_configs():
+    """The oracle on configs 1 and 2 (one thread and all host cores): config 1
+    whole pipeline; config 2 (3D 6^3, one orbit) its C relaxation, all 10^5
+    starts on all cores and 4096 of them on one thread (the oracle's Python
+    dedup is quadratic in the copies, so the full config-2 pipeline is not
+    timed)."""
+    import oracle
+    n_all = oracle.max_threads()   # a thread count, once set, stays: pass it explicitly
+    out = {"cores": n_all}
+    w1 = oi.workload_2d_4x4()
+    o = w1.orbits[0]
+    for nt in (1, n_all):
+        t = time.perf_counter()
+        rel, cp = oracle.enumerate_copies(o.d, o.L, o.phi, 1, o.orbit_id, w1.n_starts, w1.omega,
+                                          w1.eps, nthreads=nt)
+        dt = time.perf_counter() - t
+        key = "config1_1thread" if nt == 1 and n_all > 1 else "config1_all_cores"
+        out[key] = {"starts": w1.n_starts, "seconds": dt,
+                    "converged_per_s": int((rel.status == oracle.CONVERGED).sum()) / dt,
+                    "site_updates_per_s": float(rel.sweeps.sum()) * o.L ** o.d / dt,
+                    "distinct": int(len(cp.F)), "pipeline": "whole"}
+    w2 = oi.workload_3d_6cubed()
+    o = w2.orbits[0]
+    for nt, n in ((1, 4096), (n_all, w2.n_starts)):
+        t = time.perf_counter()
+        rel = oracle.relax_starts(o.d, o.L, o.phi, 1, o.orbit_id, 0, n, w2.omega, w2.eps, nthreads=nt)
+        dt = time.perf_counter() - t
+        key = "config2_1thread" if nt == 1 and n < w2.n_starts else "config2_all_cores"
+        out[key] = {"starts": n, "seconds": dt,
+                    "converged_per_s": int((rel.status == oracle.CONVERGED).sum()) / dt,
+                    "site_updates_per_s": float(rel.sweeps.sum()) * o.L ** o.d / dt,
+                    "pipeline": "relaxation (C, OpenMP over starts)"}
+    return out
 
 
 def run_reference(args):
@@ -519,6 +556,8 @@ def run_ours(args):
                                      fp_mode=gb.GC_FP_AUTO)
         serving = serve_leg(gb, args.serve_requests, sopt)
 
+    cpu_configs = oracle_configs() if args.cpu_configs else None
+
     cpu = None
     if not args.no_cpu_baseline:
         c, dt, threads = oracle_sample(orbits[0], args.cpu_starts)
@@ -547,6 +586,7 @@ def run_ours(args):
         "serving": serving,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "cpu_baseline_configs": cpu_configs,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": int(tot["kernel_launches"]),
