@@ -1564,11 +1564,97 @@ __global__ void __launch_bounds__(32 * TEAMS, 1) polish_pairs_kernel(const Polis
     }
     __syncwarp();
     bool ok = false;
+    // FP64 image in place (the last warp reduction ended every lane's
+    // double-float reads), then one FP64 pass: residual, functional,
+    // fingerprint, canonical copy; true if max div^2 < eps
+    auto fp64_pass = [&]() -> bool {
+        // FP64 image in place (the last reduction ended every lane's double-float
+        // reads), then one FP64 pass: residual, functional, fingerprint, copy
+#pragma unroll 1
+        for (int i = 0; i < 2 * L; ++i) {
+          const unsigned sa = s_st + 16u * own_el(i / L) + (unsigned)(i % L) * SS;
+          const float4 v = lds_f4<0>(sa);
+          sts_d2<0>(sa, make_double2(f2d_bits(v.x) + f2d_bits(v.z), f2d_bits(v.y) + f2d_bits(v.w)));
+        }
+        __syncwarp();
+        double2 gc;
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(gc.x), "=d"(gc.y) : "r"(st_last));
+        double r = 0.0, Fp = 0.0;
+#pragma unroll 1
+        for (int i = 0; i < 2 * L; ++i) {
+          const int P = i / L, K = i % L;
+          const unsigned e = own_el(P);
+          const unsigned so = s_st + 16u * e, uo = s_u64 + 16u * e + (unsigned)(K * D) * SS;
+          double fx = 0.0, fy = 0.0, bx = 0.0, by = 0.0;
+#pragma unroll
+          for (int mu = 0; mu < D; ++mu) {
+            double2 A, H, B, G;
+            if (mu == 0) {
+              A = lds_d2<0>(uo);
+              H = lds_d2<0>(so + (unsigned)((K + 1) % L) * SS);
+              B = lds_d2<0>(s_u64 + 16u * e + (unsigned)(((K + L - 1) % L) * D) * SS);
+              G = lds_d2<0>(so + (unsigned)((K + L - 1) % L) * SS);
+            } else {
+              const unsigned ep16 = 4u * (nbp_dl(P, mu) - s_dl), em16 = 4u * (nbm_dl(P, mu) - s_dl);
+              A = lds_d2<0>(uo + (unsigned)mu * SS);
+              H = lds_d2<0>(s_st + ep16 + (unsigned)K * SS);
+              B = lds_d2<0>(s_u64 + em16 + (unsigned)(K * D + mu) * SS);
+              G = lds_d2<0>(s_st + em16 + (unsigned)K * SS);
+            }
+            fx = fma(A.x, H.x, fx); fx = fma(-A.y, H.y, fx);
+            fy = fma(A.x, H.y, fy); fy = fma(A.y, H.x, fy);
+            bx = fma(B.x, G.x, bx); bx = fma(B.y, G.y, bx);
+            by = fma(B.x, G.y, by); by = fma(-B.y, G.x, by);
+          }
+          const double2 gx = lds_d2<0>(so + (unsigned)K * SS);
+          const double dv = fma(gx.x, fy + by, -gx.y * (fx + bx));
+          r = dmax_pos(r, dv * dv);
+          Fp += (double)D - fma(gx.x, fx, gx.y * fy);
+          const int x = K + L * (P ? line[1] : line[0]);
+          a.config[(size_t)idx * V + x] =
+              make_double2(fma(gx.x, gc.x, gx.y * gc.y), fma(gx.y, gc.x, -gx.x * gc.y));
+          if (x == 0) {   // site 0: cos(phi^theta) of its mu = 0 link
+            const double2 A = lds_d2<0>(uo), H = lds_d2<0>(so + (unsigned)SS);
+            const double tx = fma(A.x, H.x, -A.y * H.y), ty = fma(A.x, H.y, A.y * H.x);
+            a.fprint[idx] = fma(gx.x, tx, gx.y * ty);
+          }
+        }
+        ++c_pass;
+        for (int o = 16; o > 0; o >>= 1) {
+          r = dmax_pos(r, __shfl_xor_sync(0xffffffffu, r, o));
+          Fp += __shfl_xor_sync(0xffffffffu, Fp, o);
+        }
+        const bool pass = dless_pos(r, a.eps);
+        if (pass && h == 0) {
+          a.F[idx] = Fp;
+          a.resid[idx] = r;
+          a.status[idx] = kConverged;
+          ++c_conv;
+        }
+        return pass;
+    };
+    // after a rejected FP64 pass: the FP64 image split back into double-float
+    auto back_to_df = [&]() {
+#pragma unroll 1
+      for (int i = 0; i < 2 * L; ++i) {
+        const unsigned sa = s_st + 16u * own_el(i / L) + (unsigned)(i % L) * SS;
+        const double2 v = lds_d2<0>(sa);
+        const float xh = __double2float_rn(v.x), yh = __double2float_rn(v.y);
+        sts_f4<0>(sa, make_float4(xh, yh, __double2float_rn(v.x - (double)xh),
+                                  __double2float_rn(v.y - (double)yh)));
+      }
+      __syncwarp();
+    };
     if (st32 == kConverged && use_df) {
       float r_prev = 3.4e38f;
       const int inner_cap = a.inner_max;
-      bool dconv = false;
+      bool dconv = false, verify = false;
       for (int it = 0;; ++it) {
+        if (verify) {   // the FP64 pass in place of the double-float check
+          verify = false;
+          if (fp64_pass()) { ok = true; break; }
+          back_to_df();
+        }
         // double-float divergence of the lane's sites (order of df_divergence)
         float rf = 0.f;
 #pragma unroll 1
@@ -1643,72 +1729,11 @@ __global__ void __launch_bounds__(32 * TEAMS, 1) polish_pairs_kernel(const Polis
           sts_f4<0>(sa, df_rotate(lds_f4<0>(sa), fminf(fmaxf(t, -0.2f), 0.2f)));
         }
         __syncwarp();
+        // a step taken from max div^2 < 1e-16 (the second, typically) lands
+        // below eps: check that with the FP64 pass directly
+        verify = r_prev < 1e-16f;
       }
-      if (dconv) {
-        // FP64 image in place (the last reduction ended every lane's double-float
-        // reads), then one FP64 pass: residual, functional, fingerprint, copy
-#pragma unroll 1
-        for (int i = 0; i < 2 * L; ++i) {
-          const unsigned sa = s_st + 16u * own_el(i / L) + (unsigned)(i % L) * SS;
-          const float4 v = lds_f4<0>(sa);
-          sts_d2<0>(sa, make_double2(f2d_bits(v.x) + f2d_bits(v.z), f2d_bits(v.y) + f2d_bits(v.w)));
-        }
-        __syncwarp();
-        double2 gc;
-        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(gc.x), "=d"(gc.y) : "r"(st_last));
-        double r = 0.0, Fp = 0.0;
-#pragma unroll 1
-        for (int i = 0; i < 2 * L; ++i) {
-          const int P = i / L, K = i % L;
-          const unsigned e = own_el(P);
-          const unsigned so = s_st + 16u * e, uo = s_u64 + 16u * e + (unsigned)(K * D) * SS;
-          double fx = 0.0, fy = 0.0, bx = 0.0, by = 0.0;
-#pragma unroll
-          for (int mu = 0; mu < D; ++mu) {
-            double2 A, H, B, G;
-            if (mu == 0) {
-              A = lds_d2<0>(uo);
-              H = lds_d2<0>(so + (unsigned)((K + 1) % L) * SS);
-              B = lds_d2<0>(s_u64 + 16u * e + (unsigned)(((K + L - 1) % L) * D) * SS);
-              G = lds_d2<0>(so + (unsigned)((K + L - 1) % L) * SS);
-            } else {
-              const unsigned ep16 = 4u * (nbp_dl(P, mu) - s_dl), em16 = 4u * (nbm_dl(P, mu) - s_dl);
-              A = lds_d2<0>(uo + (unsigned)mu * SS);
-              H = lds_d2<0>(s_st + ep16 + (unsigned)K * SS);
-              B = lds_d2<0>(s_u64 + em16 + (unsigned)(K * D + mu) * SS);
-              G = lds_d2<0>(s_st + em16 + (unsigned)K * SS);
-            }
-            fx = fma(A.x, H.x, fx); fx = fma(-A.y, H.y, fx);
-            fy = fma(A.x, H.y, fy); fy = fma(A.y, H.x, fy);
-            bx = fma(B.x, G.x, bx); bx = fma(B.y, G.y, bx);
-            by = fma(B.x, G.y, by); by = fma(-B.y, G.x, by);
-          }
-          const double2 gx = lds_d2<0>(so + (unsigned)K * SS);
-          const double dv = fma(gx.x, fy + by, -gx.y * (fx + bx));
-          r = dmax_pos(r, dv * dv);
-          Fp += (double)D - fma(gx.x, fx, gx.y * fy);
-          const int x = K + L * (P ? line[1] : line[0]);
-          a.config[(size_t)idx * V + x] =
-              make_double2(fma(gx.x, gc.x, gx.y * gc.y), fma(gx.y, gc.x, -gx.x * gc.y));
-          if (x == 0) {   // site 0: cos(phi^theta) of its mu = 0 link
-            const double2 A = lds_d2<0>(uo), H = lds_d2<0>(so + (unsigned)SS);
-            const double tx = fma(A.x, H.x, -A.y * H.y), ty = fma(A.x, H.y, A.y * H.x);
-            a.fprint[idx] = fma(gx.x, tx, gx.y * ty);
-          }
-        }
-        ++c_pass;
-        for (int o = 16; o > 0; o >>= 1) {
-          r = dmax_pos(r, __shfl_xor_sync(0xffffffffu, r, o));
-          Fp += __shfl_xor_sync(0xffffffffu, Fp, o);
-        }
-        ok = dless_pos(r, a.eps);
-        if (ok && h == 0) {
-          a.F[idx] = Fp;
-          a.resid[idx] = r;
-          a.status[idx] = kConverged;
-          ++c_conv;
-        }
-      }
+      if (dconv) ok = fp64_pass();
     }
     if (!ok && h == 0) a.redo[atomicAdd(a.n_redo, 1ULL)] = (unsigned)idx;
     __syncwarp();
