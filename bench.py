@@ -43,7 +43,7 @@ FP64_NOMINAL_TFLOPS = 1.25          # B300 dense FP64 (DFMA = 2 flops)
 # capture of the 65536-start 4^4 case recorded under profiles/ (None = not
 # captured for the current kernel)
 TRAFFIC_POLISH_PER_START = (1.345e8 + 2.173e8) / 65536      # profiles/polish_kernel_4d_L4.md (line polish)
-TRAFFIC_RELAX_PER_START = (6.73e5 + 8.264e7) / 65536        # profiles/relax32_lines_4d_L4.md
+TRAFFIC_RELAX_PER_START = (9.91e4 + 7.4575e7) / 65536       # profiles/relax32_sheet_4d_L4.md
 
 
 def parse():
@@ -505,7 +505,10 @@ def run_ours(args):
     # polish hands back (near-singular Faddeev-Popov operators), whose single-
     # warp runs form a latency tail that other orbits' kernels fill in a batch
     dom = max((k for k in stage_ms if k != "polish_redo"), key=stage_ms.get)
-    fp32_per_update = 8 * d + 11 + (8 * d + 3) / ce
+    # FP32 pipe ops per site update: 8d for the staple's 2d complex products,
+    # 11 to blend and renormalise, and 3 per site at a check (the residual
+    # reuses the update's staple: dv = Re g Im S - Im g Re S, squared)
+    fp32_per_update = 8 * d + 11 + 3 / ce
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     fp64_peak = FP64_NOMINAL_TFLOPS / 2.0                        # DFMA per second, 1e12
     # DRAM bytes per start from the ncu capture of the small case (65536 starts),
@@ -514,7 +517,7 @@ def run_ours(args):
     n_launch_starts = args.starts
     if dom == "relax_fp32":
         achieved = rs["site_updates_fp32"] * fp32_per_update / (stage_ms[dom] / 1e3) / 1e12
-        roof = {"kernel": "relax32_lines_kernel<4,4>", "bound": "alu", "achieved": achieved,
+        roof = {"kernel": "relax32_sheet_kernel<8,1>", "bound": "alu", "achieved": achieved,
                 "peak": fp32_peak, "unit": "TOP/s (FP32 pipe ops)", "frac": achieved / fp32_peak}
     elif dom == "polish_fp64":
         # algorithmic FP32 pipe ops per site: 12 (8d + 2) + 2 per double-float

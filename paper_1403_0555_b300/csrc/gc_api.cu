@@ -708,11 +708,11 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     if (ev) GC_CUDA(cudaEventRecord(ev[0], s));
     const bool line_variant = mixed && opt.relax_variant != GC_RELAX_GENERIC;
     if (line_variant && d == 4 && o->L == 4) {
-      constexpr int kTeams = 4;
-      auto k = gc::relax32_lines_kernel<4, 4, kTeams>;
-      const size_t sm = gc::relax32_lines_smem<4, 4, kTeams>();
-      if (int rc = launch_grid(k, 64 * kTeams, sm, kTeams, b, &grid)) return rc;
-      k<<<grid, 64 * kTeams, sm, s>>>(ra);
+      constexpr int kWarps = 8;    // 224 registers: two warps per SM sub-partition
+      auto k = gc::relax32_sheet_kernel<kWarps, 1>;
+      const size_t sm = gc::relax32_sheet_smem<kWarps>();
+      if (int rc = launch_grid(k, 32 * kWarps, sm, kWarps, b, &grid)) return rc;
+      k<<<grid, 32 * kWarps, sm, s>>>(ra);
       ++o->launches;
     } else if (mixed && opt.relax_variant != GC_RELAX_GENERIC && d == 3 && o->L == 8) {
       constexpr int kTeams = 4;

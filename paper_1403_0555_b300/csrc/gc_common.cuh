@@ -61,6 +61,15 @@ __device__ __forceinline__ double2 random_unit(uint64_t seed, uint64_t orbit_id,
   }
 }
 
+// 1/sqrt(x) by the special-function unit's approximation, subnormals flushed
+// (PTX rsqrt.approx.ftz.f32).  Every caller passes a normal x
+// (at least 1e-30).
+__device__ __forceinline__ float rsqrt_sfu(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // The same construction in FP32 (bulk phase of the mixed path): the candidate
 // points are the top 24 bits of the same Philox words, so a start is the FP64
 // start to FP32 precision (an acceptance decision can differ only when

@@ -149,14 +149,14 @@ struct Fast32 {
                                                 int V, const RelaxArgs& a) {
     const R2 S = staple(u, g, nbp[p], p, d, V);
     const float n2 = fmaf(S.x, S.x, S.y * S.y);
-    if (!(n2 > 0.f)) return;
-    const float r = rsqrtf(n2) * a.omega32;
+    if (!(n2 > 1e-30f)) return;      // a vanishing staple leaves the site as it is
+    const float r = rsqrt_sfu(n2) * a.omega32;
     const R2 gx = g[p];
     const float vx = fmaf(S.x, r, a.om1_32 * gx.x);
     const float vy = fmaf(S.y, r, a.om1_32 * gx.y);
     const float m2 = fmaf(vx, vx, vy * vy);
-    if (m2 > 0.f) {
-      const float q = rsqrtf(m2);
+    if (m2 > 1e-30f) {
+      const float q = rsqrt_sfu(m2);
       g[p] = make_float2(vx * q, vy * q);
     }
   }
@@ -759,11 +759,11 @@ __device__ __noinline__ int relax32_fallback(const PolishTeam t, const float4* u
       for (int p = beg + t.tl; p < end; p += t.T) {
         const float2 S = staple32(p);
         const float n2 = fmaf(S.x, S.x, S.y * S.y);
-        if (!(n2 > 0.f)) continue;
-        const float rr = rsqrtf(n2) * om;
+        if (!(n2 > 1e-30f)) continue;
+        const float rr = rsqrt_sfu(n2) * om;
         const float2 gx = g32[p];
         const float vx = fmaf(S.x, rr, om1 * gx.x), vy = fmaf(S.y, rr, om1 * gx.y);
-        const float q = rsqrtf(fmaf(vx, vx, vy * vy));
+        const float q = rsqrt_sfu(fmaxf(fmaf(vx, vx, vy * vy), 1e-30f));
         g32[p] = make_float2(vx * q, vy * q);
       }
       __syncwarp(t.mask);
@@ -1022,9 +1022,14 @@ __global__ void __launch_bounds__(512, 1) polish_kernel(const PolishArgs a) {
 // and all site loops unroll at compile time.  A thread keeps its line's gauge
 // field and all the links touching it in registers: neighbours along axis 0
 // never leave the thread, and neighbours along the other axes are read from
-// the team's shared copy, stored [x_0][parity][h] so that every warp-wide
-// access touches 32 distinct 8-byte words.  Per site update: 8D + 11 FP32 ops,
-// 2 MUFU, 2(D-1) shared loads and 1 store.
+// the team's shared copy.  The two sites x_0 = k and k + L/2 of a line have
+// the same colour (L/2 even) and are updated together: their values are held
+// as packed pairs (re of both, im of both), so each FP32 step is one f32x2
+// instruction, and they share one 16-byte slot of the shared copy, stored
+// [slot k][parity][h] so that every quarter-warp access touches 8 distinct
+// 16-byte words.  Per pair of site updates: 8D + 13 f32x2 ops, 4 MUFU,
+// 2(D-1) 16-byte shared loads and 1 store (per site: 8D + 11 FP32 ops after
+// the paired form's two extra exact subtractions are taken away).
 //
 // Residual (exact, at no extra sweep): for the last colour, div = Im[conj(g) S]
 // is taken right after the update with the S of that update; for colour 0 it
@@ -1064,15 +1069,50 @@ __device__ __forceinline__ void sts_f2(unsigned base, float2 v) {
   asm volatile("st.shared.v2.f32 [%0+%1], {%2, %3};" ::"r"(base), "n"(OFF), "f"(v.x), "f"(v.y) : "memory");
 }
 
-// A fresh random start for the L sites of one line, written to shared memory
-// at byte address `dst` + k*stride.  Kept out of line: start generation is
-// rare next to the sweeps, and inlining the Philox rounds per site would
+template <int OFF>
+__device__ __forceinline__ float4 lds_f4(unsigned base) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+%5];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(base), "n"(OFF));
+  return v;
+}
+template <int OFF>
+__device__ __forceinline__ void sts_f4(unsigned base, float4 v) {
+  asm volatile("st.shared.v4.f32 [%0+%1], {%2, %3, %4, %5};" ::"r"(base), "n"(OFF), "f"(v.x),
+               "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
+}
+
+// Two sites of one line, x_0 = k and x_0 = k + L/2, as packed FP32 pairs so
+// that each arithmetic step on both is one f32x2 instruction:
+// re = (Re z_k, Re z_{k+L/2}), im = (Im z_k, Im z_{k+L/2}).
+struct SitePair {
+  float2 re, im;
+};
+__device__ __forceinline__ float2 bcast2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ SitePair swapped(const SitePair& p) {
+  return {make_float2(p.re.y, p.re.x), make_float2(p.im.y, p.im.x)};
+}
+__device__ __forceinline__ SitePair site_pair(float4 v) {
+  return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+__device__ __forceinline__ float4 packed(const SitePair& p) {
+  return make_float4(p.re.x, p.re.y, p.im.x, p.im.y);
+}
+
+// A fresh random start for the L sites of one line, written to the team's
+// shared copy in the paired layout: site x_0 = k sits in slot k mod (L/2)
+// (byte address `dst` + slot * `slot_bytes`), real part at float k / (L/2),
+// imaginary part at float 2 + k / (L/2).  Kept out of line: start generation
+// is rare next to the sweeps, and inlining the Philox rounds per site would
 // crowd the sweep loop out of the instruction cache.
 __device__ __noinline__ void line_start32(uint64_t seed, uint64_t orbit_id, uint64_t start,
-                                          int first_site, int L, unsigned dst, unsigned stride) {
+                                          int first_site, int L, unsigned dst, unsigned slot_bytes) {
+  const int H = L / 2;
   for (int k = 0; k < L; ++k) {
     const float2 v = random_unit32(seed, orbit_id, start, (uint64_t)(first_site + k));
-    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(dst + k * stride), "f"(v.x), "f"(v.y) : "memory");
+    const unsigned p = dst + (unsigned)(k % H) * slot_bytes + 4u * (unsigned)(k / H);
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(p), "f"(v.x) : "memory");
+    asm volatile("st.shared.f32 [%0+8], %1;" ::"r"(p), "f"(v.y) : "memory");
   }
 }
 
@@ -1104,16 +1144,30 @@ __device__ inline int half_of(int l) {
   return k;
 }
 
+// f32x2 subtraction (PTX sub.rn.f32x2), a - b per half
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
 template <int D, int L, int TEAMS>
-__global__ void __launch_bounds__(LineGeom<D, L>::NL * TEAMS, (D == 4 ? 2 : 1)) relax32_lines_kernel(const RelaxArgs a) {
+__global__ void __launch_bounds__(LineGeom<D, L>::NL * TEAMS, 1) relax32_lines_kernel(const RelaxArgs a) {
   using LG = LineGeom<D, L>;
-  constexpr int NL = LG::NL, NLH = LG::NLH, V = LG::V, NW = NL / 32;
+  constexpr int NL = LG::NL, NLH = LG::NLH, V = LG::V, NW = NL / 32, H = L / 2;
+  static_assert(H % 2 == 0, "the paired sites x_0 = k and k + L/2 must share a colour");
+  constexpr int SLOT = 2 * NLH * 16;          // bytes from slot k to slot k + 1 of a team's copy
   extern __shared__ __align__(16) unsigned char smem[];
   const int team = threadIdx.x / NL, tt = threadIdx.x % NL;
   const int q = tt / NLH, h = tt % NLH;      // q is uniform across each warp
   const int bar_id = 1 + team;
-  float2* gs = reinterpret_cast<float2*>(smem) + (size_t)team * V;    // [x0][parity][h]
-  float* red = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem) + (size_t)TEAMS * V) + team * 32;
+  float4* gs = reinterpret_cast<float4*>(smem) + (size_t)team * (V / 2);   // [slot][parity][h]
+  float* red = reinterpret_cast<float*>(reinterpret_cast<float4*>(smem) + (size_t)TEAMS * (V / 2)) + team * 32;
   long long* tidx = reinterpret_cast<long long*>(red + 16);
 
   const int l = line_of<D, L>(q, h);
@@ -1139,35 +1193,41 @@ __global__ void __launch_bounds__(LineGeom<D, L>::NL * TEAMS, (D == 4 ? 2 : 1)) 
     }
   }
   const int own = q * NLH + h;
-  // per-thread 32-bit shared addresses; site x0 = K of a line sits K*2*NLH*8 bytes further
+  // per-thread 32-bit shared addresses of slot 0; slot k sits k*SLOT bytes further
   unsigned snb[D], snm[D];
   const unsigned sgs = (unsigned)__cvta_generic_to_shared(gs);
 #pragma unroll
-  for (int mu = 0; mu < D; ++mu) { snb[mu] = sgs + 8u * nbp[mu]; snm[mu] = sgs + 8u * nbm[mu]; }
-  const unsigned sown = sgs + 8u * own;
-  // links touching the line, in registers: uf[k][mu] = u_{x,mu}, ub[k][mu] =
-  // u_{x-mu,mu} for mu >= 1 (for mu = 0 that is uf[k-1][0])
-  float2 uf[L][D], ub[L][D];
+  for (int mu = 0; mu < D; ++mu) { snb[mu] = sgs + 16u * nbp[mu]; snm[mu] = sgs + 16u * nbm[mu]; }
+  const unsigned sown = sgs + 16u * own;
+  // links touching the line, in registers, paired like the sites:
+  // af[k][mu] = u_{x,mu} and ab[k][mu] = u_{x-mu,mu} (mu >= 1) at x_0 = k, k + H;
+  // the axis-0 backward links are af[k-1][0], and for slot 0 the links at
+  // x_0 = L-1, H-1, which are af[H-1][0] with its halves exchanged
+  SitePair af[H][D], ab[H][D];
 #pragma unroll
-  for (int k = 0; k < L; ++k) {
-    const int x = k + L * l;
+  for (int k = 0; k < H; ++k) {
 #pragma unroll
     for (int mu = 0; mu < D; ++mu) {
-      uf[k][mu] = a.links32[x * D + mu];
+      const int x0 = k + L * l, x1 = x0 + H;
+      const float2 u0 = a.links32[x0 * D + mu], u1 = a.links32[x1 * D + mu];
+      af[k][mu] = {make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
       if (mu > 0) {
         int s = 1;
 #pragma unroll
         for (int m = 1; m < mu; ++m) s *= L;
-        const int xm = x + (((cl[mu] + L - 1) % L) - cl[mu]) * (s * L);
-        ub[k][mu] = a.links32[xm * D + mu];
+        const int dm = (((cl[mu] + L - 1) % L) - cl[mu]) * (s * L);
+        const float2 b0 = a.links32[(x0 + dm) * D + mu], b1 = a.links32[(x1 + dm) * D + mu];
+        ab[k][mu] = {make_float2(b0.x, b1.x), make_float2(b0.y, b1.y)};
       } else {
-        ub[k][0] = make_float2(0.f, 0.f);
+        ab[k][0] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
       }
     }
   }
-  const float om = a.omega32, om1 = a.om1_32;
+  // blend weights: the move (1 - omega) g + omega S/|S| scaled by 1/omega
+  // (omega > 0; the renormalisation removes the scale)
+  const float2 cg = bcast2(a.om1_32 / a.omega32), tiny = bcast2(1e-30f);
 
-  float2 g[L];
+  SitePair g[H];
   unsigned my_sweeps = 0, my_conv = 0, my_nconv = 0;   // thread 0's, per kernel
   auto fetch = [&]() -> long long {
     if (tt == 0) *tidx = (long long)atomicAdd(a.work_ctr, 1ULL);
@@ -1178,94 +1238,99 @@ __global__ void __launch_bounds__(LineGeom<D, L>::NL * TEAMS, (D == 4 ? 2 : 1)) 
   };
   // new start: generated into the team's shared copy; g is reloaded after the
   // caller's barrier by `reload`
-  auto init = [&](long long idx) {
-    line_start32(a.seed, a.orbit_id, a.start0 + idx, L * l, L, sown, 2u * NLH * 8u);
-  };
+  auto init = [&](long long idx) { line_start32(a.seed, a.orbit_id, a.start0 + idx, L * l, L, sown, SLOT); };
   auto reload = [&]() {
-    static_for<L>([&](auto KC) { g[decltype(KC)::value] = lds_f2<decltype(KC)::value * 2 * NLH * 8>(sown); });
+    static_for<H>([&](auto KC) { g[decltype(KC)::value] = site_pair(lds_f4<decltype(KC)::value * SLOT>(sown)); });
   };
-  // staple of the line's site x0 = K (compile time); other lines from shared memory
-  auto staple = [&](auto KC, float& sx, float& sy) {
+  // staples of slot K (compile time): the axis-0 neighbours are the line's own
+  // sites (slot K+1 and K-1, across the ends with halves exchanged), the others
+  // come from the shared copy, one 16-byte load per neighbour line.
+  //   forward  u h:       re = u.re h.re - u.im h.im, im = u.re h.im + u.im h.re
+  //   backward conj(u) h: re = u.re h.re + u.im h.im, im = u.re h.im - u.im h.re
+  // summed in six chains (three per direction), the subtracted products apart
+  auto staple = [&](auto KC, float2& sx, float2& sy) {
     constexpr int K = decltype(KC)::value;
-    const float2 gp = g[(K + 1) % L], gm = g[(K + L - 1) % L];
-    const float2 a0 = uf[K][0], b0 = uf[(K + L - 1) % L][0];
-    // forward (u g) and backward (conj(u) g) terms in separate chains
-    float fx = a0.x * gp.x, fy = a0.x * gp.y;
-    fx = fmaf(-a0.y, gp.y, fx); fy = fmaf(a0.y, gp.x, fy);
-    float bx = b0.x * gm.x, by = b0.x * gm.y;
-    bx = fmaf(b0.y, gm.y, bx); by = fmaf(-b0.y, gm.x, by);
-#pragma unroll
-    for (int mu = 1; mu < D; ++mu) {
-      const float2 hp = lds_f2<K * 2 * NLH * 8>(snb[mu]);
-      const float2 hm = lds_f2<K * 2 * NLH * 8>(snm[mu]);
-      const float2 aa = uf[K][mu], bb = ub[K][mu];
-      fx = fmaf(aa.x, hp.x, fx); fx = fmaf(-aa.y, hp.y, fx);
-      fy = fmaf(aa.x, hp.y, fy); fy = fmaf(aa.y, hp.x, fy);
-      bx = fmaf(bb.x, hm.x, bx); bx = fmaf(bb.y, hm.y, bx);
-      by = fmaf(bb.x, hm.y, by); by = fmaf(-bb.y, hm.x, by);
+    SitePair gp;
+    if constexpr (K + 1 < H) gp = g[K + 1]; else gp = swapped(g[0]);
+    // backward axis-0 neighbour: slot K-1; for slot 0 the sites x_0 = L-1 and
+    // H-1 (slot H-1 with its halves exchanged), where the products are taken
+    // unexchanged and their halves exchanged afterwards
+    constexpr int KB = (K >= 1) ? K - 1 : H - 1;
+    const SitePair& gm = g[KB];
+    const SitePair& ub = af[KB][0];
+    const SitePair& uf = af[K][0];
+    float2 xp = __fmul2_rn(uf.re, gp.re), xm = __fmul2_rn(uf.im, gp.im);
+    float2 yp = __ffma2_rn(uf.im, gp.re, __fmul2_rn(uf.re, gp.im));
+    float2 xb = __ffma2_rn(ub.im, gm.im, __fmul2_rn(ub.re, gm.re));
+    float2 yb = __fmul2_rn(ub.re, gm.im), ym = __fmul2_rn(ub.im, gm.re);
+    if constexpr (K == 0) {
+      xb = make_float2(xb.y, xb.x);
+      yb = make_float2(yb.y, yb.x);
+      ym = make_float2(ym.y, ym.x);
     }
-    sx = fx + bx;
-    sy = fy + by;
-  };
-  auto blend = [&](float2 gx, float sx, float sy) -> float2 {
-    // S = 0 exactly has probability zero; the clamp only keeps it finite
-    const float n2 = fmaxf(fmaf(sx, sx, sy * sy), 1e-30f);
-    const float r = rsqrtf(n2) * om;
-    const float vx = fmaf(sx, r, om1 * gx.x), vy = fmaf(sy, r, om1 * gx.y);
-    const float qn = rsqrtf(fmaf(vx, vx, vy * vy));
-    return make_float2(vx * qn, vy * qn);
-  };
-  // colour-0 sites of a parity-Q line: x0 = 2j + Q.  Computes the new values
-  // (not committed) and, if `pending`, the squared divergences before the move.
-  float2 gn[L / 2];
-  auto colour0 = [&](auto QC, bool pend) -> float {
-    constexpr int Q = decltype(QC)::value;
-    float r0 = 0.f;
-    static_for<L / 2>([&](auto JC) {
-      constexpr int K = 2 * decltype(JC)::value + Q;
-      float sx, sy;
-      staple(std::integral_constant<int, K>{}, sx, sy);
-      const float2 gx = g[K];
-      if (pend) { const float dv = fmaf(gx.x, sy, -gx.y * sx); r0 = fmaxf(r0, dv * dv); }
-      gn[decltype(JC)::value] = blend(gx, sx, sy);
+    static_for<D - 1>([&](auto MC) {
+      constexpr int mu = decltype(MC)::value + 1;
+      const SitePair hp = site_pair(lds_f4<K * SLOT>(snb[mu]));
+      const SitePair hm = site_pair(lds_f4<K * SLOT>(snm[mu]));
+      const SitePair& A = af[K][mu];
+      const SitePair& B = ab[K][mu];
+      xp = __ffma2_rn(A.re, hp.re, xp);
+      xm = __ffma2_rn(A.im, hp.im, xm);
+      yp = __ffma2_rn(A.re, hp.im, yp);
+      yp = __ffma2_rn(A.im, hp.re, yp);
+      xb = __ffma2_rn(B.re, hm.re, xb);
+      xb = __ffma2_rn(B.im, hm.im, xb);
+      yb = __ffma2_rn(B.re, hm.im, yb);
+      ym = __ffma2_rn(B.im, hm.re, ym);
     });
-    return r0;
+    sx = __fadd2_rn(fsub2(xp, xm), xb);
+    sy = fsub2(__fadd2_rn(yp, yb), ym);
   };
-  // colour-0 update committed at once (sweeps with no check pending)
-  auto colour0_direct = [&](auto QC) {
-    constexpr int Q = decltype(QC)::value;
-    static_for<L / 2>([&](auto JC) {
-      constexpr int K = 2 * decltype(JC)::value + Q;
-      float sx, sy;
+  // overrelaxed move of both sites: ((1 - omega)/omega) g + S/|S|, renormalised
+  auto blend = [&](const SitePair& gx, float2 sx, float2 sy) -> SitePair {
+    // S = 0 or v = 0 exactly has probability zero; the 1e-30 only keeps the
+    // reciprocal square roots finite
+    const float2 n2 = __ffma2_rn(sx, sx, __ffma2_rn(sy, sy, tiny));
+    const float2 r = make_float2(rsqrt_sfu(n2.x), rsqrt_sfu(n2.y));
+    const float2 vx = __ffma2_rn(sx, r, __fmul2_rn(cg, gx.re));
+    const float2 vy = __ffma2_rn(sy, r, __fmul2_rn(cg, gx.im));
+    const float2 m2 = __ffma2_rn(vx, vx, __ffma2_rn(vy, vy, tiny));
+    const float2 qn = make_float2(rsqrt_sfu(m2.x), rsqrt_sfu(m2.y));
+    return {__fmul2_rn(vx, qn), __fmul2_rn(vy, qn)};
+  };
+  // larger squared divergence Im[conj(v) S]^2 of the two sites
+  auto div2 = [&](const SitePair& v, float2 sx, float2 sy) -> float {
+    const float2 dv = fsub2(__fmul2_rn(v.re, sy), __fmul2_rn(v.im, sx));
+    const float2 d2 = __fmul2_rn(dv, dv);
+    return fmaxf(d2.x, d2.y);
+  };
+  auto commit = [&](auto QC, auto CC) {
+    constexpr int Q = decltype(QC)::value, C = decltype(CC)::value;
+    static_for<H / 2>([&](auto JC) {
+      constexpr int K = 2 * decltype(JC)::value + ((C + Q) & 1);
+      sts_f4<K * SLOT>(sown, packed(g[K]));
+    });
+  };
+  // Colour c of a parity-Q line: slots K = (c + Q) mod 2, + 2, ...  All staples
+  // and moves come before the phase's stores.  `before`: squared divergences
+  // before the move (colour 0 of a pending check; the new values then stay in
+  // registers, so that the shared copy still holds the checked state until the
+  // check is decided), `after`: after it.
+  auto phase = [&](auto QC, auto CC, bool before, bool after, bool store) -> float {
+    constexpr int Q = decltype(QC)::value, C = decltype(CC)::value;
+    float rr = 0.f;
+    static_for<H / 2>([&](auto JC) {
+      constexpr int K = 2 * decltype(JC)::value + ((C + Q) & 1);
+      float2 sx, sy;
       staple(std::integral_constant<int, K>{}, sx, sy);
+      if (before) rr = fmaxf(rr, div2(g[K], sx, sy));
       g[K] = blend(g[K], sx, sy);
-      sts_f2<K * 2 * NLH * 8>(sown, g[K]);
+      if (after) rr = fmaxf(rr, div2(g[K], sx, sy));
     });
+    if (store) commit(QC, CC);
+    return rr;
   };
-  auto commit0 = [&](auto QC) {
-    constexpr int Q = decltype(QC)::value;
-    static_for<L / 2>([&](auto JC) {
-      constexpr int K = 2 * decltype(JC)::value + Q;
-      g[K] = gn[decltype(JC)::value];
-      sts_f2<K * 2 * NLH * 8>(sown, g[K]);
-    });
-  };
-  // colour-1 sites x0 = 2j + 1 - Q; squared divergences after the move if `check`
-  auto colour1 = [&](auto QC, bool chk) -> float {
-    constexpr int Q = decltype(QC)::value;
-    float r1 = 0.f;
-    static_for<L / 2>([&](auto JC) {
-      constexpr int K = 2 * decltype(JC)::value + 1 - Q;
-      float sx, sy;
-      staple(std::integral_constant<int, K>{}, sx, sy);
-      const float2 v = blend(g[K], sx, sy);
-      if (chk) { const float dv = fmaf(v.x, sy, -v.y * sx); r1 = fmaxf(r1, dv * dv); }
-      g[K] = v;
-      sts_f2<K * 2 * NLH * 8>(sown, v);
-    });
-    return r1;
-  };
-  auto warp_max = [&](float v) {
+  auto warp_max = [](float v) {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
   };
@@ -1273,22 +1338,22 @@ __global__ void __launch_bounds__(LineGeom<D, L>::NL * TEAMS, (D == 4 ? 2 : 1)) 
   // the whole sweep loop is instantiated per parity (warp-uniform), so no
   // branch on q remains inside it
   auto run = [&](auto QC) {
+    using C0 = std::integral_constant<int, 0>;
+    using C1 = std::integral_constant<int, 1>;
     long long idx = fetch();
     bool live = idx < a.n;
     if (live) init(idx);
     team_bar(bar_id, NL);
     if (live) reload();
     int sweeps = 0;
-    int until_check = a.check_every;   // countdown to the next checked sweep
+    int until = a.check_every;         // countdown to the next checked sweep
     bool pending = false;              // a checked sweep waits for its colour-0 half
     float r1 = 0.f;
     while (live) {
-      if (!pending) {
-        colour0_direct(QC);
-      } else {
-        float r0 = colour0(QC, true);
-        r0 = warp_max(fmaxf(r0, r1));
-        if ((tt & 31) == 0) red[tt >> 5] = r0;
+      const float r0 = phase(QC, C0{}, pending, false, !pending);
+      if (pending) {
+        const float v = warp_max(fmaxf(r0, r1));
+        if ((tt & 31) == 0) red[tt >> 5] = v;
         team_bar(bar_id, NL);
         float r = red[0];
 #pragma unroll
@@ -1297,13 +1362,17 @@ __global__ void __launch_bounds__(LineGeom<D, L>::NL * TEAMS, (D == 4 ? 2 : 1)) 
         pending = false;
         const bool conv = r < a.eps32;
         if (conv || sweeps >= a.max_sweeps) {
-          // keep the checked state, in colour-position order for the polish
-#pragma unroll
-          for (int k = 0; k < L; ++k) {
+          // keep the checked state (the shared copy), in colour-position order
+          // for the polish
+          reload();
+          static_for<L>([&](auto KC) {
+            constexpr int k = decltype(KC)::value;
+            const SitePair& p = g[k % H];
+            const float2 v = (k < H) ? make_float2(p.re.x, p.im.x) : make_float2(p.re.y, p.im.y);
             const int x = k + L * l;
             const int colour = (k + q) & 1;
-            a.state32[(size_t)idx * V + colour * (V / 2) + (x >> 1)] = g[k];
-          }
+            a.state32[(size_t)idx * V + colour * (V / 2) + (x >> 1)] = v;
+          });
           if (tt == 0) {
             a.status[idx] = conv ? kConverged : kNotConverged;
             a.sweeps[idx] = sweeps;
@@ -1314,18 +1383,18 @@ __global__ void __launch_bounds__(LineGeom<D, L>::NL * TEAMS, (D == 4 ? 2 : 1)) 
           live = idx < a.n;
           if (live) init(idx);
           sweeps = 0;
-          until_check = a.check_every;
+          until = a.check_every;
           team_bar(bar_id, NL);
           if (live) reload();
           continue;
         }
-        commit0(QC);
+        commit(QC, C0{});
       }
       team_bar(bar_id, NL);
       ++sweeps;
-      const bool check = --until_check == 0;
-      if (check) until_check = a.check_every;
-      r1 = colour1(QC, check);
+      const bool check = --until == 0;
+      if (check) until = a.check_every;
+      r1 = phase(QC, C1{}, false, check, true);
       pending = check;
       team_bar(bar_id, NL);
     }
@@ -1342,6 +1411,254 @@ __global__ void __launch_bounds__(LineGeom<D, L>::NL * TEAMS, (D == 4 ? 2 : 1)) 
 template <int D, int L, int TEAMS>
 __host__ inline size_t relax32_lines_smem() {
   return (size_t)TEAMS * LineGeom<D, L>::V * sizeof(float2) + (size_t)TEAMS * 32 * sizeof(float);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 bulk relaxation on 4^4, one warp per start (two lines per lane)
+// ---------------------------------------------------------------------------
+// Lane j = a + 2 (x_2 + 4 x_3), a in {0, 1}, owns two lines along axis 0 at
+// the same (x_2, x_3): E at x_1 = s + 2a with s = (x_2 + x_3) mod 2 (line
+// parity x_1 + x_2 + x_3 even) and O at x_1 + 1.  Besides the axis-0
+// neighbours, E's forward and O's backward axis-1 neighbours are the lane's
+// own sites, so a site pair reads 5 neighbour lines from the warp's shared
+// copy instead of 6.  Every other neighbour line of an E line is an O line of
+// another lane and vice versa, so each such read is one uniform 16-byte load
+// per lane, touching 8 distinct 16-byte words per quarter warp.  A colour
+// phase moves E's slot c and O's slot 1 - c: two independent site pairs per
+// lane, in the same paired f32x2 arithmetic as the line kernel.  The start
+// never leaves the warp: phases end in __syncwarp, and the residual's maximum
+// is a shuffle reduction.  Layout of a warp's copy: [slot k][E, O][lane].
+template <int WARPS, int MINB>
+__global__ void __launch_bounds__(32 * WARPS, MINB) relax32_sheet_kernel(const RelaxArgs a) {
+  constexpr int D = 4, L = 4, H = 2, V = 256;
+  constexpr int ROLE = 32 * 16;     // bytes from a slot's E part to its O part
+  constexpr int SLOT = 2 * ROLE;    // bytes from slot 0 to slot 1
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, j = threadIdx.x & 31;
+  const unsigned base = (unsigned)__cvta_generic_to_shared(smem) + (unsigned)warp * (2 * SLOT);
+  const int x2 = (j >> 1) & 3, x3 = j >> 3;
+  const int x1e = ((x2 + x3) & 1) + 2 * (j & 1);
+  const int x1[2] = {x1e, (x1e + 1) & 3};
+  // byte offset (within a warp's copy) of the lane owning line (y1, y2, y3)
+  auto owner = [](int y1, int y2, int y3) -> unsigned {
+    const int t = (y1 - ((y2 + y3) & 1) + 4) & 3;
+    return 16u * (unsigned)((t >> 1) + 2 * (y2 + 4 * y3));
+  };
+  const unsigned own = base + 16u * j;
+  const unsigned a1e = base + owner((x1e + 3) & 3, x2, x3);      // E's backward axis-1 line (an O line)
+  const unsigned a1o = base + owner((x1e + 2) & 3, x2, x3);      // O's forward axis-1 line (an E line)
+  unsigned ap[2][2], am[2][2];                                   // [line][mu - 2], +mu and -mu
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    ap[r][0] = base + owner(x1[r], (x2 + 1) & 3, x3);
+    am[r][0] = base + owner(x1[r], (x2 + 3) & 3, x3);
+    ap[r][1] = base + owner(x1[r], x2, (x3 + 1) & 3);
+    am[r][1] = base + owner(x1[r], x2, (x3 + 3) & 3);
+  }
+  // links, paired like the sites (x_0 = k, k + 2): af[r][k][mu] = u_{x,mu},
+  // ab[r][k][mu] = u_{x-mu,mu} for mu = 2, 3, and for E also mu = 1 (O's
+  // backward axis-1 link is E's forward one, af[E][k][1])
+  SitePair af[2][H][D], ab[2][H][D];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int l = x1[r] + L * (x2 + L * x3);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const int s0 = k + L * l, s1 = s0 + H;
+#pragma unroll
+      for (int mu = 0; mu < D; ++mu) {
+        const float2 u0 = a.links32[s0 * D + mu], u1 = a.links32[s1 * D + mu];
+        af[r][k][mu] = {make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
+        ab[r][k][mu] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        if (mu >= 2 || (mu == 1 && r == 0)) {
+          const int c = mu == 1 ? x1[r] : (mu == 2 ? x2 : x3);
+          const int stride = mu == 1 ? L : (mu == 2 ? L * L : L * L * L);
+          const int dm = (((c + L - 1) % L) - c) * stride;
+          const float2 b0 = a.links32[(s0 + dm) * D + mu], b1 = a.links32[(s1 + dm) * D + mu];
+          ab[r][k][mu] = {make_float2(b0.x, b1.x), make_float2(b0.y, b1.y)};
+        }
+      }
+    }
+  }
+  const float2 cg = bcast2(a.om1_32 / a.omega32), tiny = bcast2(1e-30f);
+
+  SitePair g[2][H];
+  unsigned my_sweeps = 0, my_conv = 0, my_nconv = 0;   // lane 0's, per kernel
+  auto fetch = [&]() -> long long {
+    unsigned long long v = 0;
+    if (j == 0) v = atomicAdd(a.work_ctr, 1ULL);
+    return (long long)__shfl_sync(0xffffffffu, v, 0);
+  };
+  auto init = [&](long long idx) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+      line_start32(a.seed, a.orbit_id, a.start0 + idx, L * (x1[r] + L * (x2 + L * x3)), L,
+                   own + r * ROLE, SLOT);
+  };
+  auto reload = [&]() {
+    static_for<2>([&](auto RC) {
+      static_for<H>([&](auto KC) {
+        constexpr int R = decltype(RC)::value, K = decltype(KC)::value;
+        g[R][K] = site_pair(lds_f4<R * ROLE + K * SLOT>(own));
+      });
+    });
+  };
+  // forward term u h and backward term conj(u) h into the six chains
+  auto fwd = [](const SitePair& u, const SitePair& h, float2& xp, float2& xm, float2& yp) {
+    xp = __ffma2_rn(u.re, h.re, xp);
+    xm = __ffma2_rn(u.im, h.im, xm);
+    yp = __ffma2_rn(u.re, h.im, yp);
+    yp = __ffma2_rn(u.im, h.re, yp);
+  };
+  auto bwd = [](const SitePair& u, const SitePair& h, float2& xb, float2& yb, float2& ym) {
+    xb = __ffma2_rn(u.re, h.re, xb);
+    xb = __ffma2_rn(u.im, h.im, xb);
+    yb = __ffma2_rn(u.re, h.im, yb);
+    ym = __ffma2_rn(u.im, h.re, ym);
+  };
+  // staples of slot K of line R (compile time)
+  auto staple = [&](auto RC, auto KC, float2& sx, float2& sy) {
+    constexpr int R = decltype(RC)::value, K = decltype(KC)::value, N = 1 - R;
+    SitePair gp;
+    if constexpr (K + 1 < H) gp = g[R][K + 1]; else gp = swapped(g[R][0]);
+    constexpr int KB = (K >= 1) ? K - 1 : H - 1;
+    const SitePair& gm = g[R][KB];
+    const SitePair& ub = af[R][KB][0];
+    const SitePair& uf = af[R][K][0];
+    float2 xp = __fmul2_rn(uf.re, gp.re), xm = __fmul2_rn(uf.im, gp.im);
+    float2 yp = __ffma2_rn(uf.im, gp.re, __fmul2_rn(uf.re, gp.im));
+    float2 xb = __ffma2_rn(ub.im, gm.im, __fmul2_rn(ub.re, gm.re));
+    float2 yb = __fmul2_rn(ub.re, gm.im), ym = __fmul2_rn(ub.im, gm.re);
+    if constexpr (K == 0) {      // slot-0 backward axis-0 products were taken unexchanged
+      xb = make_float2(xb.y, xb.x);
+      yb = make_float2(yb.y, yb.x);
+      ym = make_float2(ym.y, ym.x);
+    }
+    // neighbour lines of the other kind from the shared copy
+    const SitePair h2p = site_pair(lds_f4<N * ROLE + K * SLOT>(ap[R][0]));
+    const SitePair h2m = site_pair(lds_f4<N * ROLE + K * SLOT>(am[R][0]));
+    const SitePair h3p = site_pair(lds_f4<N * ROLE + K * SLOT>(ap[R][1]));
+    const SitePair h3m = site_pair(lds_f4<N * ROLE + K * SLOT>(am[R][1]));
+    if constexpr (R == 0) {
+      const SitePair h1m = site_pair(lds_f4<N * ROLE + K * SLOT>(a1e));
+      fwd(af[0][K][1], g[1][K], xp, xm, yp);
+      bwd(ab[0][K][1], h1m, xb, yb, ym);
+    } else {
+      const SitePair h1p = site_pair(lds_f4<N * ROLE + K * SLOT>(a1o));
+      fwd(af[1][K][1], h1p, xp, xm, yp);
+      bwd(af[0][K][1], g[0][K], xb, yb, ym);
+    }
+    fwd(af[R][K][2], h2p, xp, xm, yp);
+    bwd(ab[R][K][2], h2m, xb, yb, ym);
+    fwd(af[R][K][3], h3p, xp, xm, yp);
+    bwd(ab[R][K][3], h3m, xb, yb, ym);
+    sx = __fadd2_rn(fsub2(xp, xm), xb);
+    sy = fsub2(__fadd2_rn(yp, yb), ym);
+  };
+  auto blend = [&](const SitePair& gx, float2 sx, float2 sy) -> SitePair {
+    const float2 n2 = __ffma2_rn(sx, sx, __ffma2_rn(sy, sy, tiny));
+    const float2 r = make_float2(rsqrt_sfu(n2.x), rsqrt_sfu(n2.y));
+    const float2 vx = __ffma2_rn(sx, r, __fmul2_rn(cg, gx.re));
+    const float2 vy = __ffma2_rn(sy, r, __fmul2_rn(cg, gx.im));
+    const float2 m2 = __ffma2_rn(vx, vx, __ffma2_rn(vy, vy, tiny));
+    const float2 qn = make_float2(rsqrt_sfu(m2.x), rsqrt_sfu(m2.y));
+    return {__fmul2_rn(vx, qn), __fmul2_rn(vy, qn)};
+  };
+  auto div2 = [&](const SitePair& v, float2 sx, float2 sy) -> float {
+    const float2 dv = fsub2(__fmul2_rn(v.re, sy), __fmul2_rn(v.im, sx));
+    const float2 d2 = __fmul2_rn(dv, dv);
+    return fmaxf(d2.x, d2.y);
+  };
+  // colour c: E's slot c and O's slot 1 - c.  `before`: squared divergences
+  // before the move (colour 0 of a pending check), else after it (`after`).
+  auto phase = [&](auto CC, bool before, bool after, bool store) -> float {
+    constexpr int C = decltype(CC)::value;
+    float rr = 0.f;
+    float2 sx0, sy0, sx1, sy1;
+    staple(std::integral_constant<int, 0>{}, std::integral_constant<int, C>{}, sx0, sy0);
+    staple(std::integral_constant<int, 1>{}, std::integral_constant<int, 1 - C>{}, sx1, sy1);
+    if (before) rr = fmaxf(div2(g[0][C], sx0, sy0), div2(g[1][1 - C], sx1, sy1));
+    g[0][C] = blend(g[0][C], sx0, sy0);
+    g[1][1 - C] = blend(g[1][1 - C], sx1, sy1);
+    if (after) rr = fmaxf(div2(g[0][C], sx0, sy0), div2(g[1][1 - C], sx1, sy1));
+    if (store) {
+      sts_f4<C * SLOT>(own, packed(g[0][C]));
+      sts_f4<ROLE + (1 - C) * SLOT>(own, packed(g[1][1 - C]));
+    }
+    return rr;
+  };
+  auto warp_max = [](float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+  };
+
+  long long idx = fetch();
+  bool live = idx < a.n;
+  if (live) init(idx);
+  __syncwarp();
+  if (live) reload();
+  int sweeps = 0, until = a.check_every;
+  bool pending = false;
+  float r1 = 0.f;
+  while (live) {
+    const float r0 = phase(std::integral_constant<int, 0>{}, pending, false, !pending);
+    if (pending) {
+      const float r = warp_max(fmaxf(r0, r1));
+      pending = false;
+      const bool conv = r < a.eps32;
+      if (conv || sweeps >= a.max_sweeps) {
+        // keep the checked state (the shared copy), in colour-position order
+        reload();
+        static_for<2>([&](auto RC) {
+          constexpr int R = decltype(RC)::value;
+          const int l = x1[R] + L * (x2 + L * x3);
+          static_for<L>([&](auto KC) {
+            constexpr int k = decltype(KC)::value;
+            const SitePair& p = g[R][k % H];
+            const float2 v = (k < H) ? make_float2(p.re.x, p.im.x) : make_float2(p.re.y, p.im.y);
+            const int x = k + L * l;
+            constexpr int colour = (k + R) & 1;
+            a.state32[(size_t)idx * V + colour * (V / 2) + (x >> 1)] = v;
+          });
+        });
+        if (j == 0) {
+          a.status[idx] = conv ? kConverged : kNotConverged;
+          a.sweeps[idx] = sweeps;
+          my_sweeps += sweeps;
+          if (conv) ++my_conv; else ++my_nconv;
+        }
+        idx = fetch();
+        live = idx < a.n;
+        __syncwarp();
+        if (live) init(idx);
+        __syncwarp();
+        if (live) reload();
+        sweeps = 0;
+        until = a.check_every;
+        continue;
+      }
+      sts_f4<0>(own, packed(g[0][0]));
+      sts_f4<ROLE + SLOT>(own, packed(g[1][1]));
+    }
+    __syncwarp();
+    ++sweeps;
+    const bool check = --until == 0;
+    if (check) until = a.check_every;
+    r1 = phase(std::integral_constant<int, 1>{}, false, check, true);
+    pending = check;
+    __syncwarp();
+  }
+  if (j == 0 && (my_sweeps | my_conv | my_nconv)) {
+    atomicAdd(&a.stats[a.stat_base + 0], (unsigned long long)my_sweeps);
+    atomicAdd(&a.stats[a.stat_base + 1], (unsigned long long)my_sweeps * V);
+    atomicAdd(&a.stats[a.stat_base + 2], (unsigned long long)my_conv);
+    atomicAdd(&a.stats[a.stat_base + 3], (unsigned long long)my_nconv);
+  }
+}
+
+template <int WARPS>
+__host__ inline size_t relax32_sheet_smem() {
+  return (size_t)WARPS * 256 * sizeof(float2);
 }
 
 // ---------------------------------------------------------------------------
@@ -1373,18 +1690,6 @@ struct PolishPairSmem {
   static constexpr size_t bytes(int teams) { return team0 + (size_t)teams * per_team; }
 };
 
-template <int OFF>
-__device__ __forceinline__ float4 lds_f4(unsigned base) {
-  float4 v;
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+%5];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(base), "n"(OFF));
-  return v;
-}
-template <int OFF>
-__device__ __forceinline__ void sts_f4(unsigned base, float4 v) {
-  asm volatile("st.shared.v4.f32 [%0+%1], {%2, %3, %4, %5};" ::"r"(base), "n"(OFF), "f"(v.x),
-               "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
-}
 template <int OFF>
 __device__ __forceinline__ float lds_f1(unsigned base) {
   float v;
