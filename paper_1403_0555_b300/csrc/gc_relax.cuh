@@ -1668,11 +1668,12 @@ __host__ inline size_t relax32_sheet_smem() {
 // The double-float Newton polish of polish_kernel, with every step's
 // arithmetic in the same order.  During the inner solve lane h keeps, for the
 // 2L sites of its two lines, the Newton weights (forward and, off axis 0,
-// backward), the right-hand side, 1/D and the correction in registers:
-// axis-0 neighbours are the lane's own sites, the other neighbours' corrections
-// are read from the team's shared copy [x_0][parity][h], so an inner SOR site
-// update reads 2(D-1) shared words, and the warp synchronises with __syncwarp
-// only.  The residual, rotation and FP64 passes run as loops over the lane's
+// backward), the right-hand side, 1/D and the correction in registers, packed
+// in pairs over the sites x_0 = k and k + L/2: axis-0 neighbours are the
+// lane's own sites, the other neighbours' corrections are read from the team's
+// paired shared copy [k][parity][h], so an inner SOR step on a site pair reads
+// 2(D-1) 8-byte words and runs as f32x2 instructions, and the warp
+// synchronises with __syncwarp only.  The residual, rotation and FP64 passes run as loops over the lane's
 // sites on the shared state (compact code: the whole kernel stays in the
 // instruction cache).  The links, double-float and FP64, sit in shared memory
 // as [x_0][mu][parity][h].  A start this common path does not finish (FP32
@@ -1685,7 +1686,8 @@ struct PolishPairSmem {
   static constexpr size_t u_df = 0;                                         // float4 [L][D][2][NLH]
   static constexpr size_t u_64 = u_df + (size_t)LG::V * D * sizeof(float4);  // double2, same order
   static constexpr size_t team0 = u_64 + (size_t)LG::V * D * sizeof(double2);
-  // per team [x0][parity][h]: state (16 B), correction (4 B), divergence (4 B)
+  // per team: state [x0][parity][h] (16 B), corrections as pairs over x0 = k,
+  // k + L/2 [k][parity][h] (8 B), divergence [x0][parity][h] (4 B)
   static constexpr size_t per_team = (size_t)LG::V * 24;
   static constexpr size_t bytes(int teams) { return team0 + (size_t)teams * per_team; }
 };
@@ -1718,7 +1720,8 @@ __global__ void __launch_bounds__(32 * TEAMS, 1) polish_pairs_kernel(const Polis
   constexpr int NLH = LG::NLH, V = LG::V;
   static_assert(NLH == 32, "one warp holds one line of each parity per lane");
   constexpr int SS = 2 * NLH * 16;   // bytes from site x0 to x0 + 1 of a line: state, links
-  constexpr int SD = 2 * NLH * 4;    //                                          correction
+  constexpr int SD = 2 * NLH * 4;    //                                          divergence
+  constexpr int SD2 = 2 * NLH * 8;   // bytes from slot k to k + 1 of the paired corrections
   extern __shared__ __align__(16) unsigned char smem[];
   const int h = threadIdx.x & 31, team = threadIdx.x >> 5;
   unsigned char* tb = smem + SM::team0 + (size_t)team * SM::per_team;
@@ -1744,7 +1747,7 @@ __global__ void __launch_bounds__(32 * TEAMS, 1) polish_pairs_kernel(const Polis
   const unsigned s_u64 = (unsigned)__cvta_generic_to_shared(smem + SM::u_64);
   // per parity P: the line, and the correction addresses of its neighbour lines
   // (parity 1 - P) along mu >= 1; element e sits at e*16 past the state and
-  // link bases, e*4 past the correction and divergence bases
+  // link bases, e*8 past the correction base and e*4 past the divergence base
   int line[2];
   unsigned dlp[2][D], dlm[2][D];
 #pragma unroll
@@ -1759,8 +1762,8 @@ __global__ void __launch_bounds__(32 * TEAMS, 1) polish_pairs_kernel(const Polis
       t /= L;
       const int lp = l + (((c + 1) % L) - c) * stride;
       const int lm = l + (((c + L - 1) % L) - c) * stride;
-      dlp[P][mu] = s_dl + 4u * ((1 - P) * NLH + half_of<D, L>(lp));
-      dlm[P][mu] = s_dl + 4u * ((1 - P) * NLH + half_of<D, L>(lm));
+      dlp[P][mu] = s_dl + 8u * ((1 - P) * NLH + half_of<D, L>(lp));
+      dlm[P][mu] = s_dl + 8u * ((1 - P) * NLH + half_of<D, L>(lm));
       stride *= L;
     }
   }
@@ -1778,75 +1781,91 @@ __global__ void __launch_bounds__(32 * TEAMS, 1) polish_pairs_kernel(const Polis
   auto nbp_dl = [&](int P, int mu) { return P ? dlp[1][mu] : dlp[0][mu]; };
   auto nbm_dl = [&](int P, int mu) { return P ? dlm[1][mu] : dlm[0][mu]; };
 
-  float b[2][L], Dv[2][L], dl[2][L];
-  float wf[2][L][D], wb[2][L][D];   // w_{x,mu}; w_{x-mu,mu} for mu >= 1
+  // Inner-solve state of the lane's two lines in packed pairs over the sites
+  // x0 = k and k + L/2 (slot k; one colour, see relax32_lines_kernel), so an
+  // SOR step on both is one f32x2 instruction per term and one 8-byte shared
+  // load per neighbour line: right-hand side, 1/D, correction, and the weights
+  // w_{x,mu} (wf) and w_{x-mu,mu} for mu >= 1 (wb).  The axis-0 backward
+  // weights of slot 0, w at x0 = L-1 and H-1, are wf[H-1][0] with its halves
+  // exchanged (w0s).
+  constexpr int H = L / 2;
+  static_assert(H % 2 == 0, "paired sites x0 = k and k + L/2 must share a colour");
+  float2 b2[2][H], Dv2[2][H], dl2[2][H], wf2[2][H][D], wb2[2][H][D], w0s[2];
   unsigned c_newton = 0, c_inner = 0, c_df = 0, c_pass = 0, c_conv = 0;   // lane 0's
+  auto el = [](float2& v, int half) -> float& { return half ? v.y : v.x; };
 
   // Newton weights of the parity-P line from the high parts, 1/D, zero correction
   auto weights = [&](auto PC, float& bd) {
     constexpr int P = decltype(PC)::value;
     const unsigned e = P * NLH + h;
-    const unsigned so = s_st + 16u * e, uo = s_udf + 16u * e, dlo = s_dl + 4u * e, dvo = s_dv + 4u * e;
+    const unsigned so = s_st + 16u * e, uo = s_udf + 16u * e, dlo = s_dl + 8u * e, dvo = s_dv + 4u * e;
     static_for<L>([&](auto KC) {
-      constexpr int K = decltype(KC)::value;
-      b[P][K] = lds_f1<K * SD>(dvo);
+      constexpr int K = decltype(KC)::value, k = K % H, hf = K / H;
+      el(b2[P][k], hf) = lds_f1<K * SD>(dvo);
       const float4 gv = lds_f4<K * SS>(so);
       static_for<D>([&](auto MC) {
         constexpr int mu = decltype(MC)::value;
         const float4 A = lds_f4<(K * D + mu) * SS>(uo);
-        float4 H;
-        if constexpr (mu == 0) H = lds_f4<((K + 1) % L) * SS>(so);
-        else H = lds_f4<K * SS>(s_st + 4u * (dlp[P][mu] - s_dl));
-        const float tx = fmaf(A.x, H.x, -A.y * H.y), ty = fmaf(A.x, H.y, A.y * H.x);
-        wf[P][K][mu] = fmaf(gv.x, tx, gv.y * ty);
+        float4 H4;
+        if constexpr (mu == 0) H4 = lds_f4<((K + 1) % L) * SS>(so);
+        else H4 = lds_f4<K * SS>(s_st + 2u * (dlp[P][mu] - s_dl));
+        const float tx = fmaf(A.x, H4.x, -A.y * H4.y), ty = fmaf(A.x, H4.y, A.y * H4.x);
+        el(wf2[P][k][mu], hf) = fmaf(gv.x, tx, gv.y * ty);
         if constexpr (mu > 0) {   // w_{x-mu,mu} = Re[conj(g_{x-mu}) u_{x-mu,mu} g_x]
-          const unsigned em16 = 4u * (dlm[P][mu] - s_dl);
+          const unsigned em16 = 2u * (dlm[P][mu] - s_dl);
           const float4 B = lds_f4<(K * D + mu) * SS>(s_udf + em16);
           const float4 G = lds_f4<K * SS>(s_st + em16);
           const float sx = fmaf(B.x, gv.x, -B.y * gv.y), sy = fmaf(B.x, gv.y, B.y * gv.x);
-          wb[P][K][mu] = fmaf(G.x, sx, G.y * sy);
+          el(wb2[P][k][mu], hf) = fmaf(G.x, sx, G.y * sy);
         }
       });
     });
+    w0s[P] = make_float2(wf2[P][H - 1][0].y, wf2[P][H - 1][0].x);
     static_for<L>([&](auto KC) {
-      constexpr int K = decltype(KC)::value;
+      constexpr int K = decltype(KC)::value, k = K % H, hf = K / H;
+      constexpr int KM = (K + L - 1) % L;
       float Dd = 0.f;
       static_for<D>([&](auto MC) {
         constexpr int mu = decltype(MC)::value;
-        if constexpr (mu == 0) Dd += wf[P][K][0] + wf[P][(K + L - 1) % L][0];
-        else Dd += wf[P][K][mu] + wb[P][K][mu];
+        if constexpr (mu == 0) Dd += el(wf2[P][k][0], hf) + el(wf2[P][KM % H][0], KM / H);
+        else Dd += el(wf2[P][k][mu], hf) + el(wb2[P][k][mu], hf);
       });
-      Dv[P][K] = Dd > 1e-6f ? __frcp_rn(Dd) : 0.f;
-      bd = fmaxf(bd, fabsf(b[P][K] * Dv[P][K]));
-      dl[P][K] = 0.f;
-      sts_f1<K * SD>(dlo, 0.f);
+      el(Dv2[P][k], hf) = Dd > 1e-6f ? __frcp_rn(Dd) : 0.f;
+      bd = fmaxf(bd, fabsf(el(b2[P][k], hf) * el(Dv2[P][k], hf)));
+    });
+    static_for<H>([&](auto KC) {
+      constexpr int k = decltype(KC)::value;
+      dl2[P][k] = make_float2(0.f, 0.f);
+      sts_f2<k * SD2>(dlo, dl2[P][k]);
     });
   };
-  // one SOR site update of the parity-P line at x0 = K; returns |t - old|
+  // one SOR step on slot k of the parity-P line (both sites, each in the order
+  // of the scalar update: b, axis 0 forward, axis 0 backward, then per mu >= 1
+  // forward and backward); returns max |t - old|
   auto sor = [&](auto PC, auto KC) -> float {
-    constexpr int P = decltype(PC)::value, K = decltype(KC)::value;
-    float acc = b[P][K];
-    static_for<D>([&](auto MC) {
-      constexpr int mu = decltype(MC)::value;
-      if constexpr (mu == 0) {
-        acc = fmaf(wf[P][K][0], dl[P][(K + 1) % L], acc);
-        acc = fmaf(wf[P][(K + L - 1) % L][0], dl[P][(K + L - 1) % L], acc);
-      } else {
-        acc = fmaf(wf[P][K][mu], lds_f1<K * SD>(dlp[P][mu]), acc);
-        acc = fmaf(wb[P][K][mu], lds_f1<K * SD>(dlm[P][mu]), acc);
-      }
+    constexpr int P = decltype(PC)::value, k = decltype(KC)::value;
+    float2 fwd, bwd, wbk;
+    if constexpr (k + 1 < H) fwd = dl2[P][k + 1]; else fwd = make_float2(dl2[P][0].y, dl2[P][0].x);
+    if constexpr (k >= 1) { bwd = dl2[P][k - 1]; wbk = wf2[P][k - 1][0]; }
+    else { bwd = make_float2(dl2[P][H - 1].y, dl2[P][H - 1].x); wbk = w0s[P]; }
+    float2 acc = __ffma2_rn(wf2[P][k][0], fwd, b2[P][k]);
+    acc = __ffma2_rn(wbk, bwd, acc);
+    static_for<D - 1>([&](auto MC) {
+      constexpr int mu = decltype(MC)::value + 1;
+      acc = __ffma2_rn(wf2[P][k][mu], lds_f2<k * SD2>(dlp[P][mu]), acc);
+      acc = __ffma2_rn(wb2[P][k][mu], lds_f2<k * SD2>(dlm[P][mu]), acc);
     });
-    const float t = acc * Dv[P][K], old = dl[P][K];
-    dl[P][K] = fmaf(om, t, om1 * old);
-    sts_f1<K * SD>(s_dl + 4u * (P * NLH + h), dl[P][K]);
-    return fabsf(t - old);
+    const float2 t = __fmul2_rn(acc, Dv2[P][k]), old = dl2[P][k];
+    dl2[P][k] = __ffma2_rn(make_float2(om, om), t, __fmul2_rn(make_float2(om1, om1), old));
+    sts_f2<k * SD2>(s_dl + 8u * (P * NLH + h), dl2[P][k]);
+    return fmaxf(fabsf(t.x - old.x), fabsf(t.y - old.y));
   };
-  // colour C (0 or 1) of both lines: x0 = 2j + (C xor P)
+  // colour C (0 or 1) of both lines: slots k = C xor P, + 2, ...
   auto colour = [&](auto CC, bool last, float& corr) {
     constexpr int C = decltype(CC)::value;
     static_for<2>([&](auto PC) {
       constexpr int P = decltype(PC)::value;
-      static_for<L / 2>([&](auto JC) {
+      static_for<H / 2>([&](auto JC) {
         const float c = sor(PC, std::integral_constant<int, 2 * decltype(JC)::value + (C ^ P)>{});
         if (last) corr = fmaxf(corr, c);
       });
@@ -1900,7 +1919,7 @@ __global__ void __launch_bounds__(32 * TEAMS, 1) polish_pairs_kernel(const Polis
               B = lds_d2<0>(s_u64 + 16u * e + (unsigned)(((K + L - 1) % L) * D) * SS);
               G = lds_d2<0>(so + (unsigned)((K + L - 1) % L) * SS);
             } else {
-              const unsigned ep16 = 4u * (nbp_dl(P, mu) - s_dl), em16 = 4u * (nbm_dl(P, mu) - s_dl);
+              const unsigned ep16 = 2u * (nbp_dl(P, mu) - s_dl), em16 = 2u * (nbm_dl(P, mu) - s_dl);
               A = lds_d2<0>(uo + (unsigned)mu * SS);
               H = lds_d2<0>(s_st + ep16 + (unsigned)K * SS);
               B = lds_d2<0>(s_u64 + em16 + (unsigned)(K * D + mu) * SS);
@@ -1977,7 +1996,7 @@ __global__ void __launch_bounds__(32 * TEAMS, 1) polish_pairs_kernel(const Polis
               B = lds_f4<0>(s_udf + 16u * e + (unsigned)(((K + L - 1) % L) * D) * SS);
               G = lds_f4<0>(so + (unsigned)((K + L - 1) % L) * SS);
             } else {
-              const unsigned ep16 = 4u * (nbp_dl(P, mu) - s_dl), em16 = 4u * (nbm_dl(P, mu) - s_dl);
+              const unsigned ep16 = 2u * (nbp_dl(P, mu) - s_dl), em16 = 2u * (nbm_dl(P, mu) - s_dl);
               A = lds_f4<0>(uo + (unsigned)mu * SS);
               H = lds_f4<0>(s_st + ep16 + (unsigned)K * SS);
               B = lds_f4<0>(s_udf + em16 + (unsigned)(K * D + mu) * SS);
@@ -2030,7 +2049,7 @@ __global__ void __launch_bounds__(32 * TEAMS, 1) polish_pairs_kernel(const Polis
           const int P = i / L, K = i % L;
           const unsigned e = own_el(P);
           const unsigned sa = s_st + 16u * e + (unsigned)K * SS;
-          const float t = lds_f1<0>(s_dl + 4u * e + (unsigned)K * SD);
+          const float t = lds_f1<0>(s_dl + 8u * e + (unsigned)(K % H) * SD2 + 4u * (unsigned)(K / H));
           sts_f4<0>(sa, df_rotate(lds_f4<0>(sa), fminf(fmaxf(t, -0.2f), 0.2f)));
         }
         __syncwarp();
