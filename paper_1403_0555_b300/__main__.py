@@ -3,11 +3,17 @@
     python -m paper_1403_0555_b300 enumerate --dim 4 --L 4 --kappa 0.714 --seed 2 \\
         --starts 65536 --precision mixed
     python -m paper_1403_0555_b300 tables --entries 2:4,4:2 --orbits 100 --mebisamples 4
+    python -m paper_1403_0555_b300 section4 --entries 2:6,3:4 --orbits 100 --mebisamples 4
+    python -m paper_1403_0555_b300 section4 --compare 2:10 --orbits 10 --mebisamples 4 \\
+        --large-mebisamples 256
 
 `enumerate` prints the orbit's statistics as one JSON line; `tables` one line
 per lattice of paper-style statistics over random uniform orbits (the number
 of minima of Table I, the global-minimum functional of Table III and the
-discovery curve of Figs. 1-3).  Orbits are seeded synthetic
+discovery curve of Figs. 1-3).  `section4` prints per lattice the global
+minima (Table III), the relative deviation of the minima from them (Fig. 8)
+and the normalised distribution of the functional (Fig. 7); with --compare,
+the bin-by-bin comparison of two sample sizes (Fig. 5).  Orbits are seeded synthetic
 inputs (orbit_inputs): von Mises(kappa) link angles, or uniform with --kappa 0.
 """
 from __future__ import annotations
@@ -46,7 +52,27 @@ def main(argv=None):
     t.add_argument("--mebisamples", type=float, default=4.0, help="starts per orbit / 1024^2")
     t.add_argument("--omega", type=float, default=1.0)
     t.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    s4 = sub.add_parser("section4", help="distribution of the functional at the minima (Section IV)")
+    s4.add_argument("--entries", default="2:4,3:4", help="comma list of d:N")
+    s4.add_argument("--compare", default=None, help="d:N: compare two sample sizes bin by bin instead")
+    s4.add_argument("--orbits", type=int, default=100)
+    s4.add_argument("--mebisamples", type=float, default=4.0, help="starts per orbit / 1024^2")
+    s4.add_argument("--large-mebisamples", type=float, default=256.0, help="the larger run of --compare")
+    s4.add_argument("--omega", type=float, default=1.0)
+    s4.add_argument("--width", type=float, default=1e-3, help="bin width of the distribution")
     a = p.parse_args(argv)
+    if a.cmd == "section4":
+        from paper_1403_0555_b300.analysis import compare_sample_sizes, section_iv_statistics
+        n = int(a.mebisamples * (1 << 20))
+        if a.compare:
+            d, N = (int(x) for x in a.compare.split(":"))
+            print(json.dumps(compare_sample_sizes(d, N, a.orbits, n, int(a.large_mebisamples * (1 << 20)),
+                                                  a.omega)), flush=True)
+            return
+        for ent in a.entries.split(","):
+            d, N = (int(x) for x in ent.split(":"))
+            print(json.dumps(section_iv_statistics(d, N, a.orbits, n, a.omega, width=a.width)), flush=True)
+        return
     if a.cmd == "tables":
         from paper_1403_0555_b300.analysis import table_statistics
         for ent in a.entries.split(","):
