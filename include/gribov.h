@@ -55,6 +55,12 @@ extern "C" {
 #define GC_RELAX_AUTO 0
 #define GC_RELAX_GENERIC 1
 
+/* dedup modes (gc_options.dedup_mode) */
+#define GC_DEDUP_CONFIG 0   /* distinct canonical configurations (and the F set)   */
+#define GC_DEDUP_F8 1       /* the paper's count only (Section III): the set of
+                               floor(F/(dV) * 1e8) with the starts reaching each;
+                               no configuration table, no first-region test       */
+
 /* per-start status */
 #define GC_START_CONVERGED 1
 #define GC_START_NOT_CONVERGED 2
@@ -93,6 +99,8 @@ typedef struct {
                            precision) (results unchanged); 2 also the sweep-unroll
                            depth (mixed precision: sweeps between residual checks,
                            replacing check_every; results move within tolerance) */
+  int dedup_mode;       /* GC_DEDUP_CONFIG or GC_DEDUP_F8 (applies per call; the
+                           F set is kept in both modes)                           */
 } gc_options;
 
 typedef struct {
@@ -202,6 +210,15 @@ int gc_server_destroy(gc_server s);
  * reaching it), lambda2[n] (NaN when untested), region[n] (GC_REGION_*). */
 int gc_fetch_copies(gc_orbit o, size_t capacity, size_t* n_distinct, double* F, double* theta,
                     uint64_t* first_start, uint64_t* count, double* lambda2, int* region);
+
+/* The paper's set of minima (Section III: minima told apart by F quantised
+ * at 1e-8): the distinct keys floor(F/(dV) * 1e8) of every converged start so
+ * far, in both dedup modes, in increasing order.  n_minima receives their
+ * number; with capacity > 0 the first min(capacity, n) are written: F_norm[i]
+ * = key * 1e-8 (the bin's lower edge) and, when count is not NULL, count[i] =
+ * the starts whose minimum fell in bin i.  Synchronises with the orbit's
+ * stream.  Returns GC_EINVAL for a NULL orbit or n_minima. */
+int gc_fetch_minima_f8(gc_orbit o, size_t capacity, size_t* n_minima, double* F_norm, uint64_t* count);
 
 /* Per-start records of the last gc_enumerate_copies call (needs
  * keep_per_start): starts first .. first+n-1 must lie in that call's range.

@@ -34,6 +34,9 @@ GC_FP_NONE = 3
 GC_RELAX_AUTO = 0
 GC_RELAX_GENERIC = 1
 
+GC_DEDUP_CONFIG = 0
+GC_DEDUP_F8 = 1
+
 GC_START_CONVERGED = 1
 GC_START_NOT_CONVERGED = 2
 GC_START_DEDUP_FAILED = 3
@@ -70,6 +73,7 @@ class gc_options(ctypes.Structure):
         ("async_", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("autotune", ctypes.c_int),
+        ("dedup_mode", ctypes.c_int),
     ]
 
 
@@ -86,7 +90,7 @@ class gc_stats(ctypes.Structure):
 
 
 EXPORTED = ("gc_set_allocator", "gc_options_default", "gc_create_orbit", "gc_enumerate_copies",
-            "gc_fetch_copies", "gc_fetch_starts", "gc_orbit_stats", "gc_destroy_orbit",
+            "gc_fetch_copies", "gc_fetch_minima_f8", "gc_fetch_starts", "gc_orbit_stats", "gc_destroy_orbit",
             "gc_last_error", "gc_version", "gc_fp_test_static", "gc_enumerate_batch",
             "gc_autotune", "gc_autotune_ex", "gc_server_create", "gc_server_submit",
             "gc_server_wait", "gc_server_destroy")
@@ -127,6 +131,8 @@ def load(build_if_stale: bool = True):
         L.gc_fetch_copies.argtypes = [ctypes.c_void_p, ctypes.c_size_t,
                                       ctypes.POINTER(ctypes.c_size_t), p_d, p_d, p_u64, p_u64,
                                       p_d, p_i]
+        L.gc_fetch_minima_f8.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
+                                         p_d, p_u64]
         L.gc_fetch_starts.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, p_i,
                                       p_i, p_d, ctypes.POINTER(ctypes.c_int64)]
         L.gc_orbit_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(gc_stats)]
@@ -260,6 +266,21 @@ def gc_autotune_ex(orbit, precision: int, mode: int) -> dict:
 
 def gc_autotune(orbit, precision: int, mode: int = 1) -> dict:
     return gc_autotune_ex(orbit, precision, mode)
+
+
+def gc_fetch_minima_f8(orbit, capacity: int | None = None) -> dict:
+    """The paper's distinct minima: F/(dV) quantised at 1e-8 (each the bin's
+    lower edge), increasing, with the number of starts that reached each."""
+    lib = load()
+    n = ctypes.c_size_t()
+    _check(lib.gc_fetch_minima_f8(orbit, 0, ctypes.byref(n), None, None))
+    m = n.value if capacity is None else min(capacity, n.value)
+    F = np.empty(m)
+    count = np.empty(m, np.uint64)
+    if m:
+        _check(lib.gc_fetch_minima_f8(orbit, m, ctypes.byref(n), _ptr(F, ctypes.c_double),
+                                      _ptr(count, ctypes.c_uint64)))
+    return {"n_minima": n.value, "F_norm": F, "count": count}
 
 
 def gc_fetch_copies(orbit, V: int, capacity: int | None = None, theta: bool = True,

@@ -110,13 +110,14 @@ struct gc_orbit_s {
   Buf links64, links32;
   // copy table
   unsigned cap = 0, nb = 0, nl = 0, f8cap = 0;
-  Buf t_cfg, t_F, t_q, t_t, t_first, t_count, t_next, t_lam, t_region, t_head, t_lock, t_f8;
+  Buf t_cfg, t_F, t_q, t_t, t_first, t_count, t_next, t_lam, t_region, t_head, t_lock, t_f8, t_f8n;
   Buf t_counters;    // n_entries, n_new (u32) | n_f8 (u64) | err[4] (i32) | n_redo (u32)
   Buf t_newlist;     // new entries of a batch [cap], then those left to FP64 [cap]
   // batch staging
   Buf s_status, s_sweeps, s_resid, s_F, s_fprint, s_config, s_state32, s_copy;
   Buf work, stats, scratch, theta_tmp;
   Buf sort_keys, sort_idx, sort_tmp;  // fetch ordering: keys [2n], indices [2n], CUB scratch
+  Buf f8_tmp;                         // F set fetch: keys [2n], starts [2n], counter
   size_t batch_cap = 0;
   uint64_t next_start = 0;
   // per-start records of the last call
@@ -160,6 +161,7 @@ struct gc_orbit_s {
     T.new_list = t_newlist.as<unsigned>();
     T.n_new = n_new();
     T.f8 = t_f8.as<unsigned long long>();
+    T.f8n = t_f8n.as<unsigned long long>();
     T.n_f8 = n_f8();
     T.err = err();
     T.cap = cap;
@@ -184,8 +186,9 @@ void fill_u64(unsigned long long* p, unsigned long long v, size_t n, cudaStream_
 }
 
 // Re-insert the keys of an old F8 set into a new one.
-__global__ void f8_rehash_kernel(const unsigned long long* old_set, unsigned old_n,
-                                 unsigned long long* set, unsigned mask, int* err) {
+__global__ void f8_rehash_kernel(const unsigned long long* old_set, const unsigned long long* old_cnt,
+                                 unsigned old_n, unsigned long long* set, unsigned long long* cnt,
+                                 unsigned mask, int* err) {
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < old_n; i += gridDim.x * blockDim.x) {
     const unsigned long long k = old_set[i];
     if (k == gc::kF8Empty) continue;
@@ -195,7 +198,20 @@ __global__ void f8_rehash_kernel(const unsigned long long* old_set, unsigned old
       if (atomicCAS(&set[slot], gc::kF8Empty, k) == gc::kF8Empty) { placed = true; break; }
       slot = (slot + 1) & mask;
     }
-    if (!placed) atomicExch(&err[2], 1);
+    if (placed) cnt[slot] = old_cnt[i];   // keys are unique: the slot is this thread's
+    else atomicExch(&err[2], 1);
+  }
+}
+
+// The occupied slots of the F set, packed (key, starts) in slot order.
+__global__ void f8_compact_kernel(const unsigned long long* set, const unsigned long long* cnt, unsigned n,
+                                  unsigned long long* keys, unsigned long long* counts, unsigned* ctr,
+                                  unsigned limit) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned long long k = set[i];
+    if (k == gc::kF8Empty) continue;
+    const unsigned j = atomicAdd(ctr, 1u);
+    if (j < limit) { keys[j] = k; counts[j] = cnt[i]; }
   }
 }
 
@@ -217,10 +233,11 @@ int table_reserve(gc_orbit o, unsigned long long need, unsigned cur, cudaStream_
   Buf head;
   ok = ok && head.ensure(nnb * 4ull, s);
   const unsigned nf8 = next_pow2(4ull * ncap);
-  Buf f8;
-  ok = ok && f8.ensure(nf8 * 8ull, s);
+  Buf f8, f8n;
+  ok = ok && f8.ensure(nf8 * 8ull, s) && f8n.ensure(nf8 * 8ull, s);
   if (!ok) {
-    for (Buf* b : {&cfg, &F, &q, &t, &first, &count, &next, &lam, &region, &newlist, &head, &f8}) b->release(s);
+    for (Buf* b : {&cfg, &F, &q, &t, &first, &count, &next, &lam, &region, &newlist, &head, &f8, &f8n})
+      b->release(s);
     return fail(GC_ENOMEM, "cannot admit a copy pool of %u entries (%.1f MiB)", ncap,
                 ncap * (V * 16.0 + 64.0) / 1048576.0);
   }
@@ -236,19 +253,21 @@ int table_reserve(gc_orbit o, unsigned long long need, unsigned cur, cudaStream_
   }
   fill_i32(head.as<int>(), -1, nnb, s);
   fill_u64(f8.as<unsigned long long>(), gc::kF8Empty, nf8, s);
-  o->launches += 2;
+  fill_u64(f8n.as<unsigned long long>(), 0ULL, nf8, s);
+  o->launches += 3;
   if (o->f8cap) {
     const unsigned blocks = std::min<unsigned>((o->f8cap + 255) / 256, 4096);
-    f8_rehash_kernel<<<blocks, 256, 0, s>>>(o->t_f8.as<unsigned long long>(), o->f8cap,
-                                              f8.as<unsigned long long>(), nf8 - 1, o->err());
+    f8_rehash_kernel<<<blocks, 256, 0, s>>>(o->t_f8.as<unsigned long long>(), o->t_f8n.as<unsigned long long>(),
+                                              o->f8cap, f8.as<unsigned long long>(),
+                                              f8n.as<unsigned long long>(), nf8 - 1, o->err());
     ++o->launches;
   }
   for (Buf* b : {&o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_count, &o->t_next, &o->t_lam,
-                 &o->t_region, &o->t_newlist, &o->t_head, &o->t_f8})
+                 &o->t_region, &o->t_newlist, &o->t_head, &o->t_f8, &o->t_f8n})
     b->release(s);
   o->t_cfg = cfg; o->t_F = F; o->t_q = q; o->t_t = t; o->t_first = first; o->t_count = count;
   o->t_next = next; o->t_lam = lam; o->t_region = region; o->t_newlist = newlist; o->t_head = head;
-  o->t_f8 = f8;
+  o->t_f8 = f8; o->t_f8n = f8n;
   o->cap = ncap; o->nb = nnb; o->f8cap = nf8;
   if (cur) {
     const unsigned blocks = std::min<unsigned>((cur + 255) / 256, 4096);
@@ -358,6 +377,7 @@ int gc_options_default(gc_options* opt) {
   opt->async = 0;
   opt->use_graph = 0;
   opt->autotune = 0;
+  opt->dedup_mode = GC_DEDUP_CONFIG;
   return GC_OK;
 }
 
@@ -443,10 +463,10 @@ int gc_destroy_orbit(gc_orbit o) {
   cudaStreamSynchronize(o->last_stream);
   cudaStream_t s = nullptr;
   for (Buf* b : {&o->links64, &o->links32, &o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_count,
-                 &o->t_next, &o->t_lam, &o->t_region, &o->t_head, &o->t_lock, &o->t_f8, &o->t_counters,
+                 &o->t_next, &o->t_lam, &o->t_region, &o->t_head, &o->t_lock, &o->t_f8, &o->t_f8n, &o->t_counters,
                  &o->t_newlist, &o->s_status, &o->s_sweeps, &o->s_resid, &o->s_F, &o->s_fprint,
                  &o->s_config, &o->s_state32, &o->s_copy, &o->work, &o->stats, &o->scratch, &o->theta_tmp,
-                 &o->sort_keys, &o->sort_idx, &o->sort_tmp})
+                 &o->sort_keys, &o->sort_idx, &o->sort_tmp, &o->f8_tmp})
     b->release(s);
   for (auto& e : o->ev)
     if (e) cudaEventDestroy(e);
@@ -480,6 +500,8 @@ int validate_options(const gc_options& opt, double omega, double eps) {
   if (!(opt.fp_tau >= 0.0)) return fail(GC_EINVAL, "fp_tau = %g < 0", opt.fp_tau);
   if (opt.lanczos_k < 2) return fail(GC_EINVAL, "lanczos_k = %d < 2", opt.lanczos_k);
   if (opt.newton_inner < 1 || opt.newton_max < 0) return fail(GC_EINVAL, "bad Newton polish settings");
+  if (opt.dedup_mode != GC_DEDUP_CONFIG && opt.dedup_mode != GC_DEDUP_F8)
+    return fail(GC_EINVAL, "unknown dedup_mode %d", opt.dedup_mode);
   return GC_OK;
 }
 
@@ -858,6 +880,7 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     da.tab.tolF = da.tab.wF;
     da.tab.delta2 = opt.dedup_delta * opt.dedup_delta;
     da.tab.f8_links = (double)d * V;
+    da.tab.f8_only = opt.dedup_mode == GC_DEDUP_F8;
     da.V = V;
     da.n = b;
     da.start0 = o->next_start;
@@ -1009,6 +1032,44 @@ int device_order(gc_orbit o, unsigned n, const unsigned** order) {
 }
 
 }  // namespace
+
+int gc_fetch_minima_f8(gc_orbit o, size_t capacity, size_t* n_minima, double* F_norm, uint64_t* count) {
+  if (!o) return fail(GC_EINVAL, "gc_fetch_minima_f8: NULL orbit");
+  if (!n_minima) return fail(GC_EINVAL, "gc_fetch_minima_f8: n_minima is NULL");
+  *n_minima = 0;
+  unsigned n_pool = 0;
+  if (int rc = read_count(o, &n_pool)) return rc;   // synchronises, checks the error flags
+  if (!o->f8cap) return GC_OK;
+  unsigned long long nf8 = 0;
+  GC_CUDA(cudaMemcpy(&nf8, o->n_f8(), 8, cudaMemcpyDeviceToHost));
+  const unsigned n = (unsigned)std::min<unsigned long long>(nf8, o->f8cap);
+  *n_minima = n;
+  if (capacity == 0 || n == 0 || !F_norm) return GC_OK;
+  const unsigned k = (unsigned)std::min<size_t>(capacity, n);
+  cudaStream_t s = o->last_stream;
+  if (!o->f8_tmp.ensure((size_t)n * 32 + 16, s)) return fail(GC_ENOMEM, "cannot admit %u F-set records", n);
+  unsigned long long* k0 = o->f8_tmp.as<unsigned long long>();
+  unsigned long long* k1 = k0 + n;
+  unsigned long long* c0 = k1 + n;
+  unsigned long long* c1 = c0 + n;
+  unsigned* ctr = reinterpret_cast<unsigned*>(c1 + n);
+  size_t tmp = 0;
+  GC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, k0, k1, c0, c1, (int)n, 0, 64, s));
+  if (!o->sort_tmp.ensure(tmp, s)) return fail(GC_ENOMEM, "cannot admit sort scratch");
+  GC_CUDA(cudaMemsetAsync(ctr, 0, 4, s));
+  const unsigned blocks = std::min<unsigned>((o->f8cap + 255) / 256, 4096);
+  f8_compact_kernel<<<blocks, 256, 0, s>>>(o->t_f8.as<unsigned long long>(), o->t_f8n.as<unsigned long long>(),
+                                           o->f8cap, k0, c0, ctr, n);
+  GC_CUDA(cub::DeviceRadixSort::SortPairs(o->sort_tmp.p, tmp, k0, k1, c0, c1, (int)n, 0, 64, s));
+  o->launches += 2;
+  std::vector<unsigned long long> keys(k), starts(count ? k : 0);
+  GC_CUDA(cudaMemcpyAsync(keys.data(), k1, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+  if (count) GC_CUDA(cudaMemcpyAsync(starts.data(), c1, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+  GC_CUDA(cudaStreamSynchronize(s));
+  for (unsigned i = 0; i < k; ++i) F_norm[i] = (double)keys[i] * 1e-8;
+  if (count) for (unsigned i = 0; i < k; ++i) count[i] = starts[i];
+  return GC_OK;
+}
 
 int gc_fetch_copies(gc_orbit o, size_t capacity, size_t* n_distinct, double* F, double* theta,
                     uint64_t* first_start, uint64_t* count, double* lambda2, int* region) {

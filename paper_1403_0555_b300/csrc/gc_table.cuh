@@ -36,11 +36,13 @@ struct TableView {
   unsigned int* new_list;  // entries created by the current batch
   unsigned int* n_new;
   unsigned long long* f8;  // open-addressing set of floor(F_norm * 1e8)
+  unsigned long long* f8n; // starts reaching each slot's key
   unsigned long long* n_f8;
   int* err;                // [0] lock timeout, [1] pool overflow, [2] F8 set full
   unsigned int cap;
   unsigned int nb_mask, nl_mask, f8_mask;
   double wF, wT, tolF, delta2, f8_links;  // f8_links = d V (F_norm = F / (d V))
+  int f8_only;             // GC_DEDUP_F8: the F set only, no configuration table
 };
 
 constexpr unsigned long long kF8Empty = ~0ULL;
@@ -142,8 +144,11 @@ __global__ void __launch_bounds__(256) dedup_kernel(const DedupArgs a) {
         if (prev == k8) { placed = true; break; }
         slot = (slot + 1) & T.f8_mask;
       }
-      if (!placed) atomicExch(&T.err[2], 1);
+      if (placed) atomicAdd(&T.f8n[slot], 1ULL);
+      else atomicExch(&T.err[2], 1);
+      if (T.f8_only) a.copy_of[i] = -1;
     }
+    if (T.f8_only) continue;   // uniform across the warp
     // fast path: most starts land on a copy that is already in the table
     int e = table_search(T, q, t, F, mine, V, lane);
     bool locked = false;
