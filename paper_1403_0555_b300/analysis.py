@@ -100,21 +100,26 @@ def section_iv_statistics(d: int, N: int, n_orbits: int, n_starts: int, omega: f
     """Section IV over n_orbits uniform orbits of N^d: the global minimum of
     F/(dV) per orbit (Table III, Fig. 6), the relative deviation of the
     minima from it (Fig. 8; minima counted as the paper does, by F/(dV)
-    quantised at 1e-8) and the normalised distribution of F/(dV) over all
-    orbits and samples (Fig. 7) as bin left edges and density at `width`."""
+    quantised at 1e-8), over the distinct minima and over the samples, and
+    the normalised distribution of F/(dV) over all orbits and samples (Fig. 7)
+    as bin left edges and density at `width`."""
     V = N ** d
-    fmin, minima, Fs, ws = [], [], [], []
+    fmin, minima, mcount, Fs, ws = [], [], [], [], []
     for st, c in orbit_runs(d, N, n_orbits, n_starts, omega, precision, seed0, check_every):
         Fn = c["F"] / (d * V)
         fmin.append(float(Fn.min()))
-        minima.append(np.unique(np.floor(Fn * 1e8)) * 1e-8)
+        keys, inv = np.unique(np.floor(Fn * 1e8), return_inverse=True)
+        minima.append(keys * 1e-8)
+        mcount.append(np.bincount(inv, weights=c["count"].astype(np.float64)))
         Fs.append(Fn)
         ws.append(c["count"])
     rel = relative_deviation_stats(minima)
+    rel_s = relative_deviation_stats(minima, mcount)
     edges, dens = normalised_distribution(Fs, ws, width)
     return {"d": d, "N": N, "orbits": n_orbits, "starts_per_orbit": n_starts, "omega": omega,
             "global_min_F_per_link": _mean_std(fmin),
             "relative_deviation": {"mean": rel["mean"], "std": rel["std"]},
+            "relative_deviation_samples": {"mean": rel_s["mean"], "std": rel_s["std"]},
             "distribution": {"width": width, "left_edges": edges.tolist(), "density": dens.tolist()}}
 
 
@@ -195,14 +200,22 @@ def relative_deviation(F) -> np.ndarray:
     return (F - Fg) / Fg
 
 
-def relative_deviation_stats(F_per_orbit) -> dict:
+def relative_deviation_stats(F_per_orbit, weights_per_orbit=None) -> dict:
     """Fig. 8: per orbit the mean and standard deviation of the relative
-    deviation over its distinct minima, then their averages over the orbits."""
+    deviation over its distinct minima, then their averages over the orbits.
+    With weights (each minimum's number of starts) the per-orbit moments are
+    taken over the samples instead."""
     means, stds = [], []
-    for F in F_per_orbit:
+    for j, F in enumerate(F_per_orbit):
         r = relative_deviation(F)
-        means.append(r.mean())
-        stds.append(r.std(ddof=1) if len(r) > 1 else 0.0)
+        if weights_per_orbit is None:
+            means.append(r.mean())
+            stds.append(r.std(ddof=1) if len(r) > 1 else 0.0)
+        else:
+            w = np.asarray(weights_per_orbit[j], dtype=np.float64)
+            m = float(np.sum(w * r) / w.sum())
+            means.append(m)
+            stds.append(float(np.sqrt(np.sum(w * (r - m) ** 2) / w.sum())))
     return {"mean": float(np.mean(means)), "std": float(np.mean(stds)), "orbits": len(means),
             "mean_per_orbit": [float(m) for m in means]}
 

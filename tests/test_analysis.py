@@ -103,3 +103,7 @@ def test_relative_deviation_and_orbit_averages():
     assert s["std"] == pytest.approx((np.std([0.0, 0.2, 1.0], ddof=1) + np.std([0.0, 0.1], ddof=1)) / 2)
     # a single minimum deviates by nothing
     assert an.relative_deviation_stats([[0.3]])["mean"] == 0.0
+    # over samples: minima 0.25 (3 starts) and 0.5 (1 start): deviations 0, 1
+    w = an.relative_deviation_stats([[0.25, 0.5]], [[3, 1]])
+    assert w["mean"] == pytest.approx(0.25)
+    assert w["std"] == pytest.approx(np.sqrt(0.75 * 0.25 ** 2 + 0.25 * 0.75 ** 2))
