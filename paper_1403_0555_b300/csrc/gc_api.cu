@@ -19,6 +19,7 @@
 #include "gc_fptest.cuh"
 #include "gc_relax.cuh"
 #include "gc_fptest_lines.cuh"
+#include "gc_slab.cuh"
 #include "gc_table.cuh"
 
 namespace {
@@ -103,6 +104,7 @@ enum StatSlot {
 
 struct gc_orbit_s {
   int d = 0, L = 0, V = 0, ncolor = 0;
+  bool slab = false;   // beyond shared memory: sweeps stream hyperplanes (gc_slab.cuh)
   uint64_t orbit_id = 0;
   gc::Geom geom{};
   int team = 32;
@@ -392,19 +394,29 @@ int gc_create_orbit(int dim, int L, const double* link_angles, uint64_t orbit_id
   if (L < 2) return fail(GC_EINVAL, "L = %d < 2", L);
   if (!link_angles) return fail(GC_EINVAL, "link_angles is NULL");
   double Vd = std::pow((double)L, dim);
-  if (Vd > gc::kMaxSites) return fail(GC_EINVAL, "lattice of %.0f sites exceeds %d", Vd, gc::kMaxSites);
+  if (Vd > gc::kMaxSlabSites)
+    return fail(GC_EINVAL, "lattice of %.0f sites exceeds %d", Vd, gc::kMaxSlabSites);
   const int V = (int)Vd;
-  // the FP64 sweep keeps links, tables and one lattice in shared memory
+  // The shared-memory kernels keep links, tables and one FP64 lattice per
+  // start in shared memory; beyond that (or beyond their 16-bit tables) the
+  // sweeps stream the lattice in hyperplanes from global memory (even L).
   const size_t need = gc::Smem(V, dim, 16, (size_t)V * 16, 1).total;
-  if (need > max_smem_optin())
-    return fail(GC_EINVAL, "lattice %d^%d needs %zu bytes of shared memory (limit %zu)", L, dim, need,
-                max_smem_optin());
+  bool slab = false;
+  if (V > gc::kMaxSites || need > max_smem_optin()) {
+    const int P = V / L;
+    if (dim < 2 || L % 2 != 0 || gc::slab_smem_bytes(P, 16) > max_smem_optin())
+      return fail(GC_EINVAL, "lattice %d^%d fits neither shared memory (%zu bytes needed, limit %zu) nor "
+                  "the hyperplane path (even L, d >= 2, three FP64 hyperplanes of %d sites)",
+                  L, dim, need, max_smem_optin(), P);
+    slab = true;
+  }
   for (int i = 0; i < V * dim; ++i)
     if (!std::isfinite(link_angles[i])) return fail(GC_EINVAL, "link angle %d is not finite", i);
 
   gc_orbit o = new (std::nothrow) gc_orbit_s;
   if (!o) return fail(GC_ENOMEM, "host allocation failed");
   o->d = dim; o->L = L; o->V = V; o->orbit_id = orbit_id;
+  o->slab = slab;
   o->ncolor = (L % 2 == 0) ? 2 : 3;
   gc::Geom& G = o->geom;
   G.d = dim; G.L = L; G.V = V; G.ncolor = o->ncolor;
@@ -441,7 +453,11 @@ int gc_create_orbit(int dim, int L, const double* link_angles, uint64_t orbit_id
     if (e != cudaSuccess) rc = fail(GC_ECUDA, "orbit upload: %s", cudaGetErrorString(e));
   }
   if (rc == GC_OK) {
-    const unsigned long long first = max_copies ? max_copies : 4096;
+    // large lattices start with a pool of about 256 MiB of copies
+    const unsigned long long first =
+        max_copies ? max_copies
+                   : (slab ? std::max<unsigned long long>(64, std::min<unsigned long long>(4096, (1ull << 28) / ((unsigned long long)V * 16)))
+                           : 4096);
     rc = table_reserve(o, first, 0, s);
   }
   if (rc == GC_OK) {
@@ -527,6 +543,7 @@ int check_errors(gc_orbit o) {
   if (flags[1]) return fail(GC_ENOMEM, "copy pool overflow");
   if (flags[2]) return fail(GC_ENOMEM, "quantised-minimum set overflow");
   if (flags[0]) return fail(GC_ETIMEDOUT, "a copy-table lock wait ran out (affected starts are marked)");
+  if (flags[3]) return fail(GC_ETIMEDOUT, "a bulk-copy wait of the hyperplane sweeps ran out");
   return GC_OK;
 }
 
@@ -547,6 +564,173 @@ Tuning cached_tuning(int d, int L, int precision, bool deep = false) {
   for (auto& kv : g_tune_cache)
     if (kv.first == tune_key(d, L, precision, deep)) return kv.second;
   return Tuning{};
+}
+
+// The path for lattices beyond shared memory (o->slab): sweeps that stream the
+// lattice in hyperplanes from global memory (FP64 for the plain path; FP32 then
+// FP64 for the mixed path, the FP64 sweeps taking the place of the Newton
+// polish), the functional and canonical copy from the FP64 state, dedup as
+// everywhere, and the first-region fast path (all weights positive: IN; else
+// untested).  The same batch structure and events as enumerate_impl.
+int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, const gc_options& opt,
+                   cudaStream_t s, bool async, bool timing, int check_every, int max_sweeps) {
+  const int V = o->V, d = o->d, L = o->L, P = V / L;
+  const bool mixed = opt.precision == GC_MIXED;
+  const size_t per_start = (size_t)V * 16 + (mixed ? (size_t)V * 8 : 0) + 48;
+  size_t B = opt.batch_starts > 0 ? (size_t)opt.batch_starts
+                                  : std::max<size_t>(2 * (size_t)sm_count(), (1ull << 30) / per_start);
+  B = std::min<size_t>(B, n_starts);
+  if (!o->s_status.ensure(B, s) || !o->s_sweeps.ensure(B * 4, s) || !o->s_resid.ensure(B * 8, s) ||
+      !o->s_F.ensure(B * 8, s) || !o->s_fprint.ensure(B * 8, s) || !o->s_config.ensure(B * V * 16, s) ||
+      !o->s_copy.ensure(B * 4, s) || (mixed && !o->s_state32.ensure(B * V * 8, s)))
+    return fail(GC_ENOMEM, "cannot admit a batch of %zu starts (%.1f MiB staging)", B, B * per_start / 1048576.0);
+  unsigned long long* wctr = o->work.as<unsigned long long>();
+  unsigned long long* stats = o->stats.as<unsigned long long>();
+  if (!o->err_unchecked) GC_CUDA(cudaMemsetAsync(o->err(), 0, 16, s));
+  o->err_unchecked = true;
+  o->last_stream = s;
+  const size_t sm64 = gc::slab_smem_bytes(P, 16), sm32 = gc::slab_smem_bytes(P, 8);
+
+  for (uint64_t done = 0; done < n_starts;) {
+    const long long b = (long long)std::min<uint64_t>(B, n_starts - done);
+    if (o->enqueued + (unsigned long long)b > o->cap) {
+      if (async) return fail(GC_ESTATE, "asynchronous enumeration needs the copy pool reserved up front");
+      unsigned cur = 0;
+      GC_CUDA(cudaMemcpyAsync(&cur, o->n_entries(), 4, cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaStreamSynchronize(s));
+      if ((unsigned long long)cur + b > o->cap)
+        if (int rc = table_reserve(o, (unsigned long long)cur + b, cur, s)) return rc;
+    }
+    cudaEvent_t* ev = nullptr;
+    if (timing) {
+      while (o->ev_pool.size() < o->ev_used + 6) {
+        cudaEvent_t e;
+        GC_CUDA(cudaEventCreate(&e));
+        o->ev_pool.push_back(e);
+      }
+      ev = o->ev_pool.data() + o->ev_used;
+      o->ev_used += 6;
+    }
+    GC_CUDA(cudaMemsetAsync(wctr, 0, 32, s));
+    GC_CUDA(cudaMemsetAsync(o->n_new(), 0, 4, s));
+
+    gc::SlabArgs sa{};
+    sa.d = d; sa.L = L; sa.V = V; sa.P = P;
+    sa.n = b;
+    sa.seed = opt.seed; sa.orbit_id = o->orbit_id; sa.start0 = o->next_start;
+    sa.omega = omega; sa.om1 = 1.0 - omega; sa.eps = eps;
+    sa.omega32 = (float)omega; sa.om1_32 = (float)(1.0 - omega); sa.eps32 = (float)opt.eps32;
+    sa.check_every = check_every; sa.max_sweeps = max_sweeps;
+    sa.status = o->s_status.as<int8_t>();
+    sa.sweeps = o->s_sweeps.as<int32_t>();
+    sa.resid = o->s_resid.as<double>();
+    sa.stats = stats;
+    sa.err = o->err();
+    sa.work_ctr = wctr;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(b, 2LL * sm_count()));
+    auto launch = [&](auto kern, size_t smem) -> int {
+      if (int rc = raise_smem_limit(kern, smem)) return rc;
+      kern<<<grid, 256, smem, s>>>(sa);
+      ++o->launches;
+      GC_CUDA(cudaGetLastError());
+      return GC_OK;
+    };
+    if (ev) GC_CUDA(cudaEventRecord(ev[0], s));
+    double2* st64 = o->s_config.as<double2>();
+    if (mixed) {
+      // FP32 sweeps from the random starts
+      sa.links = o->links32.p;
+      sa.state = o->s_state32.as<float2>();
+      sa.init = 1;
+      sa.s_sweeps = kSweeps32; sa.s_updates = kUpdates32; sa.s_conv = kConv32; sa.s_nconv = kNConv32;
+      int rc = GC_OK;
+      switch (d) {
+        case 2: rc = launch(gc::relax_slab_kernel<float2, 2>, sm32); break;
+        case 3: rc = launch(gc::relax_slab_kernel<float2, 3>, sm32); break;
+        default: rc = launch(gc::relax_slab_kernel<float2, 4>, sm32); break;
+      }
+      if (rc) return rc;
+      if (ev) GC_CUDA(cudaEventRecord(ev[1], s));
+      const size_t nv = (size_t)b * V;
+      gc::slab_promote_kernel<<<(int)std::min<size_t>((nv + 255) / 256, 4096), 256, 0, s>>>(
+          o->s_state32.as<float2>(), st64, nv);
+      ++o->launches;
+      // FP64 sweeps from there: the polish; final outcomes
+      GC_CUDA(cudaMemsetAsync(wctr, 0, 8, s));
+      sa.links = o->links64.p;
+      sa.state = st64;
+      sa.init = 0;
+      sa.s_sweeps = -1; sa.s_updates = kUpd64; sa.s_conv = kPConv; sa.s_nconv = kPNConv;
+    } else {
+      sa.links = o->links64.p;
+      sa.state = st64;
+      sa.init = 1;
+      sa.s_sweeps = kSweeps; sa.s_updates = kUpdates; sa.s_conv = kConv; sa.s_nconv = kNConv;
+    }
+    {
+      int rc = GC_OK;
+      switch (d) {
+        case 2: rc = launch(gc::relax_slab_kernel<double2, 2>, sm64); break;
+        case 3: rc = launch(gc::relax_slab_kernel<double2, 3>, sm64); break;
+        default: rc = launch(gc::relax_slab_kernel<double2, 4>, sm64); break;
+      }
+      if (rc) return rc;
+    }
+    if (ev && !mixed) GC_CUDA(cudaEventRecord(ev[1], s));
+    // functional, fingerprint and canonical copy (in place)
+    gc::slab_final_kernel<<<grid, 256, 0, s>>>(st64, o->links64.as<double2>(), d, V, L, b,
+                                               o->s_F.as<double>(), o->s_fprint.as<double>());
+    ++o->launches;
+    GC_CUDA(cudaGetLastError());
+    if (ev) {
+      GC_CUDA(cudaEventRecord(ev[2], s));
+      GC_CUDA(cudaEventRecord(ev[3], s));
+    }
+    gc::DedupArgs da{};
+    da.tab = o->view();
+    da.tab.wF = 1e-9 * std::max(1.0, (double)d * V * 1e-3);
+    da.tab.wT = 1e-5;
+    da.tab.tolF = da.tab.wF;
+    da.tab.delta2 = opt.dedup_delta * opt.dedup_delta;
+    da.tab.f8_links = (double)d * V;
+    da.tab.f8_only = opt.dedup_mode == GC_DEDUP_F8;
+    da.V = V;
+    da.n = b;
+    da.start0 = o->next_start;
+    da.status = sa.status;
+    da.F = o->s_F.as<double>();
+    da.fprint = o->s_fprint.as<double>();
+    da.config = st64;
+    da.copy_of = o->s_copy.as<int>();
+    da.stats = stats;
+    {
+      const int blocks = (int)std::max<long long>(1, std::min<long long>((b + 7) / 8, (long long)sm_count() * 8));
+      gc::dedup_kernel<<<blocks, 256, 0, s>>>(da);
+      ++o->launches;
+      GC_CUDA(cudaGetLastError());
+    }
+    if (ev) GC_CUDA(cudaEventRecord(ev[4], s));
+    if (opt.fp_mode != GC_FP_NONE) {
+      gc::slab_fp_fast_kernel<<<sm_count() * 2, 256, 0, s>>>(
+          o->t_cfg.as<double2>(), o->links64.as<double2>(), d, V, L, o->t_newlist.as<unsigned>(), o->n_new(),
+          o->t_lam.as<double>(), o->t_region.as<int>(), stats + kTests);
+      ++o->launches;
+      GC_CUDA(cudaGetLastError());
+    }
+    if (ev) GC_CUDA(cudaEventRecord(ev[5], s));
+    if (opt.keep_per_start) {
+      const size_t off = done;
+      GC_CUDA(cudaMemcpyAsync(o->rec_status.data() + off, sa.status, b, cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaMemcpyAsync(o->rec_sweeps.data() + off, sa.sweeps, b * 4, cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaMemcpyAsync(o->rec_F.data() + off, da.F, b * 8, cudaMemcpyDeviceToHost, s));
+      GC_CUDA(cudaMemcpyAsync(o->rec_copy.data() + off, da.copy_of, b * 4, cudaMemcpyDeviceToHost, s));
+    }
+    o->next_start += b;
+    o->n_starts += b;
+    o->enqueued += b;
+    done += b;
+  }
+  return GC_OK;
 }
 
 // Enqueue the whole path for n_starts starts on stream s.  With `async` no
@@ -587,6 +771,10 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     o->rec_n = 0;
   }
 
+  if (o->slab) {
+    if (prepare_only) return GC_OK;
+    return enumerate_slab(o, n_starts, omega, eps, opt, s, async, timing, check_every, max_sweeps);
+  }
   // launch shapes
   const int T = o->team;
   const int tpw = 32 / T;
@@ -977,7 +1165,7 @@ int gc_enumerate_copies(gc_orbit o, uint64_t n_starts, double omega, double eps,
   if (int rc = validate_options(opt, omega, eps)) return rc;
   if (n_starts == 0) return GC_OK;
   cudaStream_t s = (cudaStream_t)opt.stream;
-  if (opt.autotune && !have_tuning(o->d, o->L, opt.precision, deep_tuning(opt))) {
+  if (opt.autotune && !o->slab && !have_tuning(o->d, o->L, opt.precision, deep_tuning(opt))) {
     Tuning t;
     if (int rc = autotune_shape(o, opt, omega, eps, &t)) return rc;
   }
@@ -1486,7 +1674,7 @@ extern "C" int gc_enumerate_batch(gc_orbit* orbits, int n_orbits, const uint64_t
   // set-up that needs the host: tuning, copy pools, staging buffers
   for (int i = 0; i < n_orbits; ++i) {
     gc_orbit o = orbits[i];
-    if (opt.autotune && !have_tuning(o->d, o->L, opt.precision, deep_tuning(opt))) {
+    if (opt.autotune && !o->slab && !have_tuning(o->d, o->L, opt.precision, deep_tuning(opt))) {
       Tuning t;
       if (int rc = autotune_shape(o, opt, omega, eps, &t)) return rc;
     }
@@ -1551,7 +1739,8 @@ extern "C" int gc_autotune_ex(gc_orbit o, int precision, int mode, int* r_warps,
   opt.autotune = mode;
   const bool deep = deep_tuning(opt);
   Tuning t;
-  if (have_tuning(o->d, o->L, precision, deep)) t = cached_tuning(o->d, o->L, precision, deep);
+  if (o->slab) t = Tuning{};   // the hyperplane path has no launch shapes to tune
+  else if (have_tuning(o->d, o->L, precision, deep)) t = cached_tuning(o->d, o->L, precision, deep);
   else if (int rc = autotune_shape(o, opt, 1.7, 1e-24, &t)) return rc;
   if (r_warps) *r_warps = t.r_warps;
   if (p_warps) *p_warps = t.p_warps;

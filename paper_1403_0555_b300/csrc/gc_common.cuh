@@ -15,7 +15,8 @@
 namespace gc {
 
 constexpr int kMaxDim = 4;
-constexpr int kMaxSites = 4096;   // per lattice; neighbour tables use uint16
+constexpr int kMaxSites = 4096;   // per lattice in shared memory; neighbour tables use uint16
+constexpr int kMaxSlabSites = 1 << 16;   // per lattice streamed in hyperplanes (gc_slab.cuh)
 
 // ---------------------------------------------------------------------------
 // Philox4x64-10 counter-based generator (Salmon et al., SC'11): the generator
