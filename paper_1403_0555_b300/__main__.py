@@ -44,6 +44,7 @@ def main(argv=None):
     e.add_argument("--omega", type=float, default=1.7)
     e.add_argument("--eps", type=float, default=1e-24)
     e.add_argument("--check-every", type=int, default=None)
+    e.add_argument("--max-sweeps", type=int, default=None, help="sweep cap per start (library default if unset)")
     e.add_argument("--fp-mode", choices=["auto", "lanczos", "dense", "none"], default="auto")
     t = sub.add_parser("tables", help="paper-style statistics over random uniform orbits "
                                       "(number of minima, global-minimum F/(dV), discovery curve)")
@@ -90,6 +91,7 @@ def main(argv=None):
     opt = gb.gc_options_default(
         precision=gb.GC_MIXED if mixed else gb.GC_FP64,
         check_every=a.check_every or (4 if mixed else 1),
+        **({} if a.max_sweeps is None else {"max_sweeps": a.max_sweeps}),
         fp_mode={"auto": 0, "lanczos": 1, "dense": 2, "none": 3}[a.fp_mode])
     h = gb.gc_create_orbit(d, L, phi, a.seed)
     try:

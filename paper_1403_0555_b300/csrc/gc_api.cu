@@ -630,7 +630,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     const int grid = (int)std::max<long long>(1, std::min<long long>(b, 2LL * sm_count()));
     auto launch = [&](auto kern, size_t smem) -> int {
       if (int rc = raise_smem_limit(kern, smem)) return rc;
-      kern<<<grid, 256, smem, s>>>(sa);
+      kern<<<grid, 512, smem, s>>>(sa);
       ++o->launches;
       GC_CUDA(cudaGetLastError());
       return GC_OK;

@@ -152,7 +152,7 @@ template <> struct SlabOps<float2> {
 __host__ __device__ inline size_t slab_smem_bytes(int P, int elem) { return 512 + 3 * (size_t)P * elem; }
 
 template <class E, int D>
-__global__ void __launch_bounds__(256) relax_slab_kernel(const SlabArgs a) {
+__global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
   using Ops = SlabOps<E>;
   using R = typename Ops::R;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) relax_slab_kernel(const SlabArgs a) {
   const unsigned bar0 = sbase;                           // 3 x 8 bytes
   long long* tidx = reinterpret_cast<long long*>(smem + 32);
   int* abort_flag = reinterpret_cast<int*>(smem + 40);
-  R* red = reinterpret_cast<R*>(smem + 64);              // 32 per-warp partials
+  R* red = reinterpret_cast<R*>(smem + 64);              // per-warp partials (<= 16 warps)
   E* ring = reinterpret_cast<E*>(smem + 512);
   const unsigned ring_s = sbase + 512;
   const E* links = static_cast<const E*>(a.links);
@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(256) relax_slab_kernel(const SlabArgs a) {
         hp = next[j]; hm = prev[j];
         xm = (z == 0 ? L - 1 : z - 1) * P + j;
       }
-      Ops::acc_fwd(S, links[(size_t)x * D + mu], hp);
-      Ops::acc_bwd(S, links[(size_t)xm * D + mu], hm);
+      Ops::acc_fwd(S, __ldg(links + (size_t)x * D + mu), hp);
+      Ops::acc_bwd(S, __ldg(links + (size_t)xm * D + mu), hm);
       stride *= L;
     }
     return S;
