@@ -119,7 +119,9 @@ typedef struct {
   uint64_t kernel_launches;      /* kernels the library launched for this orbit */
   uint64_t df_residual_passes;   /* double-float residual passes of the polish   */
   double ms_polish_redo;         /* part of ms_polish: polish_kernel rerunning the
-                                    starts the line polish left (4^4)          */
+                                    starts the line polish left (4^4); beyond
+                                    shared memory, the FP64 sweeps of the starts
+                                    the Newton polish left plus the final pass */
   uint64_t polish_redo_starts;   /* starts it reran                              */
 } gc_stats;
 

@@ -117,6 +117,8 @@ struct gc_orbit_s {
   Buf t_newlist;     // new entries of a batch [cap], then those left to FP64 [cap]
   // batch staging
   Buf s_status, s_sweeps, s_resid, s_F, s_fprint, s_config, s_state32, s_copy;
+  Buf s_redo;        // lattices beyond shared memory: starts the Newton polish leaves to FP64 sweeps
+  Buf s_rate;        // ... and the FP32 sweeps' contraction per start
   Buf work, stats, scratch, theta_tmp;
   Buf sort_keys, sort_idx, sort_tmp;  // fetch ordering: keys [2n], indices [2n], CUB scratch
   Buf f8_tmp;                         // F set fetch: keys [2n], starts [2n], counter
@@ -481,7 +483,7 @@ int gc_destroy_orbit(gc_orbit o) {
   for (Buf* b : {&o->links64, &o->links32, &o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_count,
                  &o->t_next, &o->t_lam, &o->t_region, &o->t_head, &o->t_lock, &o->t_f8, &o->t_f8n, &o->t_counters,
                  &o->t_newlist, &o->s_status, &o->s_sweeps, &o->s_resid, &o->s_F, &o->s_fprint,
-                 &o->s_config, &o->s_state32, &o->s_copy, &o->work, &o->stats, &o->scratch, &o->theta_tmp,
+                 &o->s_config, &o->s_state32, &o->s_copy, &o->s_redo, &o->s_rate, &o->work, &o->stats, &o->scratch, &o->theta_tmp,
                  &o->sort_keys, &o->sort_idx, &o->sort_tmp, &o->f8_tmp})
     b->release(s);
   for (auto& e : o->ev)
@@ -566,12 +568,47 @@ Tuning cached_tuning(int d, int L, int precision, bool deep = false) {
   return Tuning{};
 }
 
+// One launch of the hyperplane sweeps: one CTA per start (grid CTAs), or one
+// start per cluster of kSlabCluster CTAs (as many clusters as fit at once)
+constexpr int kSlabCluster = 8;
+template <class K1, class KC>
+int launch_slab(K1 k1, KC kc, const gc::SlabArgs& sa, size_t smem, int grid, bool cluster,
+                cudaStream_t s) {
+  if (cluster) {
+    if (int rc = raise_smem_limit(kc, smem)) return rc;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kSlabCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(kSlabCluster * 64);
+    int nclusters = 0;
+    GC_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, kc, &cfg));
+    if (nclusters > 0) {
+      cfg.gridDim = dim3(kSlabCluster * nclusters);
+      GC_CUDA(cudaLaunchKernelEx(&cfg, kc, sa));
+      return GC_OK;
+    }
+    // no cluster of this shape fits: one CTA per start
+  }
+  if (int rc = raise_smem_limit(k1, smem)) return rc;
+  k1<<<grid, 512, smem, s>>>(sa);
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
 // The path for lattices beyond shared memory (o->slab): sweeps that stream the
-// lattice in hyperplanes from global memory (FP64 for the plain path; FP32 then
-// FP64 for the mixed path, the FP64 sweeps taking the place of the Newton
-// polish), the functional and canonical copy from the FP64 state, dedup as
-// everywhere, and the first-region fast path (all weights positive: IN; else
-// untested).  The same batch structure and events as enumerate_impl.
+// lattice in hyperplanes from global memory (FP64 for the plain path; for the
+// mixed path FP32 sweeps, then the inexact Newton polish, FP64 sweeps for the
+// starts it leaves), the functional and canonical copy from the FP64 state,
+// dedup as everywhere, and the first-region fast path (all weights positive:
+// IN; else untested).  The same batch structure and events as enumerate_impl.
 int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, const gc_options& opt,
                    cudaStream_t s, bool async, bool timing, int check_every, int max_sweeps) {
   const int V = o->V, d = o->d, L = o->L, P = V / L;
@@ -628,38 +665,99 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     sa.err = o->err();
     sa.work_ctr = wctr;
     const int grid = (int)std::max<long long>(1, std::min<long long>(b, 2LL * sm_count()));
-    auto launch = [&](auto kern, size_t smem) -> int {
-      if (int rc = raise_smem_limit(kern, smem)) return rc;
-      kern<<<grid, 512, smem, s>>>(sa);
+    // few starts (fewer than SMs) or a device-side list of hard starts: one
+    // start per cluster of kSlabCluster CTAs; otherwise one CTA per start
+    auto launch = [&](bool fp64, bool cluster) -> int {
+      int rc = GC_OK;
+      if (fp64) {
+        switch (d) {
+          case 2: rc = launch_slab(gc::relax_slab_kernel<double2, 2, false>, gc::relax_slab_kernel<double2, 2, true>, sa, sm64, grid, cluster, s); break;
+          case 3: rc = launch_slab(gc::relax_slab_kernel<double2, 3, false>, gc::relax_slab_kernel<double2, 3, true>, sa, sm64, grid, cluster, s); break;
+          default: rc = launch_slab(gc::relax_slab_kernel<double2, 4, false>, gc::relax_slab_kernel<double2, 4, true>, sa, sm64, grid, cluster, s); break;
+        }
+      } else {
+        switch (d) {
+          case 2: rc = launch_slab(gc::relax_slab_kernel<float2, 2, false>, gc::relax_slab_kernel<float2, 2, true>, sa, sm32, grid, cluster, s); break;
+          case 3: rc = launch_slab(gc::relax_slab_kernel<float2, 3, false>, gc::relax_slab_kernel<float2, 3, true>, sa, sm32, grid, cluster, s); break;
+          default: rc = launch_slab(gc::relax_slab_kernel<float2, 4, false>, gc::relax_slab_kernel<float2, 4, true>, sa, sm32, grid, cluster, s); break;
+        }
+      }
       ++o->launches;
-      GC_CUDA(cudaGetLastError());
-      return GC_OK;
+      return rc;
     };
+    const bool few = opt.relax_variant != GC_RELAX_GENERIC && b < sm_count();
+    const bool hard_cluster = opt.relax_variant != GC_RELAX_GENERIC;
     if (ev) GC_CUDA(cudaEventRecord(ev[0], s));
     double2* st64 = o->s_config.as<double2>();
     if (mixed) {
       // FP32 sweeps from the random starts
+      if (!o->s_rate.ensure((size_t)B * 4, s)) return fail(GC_ENOMEM, "cannot admit a batch of %zu starts", B);
       sa.links = o->links32.p;
       sa.state = o->s_state32.as<float2>();
+      sa.rate = o->s_rate.as<float>();
       sa.init = 1;
       sa.s_sweeps = kSweeps32; sa.s_updates = kUpdates32; sa.s_conv = kConv32; sa.s_nconv = kNConv32;
-      int rc = GC_OK;
-      switch (d) {
-        case 2: rc = launch(gc::relax_slab_kernel<float2, 2>, sm32); break;
-        case 3: rc = launch(gc::relax_slab_kernel<float2, 3>, sm32); break;
-        default: rc = launch(gc::relax_slab_kernel<float2, 4>, sm32); break;
-      }
-      if (rc) return rc;
+      if (int rc = launch(false, few)) return rc;
       if (ev) GC_CUDA(cudaEventRecord(ev[1], s));
       const size_t nv = (size_t)b * V;
       gc::slab_promote_kernel<<<(int)std::min<size_t>((nv + 255) / 256, 4096), 256, 0, s>>>(
           o->s_state32.as<float2>(), st64, nv);
       ++o->launches;
-      // FP64 sweeps from there: the polish; final outcomes
+      // Newton polish (one start per CTA, four CTAs per SM)
+      GC_CUDA(cudaMemsetAsync(wctr, 0, 8, s));
+      GC_CUDA(cudaMemsetAsync(o->n_redo(), 0, 4, s));
+      const int Ps = (P + 3) / 4 * 4;
+      const int grid_n = (int)std::max<long long>(1, std::min<long long>(b, 4LL * sm_count()));
+      gc::SlabNewtonArgs na{};
+      na.d = d; na.L = L; na.V = V; na.P = P; na.Ps = Ps;
+      na.links = o->links64.as<double2>();
+      na.state = st64;
+      na.n = b;
+      na.work_ctr = wctr;
+      na.eps = eps;
+      na.omega_sweeps = (float)omega;
+      na.rate = o->s_rate.as<float>();
+      na.lin_tol = 4e-4f;
+      na.inner_max = opt.newton_inner;
+      na.newton_max = opt.newton_max;
+      na.scratch_floats = gc::slab_newton_scratch_floats(d, V, L, Ps);
+      if (!o->scratch.ensure(grid_n * na.scratch_floats * 4, s) || !o->s_redo.ensure((size_t)B * 4, s))
+        return fail(GC_ENOMEM, "cannot admit the Newton scratch of %d starts (%.1f MiB)", grid_n,
+                    grid_n * na.scratch_floats * 4 / 1048576.0);
+      na.scratch = o->scratch.as<float>();
+      na.status = sa.status;
+      na.resid = sa.resid;
+      na.redo = o->s_redo.as<unsigned>();
+      na.n_redo = o->n_redo();
+      na.stats = stats;
+      na.s_steps = kNewton; na.s_inner = kInner; na.s_pass = kPass; na.s_conv = kPConv; na.s_redo = kFallback;
+      na.err = o->err();
+      {
+        const size_t smn = gc::slab_newton_smem_bytes(Ps);
+        auto launch_n = [&](auto kern) -> int {
+          if (int rc = raise_smem_limit(kern, smn)) return rc;
+          kern<<<grid_n, 256, smn, s>>>(na);
+          ++o->launches;
+          GC_CUDA(cudaGetLastError());
+          return GC_OK;
+        };
+        int rc = GC_OK;
+        switch (d) {
+          case 2: rc = launch_n(gc::slab_newton_kernel<2>); break;
+          case 3: rc = launch_n(gc::slab_newton_kernel<3>); break;
+          default: rc = launch_n(gc::slab_newton_kernel<4>); break;
+        }
+        if (rc) return rc;
+      }
+      if (ev) GC_CUDA(cudaEventRecord(ev[2], s));
+      // FP64 sweeps for the starts the polish left; final outcomes
       GC_CUDA(cudaMemsetAsync(wctr, 0, 8, s));
       sa.links = o->links64.p;
       sa.state = st64;
       sa.init = 0;
+      sa.list = o->s_redo.as<unsigned>();
+      sa.n_list = o->n_redo();
+      sa.rate = nullptr;
       sa.s_sweeps = -1; sa.s_updates = kUpd64; sa.s_conv = kPConv; sa.s_nconv = kPNConv;
     } else {
       sa.links = o->links64.p;
@@ -667,15 +765,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       sa.init = 1;
       sa.s_sweeps = kSweeps; sa.s_updates = kUpdates; sa.s_conv = kConv; sa.s_nconv = kNConv;
     }
-    {
-      int rc = GC_OK;
-      switch (d) {
-        case 2: rc = launch(gc::relax_slab_kernel<double2, 2>, sm64); break;
-        case 3: rc = launch(gc::relax_slab_kernel<double2, 3>, sm64); break;
-        default: rc = launch(gc::relax_slab_kernel<double2, 4>, sm64); break;
-      }
-      if (rc) return rc;
-    }
+    if (int rc = launch(true, mixed ? hard_cluster : few)) return rc;
     if (ev && !mixed) GC_CUDA(cudaEventRecord(ev[1], s));
     // functional, fingerprint and canonical copy (in place)
     gc::slab_final_kernel<<<grid, 256, 0, s>>>(st64, o->links64.as<double2>(), d, V, L, b,
@@ -683,7 +773,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     ++o->launches;
     GC_CUDA(cudaGetLastError());
     if (ev) {
-      GC_CUDA(cudaEventRecord(ev[2], s));
+      if (!mixed) GC_CUDA(cudaEventRecord(ev[2], s));   // mixed: after the Newton polish
       GC_CUDA(cudaEventRecord(ev[3], s));
     }
     gc::DedupArgs da{};
@@ -1842,7 +1932,7 @@ struct gc_server_s {
       if (orb) {
         // keep the results (copy table), release the staging of the batches
         for (Buf* b : {&orb->s_status, &orb->s_sweeps, &orb->s_resid, &orb->s_F, &orb->s_fprint,
-                       &orb->s_config, &orb->s_state32, &orb->s_copy})
+                       &orb->s_config, &orb->s_state32, &orb->s_copy, &orb->s_redo, &orb->s_rate, &orb->scratch})
           b->release(streams[k]);
         cudaStreamSynchronize(streams[k]);
       }

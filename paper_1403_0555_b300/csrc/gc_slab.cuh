@@ -25,7 +25,10 @@
 // Every wait on a bulk copy is bounded: when one runs out the kernel sets
 // err[3], lets the copies in flight finish (bounded again) and returns.
 #pragma once
+#include <cooperative_groups.h>
 #include "gc_relax.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace gc {
 
@@ -37,12 +40,16 @@ struct SlabArgs {
   uint64_t seed, orbit_id, start0;
   int init;                        // 1: generate the random start; 0: continue from state
   unsigned long long* work_ctr;
+  const unsigned* list;            // when set: only these batch entries, *n_list of them
+  const unsigned* n_list;
   double omega, om1, eps;          // FP64 update
   float omega32, om1_32, eps32;    // FP32 update
   int check_every, max_sweeps;
   int8_t* status;
   int32_t* sweeps;                 // init: set; continue: add
   double* resid;
+  float* rate;                     // when set: per start, the contraction of max |div| per sweep
+                                   // over the last check interval (0: none seen)
   unsigned long long* stats;
   int s_sweeps, s_updates, s_conv, s_nconv;   // stats slots (-1: none)
   int* err;                        // [3] a bulk-copy wait ran out
@@ -81,6 +88,79 @@ __device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// -- the three-plane ring ------------------------------------------------------
+// A walk over n consecutive planes z0 .. z0+n-1 (mod L) of one start's array
+// (plane z at base + z * Ps elements) with three shared-memory plane buffers:
+// load k brings plane z0 + k - 1 (mod L) into slot k mod 3, so step t sees
+// planes z-1, z and z+1 (z = z0 + t) in slots t, t+1 and t+2 (mod 3).
+// Thread 0 issues; every thread awaits.
+template <class E>
+struct PlaneRing {
+  E* ring;                 // 3 * Ps elements
+  unsigned ring_s, bar0;   // shared-window addresses of the ring and of 3 barriers
+  unsigned PB;             // bytes per plane (a multiple of 16)
+  int L, Ps;
+  unsigned parity;         // bit k: the next phase parity of barrier k
+
+  __device__ void issue(const E* base, int z0, int k) {
+    const int slot = k % 3, z = (z0 + k - 1 + L) % L;
+    mbar_expect(bar0 + 8u * slot, PB);
+    bulk_load(ring_s + (unsigned)slot * PB, base + (size_t)z * Ps, PB, bar0 + 8u * slot);
+  }
+  // false when the wait ran out
+  __device__ bool await(int k) {
+    const int slot = k % 3;
+    const bool ok = mbar_wait(bar0 + 8u * slot, (parity >> slot) & 1u);
+    parity ^= 1u << slot;
+    return ok;
+  }
+  __device__ E* plane(int k) const { return ring + (size_t)(k % 3) * Ps; }
+  __device__ unsigned plane_s(int k) const { return ring_s + (unsigned)(k % 3) * PB; }
+  // after a failed walk: give the loads still in flight a bounded time to land
+  __device__ void drain() {
+    for (int k = 0; k < 3; ++k) mbar_wait(bar0 + 8u * k, (parity >> k) & 1u);
+  }
+};
+
+// One walk: body(prev, cur, next, z) on every thread for z = z0 .. z0+n-1
+// (n >= 1); with `store` each plane goes back to global memory after its body
+// (so the walk updates the array in place: within a walk the body must only
+// write sites that no other plane's body reads, e.g. one colour).  Returns the
+// same value on every thread: false when a wait ran out.
+template <class E, class Body>
+__device__ __forceinline__ bool ring_walk(PlaneRing<E>& R, E* base, bool store, Body&& body, int z0, int n) {
+  const int tid = threadIdx.x;
+  if (tid == 0) { R.issue(base, z0, 0); R.issue(base, z0, 1); R.issue(base, z0, 2); }
+  bool ok = R.await(0);
+  ok = R.await(1) && ok;
+  ok = !__syncthreads_or(!ok);   // the same on every thread before the walk's barriers
+  for (int t = 0; t < n && ok; ++t) {
+    const int z = z0 + t;
+    ok = R.await(t + 2);
+    if (__syncthreads_or(!ok)) { ok = false; break; }
+    body(static_cast<const E*>(R.plane(t)), R.plane(t + 1), static_cast<const E*>(R.plane(t + 2)), z);
+    if (store) fence_async_smem();
+    __syncthreads();   // slot t mod 3 is free (read-only walk); plane z is complete (store)
+    if (tid == 0) {
+      if (store) {
+        bulk_store(base + (size_t)z * R.Ps, R.plane_s(t + 1), R.PB);
+        if (t + 3 <= n + 1) {
+          bulk_wait_read_1();   // the store of step t-1 (slot t mod 3) has read its buffer
+          R.issue(base, z0, t + 3);
+        }
+      } else if (t + 3 <= n + 1) {
+        R.issue(base, z0, t + 3);
+      }
+    }
+  }
+  if (store && tid == 0) bulk_wait_all();
+  return !__syncthreads_or(!ok);
+}
+template <class E, class Body>
+__device__ __forceinline__ bool ring_walk(PlaneRing<E>& R, E* base, bool store, Body&& body) {
+  return ring_walk(R, base, store, static_cast<Body&&>(body), 0, R.L);
+}
 
 // -- the site update in each precision ----------------------------------------
 template <class E> struct SlabOps;
@@ -151,65 +231,117 @@ template <> struct SlabOps<float2> {
 // shared memory: 3 barriers and scratch in the first 512 bytes, then the ring
 __host__ __device__ inline size_t slab_smem_bytes(int P, int elem) { return 512 + 3 * (size_t)P * elem; }
 
-template <class E, int D>
+// In-plane coordinates of the h-th colour-c site of plane z (row = the
+// coordinates 1 .. D-2, x0 = coordinate 0): j = in-plane index.
+template <int D>
+__device__ __forceinline__ void slab_site_of(int L, int h, int c, int z, int& j, int& x0, int& rowbase) {
+  const int H = L / 2;
+  const int row = h / H, k = h - row * H;
+  int rs = 0, t = row;
+#pragma unroll
+  for (int mu = 1; mu < D - 1; ++mu) { rs += t % L; t /= L; }
+  x0 = 2 * k + ((c + z + rs) & 1);
+  rowbase = row * L;
+  j = rowbase + x0;
+}
+
+// Neighbours of in-plane site j (coordinate 0 = x0, row start rowbase) along
+// axis mu < D-1: in-plane indices jp (forward) and jm (backward).
+template <int D>
+__device__ __forceinline__ void slab_inplane_nb(int L, int mu, int j, int x0, int rowbase, int& jp, int& jm) {
+  if (mu == 0) {
+    jp = rowbase + (x0 + 1 == L ? 0 : x0 + 1);
+    jm = rowbase + (x0 == 0 ? L - 1 : x0 - 1);
+  } else {
+    int stride = 1;
+    for (int k = 0; k < mu; ++k) stride *= L;
+    const int c = (j / stride) % L;
+    jp = j + (c + 1 == L ? -(L - 1) * stride : stride);
+    jm = j + (c == 0 ? (L - 1) * stride : -stride);
+  }
+}
+
+// The sweeps.  CL = false: one CTA per start, starts pulled from a counter.
+// CL = true: one start per thread-block cluster of C CTAs (the multi-CTA form
+// for few or hard starts), CTA q walking planes [q L / C, (q+1) L / C): a
+// colour phase reads only the other colour, so the CTAs' plane ranges are
+// independent within a phase (a neighbour plane that another CTA is storing
+// changes only in the bytes of the colour this CTA does not read); the CTAs
+// meet at one cluster barrier per phase and per residual, which also carries
+// their max div^2 and whether a wait ran out, so every CTA of a cluster takes
+// the same decisions.
+template <class E, int D, bool CL>
 __global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
   using Ops = SlabOps<E>;
   using R = typename Ops::R;
   extern __shared__ __align__(16) unsigned char smem[];
   const int L = a.L, V = a.V, P = a.P, tid = threadIdx.x, nt = blockDim.x;
-  const unsigned PB = (unsigned)(P * sizeof(E));
   const unsigned sbase = (unsigned)__cvta_generic_to_shared(smem);
-  const unsigned bar0 = sbase;                           // 3 x 8 bytes
   long long* tidx = reinterpret_cast<long long*>(smem + 32);
   int* abort_flag = reinterpret_cast<int*>(smem + 40);
   R* red = reinterpret_cast<R*>(smem + 64);              // per-warp partials (<= 16 warps)
-  E* ring = reinterpret_cast<E*>(smem + 512);
-  const unsigned ring_s = sbase + 512;
+  double* cl_slots = reinterpret_cast<double*>(smem + 192);   // [2][16] cluster exchange (rank 0's)
+  PlaneRing<E> ring{reinterpret_cast<E*>(smem + 512), sbase + 512, sbase, (unsigned)(P * sizeof(E)), L, P, 0u};
   const E* links = static_cast<const E*>(a.links);
-  const int H = L / 2;                                   // colour sites per row
+  int C = 1, q = 0, cid = 0, ncl = 1;
+  if constexpr (CL) {
+    cg::cluster_group cl = cg::this_cluster();
+    C = (int)cl.num_blocks();
+    q = (int)cl.block_rank();
+    cid = blockIdx.x / C;
+    ncl = gridDim.x / C;
+  }
+  const int z0 = q * L / C, nz = (q + 1) * L / C - z0;   // this CTA's planes (nz may be 0)
+  int round = 0;
 
   if (tid == 0) {
-    for (int k = 0; k < 3; ++k) mbar_init(bar0 + 8u * k, 1);
+    for (int k = 0; k < 3; ++k) mbar_init(sbase + 8u * k, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  unsigned parity = 0;                                   // bit k: next phase parity of barrier k
+  if constexpr (CL) cg::this_cluster().sync();   // every CTA's barriers and slots exist
   unsigned long long my_sweeps = 0, my_conv = 0, my_nconv = 0;
 
-  // load k of a walk (plane (k - 1) mod L into slot k mod 3); thread 0 only
-  auto issue = [&](const E* st, int k) {
-    const int slot = k % 3, z = (k - 1 + L) % L;
-    mbar_expect(bar0 + 8u * slot, PB);
-    bulk_load(ring_s + (unsigned)slot * PB, st + (size_t)z * P, PB, bar0 + 8u * slot);
+  // cluster-wide: max of r over the CTAs, ok = every CTA's ok (identity
+  // without a cluster).  Double-buffered slots in rank 0: round k+2 writes
+  // slot set k mod 2 only after every CTA passed barrier k+1, i.e. read round k.
+  auto combine = [&](bool& ok, double r) -> double {
+    if constexpr (!CL) {
+      return r;
+    } else {
+      cg::cluster_group cl = cg::this_cluster();
+      double* set = cl_slots + 16 * (round & 1);
+      if (tid == 0) {
+        fence_async_global();   // this CTA's completed bulk stores, before the release
+        cl.map_shared_rank(set, 0)[q] = ok ? r : -1.0;
+      }
+      cl.sync();
+      if (tid == 0) fence_async_global();   // then the next bulk loads
+      const double* src = cl.map_shared_rank(set, 0);
+      double m = 0.0;
+      bool all = true;
+      for (int k = 0; k < C; ++k) {
+        const double v = src[k];
+        if (v < 0.0) all = false; else m = fmax(m, v);
+      }
+      ok = all;
+      ++round;
+      return m;
+    }
   };
-  // every thread waits for load k; false when the wait ran out
-  auto await = [&](int k) -> bool {
-    const int slot = k % 3;
-    const bool ok = mbar_wait(bar0 + 8u * slot, (parity >> slot) & 1u);
-    parity ^= 1u << slot;
-    return ok;
-  };
-  auto fail = [&]() {
-    if (tid == 0) { atomicExch(&a.err[3], 1); *abort_flag = 1; }
-  };
+
   // the staple of in-plane site j of plane z (buffers: prev, cur, next)
   auto staple = [&](const E* prev, const E* cur, const E* next, int z, int j, int x0, int rowbase) -> E {
     E S = Ops::zero();
     const int x = z * P + j;
-    int stride = 1;
 #pragma unroll
     for (int mu = 0; mu < D; ++mu) {
       E hp, hm;
       int xm;
-      if (mu == 0) {
-        const int jp = rowbase + (x0 + 1 == L ? 0 : x0 + 1), jm = rowbase + (x0 == 0 ? L - 1 : x0 - 1);
-        hp = cur[jp]; hm = cur[jm];
-        xm = z * P + jm;
-      } else if (mu < D - 1) {
-        const int c = (j / stride) % L;
-        const int jp = j + (c + 1 == L ? -(L - 1) * stride : stride);
-        const int jm = j + (c == 0 ? (L - 1) * stride : -stride);
+      if (mu < D - 1) {
+        int jp, jm;
+        slab_inplane_nb<D>(L, mu, j, x0, rowbase, jp, jm);
         hp = cur[jp]; hm = cur[jm];
         xm = z * P + jm;
       } else {
@@ -218,72 +350,32 @@ __global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
       }
       Ops::acc_fwd(S, __ldg(links + (size_t)x * D + mu), hp);
       Ops::acc_bwd(S, __ldg(links + (size_t)xm * D + mu), hm);
-      stride *= L;
     }
     return S;
   };
-  // in-plane coordinates of the h-th colour-c site of plane z
-  auto site_of = [&](int h, int c, int z, int& j, int& x0, int& rowbase) {
-    const int row = h / H, k = h - row * H;
-    int rs = 0, t = row;
-#pragma unroll
-    for (int mu = 1; mu < D - 1; ++mu) { rs += t % L; t /= L; }
-    x0 = 2 * k + ((c + z + rs) & 1);
-    rowbase = row * L;
-    j = rowbase + x0;
-  };
-  // one colour phase over the whole lattice; false when a wait ran out
+  // one colour phase over this CTA's planes, then (cluster) the others';
+  // false everywhere when a wait ran out anywhere
   auto phase = [&](E* st, int c) -> bool {
-    if (tid == 0) { issue(st, 0); issue(st, 1); issue(st, 2); }
-    bool ok = await(0);
-    ok = await(1) && ok;
-    ok = !__syncthreads_or(!ok);   // the same on every thread before the walk's barriers
-    for (int z = 0; z < L && ok; ++z) {
-      ok = await(z + 2);
-      if (__syncthreads_or(!ok)) { ok = false; break; }
-      const E* prev = ring + (size_t)(z % 3) * P;
-      E* cur = ring + (size_t)((z + 1) % 3) * P;
-      const E* next = ring + (size_t)((z + 2) % 3) * P;
+    bool ok = nz == 0 || ring_walk(ring, st, true, [&](const E* prev, E* cur, const E* next, int z) {
       for (int h = tid; h < P / 2; h += nt) {
         int j, x0, rowbase;
-        site_of(h, c, z, j, x0, rowbase);
+        slab_site_of<D>(L, h, c, z, j, x0, rowbase);
         cur[j] = Ops::move(cur[j], staple(prev, cur, next, z, j, x0, rowbase), a);
       }
-      fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        bulk_store(st + (size_t)z * P, ring_s + (unsigned)((z + 1) % 3) * PB, PB);
-        if (z + 3 <= L + 1) {
-          bulk_wait_read_1();   // the store of step z-1 (slot z mod 3) has read its buffer
-          issue(st, z + 3);
-        }
-      }
-    }
-    if (tid == 0) bulk_wait_all();
-    return !__syncthreads_or(!ok);
+    }, z0, nz);
+    combine(ok, 0.0);
+    return ok;
   };
-  // max div^2 over the lattice (read-only walk); nan when a wait ran out
-  auto residual = [&](const E* st, bool& ok) -> R {
+  // max div^2 over the lattice (read-only walk)
+  auto residual = [&](E* st, bool& ok) -> R {
     R r = 0;
-    if (tid == 0) { issue(st, 0); issue(st, 1); issue(st, 2); }
-    ok = await(0);
-    ok = await(1) && ok;
-    ok = !__syncthreads_or(!ok);
-    for (int z = 0; z < L && ok; ++z) {
-      ok = await(z + 2);
-      if (__syncthreads_or(!ok)) { ok = false; break; }
-      const E* prev = ring + (size_t)(z % 3) * P;
-      const E* cur = ring + (size_t)((z + 1) % 3) * P;
-      const E* next = ring + (size_t)((z + 2) % 3) * P;
+    ok = nz == 0 || ring_walk(ring, st, false, [&](const E* prev, E* cur, const E* next, int z) {
       for (int j = tid; j < P; j += nt) {
         const int x0 = j % L, rowbase = j - x0;
         const R v = Ops::div2(cur[j], staple(prev, cur, next, z, j, x0, rowbase));
         r = v > r ? v : r;
       }
-      __syncthreads();   // slot z mod 3 is free
-      if (tid == 0 && z + 3 <= L + 1) issue(st, z + 3);
-    }
-    ok = !__syncthreads_or(!ok);
+    }, z0, nz);
     for (int o = 16; o > 0; o >>= 1) {
       const R w = __shfl_xor_sync(0xffffffffu, r, o);
       r = w > r ? w : r;
@@ -293,7 +385,272 @@ __global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
     r = 0;
     for (int w = 0; w < nt / 32; ++w) r = red[w] > r ? red[w] : r;
     __syncthreads();
-    return r;
+    return (R)combine(ok, (double)r);
+  };
+
+  const long long n = a.list ? (long long)*a.n_list : a.n;
+  for (long long i = cid;; i += ncl) {
+    if constexpr (!CL) {
+      if (tid == 0) *tidx = (long long)atomicAdd(a.work_ctr, 1ULL);
+      __syncthreads();
+      i = *tidx;
+      __syncthreads();
+      if (*abort_flag) break;
+    }
+    if (i >= n) break;
+    const long long idx = a.list ? (long long)a.list[i] : i;
+    E* st = static_cast<E*>(a.state) + (size_t)idx * V;
+    bool ok = true;
+    if (a.init) {
+      for (int x = z0 * P + tid; x < (z0 + nz) * P; x += nt) st[x] = Ops::start(a, idx, x);
+      fence_async_global();   // generic writes, then bulk reads of them
+      __syncthreads();
+      combine(ok, 0.0);       // (cluster) the neighbours' planes too
+    }
+    int sweeps = 0, until = a.check_every;
+    bool conv = false;
+    R r = 0, r_last = 0;
+    for (;;) {
+      if (!phase(st, 0) || !phase(st, 1)) { ok = false; break; }
+      ++sweeps;
+      if (--until == 0) {
+        until = a.check_every;
+        r_last = r;
+        r = residual(st, ok);
+        if (!ok) break;
+        conv = r < Ops::eps(a);
+        if (conv || sweeps >= a.max_sweeps) break;
+      }
+    }
+    if (!ok) {
+      // a wait ran out: flag it, let the loads still in flight land, and stop
+      // (in a cluster every CTA gets here together)
+      if (tid == 0) { atomicExch(&a.err[3], 1); *abort_flag = 1; }
+      ring.drain();
+      if (tid == 0) bulk_wait_all();
+      __syncthreads();
+      break;
+    }
+    if (tid == 0 && q == 0) {
+      a.status[idx] = conv ? kConverged : kNotConverged;
+      if (a.init) a.sweeps[idx] = sweeps; else a.sweeps[idx] += sweeps;
+      if (sizeof(R) == 8) a.resid[idx] = (double)r;
+      // the contraction of |div| per sweep over the last check interval
+      if (a.rate) a.rate[idx] = (r_last > 0 && r < r_last) ? (float)pow((double)r / (double)r_last, 0.5 / a.check_every) : 0.f;
+      my_sweeps += sweeps;
+      if (conv) ++my_conv; else ++my_nconv;
+    }
+  }
+  if (tid == 0 && q == 0) {
+    if (a.s_sweeps >= 0) atomicAdd(&a.stats[a.s_sweeps], my_sweeps);
+    if (a.s_updates >= 0) atomicAdd(&a.stats[a.s_updates], my_sweeps * (unsigned long long)V);
+    if (a.s_conv >= 0) atomicAdd(&a.stats[a.s_conv], my_conv);
+    if (a.s_nconv >= 0) atomicAdd(&a.stats[a.s_nconv], my_nconv);
+  }
+  if constexpr (CL) cg::this_cluster().sync();   // no CTA leaves while its slots may be read
+}
+
+// -- inexact Newton polish of the mixed path ----------------------------------
+// The FP32 sweeps leave each start with max div^2 below eps32; Newton steps on
+// the gauge angles then finish it (the Jacobian of div is the Faddeev-Popov
+// operator M, the Hessian of the functional of Eq. 3):
+//   1. FP64 pass: div_x = sum_mu [sin phi^theta_{x,mu} - sin phi^theta_{x-mu,mu}]
+//      and the weights w = cos phi^theta from the FP64 state; stop when
+//      max div^2 < eps; else store, as FP32, b_x = div_x / D_x and the
+//      weights over D_x (D_x = the sum of the 2d weights at x), delta = 0;
+//   2. FP32 checkerboard SOR on M delta = div, streamed through the plane
+//      ring like the sweeps, until the corrections stall below lin_tol
+//      max |b|;
+//   3. FP64 pass: g_x <- g_x exp(i delta_x).
+// The SOR parameter is set per start from Young's relation for consistently
+// ordered matrices (which the red-black ordering of this stencil gives): near
+// the minimum the FP32 sweeps at parameter w are the linear SOR on M, so the
+// contraction lambda they showed gives the Jacobi radius
+// mu^2 = (lambda + w - 1)^2 / (lambda w^2) and w_opt = 2 / (1 + sqrt(1 - mu^2)).
+// Large lattices have mu close to 1, where a fixed parameter needs many times
+// the sweeps of w_opt.  A step that does not lower max div^2 is halved (up
+// to six times); a start without descent, or still above eps after
+// newton_max steps, is listed for the FP64 sweeps (an indefinite M near a
+// saddle, which relaxation leaves and Newton would not).
+struct SlabNewtonArgs {
+  int d, L, V, P, Ps;              // Ps: plane stride of delta (P rounded up to 4 floats)
+  const double2* links;            // FP64 [x*d + mu], site order
+  double2* state;                  // n * V, site order
+  long long n;
+  unsigned long long* work_ctr;
+  double eps;
+  float omega_sweeps, lin_tol;     // the FP32 sweeps' parameter; inner stop
+  const float* rate;               // per start: their contraction per sweep (0: none)
+  int inner_max, newton_max;
+  float* scratch;                  // per CTA: (1 + 2d) V coefficients, then L * Ps delta
+  size_t scratch_floats;           // per CTA (a multiple of 4)
+  int8_t* status;
+  double* resid;
+  unsigned* redo;                  // starts left to the FP64 sweeps
+  unsigned* n_redo;
+  unsigned long long* stats;       // [kNewton] steps, [kInner] sweeps, [kPass] FP64 passes, ...
+  int s_steps, s_inner, s_pass, s_conv, s_redo;
+  int* err;
+};
+
+__host__ __device__ inline size_t slab_newton_smem_bytes(int Ps) { return 512 + 3 * (size_t)Ps * 4; }
+__host__ __device__ inline size_t slab_newton_scratch_floats(int d, int V, int L, int Ps) {
+  return (((size_t)(1 + 2 * d) * V + (size_t)L * Ps) + 3) / 4 * 4;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256, 4) slab_newton_kernel(const SlabNewtonArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int L = a.L, V = a.V, P = a.P, P2 = a.P / 2, Ps = a.Ps, tid = threadIdx.x, nt = blockDim.x;
+  const unsigned sbase = (unsigned)__cvta_generic_to_shared(smem);
+  long long* tidx = reinterpret_cast<long long*>(smem + 32);
+  int* abort_flag = reinterpret_cast<int*>(smem + 40);
+  double* redd = reinterpret_cast<double*>(smem + 64);   // per-warp partials (<= 8 warps)
+  float* redf = reinterpret_cast<float*>(smem + 192);
+  PlaneRing<float> ring{reinterpret_cast<float*>(smem + 512), sbase + 512, sbase, (unsigned)(Ps * 4), L, Ps, 0u};
+  float* coef = a.scratch + (size_t)blockIdx.x * a.scratch_floats;   // [1 + 2D][V], colour-split order
+  float* dl = coef + (size_t)(1 + 2 * D) * V;                         // [L][Ps], plane order
+
+  if (tid == 0) {
+    for (int k = 0; k < 3; ++k) mbar_init(sbase + 8u * k, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  unsigned long long my_steps = 0, my_inner = 0, my_pass = 0, my_conv = 0, my_redo = 0;
+
+  auto block_max2 = [&](double r, float f, double& ro, float& fo) {
+    for (int o = 16; o > 0; o >>= 1) {
+      r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+      f = fmaxf(f, __shfl_xor_sync(0xffffffffu, f, o));
+    }
+    if ((tid & 31) == 0) { redd[tid >> 5] = r; redf[tid >> 5] = f; }
+    __syncthreads();
+    ro = 0.0; fo = 0.f;
+    for (int w = 0; w < nt / 32; ++w) { ro = fmax(ro, redd[w]); fo = fmaxf(fo, redf[w]); }
+    __syncthreads();
+  };
+
+  // 1. FP64 residual and the FP32 system; returns max div^2, bmax = max |b|
+  auto rhs = [&](const double2* g, float& bmax) -> double {
+    double r = 0.0;
+    float bm = 0.f;
+    for (int x = tid; x < V; x += nt) {
+      int c[D];
+      int t = x;
+#pragma unroll
+      for (int mu = 0; mu < D; ++mu) { c[mu] = t % L; t /= L; }
+      const double2 gx = g[x];
+      double dv = 0.0, Ds = 0.0, wf[D], wb[D];
+      int stride = 1;
+#pragma unroll
+      for (int mu = 0; mu < D; ++mu) {
+        const int xp = x + (c[mu] + 1 == L ? -(L - 1) * stride : stride);
+        const int xm = x + (c[mu] == 0 ? (L - 1) * stride : -stride);
+        const double2 uf = a.links[(size_t)x * D + mu], ub = a.links[(size_t)xm * D + mu];
+        const double2 hp = g[xp], hm = g[xm];
+        const double tfx = uf.x * hp.x - uf.y * hp.y, tfy = uf.x * hp.y + uf.y * hp.x;   // u h_+
+        const double tbx = ub.x * hm.x + ub.y * hm.y, tby = ub.x * hm.y - ub.y * hm.x;   // conj(u') h_-
+        wf[mu] = gx.x * tfx + gx.y * tfy;                 // cos phi^theta_{x,mu}
+        wb[mu] = gx.x * tbx + gx.y * tby;                 // cos phi^theta_{x-mu,mu}
+        dv += (gx.x * tfy - gx.y * tfx) + (gx.x * tby - gx.y * tbx);
+        Ds += wf[mu] + wb[mu];
+        stride *= L;
+      }
+      r = fmax(r, dv * dv);
+      const int z = c[D - 1], j = x - z * P;
+      int rs = 0;
+#pragma unroll
+      for (int mu = 1; mu < D - 1; ++mu) rs += c[mu];
+      const size_t ci = (size_t)z * P + (size_t)((c[0] + rs + z) & 1) * P2 + (size_t)(j / L) * (L / 2) + c[0] / 2;
+      if (Ds > 0.0) {
+        const double inv = 1.0 / Ds;
+        const float bb = (float)(dv * inv);
+        coef[ci] = bb;
+        bm = fmaxf(bm, fabsf(bb));
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) {
+          coef[(size_t)(1 + mu) * V + ci] = (float)(wf[mu] * inv);
+          coef[(size_t)(1 + D + mu) * V + ci] = (float)(wb[mu] * inv);
+        }
+      } else {   // no positive diagonal: the site stays (the step may then not contract)
+        coef[ci] = 0.f;
+#pragma unroll
+        for (int mu = 0; mu < 2 * D; ++mu) coef[(size_t)(1 + mu) * V + ci] = 0.f;
+      }
+    }
+    double ro;
+    block_max2(r, bm, ro, bmax);
+    return ro;
+  };
+
+  // 2. SOR sweeps from delta = 0 in groups of four, the correction of each
+  // group's last sweep deciding (a correction 16 times the first group's
+  // means M is not positive: stop); returns the sweeps, false in ok when a
+  // wait ran out
+  auto sor = [&](float bmax, int cap, float om, bool& ok) -> int {
+    for (int x = tid; x < L * Ps; x += nt) dl[x] = 0.f;
+    fence_async_global();   // generic writes, then bulk reads of them
+    __syncthreads();
+    const float thr = a.lin_tol * bmax;
+    int k = 0;
+    float first = 0.f;
+    while (k < cap) {
+      float corr = 0.f;
+      for (int kk = 0; kk < 4; ++kk, ++k) {
+        const bool last = kk == 3;
+        for (int c = 0; c < 2; ++c) {
+          ok = ring_walk(ring, dl, true, [&](const float* prev, float* cur, const float* next, int z) {
+            const float* cp = coef + (size_t)z * P + (size_t)c * P2;
+            for (int h = tid; h < P2; h += nt) {
+              int j, x0, rowbase;
+              slab_site_of<D>(L, h, c, z, j, x0, rowbase);
+              float acc = cp[h];
+#pragma unroll
+              for (int mu = 0; mu < D; ++mu) {
+                float dp, dm;
+                if (mu < D - 1) {
+                  int jp, jm;
+                  slab_inplane_nb<D>(L, mu, j, x0, rowbase, jp, jm);
+                  dp = cur[jp]; dm = cur[jm];
+                } else {
+                  dp = next[j]; dm = prev[j];
+                }
+                acc = fmaf(cp[(size_t)(1 + mu) * V + h], dp, acc);
+                acc = fmaf(cp[(size_t)(1 + D + mu) * V + h], dm, acc);
+              }
+              const float old = cur[j], diff = acc - old;
+              if (last) corr = fmaxf(corr, fabsf(diff));
+              cur[j] = fmaf(om, diff, old);
+            }
+          });
+          if (!ok) return k;
+        }
+      }
+      double dummy;
+      block_max2(0.0, corr, dummy, corr);
+      if (corr <= thr) break;
+      if (first == 0.f) first = corr;
+      else if (!(corr < 16.f * first)) break;
+    }
+    return k;
+  };
+
+  // 3. g_x <- g_x exp(i f delta_x), renormalised (f < 0 takes part of a step back)
+  auto rotate = [&](double2* g, double f) {
+    if (tid == 0) fence_async_global();   // the ring's stores, then generic reads of delta
+    __syncthreads();
+    for (int x = tid; x < V; x += nt) {
+      const int z = x / P, j = x - z * P;
+      const double tf = f * (double)fminf(fmaxf(__ldcg(dl + (size_t)z * Ps + j), -0.2f), 0.2f);
+      double sn, cs;
+      sincos(tf, &sn, &cs);
+      const double2 gx = g[x];
+      const double nx = gx.x * cs - gx.y * sn, ny = gx.x * sn + gx.y * cs;
+      const double q = rsqrt(nx * nx + ny * ny);
+      g[x] = make_double2(nx * q, ny * q);
+    }
+    __syncthreads();
   };
 
   for (;;) {
@@ -302,48 +659,67 @@ __global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
     const long long idx = *tidx;
     __syncthreads();
     if (idx >= a.n || *abort_flag) break;
-    E* st = static_cast<E*>(a.state) + (size_t)idx * V;
-    if (a.init) {
-      for (int x = tid; x < V; x += nt) st[x] = Ops::start(a, idx, x);
-      fence_async_global();   // generic writes, then bulk reads of them
-      __syncthreads();
-    }
-    int sweeps = 0, until = a.check_every;
-    bool ok = true, conv = false;
-    R r = 0;
-    for (;;) {
-      if (!phase(st, 0) || !phase(st, 1)) { ok = false; break; }
-      ++sweeps;
-      if (--until == 0) {
-        until = a.check_every;
-        r = residual(st, ok);
-        if (!ok) break;
-        conv = r < Ops::eps(a);
-        if (conv || sweeps >= a.max_sweeps) break;
+    double2* g = a.state + (size_t)idx * V;
+    // this start's SOR parameter (Young), a little above w_opt where the
+    // rate degrades more slowly than below it
+    float om = a.omega_sweeps;
+    {
+      const float lam = a.rate ? a.rate[idx] : 0.f, w = a.omega_sweeps;
+      if (lam > w - 1.f && lam < 1.f) {
+        const float m2 = fminf((lam + w - 1.f) * (lam + w - 1.f) / (lam * w * w), 0.99999f);
+        const float wopt = 2.f / (1.f + sqrtf(1.f - m2));
+        om = fminf(wopt + 0.1f * (2.f - wopt), 1.985f);
       }
     }
+    bool ok = true, conv = false;
+    int cap = a.inner_max;
+    float bmax;
+    double r = rhs(g, bmax);
+    ++my_pass;
+    for (int it = 0;; ++it) {
+      if (r < a.eps) { conv = true; break; }
+      if (it >= a.newton_max) break;
+      ++my_steps;
+      my_inner += (unsigned long long)sor(bmax, cap, om, ok);
+      if (!ok) break;
+      const double r0 = r;
+      rotate(g, 1.0);
+      r = rhs(g, bmax);
+      ++my_pass;
+      double f = 1.0;
+      for (int h = 0; h < 6 && !(r < r0); ++h) {   // backtrack to half the step
+        rotate(g, -0.5 * f);
+        f *= 0.5;
+        r = rhs(g, bmax);
+        ++my_pass;
+      }
+      if (!(r < r0)) break;
+      if (!(r < 0.25 * r0)) cap = min(4 * cap, 8192);
+    }
     if (!ok) {
-      // a wait ran out: flag it, give the loads still in flight a bounded
-      // time to land in their buffers, and stop
-      fail();
-      for (int k = 0; k < 3; ++k) mbar_wait(bar0 + 8u * k, (parity >> k) & 1u);
+      if (tid == 0) { atomicExch(&a.err[3], 1); *abort_flag = 1; }
+      ring.drain();
       if (tid == 0) bulk_wait_all();
       __syncthreads();
       break;
     }
     if (tid == 0) {
-      a.status[idx] = conv ? kConverged : kNotConverged;
-      if (a.init) a.sweeps[idx] = sweeps; else a.sweeps[idx] += sweeps;
-      if (sizeof(R) == 8) a.resid[idx] = (double)r;
-      my_sweeps += sweeps;
-      if (conv) ++my_conv; else ++my_nconv;
+      a.resid[idx] = r;
+      if (conv) {
+        a.status[idx] = kConverged;
+        ++my_conv;
+      } else {
+        a.redo[atomicAdd(a.n_redo, 1u)] = (unsigned)idx;
+        ++my_redo;
+      }
     }
   }
   if (tid == 0) {
-    if (a.s_sweeps >= 0) atomicAdd(&a.stats[a.s_sweeps], my_sweeps);
-    if (a.s_updates >= 0) atomicAdd(&a.stats[a.s_updates], my_sweeps * (unsigned long long)V);
-    if (a.s_conv >= 0) atomicAdd(&a.stats[a.s_conv], my_conv);
-    if (a.s_nconv >= 0) atomicAdd(&a.stats[a.s_nconv], my_nconv);
+    atomicAdd(&a.stats[a.s_steps], my_steps);
+    atomicAdd(&a.stats[a.s_inner], my_inner);
+    atomicAdd(&a.stats[a.s_pass], my_pass);
+    atomicAdd(&a.stats[a.s_conv], my_conv);
+    atomicAdd(&a.stats[a.s_redo], my_redo);
   }
 }
 

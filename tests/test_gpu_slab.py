@@ -1,7 +1,8 @@
 """Lattices beyond shared memory: the sweeps stream each start's lattice in
 hyperplanes from global memory (bulk copies).  The plain path stays bit-exact
-to the oracle start by start; the mixed path (FP32 sweeps, then FP64 sweeps)
-agrees with it; the first-region fast path flags what the weights decide."""
+to the oracle start by start; the mixed path (FP32 sweeps, then the inexact
+Newton polish, FP64 sweeps for what it leaves) agrees with it; the
+first-region fast path flags what the weights decide."""
 import numpy as np
 import pytest
 
@@ -21,15 +22,19 @@ def _plain(gb, d, L, phi, oid, n, omega=1.7, eps=1e-24, **kw):
         gb.gc_destroy_orbit(h)
 
 
+@pytest.mark.parametrize("variant", ["cluster", "cta"])
 @pytest.mark.parametrize("d,L,n", [(2, 64, 24), (3, 16, 12), (2, 128, 6)])
-def test_hyperplane_plain_path_is_bit_exact_to_the_oracle(d, L, n):
+def test_hyperplane_plain_path_is_bit_exact_to_the_oracle(d, L, n, variant):
     """2D 64^2 and 3D 16^3 (links beyond shared memory) and 2D 128^2 (beyond
-    the shared-memory kernels' 4096 sites): status and sweep counts equal the
+    the shared-memory kernels' 4096 sites), fewer starts than SMs: each start
+    on a cluster of CTAs that split its planes ("cluster", the default for
+    few starts) or on one CTA ("cta").  Status and sweep counts equal the
     oracle's, F within 1e-12, each start's canonical copy within 1e-9 rad."""
     import paper_1403_0555_b300 as gb
     V = L ** d
     phi = oi.von_mises_orbit(d, L, 1.0, 7)
-    st, s, c = _plain(gb, d, L, phi, 7, n, precision=gb.GC_FP64, check_every=1)
+    rv = gb.GC_RELAX_AUTO if variant == "cluster" else gb.GC_RELAX_GENERIC
+    st, s, c = _plain(gb, d, L, phi, 7, n, precision=gb.GC_FP64, check_every=1, relax_variant=rv)
     rel = oracle.relax_starts(d, L, phi, 1, 7, 0, n, 1.7, 1e-24)
     assert np.array_equal(s["status"], rel.status.astype(np.int32))
     assert np.array_equal(s["sweeps"], rel.sweeps)
@@ -46,25 +51,52 @@ def test_hyperplane_plain_path_is_bit_exact_to_the_oracle(d, L, n):
     assert st["n_distinct"] == c["n_distinct"] > 0
 
 
+def _agree(c_a, s_a, c_b, s_b, n):
+    same = 0
+    for k in range(n):
+        ta, tb = c_a["theta"][s_a["copy_idx"][k]], c_b["theta"][s_b["copy_idx"][k]]
+        if np.max(np.abs(wrap(ta - tb))) <= 1e-6:
+            same += 1
+            assert abs(s_a["F"][k] - s_b["F"][k]) <= 1e-10 * s_a["F"][k]
+    return same
+
+
 def test_hyperplane_mixed_path_agrees_with_the_plain_path():
-    """4D 8^4 (FP32 hyperplane sweeps, then FP64 ones): every start converges to
-    the FP64 tolerance and reaches the plain path's minimum in at least 90 % of
-    the starts (the FP32 phase may settle a start near a basin boundary
-    elsewhere; 8^4 landscapes hold many close minima)."""
+    """4D 8^4 (FP32 hyperplane sweeps, then Newton steps with an FP32 SOR inner
+    solve): every start converges to the FP64 tolerance, the oracle's
+    divergence of each copy is below it, and the copy is the plain path's
+    minimum in at least 90 % of the starts (the FP32 phase may settle a start
+    near a basin boundary elsewhere; 8^4 landscapes hold many close minima)."""
     import paper_1403_0555_b300 as gb
     d, L, n = 4, 8, 32
     phi = oi.von_mises_orbit(d, L, 1.0, 3)
     st_p, s_p, c_p = _plain(gb, d, L, phi, 3, n, precision=gb.GC_FP64, check_every=1)
     st_m, s_m, c_m = _plain(gb, d, L, phi, 3, n, precision=gb.GC_MIXED, check_every=4)
     assert st_m["n_converged"] == n and st_p["n_converged"] == n
-    assert st_m["sweeps_fp32"] > 0 and st_m["site_updates_fp64"] > 0
-    same = 0
-    for k in range(n):
-        ta, tb = c_p["theta"][s_p["copy_idx"][k]], c_m["theta"][s_m["copy_idx"][k]]
-        if np.max(np.abs(wrap(ta - tb))) <= 1e-6:
-            same += 1
-            assert abs(s_p["F"][k] - s_m["F"][k]) <= 1e-10 * s_p["F"][k]
+    assert st_m["sweeps_fp32"] > 0 and st_m["newton_steps"] > 0 and st_m["newton_inner_sweeps"] > 0
+    assert st_m["polish_fallbacks"] <= n // 8
+    for k in range(c_m["n_distinct"]):
+        t = c_m["theta"][k]
+        dv = oracle.divergence(d, L, phi, np.stack([np.cos(t), np.sin(t)], axis=-1))
+        assert np.max(dv ** 2) < 2e-24
+    same = _agree(c_p, s_p, c_m, s_m, n)
     assert same >= 0.9 * n, same
+
+
+def test_hyperplane_newton_fallback_to_fp64_sweeps():
+    """3D 16^3 mixed path with no Newton steps allowed: every start goes on to
+    the FP64 hyperplane sweeps, converges, and ends at the minimum the Newton
+    polish reaches from the same FP32 state (both finish the same basin)."""
+    import paper_1403_0555_b300 as gb
+    d, L, n = 3, 16, 24
+    phi = oi.von_mises_orbit(d, L, 1.0, 5)
+    st_n, s_n, c_n = _plain(gb, d, L, phi, 5, n, precision=gb.GC_MIXED, check_every=4)
+    st_f, s_f, c_f = _plain(gb, d, L, phi, 5, n, precision=gb.GC_MIXED, check_every=4, newton_max=0)
+    assert st_n["n_converged"] == n and st_f["n_converged"] == n
+    assert st_f["polish_fallbacks"] == n and st_f["newton_steps"] == 0 and st_f["site_updates_fp64"] > 0
+    assert st_n["newton_steps"] >= n
+    assert np.array_equal(s_n["sweeps"] <= s_f["sweeps"], np.ones(n, bool))
+    assert _agree(c_n, s_n, c_f, s_f, n) >= n - 1
 
 
 def test_hyperplane_first_region_fast_path():
