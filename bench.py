@@ -64,6 +64,8 @@ def parse():
                    help="1: launch shapes only; 2: also the sweep-unroll depth")
     p.add_argument("--no-uneven", dest="uneven", action="store_false",
                    help="skip the uneven-batch leg (26 orbits of 13 lattice sizes in one graph)")
+    p.add_argument("--no-large", dest="large", action="store_false",
+                   help="skip the large-lattice leg (4D 16^4, hyperplane path)")
     p.add_argument("--serve-requests", type=int, default=100,
                    help="requests of the Poisson serving leg (0 skips it)")
     return p.parse_args()
@@ -244,6 +246,69 @@ def uneven_leg(gb, torch, check_every, steps=2):
             "value": conv / (ms / 1e3), "unit": "copies/s",
             "site_updates_per_s": upd / (ms / 1e3), "ms_per_step": ms / steps, "steps": steps,
             "launch": "one gc_enumerate_batch per step as one CUDA graph, autotuned shapes and sweep-unroll depth"}
+
+
+# ----------------------------------------------------------------------------
+# large lattice: 4D 16^4, beyond shared memory (hyperplane path)
+# ----------------------------------------------------------------------------
+
+def large_lattice_leg(gb, torch, d=4, L=16, n=592, runs=2):
+    """One orbit of 4D 16^4 (65 536 sites, von Mises kappa = 1, seed 1), 592
+    starts (four per SM) through the mixed path: FP32 hyperplane sweeps, the
+    Newton polish, the FP64 cluster sweeps of the starts it leaves, final
+    pass, dedup, fast-path region test.  Each run is timed with CUDA events on
+    the launch stream around the enumerate call; per-stage times are the
+    library's events.  HBM figures count algorithmic bytes: the FP32 sweeps
+    move each start's state (8 B/site) in and out once per colour phase and
+    read it once per residual check (the links, shared by all starts, stay in
+    L2); an inner SOR sweep reads (2d + 1) FP32 coefficients per site and moves
+    the correction (4 B/site) in and out once per phase."""
+    V = L ** d
+    phi = oi.von_mises_orbit(d, L, 1.0, 1)
+    stream = torch.cuda.current_stream()
+    opt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=4, fp_mode=gb.GC_FP_AUTO,
+                                stream=stream)
+    h = gb.gc_create_orbit(d, L, phi, 1)
+    gb.gc_enumerate_copies(h, 64, 1.7, 1e-24, opt)            # allocations, first launches
+    gb.gc_destroy_orbit(h)
+    acc = {}
+    ms = 0.0
+    for _ in range(runs):
+        h = gb.gc_create_orbit(d, L, phi, 1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gb.gc_enumerate_copies(h, n, 1.7, 1e-24, opt)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        st = gb.gc_orbit_stats(h)
+        gb.gc_destroy_orbit(h)
+        for k, v in st.items():
+            acc[k] = acc.get(k, 0) + v
+    hbm = json.load(open(PEAKS_FILE))["hbm_gbs"] if os.path.exists(PEAKS_FILE) else 6400.0
+    relax_bytes = acc["sweeps_fp32"] * V * 32 + acc["sweeps_fp32"] / 4 * V * 8 + acc["n_starts"] * V * 8
+    newton_ms = acc["ms_polish"] - acc["ms_polish_redo"]
+    inner_bytes = acc["newton_inner_sweeps"] * V * (4 * (2 * d + 1) + 16)
+    relax_gbs = relax_bytes / (acc["ms_relax"] / 1e3) / 1e9
+    inner_gbs = inner_bytes / (newton_ms / 1e3) / 1e9
+    return {"workload": f"{d}D {L}^{d} ({V} sites), von Mises kappa=1 seed 1, {n} starts, mixed, check_every 4",
+            "runs": runs, "value": acc["n_converged"] / (ms / 1e3), "unit": "copies/s",
+            "ms_per_run": ms / runs,
+            "stage_ms": {"relax_fp32": acc["ms_relax"] / runs, "newton": newton_ms / runs,
+                         "fp64_sweeps_and_final": acc["ms_polish_redo"] / runs,
+                         "dedup": acc["ms_dedup"] / runs, "fp_test": acc["ms_fptest"] / runs},
+            "converged": acc["n_converged"] // runs, "distinct": acc["n_distinct"] // runs,
+            "sweeps_fp32_per_start": acc["sweeps_fp32"] / acc["n_starts"],
+            "newton_steps_per_start": acc["newton_steps"] / acc["n_starts"],
+            "inner_sweeps_per_start": acc["newton_inner_sweeps"] / acc["n_starts"],
+            "fp64_fallback_starts": acc["polish_fallbacks"] // runs,
+            "relax_slab": {"kernel": "relax_slab_kernel<float2,4,false>", "bound": "hbm",
+                           "achieved": relax_gbs, "peak": hbm, "unit": "GB/s", "frac": relax_gbs / hbm,
+                           "bytes_per_update": 32 + 8 / 4},
+            "newton_inner": {"kernel": "slab_newton_kernel<4>", "bound": "hbm", "achieved": inner_gbs,
+                             "peak": hbm, "unit": "GB/s", "frac": inner_gbs / hbm,
+                             "note": "over the whole Newton launch, its tail of hard starts included"}}
 
 
 # ----------------------------------------------------------------------------
@@ -552,6 +617,7 @@ def run_ours(args):
     roof["launch_starts"] = n_launch_starts
 
     uneven = uneven_leg(gb, torch, args.check_every) if args.uneven else None
+    large = large_lattice_leg(gb, torch) if args.large else None
 
     serving = None
     if args.serve_requests > 0:
@@ -586,6 +652,7 @@ def run_ours(args):
         "distinct_copies_per_orbit": n_distinct,
         "plain_fp64": plain,
         "batch_uneven": uneven,
+        "large_lattice": large,
         "serving": serving,
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -703,11 +703,11 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       gc::slab_promote_kernel<<<(int)std::min<size_t>((nv + 255) / 256, 4096), 256, 0, s>>>(
           o->s_state32.as<float2>(), st64, nv);
       ++o->launches;
-      // Newton polish (one start per CTA, four CTAs per SM)
+      // Newton polish (one start per 1024-thread CTA, one CTA per SM)
       GC_CUDA(cudaMemsetAsync(wctr, 0, 8, s));
       GC_CUDA(cudaMemsetAsync(o->n_redo(), 0, 4, s));
       const int Ps = (P + 3) / 4 * 4;
-      const int grid_n = (int)std::max<long long>(1, std::min<long long>(b, 4LL * sm_count()));
+      const int grid_n = (int)std::max<long long>(1, std::min<long long>(b, (long long)sm_count()));
       gc::SlabNewtonArgs na{};
       na.d = d; na.L = L; na.V = V; na.P = P; na.Ps = Ps;
       na.links = o->links64.as<double2>();
@@ -736,7 +736,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
         const size_t smn = gc::slab_newton_smem_bytes(Ps);
         auto launch_n = [&](auto kern) -> int {
           if (int rc = raise_smem_limit(kern, smn)) return rc;
-          kern<<<grid_n, 256, smn, s>>>(na);
+          kern<<<grid_n, 1024, smn, s>>>(na);
           ++o->launches;
           GC_CUDA(cudaGetLastError());
           return GC_OK;

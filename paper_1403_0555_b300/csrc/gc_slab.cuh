@@ -471,7 +471,11 @@ __global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
 // the sweeps of w_opt.  A step that does not lower max div^2 is halved (up
 // to six times); a start without descent, or still above eps after
 // newton_max steps, is listed for the FP64 sweeps (an indefinite M near a
-// saddle, which relaxation leaves and Newton would not).
+// saddle, which relaxation leaves and Newton would not).  The inner solve of
+// a step that cut max div^2 less than 4x gets 4x the sweep cap (up to 4x
+// inner_max); a start gets 8x inner_max inner sweeps in all, so a
+// near-singular M costs a bounded time on its CTA before the FP64 sweeps
+// (one start per cluster) take it.
 struct SlabNewtonArgs {
   int d, L, V, P, Ps;              // Ps: plane stride of delta (P rounded up to 4 floats)
   const double2* links;            // FP64 [x*d + mu], site order
@@ -499,14 +503,14 @@ __host__ __device__ inline size_t slab_newton_scratch_floats(int d, int V, int L
 }
 
 template <int D>
-__global__ void __launch_bounds__(256, 4) slab_newton_kernel(const SlabNewtonArgs a) {
+__global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int L = a.L, V = a.V, P = a.P, P2 = a.P / 2, Ps = a.Ps, tid = threadIdx.x, nt = blockDim.x;
   const unsigned sbase = (unsigned)__cvta_generic_to_shared(smem);
   long long* tidx = reinterpret_cast<long long*>(smem + 32);
   int* abort_flag = reinterpret_cast<int*>(smem + 40);
-  double* redd = reinterpret_cast<double*>(smem + 64);   // per-warp partials (<= 8 warps)
-  float* redf = reinterpret_cast<float*>(smem + 192);
+  double* redd = reinterpret_cast<double*>(smem + 64);   // per-warp partials (<= 32 warps)
+  float* redf = reinterpret_cast<float*>(smem + 320);
   PlaneRing<float> ring{reinterpret_cast<float*>(smem + 512), sbase + 512, sbase, (unsigned)(Ps * 4), L, Ps, 0u};
   float* coef = a.scratch + (size_t)blockIdx.x * a.scratch_floats;   // [1 + 2D][V], colour-split order
   float* dl = coef + (size_t)(1 + 2 * D) * V;                         // [L][Ps], plane order
@@ -672,15 +676,17 @@ __global__ void __launch_bounds__(256, 4) slab_newton_kernel(const SlabNewtonArg
       }
     }
     bool ok = true, conv = false;
-    int cap = a.inner_max;
+    int cap = a.inner_max, budget = 8 * a.inner_max;   // inner sweeps per solve, per start
     float bmax;
     double r = rhs(g, bmax);
     ++my_pass;
     for (int it = 0;; ++it) {
       if (r < a.eps) { conv = true; break; }
-      if (it >= a.newton_max) break;
+      if (it >= a.newton_max || budget <= 0) break;
       ++my_steps;
-      my_inner += (unsigned long long)sor(bmax, cap, om, ok);
+      const int k = sor(bmax, min(cap, budget), om, ok);
+      my_inner += (unsigned long long)k;
+      budget -= k;
       if (!ok) break;
       const double r0 = r;
       rotate(g, 1.0);
@@ -694,7 +700,7 @@ __global__ void __launch_bounds__(256, 4) slab_newton_kernel(const SlabNewtonArg
         ++my_pass;
       }
       if (!(r < r0)) break;
-      if (!(r < 0.25 * r0)) cap = min(4 * cap, 8192);
+      if (!(r < 0.25 * r0)) cap = min(4 * cap, 4 * a.inner_max);
     }
     if (!ok) {
       if (tid == 0) { atomicExch(&a.err[3], 1); *abort_flag = 1; }
