@@ -665,8 +665,8 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     sa.err = o->err();
     sa.work_ctr = wctr;
     const int grid = (int)std::max<long long>(1, std::min<long long>(b, 2LL * sm_count()));
-    // few starts (fewer than SMs) or a device-side list of hard starts: one
-    // start per cluster of kSlabCluster CTAs; otherwise one CTA per start
+    // one start per cluster of kSlabCluster CTAs (default), or one CTA per
+    // start (GC_RELAX_GENERIC)
     auto launch = [&](bool fp64, bool cluster) -> int {
       int rc = GC_OK;
       if (fp64) {
@@ -685,8 +685,9 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       ++o->launches;
       return rc;
     };
-    const bool few = opt.relax_variant != GC_RELAX_GENERIC && b < sm_count();
-    const bool hard_cluster = opt.relax_variant != GC_RELAX_GENERIC;
+    // clusters unless GC_RELAX_GENERIC: a start's sweep count is not known in
+    // advance, and a long start on one CTA sets the batch's end
+    const bool cluster = opt.relax_variant != GC_RELAX_GENERIC;
     if (ev) GC_CUDA(cudaEventRecord(ev[0], s));
     double2* st64 = o->s_config.as<double2>();
     if (mixed) {
@@ -697,7 +698,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       sa.rate = o->s_rate.as<float>();
       sa.init = 1;
       sa.s_sweeps = kSweeps32; sa.s_updates = kUpdates32; sa.s_conv = kConv32; sa.s_nconv = kNConv32;
-      if (int rc = launch(false, few)) return rc;
+      if (int rc = launch(false, cluster)) return rc;
       if (ev) GC_CUDA(cudaEventRecord(ev[1], s));
       const size_t nv = (size_t)b * V;
       gc::slab_promote_kernel<<<(int)std::min<size_t>((nv + 255) / 256, 4096), 256, 0, s>>>(
@@ -758,6 +759,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       sa.list = o->s_redo.as<unsigned>();
       sa.n_list = o->n_redo();
       sa.rate = nullptr;
+      sa.omega_rate = o->s_rate.as<float>();   // the polish's sweeps at each start's Young parameter
       sa.s_sweeps = -1; sa.s_updates = kUpd64; sa.s_conv = kPConv; sa.s_nconv = kPNConv;
     } else {
       sa.links = o->links64.p;
@@ -765,7 +767,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       sa.init = 1;
       sa.s_sweeps = kSweeps; sa.s_updates = kUpdates; sa.s_conv = kConv; sa.s_nconv = kNConv;
     }
-    if (int rc = launch(true, mixed ? hard_cluster : few)) return rc;
+    if (int rc = launch(true, cluster)) return rc;
     if (ev && !mixed) GC_CUDA(cudaEventRecord(ev[1], s));
     // functional, fingerprint and canonical copy (in place)
     gc::slab_final_kernel<<<grid, 256, 0, s>>>(st64, o->links64.as<double2>(), d, V, L, b,

@@ -50,6 +50,9 @@ struct SlabArgs {
   double* resid;
   float* rate;                     // when set: per start, the contraction of max |div| per sweep
                                    // over the last check interval (0: none seen)
+  const float* omega_rate;         // when set (FP64 polish of hard starts): per start the
+                                   // contraction its FP32 sweeps showed at omega32; the sweeps
+                                   // then run at Young's parameter for it (young_omega)
   unsigned long long* stats;
   int s_sweeps, s_updates, s_conv, s_nconv;   // stats slots (-1: none)
   int* err;                        // [3] a bulk-copy wait ran out
@@ -162,6 +165,25 @@ __device__ __forceinline__ bool ring_walk(PlaneRing<E>& R, E* base, bool store, 
   return ring_walk(R, base, store, static_cast<Body&&>(body), 0, R.L);
 }
 
+// Overrelaxation parameter of one start's sweeps (both precisions' forms)
+struct SlabOmega {
+  double om, om1;
+  float om32, om1_32;
+};
+
+// Young's relation for consistently ordered matrices (the red-black ordering
+// of this stencil): SOR at parameter w < w_opt contracting by lam per sweep
+// means a Jacobi radius mu^2 = (lam + w - 1)^2 / (lam w^2), and
+// w_opt = 2 / (1 + sqrt(1 - mu^2)).  Returns w_opt plus a tenth of its
+// distance to 2 (the rate degrades more slowly above w_opt than below), or w
+// when lam says nothing (lam <= w - 1: w is at or above w_opt already).
+__device__ __forceinline__ float young_omega(float lam, float w) {
+  if (!(lam > w - 1.f && lam < 1.f)) return w;
+  const float m2 = fminf((lam + w - 1.f) * (lam + w - 1.f) / (lam * w * w), 0.99999f);
+  const float wopt = 2.f / (1.f + sqrtf(1.f - m2));
+  return fminf(wopt + 0.1f * (2.f - wopt), 1.985f);
+}
+
 // -- the site update in each precision ----------------------------------------
 template <class E> struct SlabOps;
 template <> struct SlabOps<double2> {
@@ -176,13 +198,13 @@ template <> struct SlabOps<double2> {
     S.x = __dadd_rn(S.x, t.x); S.y = __dadd_rn(S.y, t.y);
   }
   static __device__ __forceinline__ double2 zero() { return make_double2(0.0, 0.0); }
-  static __device__ __forceinline__ double2 move(double2 gx, double2 S, const SlabArgs& a) {
+  static __device__ __forceinline__ double2 move(double2 gx, double2 S, const SlabOmega& a) {
     const double n2 = __dadd_rn(__dmul_rn(S.x, S.x), __dmul_rn(S.y, S.y));
     if (!(n2 > 0.0)) return gx;
     const double r = __drcp_rn(__dsqrt_rn(n2));
     const double hx = __dmul_rn(S.x, r), hy = __dmul_rn(S.y, r);
-    const double vx = __dadd_rn(__dmul_rn(a.om1, gx.x), __dmul_rn(a.omega, hx));
-    const double vy = __dadd_rn(__dmul_rn(a.om1, gx.y), __dmul_rn(a.omega, hy));
+    const double vx = __dadd_rn(__dmul_rn(a.om1, gx.x), __dmul_rn(a.om, hx));
+    const double vy = __dadd_rn(__dmul_rn(a.om1, gx.y), __dmul_rn(a.om, hy));
     const double m2 = __dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy));
     if (!(m2 > 0.0)) return make_double2(hx, hy);
     const double q = __drcp_rn(__dsqrt_rn(m2));
@@ -208,10 +230,10 @@ template <> struct SlabOps<float2> {
     S.y = fmaf(u.x, h.y, S.y); S.y = fmaf(-u.y, h.x, S.y);
   }
   static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
-  static __device__ __forceinline__ float2 move(float2 gx, float2 S, const SlabArgs& a) {
+  static __device__ __forceinline__ float2 move(float2 gx, float2 S, const SlabOmega& a) {
     const float n2 = fmaf(S.x, S.x, S.y * S.y);
     if (!(n2 > 1e-30f)) return gx;   // a vanishing staple leaves the site as it is
-    const float r = rsqrt_sfu(n2) * a.omega32;
+    const float r = rsqrt_sfu(n2) * a.om32;
     const float vx = fmaf(S.x, r, a.om1_32 * gx.x), vy = fmaf(S.y, r, a.om1_32 * gx.y);
     const float m2 = fmaf(vx, vx, vy * vy);
     if (!(m2 > 1e-30f)) return gx;
@@ -302,6 +324,7 @@ __global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
   __syncthreads();
   if constexpr (CL) cg::this_cluster().sync();   // every CTA's barriers and slots exist
   unsigned long long my_sweeps = 0, my_conv = 0, my_nconv = 0;
+  SlabOmega w{};   // this start's parameter
 
   // cluster-wide: max of r over the CTAs, ok = every CTA's ok (identity
   // without a cluster).  Double-buffered slots in rank 0: round k+2 writes
@@ -360,7 +383,7 @@ __global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
       for (int h = tid; h < P / 2; h += nt) {
         int j, x0, rowbase;
         slab_site_of<D>(L, h, c, z, j, x0, rowbase);
-        cur[j] = Ops::move(cur[j], staple(prev, cur, next, z, j, x0, rowbase), a);
+        cur[j] = Ops::move(cur[j], staple(prev, cur, next, z, j, x0, rowbase), w);
       }
     }, z0, nz);
     combine(ok, 0.0);
@@ -401,6 +424,11 @@ __global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
     const long long idx = a.list ? (long long)a.list[i] : i;
     E* st = static_cast<E*>(a.state) + (size_t)idx * V;
     bool ok = true;
+    w = SlabOmega{a.omega, a.om1, a.omega32, a.om1_32};
+    if (a.omega_rate) {
+      const float wy = young_omega(a.omega_rate[idx], a.omega32);
+      w = SlabOmega{(double)wy, 1.0 - (double)wy, wy, 1.f - wy};
+    }
     if (a.init) {
       for (int x = z0 * P + tid; x < (z0 + nz) * P; x += nt) st[x] = Ops::start(a, idx, x);
       fence_async_global();   // generic writes, then bulk reads of them
@@ -462,13 +490,10 @@ __global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
 //      ring like the sweeps, until the corrections stall below lin_tol
 //      max |b|;
 //   3. FP64 pass: g_x <- g_x exp(i delta_x).
-// The SOR parameter is set per start from Young's relation for consistently
-// ordered matrices (which the red-black ordering of this stencil gives): near
-// the minimum the FP32 sweeps at parameter w are the linear SOR on M, so the
-// contraction lambda they showed gives the Jacobi radius
-// mu^2 = (lambda + w - 1)^2 / (lambda w^2) and w_opt = 2 / (1 + sqrt(1 - mu^2)).
-// Large lattices have mu close to 1, where a fixed parameter needs many times
-// the sweeps of w_opt.  A step that does not lower max div^2 is halved (up
+// The SOR parameter is set per start by young_omega: near the minimum the
+// FP32 sweeps at parameter w are the linear SOR on M, so the contraction they
+// showed gives M's Jacobi radius.  Large lattices have it close to 1, where a
+// fixed parameter needs many times the sweeps of w_opt.  A step that does not lower max div^2 is halved (up
 // to six times); a start without descent, or still above eps after
 // newton_max steps, is listed for the FP64 sweeps (an indefinite M near a
 // saddle, which relaxation leaves and Newton would not).  The inner solve of
@@ -664,17 +689,8 @@ __global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonAr
     __syncthreads();
     if (idx >= a.n || *abort_flag) break;
     double2* g = a.state + (size_t)idx * V;
-    // this start's SOR parameter (Young), a little above w_opt where the
-    // rate degrades more slowly than below it
-    float om = a.omega_sweeps;
-    {
-      const float lam = a.rate ? a.rate[idx] : 0.f, w = a.omega_sweeps;
-      if (lam > w - 1.f && lam < 1.f) {
-        const float m2 = fminf((lam + w - 1.f) * (lam + w - 1.f) / (lam * w * w), 0.99999f);
-        const float wopt = 2.f / (1.f + sqrtf(1.f - m2));
-        om = fminf(wopt + 0.1f * (2.f - wopt), 1.985f);
-      }
-    }
+    // this start's SOR parameter (Young)
+    const float om = young_omega(a.rate ? a.rate[idx] : 0.f, a.omega_sweeps);
     bool ok = true, conv = false;
     int cap = a.inner_max, budget = 8 * a.inner_max;   // inner sweeps per solve, per start
     float bmax;
