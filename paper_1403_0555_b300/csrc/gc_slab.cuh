@@ -522,23 +522,40 @@ struct SlabNewtonArgs {
   int* err;
 };
 
-__host__ __device__ inline size_t slab_newton_smem_bytes(int Ps) { return 512 + 3 * (size_t)Ps * 4; }
+__host__ __device__ inline size_t slab_newton_smem_bytes(int Ps) { return 1024 + 3 * (size_t)Ps * 4; }
 __host__ __device__ inline size_t slab_newton_scratch_floats(int d, int V, int L, int Ps) {
   return (((size_t)(1 + 2 * d) * V + (size_t)L * Ps) + 3) / 4 * 4;
 }
 
-template <int D>
+// CL = false: one start per CTA (scratch per CTA), starts from a counter.
+// CL = true: one start per cluster (scratch per cluster), CTA q taking planes
+// [q L / C, (q+1) L / C) in every pass; the CTAs meet at a cluster barrier
+// after each FP64 pass and each SOR phase, which carries the maxima (max
+// div^2 and max |b|, or the group's correction) and whether a wait ran out.
+template <int D, bool CL>
 __global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int L = a.L, V = a.V, P = a.P, P2 = a.P / 2, Ps = a.Ps, tid = threadIdx.x, nt = blockDim.x;
   const unsigned sbase = (unsigned)__cvta_generic_to_shared(smem);
   long long* tidx = reinterpret_cast<long long*>(smem + 32);
   int* abort_flag = reinterpret_cast<int*>(smem + 40);
-  double* redd = reinterpret_cast<double*>(smem + 64);   // per-warp partials (<= 32 warps)
+  double* redd = reinterpret_cast<double*>(smem + 64);     // per-warp partials (<= 32 warps)
   float* redf = reinterpret_cast<float*>(smem + 320);
-  PlaneRing<float> ring{reinterpret_cast<float*>(smem + 512), sbase + 512, sbase, (unsigned)(Ps * 4), L, Ps, 0u};
-  float* coef = a.scratch + (size_t)blockIdx.x * a.scratch_floats;   // [1 + 2D][V], colour-split order
-  float* dl = coef + (size_t)(1 + 2 * D) * V;                         // [L][Ps], plane order
+  double* cl_slots = reinterpret_cast<double*>(smem + 512);  // [2][16][2] cluster exchange (rank 0's)
+  PlaneRing<float> ring{reinterpret_cast<float*>(smem + 1024), sbase + 1024, sbase, (unsigned)(Ps * 4), L, Ps, 0u};
+  int C = 1, q = 0, cid = 0, ncl = 1;
+  if constexpr (CL) {
+    cg::cluster_group cl = cg::this_cluster();
+    C = (int)cl.num_blocks();
+    q = (int)cl.block_rank();
+    cid = blockIdx.x / C;
+    ncl = gridDim.x / C;
+  }
+  const int z0 = q * L / C, nz = (q + 1) * L / C - z0;   // this CTA's planes (nz may be 0)
+  const int x_beg = z0 * P, x_end = (z0 + nz) * P;
+  float* coef = a.scratch + (size_t)(CL ? cid : blockIdx.x) * a.scratch_floats;   // [1 + 2D][V], colour-split
+  float* dl = coef + (size_t)(1 + 2 * D) * V;                                       // [L][Ps], plane order
+  int round = 0;
 
   if (tid == 0) {
     for (int k = 0; k < 3; ++k) mbar_init(sbase + 8u * k, 1);
@@ -546,25 +563,53 @@ __global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonAr
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  if constexpr (CL) cg::this_cluster().sync();
   unsigned long long my_steps = 0, my_inner = 0, my_pass = 0, my_conv = 0, my_redo = 0;
 
-  auto block_max2 = [&](double r, float f, double& ro, float& fo) {
+  // block maxima of r and f, then (cluster) over the CTAs; ok = every CTA's ok.
+  // Double-buffered slots in rank 0 (as in the sweeps).
+  auto reduce = [&](bool& ok, double& r, float& f) {
     for (int o = 16; o > 0; o >>= 1) {
       r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
       f = fmaxf(f, __shfl_xor_sync(0xffffffffu, f, o));
     }
     if ((tid & 31) == 0) { redd[tid >> 5] = r; redf[tid >> 5] = f; }
     __syncthreads();
-    ro = 0.0; fo = 0.f;
-    for (int w = 0; w < nt / 32; ++w) { ro = fmax(ro, redd[w]); fo = fmaxf(fo, redf[w]); }
+    r = 0.0; f = 0.f;
+    for (int w = 0; w < nt / 32; ++w) { r = fmax(r, redd[w]); f = fmaxf(f, redf[w]); }
     __syncthreads();
+    if constexpr (CL) {
+      cg::cluster_group cl = cg::this_cluster();
+      double* set = cl_slots + 32 * (round & 1);
+      if (tid == 0) {
+        fence_async_global();   // completed bulk stores and generic writes, before the release
+        double* dst = cl.map_shared_rank(set, 0);
+        dst[2 * q] = ok ? r : -1.0;
+        dst[2 * q + 1] = (double)f;
+      }
+      cl.sync();
+      if (tid == 0) fence_async_global();   // then the next bulk loads
+      const double* src = cl.map_shared_rank(set, 0);
+      double m = 0.0, mf = 0.0;
+      bool all = true;
+      for (int k = 0; k < C; ++k) {
+        const double v = src[2 * k];
+        if (v < 0.0) all = false; else m = fmax(m, v);
+        mf = fmax(mf, src[2 * k + 1]);
+      }
+      ok = all;
+      r = m;
+      f = (float)mf;
+      ++round;
+    }
   };
 
-  // 1. FP64 residual and the FP32 system; returns max div^2, bmax = max |b|
+  // 1. FP64 residual and the FP32 system of this CTA's planes; returns max
+  // div^2 over the start, bmax = max |b|
   auto rhs = [&](const double2* g, float& bmax) -> double {
     double r = 0.0;
     float bm = 0.f;
-    for (int x = tid; x < V; x += nt) {
+    for (int x = x_beg + tid; x < x_end; x += nt) {
       int c[D];
       int t = x;
 #pragma unroll
@@ -608,19 +653,25 @@ __global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonAr
         for (int mu = 0; mu < 2 * D; ++mu) coef[(size_t)(1 + mu) * V + ci] = 0.f;
       }
     }
-    double ro;
-    block_max2(r, bm, ro, bmax);
-    return ro;
+    bool ok = true;
+    reduce(ok, r, bm);
+    bmax = bm;
+    return r;
   };
 
   // 2. SOR sweeps from delta = 0 in groups of four, the correction of each
   // group's last sweep deciding (a correction 16 times the first group's
   // means M is not positive: stop); returns the sweeps, false in ok when a
-  // wait ran out
+  // wait ran out (the same on every CTA)
   auto sor = [&](float bmax, int cap, float om, bool& ok) -> int {
-    for (int x = tid; x < L * Ps; x += nt) dl[x] = 0.f;
+    for (int x = tid; x < nz * Ps; x += nt) dl[(size_t)z0 * Ps + x] = 0.f;
     fence_async_global();   // generic writes, then bulk reads of them
     __syncthreads();
+    {
+      double r0 = 0.0;
+      float f0 = 0.f;
+      reduce(ok, r0, f0);   // (cluster) the neighbours' zeros too
+    }
     const float thr = a.lin_tol * bmax;
     int k = 0;
     float first = 0.f;
@@ -629,7 +680,7 @@ __global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonAr
       for (int kk = 0; kk < 4; ++kk, ++k) {
         const bool last = kk == 3;
         for (int c = 0; c < 2; ++c) {
-          ok = ring_walk(ring, dl, true, [&](const float* prev, float* cur, const float* next, int z) {
+          ok = nz == 0 || ring_walk(ring, dl, true, [&](const float* prev, float* cur, const float* next, int z) {
             const float* cp = coef + (size_t)z * P + (size_t)c * P2;
             for (int h = tid; h < P2; h += nt) {
               int j, x0, rowbase;
@@ -652,12 +703,17 @@ __global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonAr
               if (last) corr = fmaxf(corr, fabsf(diff));
               cur[j] = fmaf(om, diff, old);
             }
-          });
+          }, z0, nz);
+          if constexpr (CL) {
+            double r0 = 0.0;
+            float f0 = 0.f;
+            reduce(ok, r0, f0);
+          }
           if (!ok) return k;
         }
       }
-      double dummy;
-      block_max2(0.0, corr, dummy, corr);
+      double dummy = 0.0;
+      reduce(ok, dummy, corr);
       if (corr <= thr) break;
       if (first == 0.f) first = corr;
       else if (!(corr < 16.f * first)) break;
@@ -665,29 +721,41 @@ __global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonAr
     return k;
   };
 
-  // 3. g_x <- g_x exp(i f delta_x), renormalised (f < 0 takes part of a step back)
+  // 3. g_x <- g_x exp(i f delta_x) on this CTA's planes, renormalised (f < 0
+  // takes part of a step back); then (cluster) every CTA's rotation is seen
   auto rotate = [&](double2* g, double f) {
     if (tid == 0) fence_async_global();   // the ring's stores, then generic reads of delta
     __syncthreads();
-    for (int x = tid; x < V; x += nt) {
+    for (int x = x_beg + tid; x < x_end; x += nt) {
       const int z = x / P, j = x - z * P;
       const double tf = f * (double)fminf(fmaxf(__ldcg(dl + (size_t)z * Ps + j), -0.2f), 0.2f);
       double sn, cs;
       sincos(tf, &sn, &cs);
       const double2 gx = g[x];
       const double nx = gx.x * cs - gx.y * sn, ny = gx.x * sn + gx.y * cs;
-      const double q = rsqrt(nx * nx + ny * ny);
-      g[x] = make_double2(nx * q, ny * q);
+      const double qn = rsqrt(nx * nx + ny * ny);
+      g[x] = make_double2(nx * qn, ny * qn);
     }
     __syncthreads();
+    if constexpr (CL) {
+      bool ok = true;
+      double r0 = 0.0;
+      float f0 = 0.f;
+      reduce(ok, r0, f0);
+    }
   };
 
-  for (;;) {
-    if (tid == 0) *tidx = (long long)atomicAdd(a.work_ctr, 1ULL);
-    __syncthreads();
-    const long long idx = *tidx;
-    __syncthreads();
-    if (idx >= a.n || *abort_flag) break;
+  const long long n = a.n;
+  for (long long i = cid;; i += ncl) {
+    if constexpr (!CL) {
+      if (tid == 0) *tidx = (long long)atomicAdd(a.work_ctr, 1ULL);
+      __syncthreads();
+      i = *tidx;
+      __syncthreads();
+      if (*abort_flag) break;
+    }
+    if (i >= n) break;
+    const long long idx = i;
     double2* g = a.state + (size_t)idx * V;
     // this start's SOR parameter (Young)
     const float om = young_omega(a.rate ? a.rate[idx] : 0.f, a.omega_sweeps);
@@ -719,13 +787,14 @@ __global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonAr
       if (!(r < 0.25 * r0)) cap = min(4 * cap, 4 * a.inner_max);
     }
     if (!ok) {
+      // (in a cluster every CTA gets here together)
       if (tid == 0) { atomicExch(&a.err[3], 1); *abort_flag = 1; }
       ring.drain();
       if (tid == 0) bulk_wait_all();
       __syncthreads();
       break;
     }
-    if (tid == 0) {
+    if (tid == 0 && q == 0) {
       a.resid[idx] = r;
       if (conv) {
         a.status[idx] = kConverged;
@@ -736,13 +805,14 @@ __global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonAr
       }
     }
   }
-  if (tid == 0) {
+  if (tid == 0 && q == 0) {
     atomicAdd(&a.stats[a.s_steps], my_steps);
     atomicAdd(&a.stats[a.s_inner], my_inner);
     atomicAdd(&a.stats[a.s_pass], my_pass);
     atomicAdd(&a.stats[a.s_conv], my_conv);
     atomicAdd(&a.stats[a.s_redo], my_redo);
   }
+  if constexpr (CL) cg::this_cluster().sync();   // no CTA leaves while its slots may be read
 }
 
 // FP32 state -> FP64, renormalised (the mixed path's hand-over to the FP64 sweeps)

@@ -99,6 +99,28 @@ def test_hyperplane_newton_fallback_to_fp64_sweeps():
     assert _agree(c_n, s_n, c_f, s_f, n) >= n - 1
 
 
+def test_hyperplane_cluster_and_cta_forms_agree_bitwise():
+    """3D 16^3 mixed path with 8 starts, so that every start gets a cluster in
+    the FP32 sweeps, the Newton polish and the FP64 sweeps: the cluster form
+    splits each pass by planes but keeps every site's arithmetic and the
+    maxima, so it equals the one-CTA form bit for bit (statuses, sweep and
+    Newton counts, F, every copy's angles)."""
+    import paper_1403_0555_b300 as gb
+    d, L, n = 3, 16, 8
+    phi = oi.von_mises_orbit(d, L, 1.0, 9)
+    st_c, s_c, c_c = _plain(gb, d, L, phi, 9, n, precision=gb.GC_MIXED, check_every=4,
+                            relax_variant=gb.GC_RELAX_AUTO)
+    st_g, s_g, c_g = _plain(gb, d, L, phi, 9, n, precision=gb.GC_MIXED, check_every=4,
+                            relax_variant=gb.GC_RELAX_GENERIC)
+    assert st_c["n_converged"] == n
+    for k in ("n_converged", "n_distinct", "sweeps_fp32", "newton_steps", "newton_inner_sweeps",
+              "polish_fallbacks", "fp64_residual_passes", "site_updates_fp64"):
+        assert st_c[k] == st_g[k], k
+    for k in ("status", "sweeps", "F", "copy_idx"):
+        assert np.array_equal(s_c[k], s_g[k]), k
+    assert np.array_equal(c_c["theta"], c_g["theta"]) and np.array_equal(c_c["F"], c_g["F"])
+
+
 def test_hyperplane_first_region_fast_path():
     """Region flags of the fast path: IN exactly when every weight
     cos(phi^theta) is positive (the oracle's weights of each copy), else
