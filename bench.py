@@ -303,10 +303,10 @@ def large_lattice_leg(gb, torch, d=4, L=16, n=592, runs=2):
             "newton_steps_per_start": acc["newton_steps"] / acc["n_starts"],
             "inner_sweeps_per_start": acc["newton_inner_sweeps"] / acc["n_starts"],
             "fp64_fallback_starts": acc["polish_fallbacks"] // runs,
-            "relax_slab": {"kernel": "relax_slab_kernel<float2,4,false>", "bound": "hbm",
+            "relax_slab": {"kernel": "relax_slab_kernel<float2,4,true> (8-CTA clusters)", "bound": "hbm",
                            "achieved": relax_gbs, "peak": hbm, "unit": "GB/s", "frac": relax_gbs / hbm,
                            "bytes_per_update": 32 + 8 / 4},
-            "newton_inner": {"kernel": "slab_newton_kernel<4>", "bound": "hbm", "achieved": inner_gbs,
+            "newton_inner": {"kernel": "slab_newton_kernel<4,false>", "bound": "hbm", "achieved": inner_gbs,
                              "peak": hbm, "unit": "GB/s", "frac": inner_gbs / hbm,
                              "note": "over the whole Newton launch, its tail of hard starts included"}}
 
