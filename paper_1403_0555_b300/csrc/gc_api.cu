@@ -569,17 +569,18 @@ Tuning cached_tuning(int d, int L, int precision, bool deep = false) {
 }
 
 // One launch of the hyperplane sweeps: one CTA per start (grid CTAs), or one
-// start per cluster of kSlabCluster CTAs (as many clusters as fit at once)
-constexpr int kSlabCluster = 8;
+// start per cluster of kSlabCluster CTAs (as many clusters as fit at once),
+// or, with `wide` (a handful of hard starts), of kSlabClusterWide CTAs where
+// that non-portable size fits
+constexpr int kSlabCluster = 8, kSlabClusterWide = 16;
 template <class K1, class KC>
 int launch_slab(K1 k1, KC kc, const gc::SlabArgs& sa, size_t smem, int grid, bool cluster,
-                cudaStream_t s) {
+                cudaStream_t s, bool wide = false) {
   if (cluster) {
     if (int rc = raise_smem_limit(kc, smem)) return rc;
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kSlabCluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.blockDim = dim3(512);
@@ -587,11 +588,25 @@ int launch_slab(K1 k1, KC kc, const gc::SlabArgs& sa, size_t smem, int grid, boo
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cfg.gridDim = dim3(kSlabCluster * 64);
-    int nclusters = 0;
-    GC_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, kc, &cfg));
+    int nclusters = 0, csize = kSlabCluster;
+    if (wide) {
+      GC_CUDA(cudaFuncSetAttribute(kc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+      csize = kSlabClusterWide;
+      attr[0].val.clusterDim.x = csize;
+      cfg.gridDim = dim3(csize * 8);
+      if (cudaOccupancyMaxActiveClusters(&nclusters, kc, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        nclusters = 0;
+      }
+    }
+    if (nclusters == 0) {
+      csize = kSlabCluster;
+      attr[0].val.clusterDim.x = csize;
+      cfg.gridDim = dim3(csize * 64);
+      GC_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, kc, &cfg));
+    }
     if (nclusters > 0) {
-      cfg.gridDim = dim3(kSlabCluster * nclusters);
+      cfg.gridDim = dim3(csize * nclusters);
       GC_CUDA(cudaLaunchKernelEx(&cfg, kc, sa));
       return GC_OK;
     }
@@ -667,13 +682,13 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     const int grid = (int)std::max<long long>(1, std::min<long long>(b, 2LL * sm_count()));
     // one start per cluster of kSlabCluster CTAs (default), or one CTA per
     // start (GC_RELAX_GENERIC)
-    auto launch = [&](bool fp64, bool cluster) -> int {
+    auto launch = [&](bool fp64, bool cluster, bool wide = false) -> int {
       int rc = GC_OK;
       if (fp64) {
         switch (d) {
-          case 2: rc = launch_slab(gc::relax_slab_kernel<double2, 2, false>, gc::relax_slab_kernel<double2, 2, true>, sa, sm64, grid, cluster, s); break;
-          case 3: rc = launch_slab(gc::relax_slab_kernel<double2, 3, false>, gc::relax_slab_kernel<double2, 3, true>, sa, sm64, grid, cluster, s); break;
-          default: rc = launch_slab(gc::relax_slab_kernel<double2, 4, false>, gc::relax_slab_kernel<double2, 4, true>, sa, sm64, grid, cluster, s); break;
+          case 2: rc = launch_slab(gc::relax_slab_kernel<double2, 2, false>, gc::relax_slab_kernel<double2, 2, true>, sa, sm64, grid, cluster, s, wide); break;
+          case 3: rc = launch_slab(gc::relax_slab_kernel<double2, 3, false>, gc::relax_slab_kernel<double2, 3, true>, sa, sm64, grid, cluster, s, wide); break;
+          default: rc = launch_slab(gc::relax_slab_kernel<double2, 4, false>, gc::relax_slab_kernel<double2, 4, true>, sa, sm64, grid, cluster, s, wide); break;
         }
       } else {
         switch (d) {
@@ -798,7 +813,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       sa.init = 1;
       sa.s_sweeps = kSweeps; sa.s_updates = kUpdates; sa.s_conv = kConv; sa.s_nconv = kNConv;
     }
-    if (int rc = launch(true, cluster)) return rc;
+    if (int rc = launch(true, cluster, mixed)) return rc;   // mixed: the few starts Newton left
     if (ev && !mixed) GC_CUDA(cudaEventRecord(ev[1], s));
     // functional, fingerprint and canonical copy (in place)
     gc::slab_final_kernel<<<grid, 256, 0, s>>>(st64, o->links64.as<double2>(), d, V, L, b,

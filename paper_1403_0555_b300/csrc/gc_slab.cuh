@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
 // newton_max steps, is listed for the FP64 sweeps (an indefinite M near a
 // saddle, which relaxation leaves and Newton would not).  The inner solve of
 // a step that cut max div^2 less than 4x gets 4x the sweep cap (up to 4x
-// inner_max); a start gets 8x inner_max inner sweeps in all, so a
+// inner_max); a start gets 4x inner_max inner sweeps in all, so a
 // near-singular M costs a bounded time on its CTA before the FP64 sweeps
 // (one start per cluster) take it.
 struct SlabNewtonArgs {
@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonAr
     // this start's SOR parameter (Young)
     const float om = young_omega(a.rate ? a.rate[idx] : 0.f, a.omega_sweeps);
     bool ok = true, conv = false;
-    int cap = a.inner_max, budget = 8 * a.inner_max;   // inner sweeps per solve, per start
+    int cap = a.inner_max, budget = 4 * a.inner_max;   // inner sweeps per solve, per start
     float bmax;
     double r = rhs(g, bmax);
     ++my_pass;
