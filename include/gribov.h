@@ -83,7 +83,8 @@ typedef struct {
   double dedup_delta;   /* copies are one when max_x |g'_A - g'_B| <= delta        */
   double fp_tau;        /* marginal band of the Faddeev-Popov test                 */
   int fp_mode;          /* GC_FP_*                                                  */
-  int lanczos_k;        /* cap on FP64 Lanczos steps (<= V-1 is used)               */
+  int lanczos_k;        /* cap on FP64 Lanczos steps (<= V-1 is used; at least 8L
+                           on lattices beyond shared memory)                       */
   uint64_t seed;        /* start generator key word 0 (word 1 is the orbit id)     */
   int keep_per_start;   /* keep the last call's per-start records for fetch_starts */
   int newton_inner;     /* GC_MIXED: cap on FP32 SOR sweeps per Newton polish step */

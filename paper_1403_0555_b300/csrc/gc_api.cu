@@ -622,8 +622,8 @@ int launch_slab(K1 k1, KC kc, const gc::SlabArgs& sa, size_t smem, int grid, boo
 // lattice in hyperplanes from global memory (FP64 for the plain path; for the
 // mixed path FP32 sweeps, then the inexact Newton polish, FP64 sweeps for the
 // starts it leaves), the functional and canonical copy from the FP64 state,
-// dedup as everywhere, and the first-region fast path (all weights positive:
-// IN; else untested).  The same batch structure and events as enumerate_impl.
+// dedup as everywhere, and the first-region test by Lanczos with vectors in
+// global memory.  The same batch structure and events as enumerate_impl.
 int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, const gc_options& opt,
                    cudaStream_t s, bool async, bool timing, int check_every, int max_sweeps) {
   const int V = o->V, d = o->d, L = o->L, P = V / L;
@@ -849,11 +849,72 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     }
     if (ev) GC_CUDA(cudaEventRecord(ev[4], s));
     if (opt.fp_mode != GC_FP_NONE) {
-      gc::slab_fp_fast_kernel<<<sm_count() * 2, 256, 0, s>>>(
-          o->t_cfg.as<double2>(), o->links64.as<double2>(), d, V, L, o->t_newlist.as<unsigned>(), o->n_new(),
-          o->t_lam.as<double>(), o->t_region.as<int>(), stats + kTests);
-      ++o->launches;
-      GC_CUDA(cudaGetLastError());
+      // first-region test of the batch's new copies: Lanczos with vectors in
+      // global memory, one copy per 1024-thread CTA.  Auto: an FP32 screen,
+      // then FP64 for the copies it leaves; otherwise FP64 for every copy (the
+      // dense mode's full-dimension run has no large-lattice form: Lanczos to
+      // lanczos_k steps)
+      // the low end of a large lattice's spectrum needs about 8L steps
+      const int kmax = std::min(std::max(opt.lanczos_k, 8 * L), V - 1);
+      const int grid_f = sm_count();
+      const size_t sb32 = gc::slab_fp_scratch_bytes<float>(d, V), sb64 = gc::slab_fp_scratch_bytes<double>(d, V);
+      if (!o->scratch.ensure((size_t)grid_f * sb64, s) || !o->s_redo.ensure((size_t)B * 4, s))
+        return fail(GC_ENOMEM, "cannot admit the first-region test scratch (%.1f MiB)", grid_f * sb64 / 1048576.0);
+      gc::SlabFpArgs fa{};
+      fa.cfg = o->t_cfg.as<double2>();
+      fa.links = o->links64.as<double2>();
+      fa.d = d; fa.L = L; fa.V = V;
+      fa.lambda2 = o->t_lam.as<double>();
+      fa.region = o->t_region.as<int>();
+      fa.tau = opt.fp_tau;
+      fa.margin = 1e-3;
+      fa.kmax = kmax;
+      fa.seed = opt.seed;
+      fa.scratch = o->scratch.as<unsigned char>();
+      fa.stats = stats;
+      fa.s_tests = kTests; fa.s_tests64 = kTests64; fa.s_steps = kLanczos;
+      auto launch_f = [&](bool fp32) -> int {
+        const size_t smf = gc::slab_fp_smem_bytes(kmax, fp32 ? 4 : 8);
+        auto go = [&](auto kern) -> int {
+          if (int rc = raise_smem_limit(kern, smf)) return rc;
+          kern<<<grid_f, 1024, smf, s>>>(fa);
+          ++o->launches;
+          GC_CUDA(cudaGetLastError());
+          return GC_OK;
+        };
+        if (fp32) {
+          switch (d) {
+            case 2: return go(gc::slab_fp_lanczos_kernel<float, 2>);
+            case 3: return go(gc::slab_fp_lanczos_kernel<float, 3>);
+            default: return go(gc::slab_fp_lanczos_kernel<float, 4>);
+          }
+        }
+        switch (d) {
+          case 2: return go(gc::slab_fp_lanczos_kernel<double, 2>);
+          case 3: return go(gc::slab_fp_lanczos_kernel<double, 3>);
+          default: return go(gc::slab_fp_lanczos_kernel<double, 4>);
+        }
+      };
+      if (opt.fp_mode == GC_FP_AUTO) {
+        GC_CUDA(cudaMemsetAsync(o->n_redo(), 0, 4, s));
+        fa.list = o->t_newlist.as<unsigned>();
+        fa.n_list = o->n_new();
+        fa.redo = o->s_redo.as<unsigned>();
+        fa.n_redo = o->n_redo();
+        fa.tol = 1e-5;
+        fa.scratch_bytes = sb32;
+        if (int rc = launch_f(true)) return rc;
+        fa.list = o->s_redo.as<unsigned>();
+        fa.n_list = o->n_redo();
+        fa.count_tests = 0;
+      } else {
+        fa.list = o->t_newlist.as<unsigned>();
+        fa.n_list = o->n_new();
+        fa.count_tests = 1;
+      }
+      fa.tol = 1e-12;
+      fa.scratch_bytes = sb64;
+      if (int rc = launch_f(false)) return rc;
     }
     if (ev) GC_CUDA(cudaEventRecord(ev[5], s));
     if (opt.keep_per_start) {

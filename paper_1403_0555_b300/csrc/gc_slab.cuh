@@ -26,6 +26,7 @@
 // err[3], lets the copies in flight finish (bounded again) and returns.
 #pragma once
 #include <cooperative_groups.h>
+#include "gc_fptest.cuh"
 #include "gc_relax.cuh"
 
 namespace cg = cooperative_groups;
@@ -863,42 +864,216 @@ __global__ void __launch_bounds__(256) slab_final_kernel(double2* state, const d
   }
 }
 
-// First-region fast path for the copies a batch created: all weights
-// cos(phi^theta) > 0 make the Faddeev-Popov operator a weighted graph
-// Laplacian with positive weights, so lambda_2 > 0 (region IN); otherwise the
-// copy is left untested (-1).  lambda_2 itself is not computed (NaN).
-__global__ void __launch_bounds__(256) slab_fp_fast_kernel(const double2* cfg, const double2* links, int d,
-                                                           int V, int L, const unsigned* list,
-                                                           const unsigned* n_list, double* lambda2,
-                                                           int* region, unsigned long long* tests) {
-  __shared__ int neg;
-  const unsigned n = *n_list;
-  for (unsigned i = blockIdx.x; i < n; i += gridDim.x) {
-    const unsigned e = list[i];
-    const double2* g = cfg + (size_t)e * V;
-    if (threadIdx.x == 0) neg = 0;
+// -- first-region test beyond shared memory ----------------------------------
+// Lanczos on the Faddeev-Popov operator M restricted to 1^perp (every vector
+// projected off the mean), as on small lattices, with the copy's weights and
+// the three Lanczos vectors in a global scratch slot per CTA (one copy per
+// 1024-thread CTA at a time).  The smallest eigenvalue of the tridiagonal is
+// located by the same Sturm multisection every 8 steps from step 16 on;
+// Lanczos stops when it moves by less than tol relative.  R = float: the
+// screen (a copy with lambda_2 above `margin` is IN, every other copy goes to
+// the redo list); R = double: lambda_2 and the region (tau) of every listed
+// copy.  Neighbours come from a per-site byte of wrap flags (bit 2 mu: x_mu =
+// L - 1, bit 2 mu + 1: x_mu = 0), so the matvec takes no integer division.
+struct SlabFpArgs {
+  const double2* cfg;              // table configurations [entry][V]
+  const double2* links;            // FP64 [x*d + mu]
+  int d, L, V;
+  const unsigned* list;            // entries to test, *n_list of them
+  const unsigned* n_list;
+  unsigned* redo;                  // the screen's undecided entries
+  unsigned* n_redo;
+  double* lambda2;
+  int* region;
+  double tau, margin, tol;
+  int kmax;
+  uint64_t seed;
+  unsigned char* scratch;          // per CTA: weights [d][V], vprev, vcur, z [V] (R), wrap [V]
+  size_t scratch_bytes;            // per CTA (a multiple of 16)
+  unsigned long long* stats;
+  int s_tests, s_tests64, s_steps;
+  int count_tests;                 // R = double: also count the copies as tests (no screen ran)
+};
+
+template <class R>
+__host__ __device__ inline size_t slab_fp_scratch_bytes(int d, int V) {
+  return (((size_t)(d + 3) * V * sizeof(R) + (size_t)V) + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t slab_fp_smem_bytes(int kmax, int elem) {
+  return 1024 + 2 * (((size_t)(kmax + 2) * elem + 15) / 16 * 16);
+}
+
+template <class R, int D>
+__global__ void __launch_bounds__(1024, 1) slab_fp_lanczos_kernel(const SlabFpArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int L = a.L, V = a.V, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  const int kmax = a.kmax;
+  R* red = reinterpret_cast<R*>(smem);                 // [2][32] per-warp partials (<= 512 B)
+  R* bcast = reinterpret_cast<R*>(smem + 512);         // [2]
+  R* alpha = reinterpret_cast<R*>(smem + 1024);
+  R* beta2 = alpha + ((size_t)(kmax + 2) * sizeof(R) + 15) / 16 * 16 / sizeof(R);
+  unsigned char* base = a.scratch + (size_t)blockIdx.x * a.scratch_bytes;
+  R* w = reinterpret_cast<R*>(base);                   // [D][V]
+  R* vprev = w + (size_t)D * V;
+  R* vcur = vprev + V;
+  R* z = vcur + V;
+  unsigned char* wrap = reinterpret_cast<unsigned char*>(z + V);
+  int strides[D];
+  {
+    int st = 1;
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) { strides[mu] = st; st *= L; }
+  }
+  for (int x = tid; x < V; x += nt) {
+    int t = x;
+    unsigned f = 0;
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) {
+      const int c = t % L;
+      t /= L;
+      if (c == L - 1) f |= 1u << (2 * mu);
+      if (c == 0) f |= 2u << (2 * mu);
+    }
+    wrap[x] = (unsigned char)f;
+  }
+  __syncthreads();
+  // block sums of two values (every thread gets both)
+  auto sum2 = [&](R& p, R& q) {
+    for (int o = 16; o > 0; o >>= 1) {
+      p += __shfl_xor_sync(0xffffffffu, p, o);
+      q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    if (lane == 0) { red[wid] = p; red[32 + wid] = q; }
     __syncthreads();
-    int mine = 0;
-    for (int x = threadIdx.x; x < V && !mine; x += blockDim.x) {
+    p = 0; q = 0;
+    for (int k = 0; k < nt / 32; ++k) { p += red[k]; q += red[32 + k]; }
+    __syncthreads();
+  };
+  auto nbr = [&](int x, unsigned f, int mu, int& xp, int& xm) {
+    const int st = strides[mu];
+    xp = x + ((f >> (2 * mu)) & 1u ? -(L - 1) * st : st);
+    xm = x + ((f >> (2 * mu + 1)) & 1u ? (L - 1) * st : -st);
+  };
+  const unsigned n = *a.n_list;
+  unsigned long long my_steps = 0, my_tests = 0;
+  for (unsigned i = blockIdx.x; i < n; i += gridDim.x) {
+    const unsigned e = a.list[i];
+    const double2* g = a.cfg + (size_t)e * V;
+    // weights cos(phi^theta_{x,mu}) = Re[conj(g_x) u_{x,mu} g_{x+mu}]
+    for (int x = tid; x < V; x += nt) {
       const double2 gx = g[x];
-      int stride = 1;
-      for (int mu = 0; mu < d; ++mu) {
-        const int c = (x / stride) % L;
-        const int xp = x + (c + 1 == L ? -(L - 1) * stride : stride);
-        const double2 h = g[xp], u = links[(size_t)x * d + mu];
-        const double w = gx.x * (u.x * h.x - u.y * h.y) + gx.y * (u.x * h.y + u.y * h.x);
-        if (!(w > 0.0)) mine = 1;
-        stride *= L;
+      const unsigned f = wrap[x];
+#pragma unroll
+      for (int mu = 0; mu < D; ++mu) {
+        int xp, xm;
+        nbr(x, f, mu, xp, xm);
+        const double2 h = g[xp], u = a.links[(size_t)x * D + mu];
+        w[(size_t)mu * V + x] = (R)(gx.x * (u.x * h.x - u.y * h.y) + gx.y * (u.x * h.y + u.y * h.x));
       }
     }
-    if (mine) atomicOr(&neg, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      region[e] = neg ? -1 : 1;
-      lambda2[e] = __longlong_as_double(0x7ff8000000000000LL);
-      atomicAdd(tests, 1ULL);
+    // random start vector orthogonal to the constant mode
+    R s = 0, dummy = 0;
+    for (int x = tid; x < V; x += nt) {
+      const U64x4 r = philox4x64_10(e, (uint64_t)x, 0, 1, a.seed, 0x4C414E43ULL);
+      const R v = (R)(unsigned)(r.v[0] >> 40) * (R)0x1.0p-24 - (R)0.5;
+      vcur[x] = v;
+      vprev[x] = 0;
+      s += v;
+    }
+    sum2(s, dummy);
+    s /= (R)V;
+    R nn = 0;
+    for (int x = tid; x < V; x += nt) { const R v = vcur[x] - s; vcur[x] = v; nn += v * v; }
+    dummy = 0;
+    sum2(nn, dummy);
+    {
+      const R inv0 = (R)1 / sqrt(nn);
+      for (int x = tid; x < V; x += nt) vcur[x] *= inv0;
     }
     __syncthreads();
+    const R bound = (R)(4 * D + 1);
+    R b = 0, theta = bound, theta_prev = bound, theta_pp = bound;
+    int j = 0;
+    for (; j < kmax; ++j) {
+      R al = 0;
+      for (int x = tid; x < V; x += nt) {
+        const unsigned f = wrap[x];
+        const R vx = vcur[x];
+        R acc = 0;
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) {
+          int xp, xm;
+          nbr(x, f, mu, xp, xm);
+          acc = fma(w[(size_t)mu * V + x], vx - vcur[xp], acc);
+          acc = fma(w[(size_t)mu * V + xm], vx - vcur[xm], acc);
+        }
+        const R mv = acc - b * vprev[x];
+        z[x] = mv;
+        al += mv * vx;
+      }
+      dummy = 0;
+      sum2(al, dummy);
+      R m = 0, zz = 0;
+      for (int x = tid; x < V; x += nt) {
+        const R v = z[x] - al * vcur[x];
+        z[x] = v;
+        m += v;
+        zz += v * v;
+      }
+      sum2(m, zz);
+      m /= (R)V;
+      const R bn = sqrt(fmax(zz - (R)V * m * m, (R)0));   // |z - m|
+      if (tid == 0) { alpha[j] = al; beta2[j + 1] = bn * bn; }
+      __syncthreads();
+      const bool last = (j + 1 == kmax) || bn < (R)1e-12;
+      if (last || ((j + 1) % 8 == 0 && j + 1 >= 16)) {
+        if (wid == 0) {
+          R lo = -bound, hi = bound;
+          if (theta_prev < bound) {
+            const R slack = (R)2 * tri_rel<R>() * fmax(fabs(theta_prev), (R)1);
+            hi = theta_prev + slack;
+            if (theta_pp < bound) {
+              const R l = theta_prev - (R)4 * fmax(theta_pp - theta_prev, slack);
+              if (sturm_count<R>(alpha, beta2, j + 1, l) == 0) lo = l;
+            }
+          }
+          const R th = tri_min<R>(alpha, beta2, j + 1, lo, hi, lane);
+          if (lane == 0) bcast[0] = th;
+        }
+        __syncthreads();
+        theta = bcast[0];
+        __syncthreads();
+        if (last) { ++j; break; }
+        if (fabs(theta - theta_prev) <= (R)a.tol * fmax(fabs(theta), (R)1e-3)) { ++j; break; }
+        theta_pp = theta_prev;
+        theta_prev = theta;
+      }
+      const R ib = (R)1 / bn;
+      for (int x = tid; x < V; x += nt) { vprev[x] = vcur[x]; vcur[x] = (z[x] - m) * ib; }
+      b = bn;
+      __syncthreads();
+    }
+    my_steps += j;
+    ++my_tests;
+    if (tid == 0) {
+      if (sizeof(R) == 4) {
+        if (theta > (R)a.margin) {
+          a.lambda2[e] = (double)theta;
+          a.region[e] = kRegionIn;
+        } else {
+          a.redo[atomicAdd(a.n_redo, 1u)] = e;
+        }
+      } else {
+        a.lambda2[e] = (double)theta;
+        a.region[e] = region_of((double)theta, a.tau);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    atomicAdd(&a.stats[a.s_steps], my_steps);
+    if (sizeof(R) == 4 || a.count_tests) atomicAdd(&a.stats[a.s_tests], my_tests);
+    if (sizeof(R) == 8) atomicAdd(&a.stats[a.s_tests64], my_tests);
   }
 }
 
