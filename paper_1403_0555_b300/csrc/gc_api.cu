@@ -862,6 +862,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
         return fail(GC_ENOMEM, "cannot admit the first-region test scratch (%.1f MiB)", grid_f * sb64 / 1048576.0);
       gc::SlabFpArgs fa{};
       fa.cfg = o->t_cfg.as<double2>();
+      fa.first_start = o->t_first.as<unsigned long long>();
       fa.links = o->links64.as<double2>();
       fa.d = d; fa.L = L; fa.V = V;
       fa.lambda2 = o->t_lam.as<double>();

@@ -877,6 +877,7 @@ __global__ void __launch_bounds__(256) slab_final_kernel(double2* state, const d
 // L - 1, bit 2 mu + 1: x_mu = 0), so the matvec takes no integer division.
 struct SlabFpArgs {
   const double2* cfg;              // table configurations [entry][V]
+  const unsigned long long* first_start;   // per entry: the lowest start reaching it
   const double2* links;            // FP64 [x*d + mu]
   int d, L, V;
   const unsigned* list;            // entries to test, *n_list of them
@@ -971,10 +972,13 @@ __global__ void __launch_bounds__(1024, 1) slab_fp_lanczos_kernel(const SlabFpAr
         w[(size_t)mu * V + x] = (R)(gx.x * (u.x * h.x - u.y * h.y) + gx.y * (u.x * h.y + u.y * h.x));
       }
     }
-    // random start vector orthogonal to the constant mode
+    // random start vector orthogonal to the constant mode, keyed by the
+    // copy's first start (not its table slot, which depends on the order of
+    // insertion), so that a Ritz value short of convergence is reproducible
+    const unsigned long long key = a.first_start[e];
     R s = 0, dummy = 0;
     for (int x = tid; x < V; x += nt) {
-      const U64x4 r = philox4x64_10(e, (uint64_t)x, 0, 1, a.seed, 0x4C414E43ULL);
+      const U64x4 r = philox4x64_10(key, (uint64_t)x, 0, 1, a.seed, 0x4C414E43ULL);
       const R v = (R)(unsigned)(r.v[0] >> 40) * (R)0x1.0p-24 - (R)0.5;
       vcur[x] = v;
       vprev[x] = 0;

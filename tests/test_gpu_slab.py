@@ -144,3 +144,38 @@ def test_hyperplane_first_region_lanczos_matches_the_oracle(mode):
         else:
             assert abs(c["lambda2"][k] - lam) <= tol * max(1.0, abs(lam)), (k, c["lambda2"][k], lam)
         assert c["region"][k] == oracle.region_flag(lam, 1e-9)
+
+
+def test_hyperplane_requests_served_alongside_others():
+    """Serving: two large-lattice requests (2D 64^2 and 3D 16^3, mixed path)
+    admitted while a small 4^4 request runs give the same copies, statistics
+    and region flags as when run alone (every stage is per start or per copy,
+    with no dependence on what shares the GPU)."""
+    import paper_1403_0555_b300 as gb
+    opt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=4)
+    reqs = [(4, 4, 20000), (2, 64, 12), (3, 16, 10)]
+    srv = gb.gc_server_create(3, 0, opt)
+    try:
+        tickets = []
+        for i, (d, L, n) in enumerate(reqs):
+            phi = oi.von_mises_orbit(d, L, 1.0, 70 + i)
+            tickets.append((gb.gc_server_submit(srv, d, L, phi, 70 + i, n), d, L, n, phi, i))
+        for t, d, L, n, phi, i in tickets:
+            status, latency, orb = gb.gc_server_wait(srv, t, 300.0)
+            assert status == gb.GC_OK and orb is not None and latency > 0
+            mixed = gb.gc_fetch_copies(orb, L ** d)
+            mst = gb.gc_orbit_stats(orb)
+            gb.gc_destroy_orbit(orb)
+            h = gb.gc_create_orbit(d, L, phi, 70 + i)
+            try:
+                gb.gc_enumerate_copies(h, n, 1.7, 1e-24, opt)
+                alone, ast = gb.gc_fetch_copies(h, L ** d), gb.gc_orbit_stats(h)
+            finally:
+                gb.gc_destroy_orbit(h)
+            assert mixed["n_distinct"] == alone["n_distinct"] > 0
+            for k in ("F", "first_start", "count", "region", "lambda2", "theta"):
+                assert np.array_equal(mixed[k], alone[k]), (d, L, k)
+            for k in ("n_converged", "newton_steps", "newton_inner_sweeps", "sweeps_fp32"):
+                assert mst[k] == ast[k], (d, L, k)
+    finally:
+        gb.gc_server_destroy(srv)
