@@ -1991,14 +1991,26 @@ struct Request {
 
 // Device bytes a request holds while it runs: links, a copy pool sized for
 // min(n, 65536) copies (it grows on demand), the quantised-minimum set,
-// buckets and one staging batch.
+// buckets and one staging batch; beyond shared memory (the hyperplane path,
+// the same test as gc_create_orbit's) also the per-SM scratch of the Newton
+// polish and of the first-region test.
 size_t request_bytes(int dim, int L, uint64_t n, int precision) {
   const double V = std::pow((double)L, dim);
   const double cap = (double)std::min<uint64_t>(n, 65536);
   const double per_copy = V * 16 + 64 + 4 * 8 + 2 * 4;
   const double per_start = V * 16 + (precision == GC_MIXED ? V * 8 : 0) + 48;
-  const double batch = std::min((double)n, std::max(4096.0, (double)(1ull << 30) / per_start));
-  return (size_t)(V * dim * 24 + cap * per_copy + batch * per_start + (1 << 20));
+  double batch = std::min((double)n, std::max(4096.0, (double)(1ull << 30) / per_start));
+  double extra = 0.0;
+  const int Vi = (int)V;
+  if (V <= gc::kMaxSlabSites &&
+      (Vi > gc::kMaxSites || gc::Smem(Vi, dim, 16, (size_t)Vi * 16, 1).total > max_smem_optin())) {
+    batch = std::min((double)n, std::max(2.0 * sm_count(), (double)(1ull << 30) / per_start));
+    const int Ps = (Vi / L + 3) / 4 * 4;
+    const double newton = precision == GC_MIXED ? (double)gc::slab_newton_scratch_floats(dim, Vi, L, Ps) * 4 : 0.0;
+    const double fp = (double)gc::slab_fp_scratch_bytes<double>(dim, Vi);
+    extra = sm_count() * std::max(newton, fp) + batch * 8;
+  }
+  return (size_t)(V * dim * 24 + cap * per_copy + batch * per_start + extra + (1 << 20));
 }
 
 }  // namespace
