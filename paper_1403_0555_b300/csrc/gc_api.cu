@@ -147,6 +147,7 @@ struct gc_orbit_s {
   unsigned long long* n_f8() const { return reinterpret_cast<unsigned long long*>(t_counters.as<char>() + 8); }
   int* err() const { return reinterpret_cast<int*>(t_counters.as<char>() + 16); }
   unsigned* n_redo() const { return reinterpret_cast<unsigned*>(t_counters.as<char>() + 32); }
+  unsigned* n_redo2() const { return reinterpret_cast<unsigned*>(t_counters.as<char>() + 40); }
 
   gc::TableView view() const {
     gc::TableView T{};
@@ -719,11 +720,14 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       gc::slab_promote_kernel<<<(int)std::min<size_t>((nv + 255) / 256, 4096), 256, 0, s>>>(
           o->s_state32.as<float2>(), st64, nv);
       ++o->launches;
-      // Newton polish: one start per 1024-thread CTA (one CTA per SM), or one
-      // start per cluster of kSlabCluster CTAs when there are no more starts
-      // than clusters fit (not with GC_RELAX_GENERIC)
+      // Newton polish.  One start per 1024-thread CTA (one CTA per SM) with
+      // an inner budget of 2x newton_inner, then the few starts that exceed
+      // it once more on clusters of kSlabCluster CTAs (a hard start runs 8
+      // CTAs wide instead of holding one CTA for the whole launch) with 6x.
+      // When every start gets a cluster at once, one cluster launch with 4x;
+      // GC_RELAX_GENERIC: one CTA per start with 4x.
       GC_CUDA(cudaMemsetAsync(wctr, 0, 8, s));
-      GC_CUDA(cudaMemsetAsync(o->n_redo(), 0, 4, s));
+      GC_CUDA(cudaMemsetAsync(o->n_redo(), 0, 16, s));   // n_redo, n_redo2
       const int Ps = (P + 3) / 4 * 4;
       const size_t smn = gc::slab_newton_smem_bytes(Ps);
       gc::SlabNewtonArgs na{};
@@ -741,60 +745,69 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       na.scratch_floats = gc::slab_newton_scratch_floats(d, V, L, Ps);
       na.status = sa.status;
       na.resid = sa.resid;
-      na.redo = o->s_redo.as<unsigned>();
-      na.n_redo = o->n_redo();
       na.stats = stats;
       na.s_steps = kNewton; na.s_inner = kInner; na.s_pass = kPass; na.s_conv = kPConv; na.s_redo = kFallback;
       na.err = o->err();
+      if (!o->s_redo.ensure((size_t)B * 8, s)) return fail(GC_ENOMEM, "cannot admit a batch of %zu starts", B);
+      unsigned* redo1 = o->s_redo.as<unsigned>();
+      unsigned* redo2 = redo1 + B;
+      const unsigned* final_list = redo1;
+      const unsigned* final_n = o->n_redo();
       {
-        auto launch_n = [&](auto k1, auto kc) -> int {
-          cudaLaunchConfig_t cfg{};
-          cudaLaunchAttribute attr[1];
-          attr[0].id = cudaLaunchAttributeClusterDimension;
-          attr[0].val.clusterDim.x = kSlabCluster;
-          attr[0].val.clusterDim.y = 1;
-          attr[0].val.clusterDim.z = 1;
-          cfg.blockDim = dim3(1024);
-          cfg.dynamicSmemBytes = smn;
-          cfg.stream = s;
-          cfg.attrs = attr;
-          cfg.numAttrs = 1;
-          cfg.gridDim = dim3(kSlabCluster * 16);
-          int ncl = 0;
-          if (cluster) {
-            if (int rc = raise_smem_limit(kc, smn)) return rc;
-            GC_CUDA(cudaOccupancyMaxActiveClusters(&ncl, kc, &cfg));
-            // clusters only when every start gets one (latency); with more
-            // starts one CTA per start has twice the throughput (measured:
-            // 304 against 646 ms for 592 starts of 4D 16^4; a cluster CTA
-            // walks L/8 planes between cluster barriers)
-            if ((long long)ncl < b) ncl = 0;
-          }
-          // scratch per start in flight: per cluster, else per CTA
-          const int slots = ncl > 0 ? ncl : (int)std::max<long long>(1, std::min<long long>(b, (long long)sm_count()));
-          if (!o->scratch.ensure((size_t)slots * na.scratch_floats * 4, s) || !o->s_redo.ensure((size_t)B * 4, s))
-            return fail(GC_ENOMEM, "cannot admit the Newton scratch of %d starts (%.1f MiB)", slots,
-                        slots * na.scratch_floats * 4 / 1048576.0);
-          na.scratch = o->scratch.as<float>();
-          na.redo = o->s_redo.as<unsigned>();
-          if (ncl > 0) {
-            cfg.gridDim = dim3(kSlabCluster * ncl);
-            GC_CUDA(cudaLaunchKernelEx(&cfg, kc, na));
-          } else {
-            if (int rc = raise_smem_limit(k1, smn)) return rc;
-            k1<<<slots, 1024, smn, s>>>(na);
-            GC_CUDA(cudaGetLastError());
-          }
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kSlabCluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(1024);
+        cfg.dynamicSmemBytes = smn;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(kSlabCluster * 16);
+        int ncl = 0;
+        auto kc = d == 2 ? gc::slab_newton_kernel<2, true> : (d == 3 ? gc::slab_newton_kernel<3, true> : gc::slab_newton_kernel<4, true>);
+        auto k1 = d == 2 ? gc::slab_newton_kernel<2, false> : (d == 3 ? gc::slab_newton_kernel<3, false> : gc::slab_newton_kernel<4, false>);
+        if (cluster) {
+          if (int rc = raise_smem_limit(kc, smn)) return rc;
+          GC_CUDA(cudaOccupancyMaxActiveClusters(&ncl, kc, &cfg));
+        }
+        const int grid1 = (int)std::max<long long>(1, std::min<long long>(b, (long long)sm_count()));
+        const int slots = std::max(grid1, ncl);
+        if (!o->scratch.ensure((size_t)slots * na.scratch_floats * 4, s))
+          return fail(GC_ENOMEM, "cannot admit the Newton scratch of %d starts (%.1f MiB)", slots,
+                      slots * na.scratch_floats * 4 / 1048576.0);
+        na.scratch = o->scratch.as<float>();
+        auto run_cluster = [&]() -> int {
+          cfg.gridDim = dim3(kSlabCluster * ncl);
+          GC_CUDA(cudaLaunchKernelEx(&cfg, kc, na));
           ++o->launches;
           return GC_OK;
         };
-        int rc = GC_OK;
-        switch (d) {
-          case 2: rc = launch_n(gc::slab_newton_kernel<2, false>, gc::slab_newton_kernel<2, true>); break;
-          case 3: rc = launch_n(gc::slab_newton_kernel<3, false>, gc::slab_newton_kernel<3, true>); break;
-          default: rc = launch_n(gc::slab_newton_kernel<4, false>, gc::slab_newton_kernel<4, true>); break;
+        if (ncl > 0 && (long long)ncl >= b) {            // every start on its own cluster
+          na.budget = 4 * opt.newton_inner;
+          na.redo = redo1; na.n_redo = o->n_redo();
+          if (int rc = run_cluster()) return rc;
+        } else {
+          if (int rc = raise_smem_limit(k1, smn)) return rc;
+          const bool staged = ncl > 0;
+          na.budget = (staged ? 2 : 4) * opt.newton_inner;
+          na.redo = redo1; na.n_redo = o->n_redo();
+          na.s_redo = staged ? -1 : kFallback;
+          k1<<<grid1, 1024, smn, s>>>(na);
+          ++o->launches;
+          GC_CUDA(cudaGetLastError());
+          if (staged) {
+            na.list = redo1; na.n_list = o->n_redo();
+            na.budget = 6 * opt.newton_inner;
+            na.redo = redo2; na.n_redo = o->n_redo2();
+            na.s_redo = kFallback;
+            if (int rc = run_cluster()) return rc;
+            final_list = redo2;
+            final_n = o->n_redo2();
+          }
         }
-        if (rc) return rc;
       }
       if (ev) GC_CUDA(cudaEventRecord(ev[2], s));
       // FP64 sweeps for the starts the polish left; final outcomes
@@ -802,8 +815,8 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       sa.links = o->links64.p;
       sa.state = st64;
       sa.init = 0;
-      sa.list = o->s_redo.as<unsigned>();
-      sa.n_list = o->n_redo();
+      sa.list = final_list;
+      sa.n_list = final_n;
       sa.rate = nullptr;
       sa.omega_rate = o->s_rate.as<float>();   // the polish's sweeps at each start's Young parameter
       sa.s_sweeps = -1; sa.s_updates = kUpd64; sa.s_conv = kPConv; sa.s_nconv = kPNConv;

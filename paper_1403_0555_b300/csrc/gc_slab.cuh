@@ -499,16 +499,20 @@ __global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
 // newton_max steps, is listed for the FP64 sweeps (an indefinite M near a
 // saddle, which relaxation leaves and Newton would not).  The inner solve of
 // a step that cut max div^2 less than 4x gets 4x the sweep cap (up to 4x
-// inner_max); a start gets 4x inner_max inner sweeps in all, so a
-// near-singular M costs a bounded time on its CTA before the FP64 sweeps
-// (one start per cluster) take it.
+// inner_max); a start gets `budget` inner sweeps in a launch, so a
+// near-singular M holds one CTA for a bounded time: the host then runs the
+// few such starts again on clusters (CL), and what is left on the FP64
+// sweeps.
 struct SlabNewtonArgs {
   int d, L, V, P, Ps;              // Ps: plane stride of delta (P rounded up to 4 floats)
   const double2* links;            // FP64 [x*d + mu], site order
   double2* state;                  // n * V, site order
   long long n;
+  const unsigned* list;            // when set: only these batch entries, *n_list of them
+  const unsigned* n_list;
   unsigned long long* work_ctr;
   double eps;
+  int budget;                      // inner sweeps a start may take in this launch
   float omega_sweeps, lin_tol;     // the FP32 sweeps' parameter; inner stop
   const float* rate;               // per start: their contraction per sweep (0: none)
   int inner_max, newton_max;
@@ -746,7 +750,7 @@ __global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonAr
     }
   };
 
-  const long long n = a.n;
+  const long long n = a.list ? (long long)*a.n_list : a.n;
   for (long long i = cid;; i += ncl) {
     if constexpr (!CL) {
       if (tid == 0) *tidx = (long long)atomicAdd(a.work_ctr, 1ULL);
@@ -756,12 +760,12 @@ __global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonAr
       if (*abort_flag) break;
     }
     if (i >= n) break;
-    const long long idx = i;
+    const long long idx = a.list ? (long long)a.list[i] : i;
     double2* g = a.state + (size_t)idx * V;
     // this start's SOR parameter (Young)
     const float om = young_omega(a.rate ? a.rate[idx] : 0.f, a.omega_sweeps);
     bool ok = true, conv = false;
-    int cap = a.inner_max, budget = 4 * a.inner_max;   // inner sweeps per solve, per start
+    int cap = a.inner_max, budget = a.budget;   // inner sweeps per solve, per start
     float bmax;
     double r = rhs(g, bmax);
     ++my_pass;
@@ -811,7 +815,7 @@ __global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonAr
     atomicAdd(&a.stats[a.s_inner], my_inner);
     atomicAdd(&a.stats[a.s_pass], my_pass);
     atomicAdd(&a.stats[a.s_conv], my_conv);
-    atomicAdd(&a.stats[a.s_redo], my_redo);
+    if (a.s_redo >= 0) atomicAdd(&a.stats[a.s_redo], my_redo);
   }
   if constexpr (CL) cg::this_cluster().sync();   // no CTA leaves while its slots may be read
 }
