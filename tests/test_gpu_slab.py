@@ -179,3 +179,25 @@ def test_hyperplane_requests_served_alongside_others():
                 assert mst[k] == ast[k], (d, L, k)
     finally:
         gb.gc_server_destroy(srv)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_hyperplane_batches_give_the_single_batch_result(precision):
+    """2D 64^2, 20 starts split into device batches of 7 (three batches, the
+    last ragged) against one batch: every stage works per start or per copy,
+    so statuses, sweeps, F and the copy table (first starts, counts, angles,
+    region flags) are identical."""
+    import paper_1403_0555_b300 as gb
+    d, L, n = 2, 64, 20
+    phi = oi.von_mises_orbit(d, L, 1.0, 13)
+    prec = gb.GC_FP64 if precision == "fp64" else gb.GC_MIXED
+    ce = 1 if precision == "fp64" else 4
+    st_1, s_1, c_1 = _plain(gb, d, L, phi, 13, n, precision=prec, check_every=ce)
+    st_b, s_b, c_b = _plain(gb, d, L, phi, 13, n, precision=prec, check_every=ce, batch_starts=7)
+    for k in ("status", "sweeps", "F", "copy_idx"):
+        assert np.array_equal(s_1[k], s_b[k]), k
+    assert c_1["n_distinct"] == c_b["n_distinct"] > 0
+    for k in ("F", "first_start", "count", "theta", "region"):
+        assert np.array_equal(c_1[k], c_b[k]), k
+    for k in ("n_converged", "sweeps_fp32", "site_updates_fp64", "newton_steps"):
+        assert st_1[k] == st_b[k], k
