@@ -714,7 +714,48 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       sa.rate = o->s_rate.as<float>();
       sa.init = 1;
       sa.s_sweeps = kSweeps32; sa.s_updates = kUpdates32; sa.s_conv = kConv32; sa.s_nconv = kNConv32;
-      if (int rc = launch(false, cluster)) return rc;
+      // the lattice in a cluster's distributed shared memory when a 16- (else
+      // 8-) CTA cluster's planes and links fit and each CTA holds at least 4
+      // planes; else the hyperplane streaming.  With fewer planes per CTA
+      // most axis-(d-1) neighbours are remote and the per-phase cluster
+      // barrier dominates (measured on 592 starts: 2D 256^2, 16 planes per
+      // CTA, 762 ms against 3180 ms streamed; 3D 40^3, 2-3 planes, 595
+      // against 473; 4D 16^4, one plane, 713 against 490)
+      bool dsm = false;
+      if (cluster) {
+        auto kd = d == 2 ? gc::relax_dsmem_kernel<2> : (d == 3 ? gc::relax_dsmem_kernel<3> : gc::relax_dsmem_kernel<4>);
+        for (int C : {kSlabClusterWide, kSlabCluster}) {
+          const size_t smd = gc::dsmem_smem_bytes(d, L, P, C);
+          if (L < 4 * C || smd > max_smem_optin()) continue;
+          if (int rc = raise_smem_limit(kd, smd)) return rc;
+          if (C > 8) GC_CUDA(cudaFuncSetAttribute(kd, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+          cudaLaunchConfig_t cfg{};
+          cudaLaunchAttribute attr[1];
+          attr[0].id = cudaLaunchAttributeClusterDimension;
+          attr[0].val.clusterDim.x = C;
+          attr[0].val.clusterDim.y = 1;
+          attr[0].val.clusterDim.z = 1;
+          cfg.blockDim = dim3(P / 2 >= 1024 ? 1024 : 256);
+          cfg.dynamicSmemBytes = smd;
+          cfg.stream = s;
+          cfg.attrs = attr;
+          cfg.numAttrs = 1;
+          cfg.gridDim = dim3(C * 8);
+          int ncl = 0;
+          if (cudaOccupancyMaxActiveClusters(&ncl, kd, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            ncl = 0;
+          }
+          if (ncl <= 0) continue;
+          cfg.gridDim = dim3(C * ncl);
+          GC_CUDA(cudaLaunchKernelEx(&cfg, kd, sa));
+          ++o->launches;
+          dsm = true;
+          break;
+        }
+      }
+      if (!dsm)
+        if (int rc = launch(false, cluster)) return rc;
       if (ev) GC_CUDA(cudaEventRecord(ev[1], s));
       const size_t nv = (size_t)b * V;
       gc::slab_promote_kernel<<<(int)std::min<size_t>((nv + 255) / 256, 4096), 256, 0, s>>>(

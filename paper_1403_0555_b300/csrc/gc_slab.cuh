@@ -479,6 +479,155 @@ __global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
   if constexpr (CL) cg::this_cluster().sync();   // no CTA leaves while its slots may be read
 }
 
+// -- FP32 sweeps with the lattice in a cluster's distributed shared memory ----
+// One start per cluster of C CTAs (C <= L), CTA q holding the state of its
+// planes [q L / C, (q+1) L / C) and those planes' links, for the whole
+// launch: the links are loaded once (every start of the batch has the same
+// orbit) and the state never leaves shared memory while a start relaxes.  A
+// site's neighbours along axis d-1 across the CTA's first or last plane, and
+// the backward links there, are read from the neighbouring CTAs' shared
+// memory (distributed shared memory); one cluster barrier per colour phase
+// orders the phases.  Per site the operations are relax_slab_kernel's
+// (SlabOps<float2>, same order), so the results are the same bit for bit.
+// FP32 only: the state and the links of a 16-CTA cluster's planes fit
+// (5 x 8 B per site for d = 4) where FP64's would not.
+__host__ __device__ inline size_t dsmem_smem_bytes(int d, int L, int P, int C) {
+  const int nzmax = (L + C - 1) / C;
+  return 1024 + (size_t)nzmax * P * 8 * (1 + d);
+}
+
+template <int D>
+__global__ void __launch_bounds__(1024, 1) relax_dsmem_kernel(const SlabArgs a) {
+  using Ops = SlabOps<float2>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), q = (int)cl.block_rank();
+  const int cid = blockIdx.x / C, ncl = gridDim.x / C;
+  const int L = a.L, V = a.V, P = a.P, P2 = a.P / 2, tid = threadIdx.x, nt = blockDim.x;
+  const int nzmax = (L + C - 1) / C;
+  const int z0 = q * L / C, nz = (q + 1) * L / C - z0;            // >= 1 (C <= L)
+  const int qp = (q + C - 1) % C, qn = (q + 1) % C;
+  const int nz_prev = (qp + 1) * L / C - qp * L / C;
+  float* red = reinterpret_cast<float*>(smem + 64);               // per-warp partials (<= 32 warps)
+  double* cl_slots = reinterpret_cast<double*>(smem + 256);       // [2][16] exchange (rank 0's)
+  float2* st = reinterpret_cast<float2*>(smem + 1024);            // [nzmax][P] state, own planes
+  float2* lk = st + (size_t)nzmax * P;                            // [nzmax][P][D] links, own planes
+  // the planes next to this CTA's, in the neighbouring CTAs' shared memory
+  const float2* st_prev = cl.map_shared_rank(st, qp) + (size_t)(nz_prev - 1) * P;   // plane z0 - 1
+  const float2* st_next = cl.map_shared_rank(st, qn);                                // plane z0 + nz
+  const float2* lk_prev = cl.map_shared_rank(lk, qp) + (size_t)(nz_prev - 1) * P * D;
+  const float2* links = static_cast<const float2*>(a.links);
+  for (int k = tid; k < nz * P * D; k += nt) lk[k] = links[(size_t)z0 * P * D + k];
+  int round = 0;
+  unsigned long long my_sweeps = 0, my_conv = 0, my_nconv = 0;
+  const SlabOmega w{a.omega, a.om1, a.omega32, a.om1_32};
+  __syncthreads();
+  cl.sync();
+
+  // cluster-wide max of r (rank 0 holds double-buffered slots)
+  auto cmax = [&](float r) -> float {
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if ((tid & 31) == 0) red[tid >> 5] = r;
+    __syncthreads();
+    r = 0.f;
+    for (int k = 0; k < nt / 32; ++k) r = fmaxf(r, red[k]);
+    __syncthreads();
+    double* set = cl_slots + 16 * (round & 1);
+    if (tid == 0) cl.map_shared_rank(set, 0)[q] = (double)r;
+    cl.sync();
+    const double* src = cl.map_shared_rank(set, 0);
+    double m = 0.0;
+    for (int k = 0; k < C; ++k) m = fmax(m, src[k]);
+    ++round;
+    return (float)m;
+  };
+  // staple of site j (x0, rowbase) of own plane t
+  auto staple = [&](int t, int j, int x0, int rowbase) -> float2 {
+    const float2* cur = st + (size_t)t * P;
+    const float2* prev = t > 0 ? cur - P : st_prev;
+    const float2* next = t + 1 < nz ? cur + P : st_next;
+    const float2* lkc = lk + (size_t)t * P * D;
+    const float2* lkm = t > 0 ? lkc - (size_t)P * D : lk_prev;
+    float2 S = Ops::zero();
+#pragma unroll
+    for (int mu = 0; mu < D; ++mu) {
+      float2 hp, hm, ub;
+      if (mu < D - 1) {
+        int jp, jm;
+        slab_inplane_nb<D>(L, mu, j, x0, rowbase, jp, jm);
+        hp = cur[jp]; hm = cur[jm];
+        ub = lkc[(size_t)jm * D + mu];
+      } else {
+        hp = next[j]; hm = prev[j];
+        ub = lkm[(size_t)j * D + mu];
+      }
+      Ops::acc_fwd(S, lkc[(size_t)j * D + mu], hp);
+      Ops::acc_bwd(S, ub, hm);
+    }
+    return S;
+  };
+  auto phase = [&](int c) {
+    for (int t = 0; t < nz; ++t) {
+      float2* cur = st + (size_t)t * P;
+      for (int h = tid; h < P2; h += nt) {
+        int j, x0, rowbase;
+        slab_site_of<D>(L, h, c, z0 + t, j, x0, rowbase);
+        cur[j] = Ops::move(cur[j], staple(t, j, x0, rowbase), w);
+      }
+    }
+    cl.sync();   // this phase's updates, everywhere, before the next phase reads them
+  };
+  auto residual = [&]() -> float {
+    float r = 0.f;
+    for (int t = 0; t < nz; ++t)
+      for (int j = tid; j < P; j += nt) {
+        const int x0 = j % L, rowbase = j - x0;
+        r = fmaxf(r, Ops::div2(st[(size_t)t * P + j], staple(t, j, x0, rowbase)));
+      }
+    return cmax(r);
+  };
+
+  const long long n = a.list ? (long long)*a.n_list : a.n;
+  for (long long i = cid; i < n; i += ncl) {
+    const long long idx = a.list ? (long long)a.list[i] : i;
+    float2* out = static_cast<float2*>(a.state) + (size_t)idx * V + (size_t)z0 * P;
+    for (int x = tid; x < nz * P; x += nt)
+      st[x] = a.init ? Ops::start(a, idx, z0 * P + x) : out[x];
+    cl.sync();
+    int sweeps = 0, until = a.check_every;
+    bool conv = false;
+    float r = 0.f, r_last = 0.f;
+    for (;;) {
+      phase(0);
+      phase(1);
+      ++sweeps;
+      if (--until == 0) {
+        until = a.check_every;
+        r_last = r;
+        r = residual();
+        conv = r < a.eps32;
+        if (conv || sweeps >= a.max_sweeps) break;
+      }
+    }
+    for (int x = tid; x < nz * P; x += nt) out[x] = st[x];
+    if (tid == 0 && q == 0) {
+      a.status[idx] = conv ? kConverged : kNotConverged;
+      if (a.init) a.sweeps[idx] = sweeps; else a.sweeps[idx] += sweeps;
+      if (a.rate) a.rate[idx] = (r_last > 0.f && r < r_last) ? (float)pow((double)r / (double)r_last, 0.5 / a.check_every) : 0.f;
+      my_sweeps += sweeps;
+      if (conv) ++my_conv; else ++my_nconv;
+    }
+    cl.sync();   // the neighbours are done reading this start's planes
+  }
+  if (tid == 0 && q == 0) {
+    if (a.s_sweeps >= 0) atomicAdd(&a.stats[a.s_sweeps], my_sweeps);
+    if (a.s_updates >= 0) atomicAdd(&a.stats[a.s_updates], my_sweeps * (unsigned long long)V);
+    if (a.s_conv >= 0) atomicAdd(&a.stats[a.s_conv], my_conv);
+    if (a.s_nconv >= 0) atomicAdd(&a.stats[a.s_nconv], my_nconv);
+  }
+  cl.sync();     // no CTA leaves while its shared memory may be read
+}
+
 // -- inexact Newton polish of the mixed path ----------------------------------
 // The FP32 sweeps leave each start with max div^2 below eps32; Newton steps on
 // the gauge angles then finish it (the Jacobian of div is the Faddeev-Popov

@@ -99,14 +99,17 @@ def test_hyperplane_newton_fallback_to_fp64_sweeps():
     assert _agree(c_n, s_n, c_f, s_f, n) >= n - 1
 
 
-def test_hyperplane_cluster_and_cta_forms_agree_bitwise():
-    """3D 16^3 mixed path with 8 starts, so that every start gets a cluster in
-    the FP32 sweeps, the Newton polish and the FP64 sweeps: the cluster form
-    splits each pass by planes but keeps every site's arithmetic and the
-    maxima, so it equals the one-CTA form bit for bit (statuses, sweep and
-    Newton counts, F, every copy's angles)."""
+@pytest.mark.parametrize("d,L", [(3, 16), (2, 64)])
+def test_hyperplane_cluster_and_cta_forms_agree_bitwise(d, L):
+    """Mixed path with 8 starts, so that every start gets a cluster in the
+    FP32 sweeps, the Newton polish and the FP64 sweeps (3D 16^3: streamed
+    hyperplanes; 2D 64^2: the FP32 sweeps with the lattice in the cluster's
+    distributed shared memory, 4 planes per CTA): the cluster forms split each
+    pass by planes but keep every site's arithmetic and the maxima, so they
+    equal the one-CTA form bit for bit (statuses, sweep and Newton counts, F,
+    every copy's angles)."""
     import paper_1403_0555_b300 as gb
-    d, L, n = 3, 16, 8
+    n = 8
     phi = oi.von_mises_orbit(d, L, 1.0, 9)
     st_c, s_c, c_c = _plain(gb, d, L, phi, 9, n, precision=gb.GC_MIXED, check_every=4,
                             relax_variant=gb.GC_RELAX_AUTO)
