@@ -385,6 +385,7 @@ def stats_delta(a, b):
 def run_ours(args):
     import torch
     import paper_1403_0555_b300 as gb
+    from paper_1403_0555_b300.replicas import rank_seed, reduce_timing
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -413,10 +414,10 @@ def run_ours(args):
     # weak scaling: with N > 1 every rank runs the whole eight-orbit workload
     # shape on orbits of its own seeds (no data-path collective)
     def step_orbits(k):
-        if world == 1:
+        if rank == 0:
             return orbits
-        return [oi.Orbit(o.name, o.d, o.L, oi.von_mises_orbit(4, 4, oi.kappa_grid_4d()[j], 1000 * rank + j + 1),
-                         1000 * rank + j + 1) for j, o in enumerate(orbits)]
+        return [oi.Orbit(o.name, o.d, o.L, oi.von_mises_orbit(4, 4, oi.kappa_grid_4d()[j], rank_seed(rank, j)),
+                         rank_seed(rank, j)) for j, o in enumerate(orbits)]
 
     def create(orbs):
         return [gb.gc_create_orbit(d, L, o.phi, o.orbit_id, args.starts) for o in orbs]
@@ -466,14 +467,7 @@ def run_ours(args):
         clocks = clk.stop()
     tot = {k: sum(s_[k] for s_ in stats) for k in stats[0]}
     conv = tot["n_converged"]
-    ms_max = ms
-    conv_all = conv
-    if dist is not None:
-        t = torch.tensor([ms, conv], dtype=torch.float64, device="cuda")
-        m = t.clone()
-        dist.all_reduce(m, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms_max, conv_all = float(m[0]), float(t[1])
+    ms_max, conv_all = reduce_timing(dist, ms, conv, device="cuda")
     value = conv_all / (ms_max / 1000.0)
     upd = tot["site_updates_fp32"] + tot["site_updates_fp64"]
 
@@ -512,12 +506,7 @@ def run_ours(args):
                 gb.gc_destroy_orbit(h)
     barrier()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s, e2e_conv], dtype=torch.float64, device="cuda")
-        m = t.clone()
-        dist.all_reduce(m, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        e2e_s, e2e_conv = float(m[0]), float(t[1])
+    e2e_s, e2e_conv = reduce_timing(dist, e2e_s, e2e_conv, device="cuda")
     e2e = {"value": e2e_conv / e2e_s, "unit": "copies/s",
            "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
 
