@@ -922,32 +922,67 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       fa.lambda2 = o->t_lam.as<double>();
       fa.region = o->t_region.as<int>();
       fa.tau = opt.fp_tau;
-      fa.margin = 1e-3;
+      // FP32 Lanczos resolves the bottom of the spectrum to about eps32 |M|
+      // (~1e-6 here); large lattices have lambda_2 of 1e-4 .. 1e-2, so the
+      // screen decides above 1e-4 and FP64 takes the copies near zero
+      fa.margin = 1e-4;
       fa.kmax = kmax;
       fa.seed = opt.seed;
       fa.scratch = o->scratch.as<unsigned char>();
       fa.stats = stats;
       fa.s_tests = kTests; fa.s_tests64 = kTests64; fa.s_steps = kLanczos;
+      // fp32: the screen, one copy per CTA.  FP64: one copy per cluster of 16
+      // (else 8) CTAs: in auto mode it takes the few copies the screen leaves,
+      // which one CTA each would run as a latency tail (a copy on one CTA:
+      // ~0.34 ms per Lanczos step of 4D 16^4)
       auto launch_f = [&](bool fp32) -> int {
         const size_t smf = gc::slab_fp_smem_bytes(kmax, fp32 ? 4 : 8);
-        auto go = [&](auto kern) -> int {
-          if (int rc = raise_smem_limit(kern, smf)) return rc;
-          kern<<<grid_f, 1024, smf, s>>>(fa);
+        auto go = [&](auto k1, auto kc) -> int {
+          if (!fp32 && cluster) {
+            if (int rc = raise_smem_limit(kc, smf)) return rc;
+            for (int C : {kSlabClusterWide, kSlabCluster}) {
+              if (C > 8) GC_CUDA(cudaFuncSetAttribute(kc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+              cudaLaunchConfig_t cfg{};
+              cudaLaunchAttribute attr[1];
+              attr[0].id = cudaLaunchAttributeClusterDimension;
+              attr[0].val.clusterDim.x = C;
+              attr[0].val.clusterDim.y = 1;
+              attr[0].val.clusterDim.z = 1;
+              cfg.blockDim = dim3(1024);
+              cfg.dynamicSmemBytes = smf;
+              cfg.stream = s;
+              cfg.attrs = attr;
+              cfg.numAttrs = 1;
+              cfg.gridDim = dim3(C * 8);
+              int ncl = 0;
+              if (cudaOccupancyMaxActiveClusters(&ncl, kc, &cfg) != cudaSuccess) {
+                cudaGetLastError();
+                ncl = 0;
+              }
+              if (ncl <= 0) continue;
+              cfg.gridDim = dim3(C * ncl);
+              GC_CUDA(cudaLaunchKernelEx(&cfg, kc, fa));
+              ++o->launches;
+              return GC_OK;
+            }
+          }
+          if (int rc = raise_smem_limit(k1, smf)) return rc;
+          k1<<<grid_f, 1024, smf, s>>>(fa);
           ++o->launches;
           GC_CUDA(cudaGetLastError());
           return GC_OK;
         };
         if (fp32) {
           switch (d) {
-            case 2: return go(gc::slab_fp_lanczos_kernel<float, 2>);
-            case 3: return go(gc::slab_fp_lanczos_kernel<float, 3>);
-            default: return go(gc::slab_fp_lanczos_kernel<float, 4>);
+            case 2: return go(gc::slab_fp_lanczos_kernel<float, 2, false>, gc::slab_fp_lanczos_kernel<float, 2, true>);
+            case 3: return go(gc::slab_fp_lanczos_kernel<float, 3, false>, gc::slab_fp_lanczos_kernel<float, 3, true>);
+            default: return go(gc::slab_fp_lanczos_kernel<float, 4, false>, gc::slab_fp_lanczos_kernel<float, 4, true>);
           }
         }
         switch (d) {
-          case 2: return go(gc::slab_fp_lanczos_kernel<double, 2>);
-          case 3: return go(gc::slab_fp_lanczos_kernel<double, 3>);
-          default: return go(gc::slab_fp_lanczos_kernel<double, 4>);
+          case 2: return go(gc::slab_fp_lanczos_kernel<double, 2, false>, gc::slab_fp_lanczos_kernel<double, 2, true>);
+          case 3: return go(gc::slab_fp_lanczos_kernel<double, 3, false>, gc::slab_fp_lanczos_kernel<double, 3, true>);
+          default: return go(gc::slab_fp_lanczos_kernel<double, 4, false>, gc::slab_fp_lanczos_kernel<double, 4, true>);
         }
       };
       if (opt.fp_mode == GC_FP_AUTO) {

@@ -1054,31 +1054,48 @@ __host__ __device__ inline size_t slab_fp_scratch_bytes(int d, int V) {
   return (((size_t)(d + 3) * V * sizeof(R) + (size_t)V) + 15) / 16 * 16;
 }
 __host__ __device__ inline size_t slab_fp_smem_bytes(int kmax, int elem) {
-  return 1024 + 2 * (((size_t)(kmax + 2) * elem + 15) / 16 * 16);
+  return 1152 + 2 * (((size_t)(kmax + 2) * elem + 15) / 16 * 16);
 }
 
-template <class R, int D>
+// CL = false: one copy per CTA.  CL = true: one copy per cluster, CTA q
+// taking sites [q V / C, (q+1) V / C) in every pass (the vectors and weights
+// stay in global memory, so the matvec reads the other CTAs' entries there);
+// a cluster barrier follows every pass whose output other CTAs read, and the
+// dot products are summed over the CTAs in rank order, the same on every CTA,
+// so every CTA keeps the same tridiagonal and reaches the same decisions.
+template <class R, int D, bool CL>
 __global__ void __launch_bounds__(1024, 1) slab_fp_lanczos_kernel(const SlabFpArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int L = a.L, V = a.V, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
   const int kmax = a.kmax;
   R* red = reinterpret_cast<R*>(smem);                 // [2][32] per-warp partials (<= 512 B)
   R* bcast = reinterpret_cast<R*>(smem + 512);         // [2]
-  R* alpha = reinterpret_cast<R*>(smem + 1024);
+  double* cl_slots = reinterpret_cast<double*>(smem + 528);   // [2][16][2] (rank 0's), to 1040
+  R* alpha = reinterpret_cast<R*>(smem + 1152);
   R* beta2 = alpha + ((size_t)(kmax + 2) * sizeof(R) + 15) / 16 * 16 / sizeof(R);
-  unsigned char* base = a.scratch + (size_t)blockIdx.x * a.scratch_bytes;
+  int C = 1, q = 0, cid = blockIdx.x, ncl = gridDim.x;
+  if constexpr (CL) {
+    cg::cluster_group cl = cg::this_cluster();
+    C = (int)cl.num_blocks();
+    q = (int)cl.block_rank();
+    cid = blockIdx.x / C;
+    ncl = gridDim.x / C;
+  }
+  const int xb = (int)((long long)q * V / C), xe = (int)((long long)(q + 1) * V / C);   // this CTA's sites
+  unsigned char* base = a.scratch + (size_t)cid * a.scratch_bytes;
   R* w = reinterpret_cast<R*>(base);                   // [D][V]
   R* vprev = w + (size_t)D * V;
   R* vcur = vprev + V;
   R* z = vcur + V;
   unsigned char* wrap = reinterpret_cast<unsigned char*>(z + V);
+  int round = 0;
   int strides[D];
   {
     int st = 1;
 #pragma unroll
     for (int mu = 0; mu < D; ++mu) { strides[mu] = st; st *= L; }
   }
-  for (int x = tid; x < V; x += nt) {
+  for (int x = xb + tid; x < xe; x += nt) {
     int t = x;
     unsigned f = 0;
 #pragma unroll
@@ -1091,17 +1108,49 @@ __global__ void __launch_bounds__(1024, 1) slab_fp_lanczos_kernel(const SlabFpAr
     wrap[x] = (unsigned char)f;
   }
   __syncthreads();
-  // block sums of two values (every thread gets both)
-  auto sum2 = [&](R& p, R& q) {
+  // the other CTAs' writes of the last pass are seen (identity without a cluster)
+  auto csync = [&]() {
+    if constexpr (CL) cg::this_cluster().sync(); else __syncthreads();
+  };
+  // sums of two values over the block, then (cluster) over the CTAs in rank
+  // order; every thread of every CTA gets both
+  auto sum2 = [&](R& p, R& r2) {
     for (int o = 16; o > 0; o >>= 1) {
       p += __shfl_xor_sync(0xffffffffu, p, o);
-      q += __shfl_xor_sync(0xffffffffu, q, o);
+      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
     }
-    if (lane == 0) { red[wid] = p; red[32 + wid] = q; }
+    if (lane == 0) { red[wid] = p; red[32 + wid] = r2; }
     __syncthreads();
-    p = 0; q = 0;
-    for (int k = 0; k < nt / 32; ++k) { p += red[k]; q += red[32 + k]; }
+    p = 0; r2 = 0;
+    for (int k = 0; k < nt / 32; ++k) { p += red[k]; r2 += red[32 + k]; }
     __syncthreads();
+    if constexpr (CL) {
+      cg::cluster_group cl = cg::this_cluster();
+      double* set = cl_slots + 32 * (round & 1);
+      if (tid == 0) {
+        double* dst = cl.map_shared_rank(set, 0);
+        dst[2 * q] = (double)p;
+        dst[2 * q + 1] = (double)r2;
+      }
+      cl.sync();
+      // warp 0 reads the C partials (one remote load per lane), lane 0 sums
+      // them in rank order, and the block reads the result locally
+      if (wid == 0) {
+        const double* src = cl.map_shared_rank(set, 0);
+        const double vp = lane < C ? src[2 * lane] : 0.0, vq = lane < C ? src[2 * lane + 1] : 0.0;
+        R sp = 0, sq = 0;
+        for (int k = 0; k < C; ++k) {
+          sp += (R)__shfl_sync(0xffffffffu, vp, k);
+          sq += (R)__shfl_sync(0xffffffffu, vq, k);
+        }
+        if (lane == 0) { bcast[0] = sp; bcast[1] = sq; }
+      }
+      __syncthreads();
+      p = bcast[0];
+      r2 = bcast[1];
+      __syncthreads();
+      ++round;
+    }
   };
   auto nbr = [&](int x, unsigned f, int mu, int& xp, int& xm) {
     const int st = strides[mu];
@@ -1110,11 +1159,11 @@ __global__ void __launch_bounds__(1024, 1) slab_fp_lanczos_kernel(const SlabFpAr
   };
   const unsigned n = *a.n_list;
   unsigned long long my_steps = 0, my_tests = 0;
-  for (unsigned i = blockIdx.x; i < n; i += gridDim.x) {
+  for (unsigned i = cid; i < n; i += ncl) {
     const unsigned e = a.list[i];
     const double2* g = a.cfg + (size_t)e * V;
     // weights cos(phi^theta_{x,mu}) = Re[conj(g_x) u_{x,mu} g_{x+mu}]
-    for (int x = tid; x < V; x += nt) {
+    for (int x = xb + tid; x < xe; x += nt) {
       const double2 gx = g[x];
       const unsigned f = wrap[x];
 #pragma unroll
@@ -1130,7 +1179,7 @@ __global__ void __launch_bounds__(1024, 1) slab_fp_lanczos_kernel(const SlabFpAr
     // insertion), so that a Ritz value short of convergence is reproducible
     const unsigned long long key = a.first_start[e];
     R s = 0, dummy = 0;
-    for (int x = tid; x < V; x += nt) {
+    for (int x = xb + tid; x < xe; x += nt) {
       const U64x4 r = philox4x64_10(key, (uint64_t)x, 0, 1, a.seed, 0x4C414E43ULL);
       const R v = (R)(unsigned)(r.v[0] >> 40) * (R)0x1.0p-24 - (R)0.5;
       vcur[x] = v;
@@ -1140,20 +1189,20 @@ __global__ void __launch_bounds__(1024, 1) slab_fp_lanczos_kernel(const SlabFpAr
     sum2(s, dummy);
     s /= (R)V;
     R nn = 0;
-    for (int x = tid; x < V; x += nt) { const R v = vcur[x] - s; vcur[x] = v; nn += v * v; }
+    for (int x = xb + tid; x < xe; x += nt) { const R v = vcur[x] - s; vcur[x] = v; nn += v * v; }
     dummy = 0;
     sum2(nn, dummy);
     {
       const R inv0 = (R)1 / sqrt(nn);
-      for (int x = tid; x < V; x += nt) vcur[x] *= inv0;
+      for (int x = xb + tid; x < xe; x += nt) vcur[x] *= inv0;
     }
-    __syncthreads();
+    csync();   // the weights and the start vector, everywhere
     const R bound = (R)(4 * D + 1);
     R b = 0, theta = bound, theta_prev = bound, theta_pp = bound;
     int j = 0;
     for (; j < kmax; ++j) {
       R al = 0;
-      for (int x = tid; x < V; x += nt) {
+      for (int x = xb + tid; x < xe; x += nt) {
         const unsigned f = wrap[x];
         const R vx = vcur[x];
         R acc = 0;
@@ -1171,7 +1220,7 @@ __global__ void __launch_bounds__(1024, 1) slab_fp_lanczos_kernel(const SlabFpAr
       dummy = 0;
       sum2(al, dummy);
       R m = 0, zz = 0;
-      for (int x = tid; x < V; x += nt) {
+      for (int x = xb + tid; x < xe; x += nt) {
         const R v = z[x] - al * vcur[x];
         z[x] = v;
         m += v;
@@ -1206,13 +1255,13 @@ __global__ void __launch_bounds__(1024, 1) slab_fp_lanczos_kernel(const SlabFpAr
         theta_prev = theta;
       }
       const R ib = (R)1 / bn;
-      for (int x = tid; x < V; x += nt) { vprev[x] = vcur[x]; vcur[x] = (z[x] - m) * ib; }
+      for (int x = xb + tid; x < xe; x += nt) { vprev[x] = vcur[x]; vcur[x] = (z[x] - m) * ib; }
       b = bn;
-      __syncthreads();
+      csync();   // the new vector, everywhere, before the next matvec
     }
     my_steps += j;
     ++my_tests;
-    if (tid == 0) {
+    if (tid == 0 && q == 0) {
       if (sizeof(R) == 4) {
         if (theta > (R)a.margin) {
           a.lambda2[e] = (double)theta;
@@ -1225,13 +1274,14 @@ __global__ void __launch_bounds__(1024, 1) slab_fp_lanczos_kernel(const SlabFpAr
         a.region[e] = region_of((double)theta, a.tau);
       }
     }
-    __syncthreads();
+    csync();   // this copy's scratch is reused by the next
   }
-  if (tid == 0) {
+  if (tid == 0 && q == 0) {
     atomicAdd(&a.stats[a.s_steps], my_steps);
     if (sizeof(R) == 4 || a.count_tests) atomicAdd(&a.stats[a.s_tests], my_tests);
     if (sizeof(R) == 8) atomicAdd(&a.stats[a.s_tests64], my_tests);
   }
+  if constexpr (CL) cg::this_cluster().sync();   // no CTA leaves while its slots may be read
 }
 
 }  // namespace gc

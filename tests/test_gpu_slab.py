@@ -130,7 +130,7 @@ def test_hyperplane_first_region_lanczos_matches_the_oracle(mode):
     copy by the large-lattice Lanczos (vectors in global memory) against the
     oracle's dense eigensolve of the same copy.  FP64 Lanczos (`lanczos`): a
     Ritz value, so at or above lambda_2 and within 1e-4 relative of it; the
-    FP32 screen (`auto`: it decides copies above 1e-3 and hands the rest to
+    FP32 screen (`auto`: it decides copies above 1e-4 and hands the rest to
     FP64) within 1e-4; region flags equal."""
     import paper_1403_0555_b300 as gb
     d, L, n = 2, 64, 6
