@@ -569,6 +569,65 @@ Tuning cached_tuning(int d, int L, int precision, bool deep = false) {
   return Tuning{};
 }
 
+// Thread-block clusters of `csize` CTAs (`threads` threads, `smem` bytes of
+// dynamic shared memory) that fit on the GPU at once, 0 when none does;
+// queried once per kernel and shape, so that a launch inside a stream capture
+// makes no query
+template <class K>
+int cluster_count(K kernel, int threads, size_t smem, int csize, int* out) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t, int, int>, int> cache;
+  int dev = 0;
+  GC_CUDA(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(reinterpret_cast<const void*>(kernel), threads, smem, csize, dev);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    const auto it = cache.find(key);
+    if (it != cache.end()) { *out = it->second; return GC_OK; }
+  }
+  if (int rc = raise_smem_limit(kernel, smem)) return rc;
+  if (csize > 8) GC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(csize * 8);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = n;
+  *out = n;
+  return GC_OK;
+}
+
+// Launch `kernel` on `ncl` clusters of `csize` CTAs
+template <class K, class A>
+int launch_clusters(K kernel, const A& args, int threads, size_t smem, int csize, int ncl, cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(csize * ncl);
+  GC_CUDA(cudaLaunchKernelEx(&cfg, kernel, args));
+  return GC_OK;
+}
+
 // One launch of the hyperplane sweeps: one CTA per start (grid CTAs), or one
 // start per cluster of kSlabCluster CTAs (as many clusters as fit at once),
 // or, with `wide` (a handful of hard starts), of kSlabClusterWide CTAs where
@@ -578,38 +637,11 @@ template <class K1, class KC>
 int launch_slab(K1 k1, KC kc, const gc::SlabArgs& sa, size_t smem, int grid, bool cluster,
                 cudaStream_t s, bool wide = false) {
   if (cluster) {
-    if (int rc = raise_smem_limit(kc, smem)) return rc;
-    cudaLaunchConfig_t cfg{};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(512);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0, csize = kSlabCluster;
-    if (wide) {
-      GC_CUDA(cudaFuncSetAttribute(kc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-      csize = kSlabClusterWide;
-      attr[0].val.clusterDim.x = csize;
-      cfg.gridDim = dim3(csize * 8);
-      if (cudaOccupancyMaxActiveClusters(&nclusters, kc, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        nclusters = 0;
-      }
-    }
-    if (nclusters == 0) {
-      csize = kSlabCluster;
-      attr[0].val.clusterDim.x = csize;
-      cfg.gridDim = dim3(csize * 64);
-      GC_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, kc, &cfg));
-    }
-    if (nclusters > 0) {
-      cfg.gridDim = dim3(csize * nclusters);
-      GC_CUDA(cudaLaunchKernelEx(&cfg, kc, sa));
-      return GC_OK;
+    for (int csize : {kSlabClusterWide, kSlabCluster}) {
+      if (csize == kSlabClusterWide && !wide) continue;
+      int ncl = 0;
+      if (int rc = cluster_count(kc, 512, smem, csize, &ncl)) return rc;
+      if (ncl > 0) return launch_clusters(kc, sa, 512, smem, csize, ncl, s);
     }
     // no cluster of this shape fits: one CTA per start
   }
@@ -617,6 +649,76 @@ int launch_slab(K1 k1, KC kc, const gc::SlabArgs& sa, size_t smem, int grid, boo
   k1<<<grid, 512, smem, s>>>(sa);
   GC_CUDA(cudaGetLastError());
   return GC_OK;
+}
+
+// Everything the hyperplane path of a call allocates or queries, done before
+// any of its work is enqueued, so that a batch can be captured as a graph:
+// the staging of B starts, the per-start rate and redo lists, the Newton and
+// first-region scratch, and the shared-memory limits and cluster counts of
+// every launch shape.  Returns B, the starts per device batch.
+template <int D>
+int slab_prepare_d(gc_orbit o, uint64_t n_starts, const gc_options& opt, cudaStream_t s, size_t* B_out) {
+  const int V = o->V, L = o->L, P = V / L;
+  const bool mixed = opt.precision == GC_MIXED, cluster = opt.relax_variant != GC_RELAX_GENERIC;
+  const size_t per_start = (size_t)V * 16 + (mixed ? (size_t)V * 8 : 0) + 48;
+  size_t B = opt.batch_starts > 0 ? (size_t)opt.batch_starts
+                                  : std::max<size_t>(2 * (size_t)sm_count(), (1ull << 30) / per_start);
+  B = std::min<size_t>(B, n_starts);
+  if (!o->s_status.ensure(B, s) || !o->s_sweeps.ensure(B * 4, s) || !o->s_resid.ensure(B * 8, s) ||
+      !o->s_F.ensure(B * 8, s) || !o->s_fprint.ensure(B * 8, s) || !o->s_config.ensure(B * V * 16, s) ||
+      !o->s_copy.ensure(B * 4, s) || (mixed && !o->s_state32.ensure(B * V * 8, s)) ||
+      (mixed && !o->s_rate.ensure(B * 4, s)) || !o->s_redo.ensure(B * 8, s))
+    return fail(GC_ENOMEM, "cannot admit a batch of %zu starts (%.1f MiB staging)", B, B * per_start / 1048576.0);
+  int x = 0;
+  const size_t sm64 = gc::slab_smem_bytes(P, 16), sm32 = gc::slab_smem_bytes(P, 8);
+  if (int rc = raise_smem_limit(gc::relax_slab_kernel<double2, D, false>, sm64)) return rc;
+  if (cluster) {
+    if (int rc = cluster_count(gc::relax_slab_kernel<double2, D, true>, 512, sm64, kSlabCluster, &x)) return rc;
+    if (mixed)
+      if (int rc = cluster_count(gc::relax_slab_kernel<double2, D, true>, 512, sm64, kSlabClusterWide, &x)) return rc;
+  }
+  size_t scratch = 0;
+  if (mixed) {
+    if (int rc = raise_smem_limit(gc::relax_slab_kernel<float2, D, false>, sm32)) return rc;
+    if (cluster) {
+      if (int rc = cluster_count(gc::relax_slab_kernel<float2, D, true>, 512, sm32, kSlabCluster, &x)) return rc;
+      for (int C : {kSlabClusterWide, kSlabCluster}) {
+        const size_t smd = gc::dsmem_smem_bytes(D, L, P, C);
+        if (L < 4 * C || smd > max_smem_optin()) continue;
+        if (int rc = cluster_count(gc::relax_dsmem_kernel<D>, P / 2 >= 1024 ? 1024 : 256, smd, C, &x)) return rc;
+      }
+    }
+    const int Ps = (P + 3) / 4 * 4;
+    const size_t smn = gc::slab_newton_smem_bytes(Ps);
+    if (int rc = raise_smem_limit(gc::slab_newton_kernel<D, false>, smn)) return rc;
+    int ncl = 0;
+    if (cluster)
+      if (int rc = cluster_count(gc::slab_newton_kernel<D, true>, 1024, smn, kSlabCluster, &ncl)) return rc;
+    const int slots = std::max((int)std::min<size_t>(B, (size_t)sm_count()), ncl);
+    scratch = std::max(scratch, (size_t)slots * gc::slab_newton_scratch_floats(D, V, L, Ps) * 4);
+  }
+  if (opt.fp_mode != GC_FP_NONE) {
+    const int kmax = std::min(std::max(opt.lanczos_k, 8 * L), V - 1);
+    const size_t smf32 = gc::slab_fp_smem_bytes(kmax, 4), smf64 = gc::slab_fp_smem_bytes(kmax, 8);
+    if (int rc = raise_smem_limit(gc::slab_fp_lanczos_kernel<float, D, false>, smf32)) return rc;
+    if (int rc = raise_smem_limit(gc::slab_fp_lanczos_kernel<double, D, false>, smf64)) return rc;
+    if (cluster)
+      for (int C : {kSlabClusterWide, kSlabCluster})
+        if (int rc = cluster_count(gc::slab_fp_lanczos_kernel<double, D, true>, 1024, smf64, C, &x)) return rc;
+    scratch = std::max(scratch, (size_t)sm_count() * gc::slab_fp_scratch_bytes<double>(D, V));
+  }
+  if (scratch && !o->scratch.ensure(scratch, s))
+    return fail(GC_ENOMEM, "cannot admit the large-lattice scratch (%.1f MiB)", scratch / 1048576.0);
+  *B_out = B;
+  return GC_OK;
+}
+
+int slab_prepare(gc_orbit o, uint64_t n_starts, const gc_options& opt, cudaStream_t s, size_t* B_out) {
+  switch (o->d) {
+    case 2: return slab_prepare_d<2>(o, n_starts, opt, s, B_out);
+    case 3: return slab_prepare_d<3>(o, n_starts, opt, s, B_out);
+    default: return slab_prepare_d<4>(o, n_starts, opt, s, B_out);
+  }
 }
 
 // The path for lattices beyond shared memory (o->slab): sweeps that stream the
@@ -629,14 +731,8 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
                    cudaStream_t s, bool async, bool timing, int check_every, int max_sweeps) {
   const int V = o->V, d = o->d, L = o->L, P = V / L;
   const bool mixed = opt.precision == GC_MIXED;
-  const size_t per_start = (size_t)V * 16 + (mixed ? (size_t)V * 8 : 0) + 48;
-  size_t B = opt.batch_starts > 0 ? (size_t)opt.batch_starts
-                                  : std::max<size_t>(2 * (size_t)sm_count(), (1ull << 30) / per_start);
-  B = std::min<size_t>(B, n_starts);
-  if (!o->s_status.ensure(B, s) || !o->s_sweeps.ensure(B * 4, s) || !o->s_resid.ensure(B * 8, s) ||
-      !o->s_F.ensure(B * 8, s) || !o->s_fprint.ensure(B * 8, s) || !o->s_config.ensure(B * V * 16, s) ||
-      !o->s_copy.ensure(B * 4, s) || (mixed && !o->s_state32.ensure(B * V * 8, s)))
-    return fail(GC_ENOMEM, "cannot admit a batch of %zu starts (%.1f MiB staging)", B, B * per_start / 1048576.0);
+  size_t B = 0;
+  if (int rc = slab_prepare(o, n_starts, opt, s, &B)) return rc;
   unsigned long long* wctr = o->work.as<unsigned long long>();
   unsigned long long* stats = o->stats.as<unsigned long long>();
   if (!o->err_unchecked) GC_CUDA(cudaMemsetAsync(o->err(), 0, 16, s));
@@ -727,28 +823,11 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
         for (int C : {kSlabClusterWide, kSlabCluster}) {
           const size_t smd = gc::dsmem_smem_bytes(d, L, P, C);
           if (L < 4 * C || smd > max_smem_optin()) continue;
-          if (int rc = raise_smem_limit(kd, smd)) return rc;
-          if (C > 8) GC_CUDA(cudaFuncSetAttribute(kd, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-          cudaLaunchConfig_t cfg{};
-          cudaLaunchAttribute attr[1];
-          attr[0].id = cudaLaunchAttributeClusterDimension;
-          attr[0].val.clusterDim.x = C;
-          attr[0].val.clusterDim.y = 1;
-          attr[0].val.clusterDim.z = 1;
-          cfg.blockDim = dim3(P / 2 >= 1024 ? 1024 : 256);
-          cfg.dynamicSmemBytes = smd;
-          cfg.stream = s;
-          cfg.attrs = attr;
-          cfg.numAttrs = 1;
-          cfg.gridDim = dim3(C * 8);
+          const int thr = P / 2 >= 1024 ? 1024 : 256;
           int ncl = 0;
-          if (cudaOccupancyMaxActiveClusters(&ncl, kd, &cfg) != cudaSuccess) {
-            cudaGetLastError();
-            ncl = 0;
-          }
+          if (int rc = cluster_count(kd, thr, smd, C, &ncl)) return rc;
           if (ncl <= 0) continue;
-          cfg.gridDim = dim3(C * ncl);
-          GC_CUDA(cudaLaunchKernelEx(&cfg, kd, sa));
+          if (int rc = launch_clusters(kd, sa, thr, smd, C, ncl, s)) return rc;
           ++o->launches;
           dsm = true;
           break;
@@ -795,25 +874,11 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       const unsigned* final_list = redo1;
       const unsigned* final_n = o->n_redo();
       {
-        cudaLaunchConfig_t cfg{};
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = kSlabCluster;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.blockDim = dim3(1024);
-        cfg.dynamicSmemBytes = smn;
-        cfg.stream = s;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cfg.gridDim = dim3(kSlabCluster * 16);
         int ncl = 0;
         auto kc = d == 2 ? gc::slab_newton_kernel<2, true> : (d == 3 ? gc::slab_newton_kernel<3, true> : gc::slab_newton_kernel<4, true>);
         auto k1 = d == 2 ? gc::slab_newton_kernel<2, false> : (d == 3 ? gc::slab_newton_kernel<3, false> : gc::slab_newton_kernel<4, false>);
-        if (cluster) {
-          if (int rc = raise_smem_limit(kc, smn)) return rc;
-          GC_CUDA(cudaOccupancyMaxActiveClusters(&ncl, kc, &cfg));
-        }
+        if (cluster)
+          if (int rc = cluster_count(kc, 1024, smn, kSlabCluster, &ncl)) return rc;
         const int grid1 = (int)std::max<long long>(1, std::min<long long>(b, (long long)sm_count()));
         const int slots = std::max(grid1, ncl);
         if (!o->scratch.ensure((size_t)slots * na.scratch_floats * 4, s))
@@ -821,8 +886,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
                       slots * na.scratch_floats * 4 / 1048576.0);
         na.scratch = o->scratch.as<float>();
         auto run_cluster = [&]() -> int {
-          cfg.gridDim = dim3(kSlabCluster * ncl);
-          GC_CUDA(cudaLaunchKernelEx(&cfg, kc, na));
+          if (int rc = launch_clusters(kc, na, 1024, smn, kSlabCluster, ncl, s)) return rc;
           ++o->launches;
           return GC_OK;
         };
@@ -939,29 +1003,11 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
         const size_t smf = gc::slab_fp_smem_bytes(kmax, fp32 ? 4 : 8);
         auto go = [&](auto k1, auto kc) -> int {
           if (!fp32 && cluster) {
-            if (int rc = raise_smem_limit(kc, smf)) return rc;
             for (int C : {kSlabClusterWide, kSlabCluster}) {
-              if (C > 8) GC_CUDA(cudaFuncSetAttribute(kc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-              cudaLaunchConfig_t cfg{};
-              cudaLaunchAttribute attr[1];
-              attr[0].id = cudaLaunchAttributeClusterDimension;
-              attr[0].val.clusterDim.x = C;
-              attr[0].val.clusterDim.y = 1;
-              attr[0].val.clusterDim.z = 1;
-              cfg.blockDim = dim3(1024);
-              cfg.dynamicSmemBytes = smf;
-              cfg.stream = s;
-              cfg.attrs = attr;
-              cfg.numAttrs = 1;
-              cfg.gridDim = dim3(C * 8);
               int ncl = 0;
-              if (cudaOccupancyMaxActiveClusters(&ncl, kc, &cfg) != cudaSuccess) {
-                cudaGetLastError();
-                ncl = 0;
-              }
+              if (int rc = cluster_count(kc, 1024, smf, C, &ncl)) return rc;
               if (ncl <= 0) continue;
-              cfg.gridDim = dim3(C * ncl);
-              GC_CUDA(cudaLaunchKernelEx(&cfg, kc, fa));
+              if (int rc = launch_clusters(kc, fa, 1024, smf, C, ncl, s)) return rc;
               ++o->launches;
               return GC_OK;
             }
@@ -1061,7 +1107,10 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
   }
 
   if (o->slab) {
-    if (prepare_only) return GC_OK;
+    if (prepare_only) {
+      size_t B_slab = 0;
+      return slab_prepare(o, n_starts, opt, s, &B_slab);
+    }
     return enumerate_slab(o, n_starts, omega, eps, opt, s, async, timing, check_every, max_sweeps);
   }
   // launch shapes
@@ -1997,6 +2046,7 @@ extern "C" int gc_enumerate_batch(gc_orbit* orbits, int n_orbits, const uint64_t
   }
   if (opt.use_graph) {
     const cudaError_t e = cudaStreamEndCapture(origin, &graph);
+    if (rc != GC_OK) cudaGetLastError();   // a failed capture's error is not left for the next call
     if (rc == GC_OK && e != cudaSuccess) rc = fail(GC_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
     if (rc == GC_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = fail(GC_ECUDA, "cudaGraphInstantiate failed");
     if (rc == GC_OK && cudaGraphLaunch(exec, origin) != cudaSuccess) rc = fail(GC_ECUDA, "cudaGraphLaunch failed");

@@ -204,3 +204,35 @@ def test_hyperplane_batches_give_the_single_batch_result(precision):
         assert np.array_equal(c_1[k], c_b[k]), k
     for k in ("n_converged", "sweeps_fp32", "site_updates_fp64", "newton_steps"):
         assert st_1[k] == st_b[k], k
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_hyperplane_orbit_in_a_batch(use_graph):
+    """A 4^4 orbit and a 2D 64^2 orbit (the hyperplane path) in one
+    gc_enumerate_batch call, plainly and captured as one CUDA graph (every
+    buffer and launch query of the hyperplane path is set up before the
+    capture): each orbit's copies equal its single call."""
+    import torch
+    import paper_1403_0555_b300 as gb
+    side = torch.cuda.Stream()
+    specs = [(4, 4, 4000, 1), (2, 64, 12, 2)]
+    opt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=4, stream=side, use_graph=use_graph)
+    hs = [gb.gc_create_orbit(d, L, oi.von_mises_orbit(d, L, 1.0, sd), sd, n) for d, L, n, sd in specs]
+    try:
+        with torch.cuda.stream(side):
+            gb.gc_enumerate_batch(hs, [n for _, _, n, _ in specs], 1.7, 1e-24, opt)
+        side.synchronize()
+        got = [gb.gc_fetch_copies(h, L ** d) for h, (d, L, _, _) in zip(hs, specs)]
+    finally:
+        for h in hs:
+            gb.gc_destroy_orbit(h)
+    for (d, L, n, sd), c in zip(specs, got):
+        h = gb.gc_create_orbit(d, L, oi.von_mises_orbit(d, L, 1.0, sd), sd)
+        try:
+            gb.gc_enumerate_copies(h, n, 1.7, 1e-24, gb.gc_options_default(precision=gb.GC_MIXED, check_every=4))
+            ref = gb.gc_fetch_copies(h, L ** d)
+        finally:
+            gb.gc_destroy_orbit(h)
+        assert c["n_distinct"] == ref["n_distinct"] > 0
+        for k in ("F", "theta", "first_start", "count", "region", "lambda2"):
+            assert np.array_equal(c[k], ref[k]), (d, L, k)
