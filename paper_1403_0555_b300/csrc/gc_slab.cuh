@@ -166,10 +166,13 @@ __device__ __forceinline__ bool ring_walk(PlaneRing<E>& R, E* base, bool store, 
   return ring_walk(R, base, store, static_cast<Body&&>(body), 0, R.L);
 }
 
-// Overrelaxation parameter of one start's sweeps (both precisions' forms)
+// Overrelaxation parameter of one start's sweeps (both precisions' forms);
+// `fast`: FP64 normalisation by rsqrt, for sweeps that need not follow the
+// oracle's correctly rounded operations (the polish of hard starts)
 struct SlabOmega {
   double om, om1;
   float om32, om1_32;
+  bool fast;
 };
 
 // Young's relation for consistently ordered matrices (the red-black ordering
@@ -200,6 +203,16 @@ template <> struct SlabOps<double2> {
   }
   static __device__ __forceinline__ double2 zero() { return make_double2(0.0, 0.0); }
   static __device__ __forceinline__ double2 move(double2 gx, double2 S, const SlabOmega& a) {
+    if (a.fast) {
+      const double n2 = S.x * S.x + S.y * S.y;
+      if (!(n2 > 0.0)) return gx;
+      const double r = rsqrt(n2) * a.om;
+      const double vx = fma(S.x, r, a.om1 * gx.x), vy = fma(S.y, r, a.om1 * gx.y);
+      const double m2 = vx * vx + vy * vy;
+      if (!(m2 > 0.0)) return gx;
+      const double q = rsqrt(m2);
+      return make_double2(vx * q, vy * q);
+    }
     const double n2 = __dadd_rn(__dmul_rn(S.x, S.x), __dmul_rn(S.y, S.y));
     if (!(n2 > 0.0)) return gx;
     const double r = __drcp_rn(__dsqrt_rn(n2));
@@ -425,10 +438,10 @@ __global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
     const long long idx = a.list ? (long long)a.list[i] : i;
     E* st = static_cast<E*>(a.state) + (size_t)idx * V;
     bool ok = true;
-    w = SlabOmega{a.omega, a.om1, a.omega32, a.om1_32};
-    if (a.omega_rate) {
+    w = SlabOmega{a.omega, a.om1, a.omega32, a.om1_32, false};
+    if (a.omega_rate) {   // the polish of hard starts: Young's parameter, rsqrt normalisation
       const float wy = young_omega(a.omega_rate[idx], a.omega32);
-      w = SlabOmega{(double)wy, 1.0 - (double)wy, wy, 1.f - wy};
+      w = SlabOmega{(double)wy, 1.0 - (double)wy, wy, 1.f - wy, true};
     }
     if (a.init) {
       for (int x = z0 * P + tid; x < (z0 + nz) * P; x += nt) st[x] = Ops::start(a, idx, x);
@@ -520,7 +533,7 @@ __global__ void __launch_bounds__(1024, 1) relax_dsmem_kernel(const SlabArgs a) 
   for (int k = tid; k < nz * P * D; k += nt) lk[k] = links[(size_t)z0 * P * D + k];
   int round = 0;
   unsigned long long my_sweeps = 0, my_conv = 0, my_nconv = 0;
-  const SlabOmega w{a.omega, a.om1, a.omega32, a.om1_32};
+  const SlabOmega w{a.omega, a.om1, a.omega32, a.om1_32, false};
   __syncthreads();
   cl.sync();
 
