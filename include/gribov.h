@@ -142,8 +142,13 @@ int gc_options_default(gc_options* opt);
  * The library stores (cos phi, sin phi) in FP64 and FP32 (no trigonometry in
  * the sweeps).  orbit_id keys the random starts together with the seed.
  * max_copies sizes the first copy pool (0 = automatic; it grows on demand).
- * d in 1..4, L >= 2, and the lattice must fit the shared-memory path
- * (V*d links of 16 bytes plus tables; e.g. up to 6^4, 14^3, 63^2). */
+ * d in 1..4, L >= 2.  Lattices whose links and tables fit one CTA's shared
+ * memory (e.g. up to 6^4, 14^3, 63^2) take the shared-memory kernels; larger
+ * ones, up to V = 65 536 sites with even L and d >= 2 (e.g. 16^4, 40^3,
+ * 256^2), take the path for lattices beyond shared memory: hyperplanes of
+ * each start streamed from global memory, or held in a cluster's distributed
+ * shared memory, with the first-region test by Lanczos in global memory.
+ * Anything else is GC_EINVAL. */
 int gc_create_orbit(int dim, int L, const double* link_angles, uint64_t orbit_id,
                     size_t max_copies, gc_orbit* out);
 
