@@ -236,3 +236,15 @@ def test_hyperplane_orbit_in_a_batch(use_graph):
         assert c["n_distinct"] == ref["n_distinct"] > 0
         for k in ("F", "theta", "first_start", "count", "region", "lambda2"):
             assert np.array_equal(c[k], ref[k]), (d, L, k)
+
+
+@pytest.mark.parametrize("d,L", [(3, 17), (4, 18), (1, 5000), (2, 300)])
+def test_lattices_neither_path_takes_are_refused(d, L):
+    """Beyond shared memory only even L, d >= 2 and V <= 65 536 are taken:
+    3D 17^3 (odd L), 4D 18^4 (V = 104 976), 1D of 5000 sites and 2D 300^2
+    (V = 90 000) are GC_EINVAL at gc_create_orbit, with nothing allocated."""
+    import paper_1403_0555_b300 as gb
+    phi = np.zeros((L ** d, d))
+    with pytest.raises(gb.GribovError) as e:
+        gb.gc_create_orbit(d, L, phi, 1)
+    assert e.value.code == gb.GC_EINVAL
