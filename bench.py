@@ -44,6 +44,10 @@ FP64_NOMINAL_TFLOPS = 1.25          # B300 dense FP64 (DFMA = 2 flops)
 # captured for the current kernel)
 TRAFFIC_POLISH_PER_START = (1.345e8 + 2.173e8) / 65536      # profiles/polish_kernel_4d_L4.md (line polish)
 TRAFFIC_RELAX_PER_START = (9.91e4 + 7.4575e7) / 65536       # profiles/relax32_sheet_4d_L4.md
+# DRAM traffic per launch of the large-lattice leg's kernels (its own workload,
+# 592 starts of 4D 16^4), from ncu: profiles/slab_traffic_4d_L16.md
+TRAFFIC_SLAB_RELAX32 = 2.3812352e7 + 3.24274688e8
+TRAFFIC_SLAB_NEWTON1 = 3.04189452544e11 + 5.7821506304e10
 
 
 def parse():
@@ -305,10 +309,16 @@ def large_lattice_leg(gb, torch, d=4, L=16, n=592, runs=2):
             "fp64_fallback_starts": acc["polish_fallbacks"] // runs,
             "relax_slab": {"kernel": "relax_slab_kernel<float2,4,true> (8-CTA clusters)", "bound": "hbm",
                            "achieved": relax_gbs, "peak": hbm, "unit": "GB/s", "frac": relax_gbs / hbm,
-                           "bytes_per_update": 32 + 8 / 4},
-            "newton_inner": {"kernel": "slab_newton_kernel<4,false>", "bound": "hbm", "achieved": inner_gbs,
-                             "peak": hbm, "unit": "GB/s", "frac": inner_gbs / hbm,
-                             "note": "over the whole Newton launch, its tail of hard starts included"}}
+                           "bytes_per_update": 32 + 8 / 4, "traffic": TRAFFIC_SLAB_RELAX32,
+                           "note": "algorithmic state traffic; with 37 starts in flight (19 MB) L2 serves it "
+                                   "(traffic = DRAM bytes per launch, ncu), so the kernel is bound by L2 "
+                                   "and link-load latency, not HBM"},
+            "newton_inner": {"kernel": "slab_newton_kernel<4,·> (both stages)", "bound": "hbm",
+                             "achieved": inner_gbs, "peak": hbm, "unit": "GB/s", "frac": inner_gbs / hbm,
+                             "traffic": TRAFFIC_SLAB_NEWTON1,
+                             "note": "over both Newton launches, the hard starts' cluster stage included; "
+                                     "traffic = DRAM bytes of the one-CTA stage (ncu), as its algorithmic "
+                                     "inner-sweep bytes predict"}}
 
 
 # ----------------------------------------------------------------------------
