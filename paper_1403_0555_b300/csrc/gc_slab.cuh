@@ -14,8 +14,9 @@
 //
 // Per sweep and start the state is read twice and written once (one load and
 // one store of every plane per colour phase, each store holding the whole
-// plane); the links are shared by every start of the orbit and stay in L2.  So
-// with many starts in flight the sweeps are bound by HBM bandwidth.
+// plane); the links are shared by every start of the orbit and stay in L2.
+// With the starts in flight beyond L2 the sweeps would be bound by HBM
+// bandwidth; one start per cluster keeps few in flight, and L2 serves them.
 //
 // The residual is a separate read-only walk every check_every sweeps (the
 // state after the sweep), so the checked state is the state kept.  The FP64
@@ -24,6 +25,12 @@
 //
 // Every wait on a bulk copy is bounded: when one runs out the kernel sets
 // err[3], lets the copies in flight finish (bounded again) and returns.
+//
+// Also here, for the same lattices: the FP32 sweeps with the lattice held in a
+// cluster's distributed shared memory (relax_dsmem_kernel), the inexact Newton
+// polish of the mixed path (slab_newton_kernel), the functional and canonical
+// copy (slab_final_kernel) and the first-region test by Lanczos with vectors
+// in global memory (slab_fp_lanczos_kernel).
 #pragma once
 #include <cooperative_groups.h>
 #include "gc_fptest.cuh"
