@@ -1219,34 +1219,43 @@ __global__ void __launch_bounds__(1024, 1) slab_fp_lanczos_kernel(const SlabFpAr
     csync();   // the weights and the start vector, everywhere
     const R bound = (R)(4 * D + 1);
     R b = 0, theta = bound, theta_prev = bound, theta_pp = bound;
+    // The current vector is (vr[x] - mb) * ibv: the previous step's raw z,
+    // normalised where it is read, so that a step takes two passes over the
+    // sites (the same values as storing it normalised in a third pass)
+    R* vp = vprev;   // v_{j-1}, normalised
+    R* vr = vcur;    // raw v_j
+    R* zs = z;       // z_j
+    R mb = 0, ibv = 1;
     int j = 0;
     for (; j < kmax; ++j) {
       R al = 0;
       for (int x = xb + tid; x < xe; x += nt) {
         const unsigned f = wrap[x];
-        const R vx = vcur[x];
+        const R vx = (vr[x] - mb) * ibv;
         R acc = 0;
 #pragma unroll
         for (int mu = 0; mu < D; ++mu) {
           int xp, xm;
           nbr(x, f, mu, xp, xm);
-          acc = fma(w[(size_t)mu * V + x], vx - vcur[xp], acc);
-          acc = fma(w[(size_t)mu * V + xm], vx - vcur[xm], acc);
+          acc = fma(w[(size_t)mu * V + x], vx - (vr[xp] - mb) * ibv, acc);
+          acc = fma(w[(size_t)mu * V + xm], vx - (vr[xm] - mb) * ibv, acc);
         }
-        const R mv = acc - b * vprev[x];
-        z[x] = mv;
+        const R mv = acc - b * vp[x];
+        zs[x] = mv;
         al += mv * vx;
       }
       dummy = 0;
-      sum2(al, dummy);
+      sum2(al, dummy);   // (and every CTA's matvec is done before vr is rewritten)
       R m = 0, zz = 0;
       for (int x = xb + tid; x < xe; x += nt) {
-        const R v = z[x] - al * vcur[x];
-        z[x] = v;
+        const R vx = (vr[x] - mb) * ibv;
+        const R v = zs[x] - al * vx;
+        zs[x] = v;
+        vr[x] = vx;      // v_j normalised in place: the next step's v_{j-1}
         m += v;
         zz += v * v;
       }
-      sum2(m, zz);
+      sum2(m, zz);       // (cluster) also orders this pass's writes before the next matvec
       m /= (R)V;
       const R bn = sqrt(fmax(zz - (R)V * m * m, (R)0));   // |z - m|
       if (tid == 0) { alpha[j] = al; beta2[j + 1] = bn * bn; }
@@ -1274,10 +1283,14 @@ __global__ void __launch_bounds__(1024, 1) slab_fp_lanczos_kernel(const SlabFpAr
         theta_pp = theta_prev;
         theta_prev = theta;
       }
-      const R ib = (R)1 / bn;
-      for (int x = xb + tid; x < xe; x += nt) { vprev[x] = vcur[x]; vcur[x] = (z[x] - m) * ib; }
+      // v_{j-1} <- v_j, raw v_{j+1} <- z_j, scratch <- the old v_{j-1}
+      R* t = vp;
+      vp = vr;
+      vr = zs;
+      zs = t;
+      mb = m;
+      ibv = (R)1 / bn;
       b = bn;
-      csync();   // the new vector, everywhere, before the next matvec
     }
     my_steps += j;
     ++my_tests;
