@@ -248,3 +248,28 @@ def test_lattices_neither_path_takes_are_refused(d, L):
     with pytest.raises(gb.GribovError) as e:
         gb.gc_create_orbit(d, L, phi, 1)
     assert e.value.code == gb.GC_EINVAL
+
+
+def test_hyperplane_f8_minima():
+    """The paper's count (F/(dV) quantised at 1e-8, with the starts reaching
+    each) on 2D 64^2, plain path: equal to the oracle's, in the configuration
+    mode and in the F-only mode (which keeps no configurations)."""
+    import paper_1403_0555_b300 as gb
+    d, L, n = 2, 64, 12
+    phi = oi.von_mises_orbit(d, L, 1.0, 17)
+    rel = oracle.relax_starts(d, L, phi, 1, 17, 0, n, 1.7, 1e-24)
+    _, th = oracle.canonical(rel.g)
+    conv = rel.status == oracle.CONVERGED
+    F = oracle.functional(d, L, phi, th)
+    keys, counts = np.unique(np.floor(oracle.f_norm(F[conv], d, L) * 1e8).astype(np.int64), return_counts=True)
+    for mode in (gb.GC_DEDUP_CONFIG, gb.GC_DEDUP_F8):
+        h = gb.gc_create_orbit(d, L, phi, 17)
+        try:
+            gb.gc_enumerate_copies(h, n, 1.7, 1e-24, gb.gc_options_default(precision=gb.GC_FP64, check_every=1,
+                                                                          dedup_mode=mode))
+            m, st = gb.gc_fetch_minima_f8(h), gb.gc_orbit_stats(h)
+        finally:
+            gb.gc_destroy_orbit(h)
+        assert np.array_equal(np.round(m["F_norm"] * 1e8).astype(np.int64), keys)
+        assert np.array_equal(m["count"].astype(np.int64), counts)
+        assert (st["n_distinct"] == 0) == (mode == gb.GC_DEDUP_F8)
