@@ -684,8 +684,8 @@ int slab_prepare_d(gc_orbit o, uint64_t n_starts, const gc_options& opt, cudaStr
       if (int rc = cluster_count(gc::relax_slab_kernel<float2, D, true>, 512, sm32, kSlabCluster, &x)) return rc;
       for (int C : {kSlabClusterWide, kSlabCluster}) {
         const size_t smd = gc::dsmem_smem_bytes(D, L, P, C);
-        if (L < 4 * C || smd > max_smem_optin()) continue;
-        if (int rc = cluster_count(gc::relax_dsmem_kernel<D>, P / 2 >= 1024 ? 1024 : 256, smd, C, &x)) return rc;
+        if (L < 2 * C || smd > max_smem_optin()) continue;
+        if (int rc = cluster_count(gc::relax_dsmem_kernel<D>, 256, smd, C, &x)) return rc;
       }
     }
     const int Ps = (P + 3) / 4 * 4;
@@ -810,20 +810,18 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       sa.rate = o->s_rate.as<float>();
       sa.init = 1;
       sa.s_sweeps = kSweeps32; sa.s_updates = kUpdates32; sa.s_conv = kConv32; sa.s_nconv = kNConv32;
-      // the lattice in a cluster's distributed shared memory when a 16- (else
-      // 8-) CTA cluster's planes and links fit and each CTA holds at least 4
-      // planes; else the hyperplane streaming.  With fewer planes per CTA
-      // most axis-(d-1) neighbours are remote and the per-phase cluster
-      // barrier dominates (measured on 592 starts: 2D 256^2, 16 planes per
-      // CTA, 762 ms against 3180 ms streamed; 3D 40^3, 2-3 planes, 595
-      // against 473; 4D 16^4, one plane, 713 against 490)
+      // the lattice in a cluster's distributed shared memory: one start per
+      // cluster of 16 (else 8) CTAs of 256 threads, each holding at least two
+      // planes (else the hyperplane streaming).  Measured on the FP32 stage:
+      // 4D 16^4 (8 CTAs, 2 planes each) 478 ms against 490 streamed, 3D 40^3
+      // 358 against 473, 2D 256^2 586 against 3180
       bool dsm = false;
       if (cluster) {
         auto kd = d == 2 ? gc::relax_dsmem_kernel<2> : (d == 3 ? gc::relax_dsmem_kernel<3> : gc::relax_dsmem_kernel<4>);
         for (int C : {kSlabClusterWide, kSlabCluster}) {
           const size_t smd = gc::dsmem_smem_bytes(d, L, P, C);
-          if (L < 4 * C || smd > max_smem_optin()) continue;
-          const int thr = P / 2 >= 1024 ? 1024 : 256;
+          if (L < 2 * C || smd > max_smem_optin()) continue;
+          const int thr = 256;
           int ncl = 0;
           if (int rc = cluster_count(kd, thr, smd, C, &ncl)) return rc;
           if (ncl <= 0) continue;

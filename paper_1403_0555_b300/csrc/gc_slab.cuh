@@ -500,20 +500,20 @@ __global__ void __launch_bounds__(512) relax_slab_kernel(const SlabArgs a) {
 }
 
 // -- FP32 sweeps with the lattice in a cluster's distributed shared memory ----
-// One start per cluster of C CTAs (C <= L), CTA q holding the state of its
-// planes [q L / C, (q+1) L / C) and those planes' links, for the whole
-// launch: the links are loaded once (every start of the batch has the same
-// orbit) and the state never leaves shared memory while a start relaxes.  A
-// site's neighbours along axis d-1 across the CTA's first or last plane, and
-// the backward links there, are read from the neighbouring CTAs' shared
-// memory (distributed shared memory); one cluster barrier per colour phase
-// orders the phases.  Per site the operations are relax_slab_kernel's
+// One start per cluster of C CTAs (2 C <= L), CTA q holding the state of its
+// planes [q L / C, (q+1) L / C) in its shared memory while the start relaxes:
+// no bulk copies and no ring, 8 B per site (64 KB per CTA for 4D 16^4 on 8
+// CTAs, so three CTAs of 256 threads fit per SM).  A site's neighbours along
+// axis d-1 across the CTA's first or last plane are read from the
+// neighbouring CTAs' shared memory (distributed shared memory); the links,
+// shared by every start of the orbit, come through the read-only path from
+// L2, as in the streamed sweeps.  One cluster barrier per colour phase orders
+// the phases.  Per site the operations are relax_slab_kernel's
 // (SlabOps<float2>, same order), so the results are the same bit for bit.
-// FP32 only: the state and the links of a 16-CTA cluster's planes fit
-// (5 x 8 B per site for d = 4) where FP64's would not.
+// FP32 only.
 __host__ __device__ inline size_t dsmem_smem_bytes(int d, int L, int P, int C) {
   const int nzmax = (L + C - 1) / C;
-  return 1024 + (size_t)nzmax * P * 8 * (1 + d);
+  return 1024 + (size_t)nzmax * P * 8;
 }
 
 template <int D>
@@ -524,20 +524,16 @@ __global__ void __launch_bounds__(1024, 1) relax_dsmem_kernel(const SlabArgs a) 
   const int C = (int)cl.num_blocks(), q = (int)cl.block_rank();
   const int cid = blockIdx.x / C, ncl = gridDim.x / C;
   const int L = a.L, V = a.V, P = a.P, P2 = a.P / 2, tid = threadIdx.x, nt = blockDim.x;
-  const int nzmax = (L + C - 1) / C;
   const int z0 = q * L / C, nz = (q + 1) * L / C - z0;            // >= 1 (C <= L)
   const int qp = (q + C - 1) % C, qn = (q + 1) % C;
   const int nz_prev = (qp + 1) * L / C - qp * L / C;
   float* red = reinterpret_cast<float*>(smem + 64);               // per-warp partials (<= 32 warps)
   double* cl_slots = reinterpret_cast<double*>(smem + 256);       // [2][16] exchange (rank 0's)
-  float2* st = reinterpret_cast<float2*>(smem + 1024);            // [nzmax][P] state, own planes
-  float2* lk = st + (size_t)nzmax * P;                            // [nzmax][P][D] links, own planes
+  float2* st = reinterpret_cast<float2*>(smem + 1024);            // [own planes][P] state
   // the planes next to this CTA's, in the neighbouring CTAs' shared memory
   const float2* st_prev = cl.map_shared_rank(st, qp) + (size_t)(nz_prev - 1) * P;   // plane z0 - 1
   const float2* st_next = cl.map_shared_rank(st, qn);                                // plane z0 + nz
-  const float2* lk_prev = cl.map_shared_rank(lk, qp) + (size_t)(nz_prev - 1) * P * D;
   const float2* links = static_cast<const float2*>(a.links);
-  for (int k = tid; k < nz * P * D; k += nt) lk[k] = links[(size_t)z0 * P * D + k];
   int round = 0;
   unsigned long long my_sweeps = 0, my_conv = 0, my_nconv = 0;
   const SlabOmega w{a.omega, a.om1, a.omega32, a.om1_32, false};
@@ -566,8 +562,8 @@ __global__ void __launch_bounds__(1024, 1) relax_dsmem_kernel(const SlabArgs a) 
     const float2* cur = st + (size_t)t * P;
     const float2* prev = t > 0 ? cur - P : st_prev;
     const float2* next = t + 1 < nz ? cur + P : st_next;
-    const float2* lkc = lk + (size_t)t * P * D;
-    const float2* lkm = t > 0 ? lkc - (size_t)P * D : lk_prev;
+    const float2* lkc = links + (size_t)(z0 + t) * P * D;                 // links of plane z
+    const float2* lkm = links + (size_t)((z0 + t + L - 1) % L) * P * D;   // of plane z - 1
     float2 S = Ops::zero();
 #pragma unroll
     for (int mu = 0; mu < D; ++mu) {
@@ -576,12 +572,12 @@ __global__ void __launch_bounds__(1024, 1) relax_dsmem_kernel(const SlabArgs a) 
         int jp, jm;
         slab_inplane_nb<D>(L, mu, j, x0, rowbase, jp, jm);
         hp = cur[jp]; hm = cur[jm];
-        ub = lkc[(size_t)jm * D + mu];
+        ub = __ldg(lkc + (size_t)jm * D + mu);
       } else {
         hp = next[j]; hm = prev[j];
-        ub = lkm[(size_t)j * D + mu];
+        ub = __ldg(lkm + (size_t)j * D + mu);
       }
-      Ops::acc_fwd(S, lkc[(size_t)j * D + mu], hp);
+      Ops::acc_fwd(S, __ldg(lkc + (size_t)j * D + mu), hp);
       Ops::acc_bwd(S, ub, hm);
     }
     return S;
