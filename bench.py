@@ -46,8 +46,8 @@ TRAFFIC_POLISH_PER_START = (1.345e8 + 2.173e8) / 65536      # profiles/polish_ke
 TRAFFIC_RELAX_PER_START = (9.91e4 + 7.4575e7) / 65536       # profiles/relax32_sheet_4d_L4.md
 # DRAM traffic per launch of the large-lattice leg's kernels (its own workload,
 # 592 starts of 4D 16^4), from ncu: profiles/slab_traffic_4d_L16.md
-TRAFFIC_SLAB_RELAX32 = 2.3812352e7 + 3.24274688e8
 TRAFFIC_SLAB_NEWTON1 = 3.04189452544e11 + 5.7821506304e10
+TRAFFIC_SLAB_DSMEM32 = 2.1208832e7 + 2.71034368e8
 
 
 def parse():
@@ -307,12 +307,13 @@ def large_lattice_leg(gb, torch, d=4, L=16, n=592, runs=2):
             "newton_steps_per_start": acc["newton_steps"] / acc["n_starts"],
             "inner_sweeps_per_start": acc["newton_inner_sweeps"] / acc["n_starts"],
             "fp64_fallback_starts": acc["polish_fallbacks"] // runs,
-            "relax_slab": {"kernel": "relax_slab_kernel<float2,4,true> (8-CTA clusters)", "bound": "hbm",
-                           "achieved": relax_gbs, "peak": hbm, "unit": "GB/s", "frac": relax_gbs / hbm,
-                           "bytes_per_update": 32 + 8 / 4, "traffic": TRAFFIC_SLAB_RELAX32,
-                           "note": "algorithmic state traffic; with 37 starts in flight (19 MB) L2 serves it "
-                                   "(traffic = DRAM bytes per launch, ncu), so the kernel is bound by L2 "
-                                   "and link-load latency, not HBM"},
+            "relax_slab": {"kernel": "relax_dsmem_kernel<4> (8-CTA clusters, state in distributed shared memory)",
+                           "bound": "hbm", "achieved": relax_gbs, "peak": hbm, "unit": "GB/s",
+                           "frac": relax_gbs / hbm, "bytes_per_update": 32 + 8 / 4,
+                           "traffic": TRAFFIC_SLAB_DSMEM32,
+                           "note": "the state traffic the streamed form would move (34 B per update); here the "
+                                   "state stays in the cluster's shared memory and only the links come from "
+                                   "L2, so DRAM (traffic, ncu) sees the starts' generation and write-back"},
             "newton_inner": {"kernel": "slab_newton_kernel<4,·> (both stages)", "bound": "hbm",
                              "achieved": inner_gbs, "peak": hbm, "unit": "GB/s", "frac": inner_gbs / hbm,
                              "traffic": TRAFFIC_SLAB_NEWTON1,
