@@ -694,7 +694,7 @@ int slab_prepare_d(gc_orbit o, uint64_t n_starts, const gc_options& opt, cudaStr
     int ncl = 0;
     if (cluster)
       if (int rc = cluster_count(gc::slab_newton_kernel<D, true>, 1024, smn, kSlabCluster, &ncl)) return rc;
-    const int slots = std::max((int)std::min<size_t>(B, (size_t)sm_count()), ncl);
+    const int slots = std::max((int)std::min<size_t>(B, 4 * (size_t)sm_count()), ncl);
     scratch = std::max(scratch, (size_t)slots * gc::slab_newton_scratch_floats(D, V, L, Ps) * 4);
   }
   if (opt.fp_mode != GC_FP_NONE) {
@@ -838,10 +838,10 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       gc::slab_promote_kernel<<<(int)std::min<size_t>((nv + 255) / 256, 4096), 256, 0, s>>>(
           o->s_state32.as<float2>(), st64, nv);
       ++o->launches;
-      // Newton polish.  One start per 1024-thread CTA (one CTA per SM) with
-      // an inner budget of 2x newton_inner, then the few starts that exceed
-      // it once more on clusters of kSlabCluster CTAs (a hard start runs 8
-      // CTAs wide instead of holding one CTA for the whole launch) with 6x.
+      // Newton polish.  One start per 256-thread CTA (four per SM) with an
+      // inner budget of newton_inner, then the starts that exceed it once more
+      // on clusters of kSlabCluster 1024-thread CTAs with 6x (a hard start runs
+      // 8 SMs wide instead of holding one small CTA for the whole launch).
       // When every start gets a cluster at once, one cluster launch with 4x;
       // GC_RELAX_GENERIC: one CTA per start with 4x.
       GC_CUDA(cudaMemsetAsync(wctr, 0, 8, s));
@@ -877,7 +877,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
         auto k1 = d == 2 ? gc::slab_newton_kernel<2, false> : (d == 3 ? gc::slab_newton_kernel<3, false> : gc::slab_newton_kernel<4, false>);
         if (cluster)
           if (int rc = cluster_count(kc, 1024, smn, kSlabCluster, &ncl)) return rc;
-        const int grid1 = (int)std::max<long long>(1, std::min<long long>(b, (long long)sm_count()));
+        const int grid1 = (int)std::max<long long>(1, std::min<long long>(b, 4LL * sm_count()));
         const int slots = std::max(grid1, ncl);
         if (!o->scratch.ensure((size_t)slots * na.scratch_floats * 4, s))
           return fail(GC_ENOMEM, "cannot admit the Newton scratch of %d starts (%.1f MiB)", slots,
@@ -895,10 +895,10 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
         } else {
           if (int rc = raise_smem_limit(k1, smn)) return rc;
           const bool staged = ncl > 0;
-          na.budget = (staged ? 2 : 4) * opt.newton_inner;
+          na.budget = (staged ? 1 : 4) * opt.newton_inner;
           na.redo = redo1; na.n_redo = o->n_redo();
           na.s_redo = staged ? -1 : kFallback;
-          k1<<<grid1, 1024, smn, s>>>(na);
+          k1<<<grid1, 256, smn, s>>>(na);
           ++o->launches;
           GC_CUDA(cudaGetLastError());
           if (staged) {
