@@ -46,7 +46,7 @@ TRAFFIC_POLISH_PER_START = (1.345e8 + 2.173e8) / 65536      # profiles/polish_ke
 TRAFFIC_RELAX_PER_START = (9.91e4 + 7.4575e7) / 65536       # profiles/relax32_sheet_4d_L4.md
 # DRAM traffic per launch of the large-lattice leg's kernels (its own workload,
 # 592 starts of 4D 16^4), from ncu: profiles/slab_traffic_4d_L16.md
-TRAFFIC_SLAB_NEWTON1 = 3.04189452544e11 + 5.7821506304e10
+TRAFFIC_SLAB_NEWTON1 = 2.92208894464e11 + 5.7204921344e10
 TRAFFIC_SLAB_DSMEM32 = 2.1208832e7 + 2.71034368e8
 
 
