@@ -290,6 +290,19 @@ def large_lattice_leg(gb, torch, d=4, L=16, n=592, runs=2):
         gb.gc_destroy_orbit(h)
         for k, v in st.items():
             acc[k] = acc.get(k, 0) + v
+    # the plain FP64 path on a sample of the same orbit (hyperplane sweeps, bit-exact to the oracle)
+    plain_n = 148
+    popt = gb.gc_options_default(precision=gb.GC_FP64, check_every=1, fp_mode=gb.GC_FP_AUTO, stream=stream)
+    h = gb.gc_create_orbit(d, L, phi, 1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    gb.gc_enumerate_copies(h, plain_n, 1.7, 1e-24, popt)
+    e1.record(stream)
+    e1.synchronize()
+    pst = gb.gc_orbit_stats(h)
+    gb.gc_destroy_orbit(h)
+    plain_value = pst["n_converged"] / (e0.elapsed_time(e1) / 1e3)
     hbm = json.load(open(PEAKS_FILE))["hbm_gbs"] if os.path.exists(PEAKS_FILE) else 6400.0
     relax_bytes = acc["sweeps_fp32"] * V * 32 + acc["sweeps_fp32"] / 4 * V * 8 + acc["n_starts"] * V * 8
     newton_ms = acc["ms_polish"] - acc["ms_polish_redo"]
@@ -307,6 +320,9 @@ def large_lattice_leg(gb, torch, d=4, L=16, n=592, runs=2):
             "newton_steps_per_start": acc["newton_steps"] / acc["n_starts"],
             "inner_sweeps_per_start": acc["newton_inner_sweeps"] / acc["n_starts"],
             "fp64_fallback_starts": acc["polish_fallbacks"] // runs,
+            "plain_fp64": {"starts": plain_n, "value": plain_value, "unit": "copies/s",
+                           "sweeps_per_start": pst["sweeps_fp64"] / max(1, pst["n_starts"]),
+                           "mixed_over_plain": (acc["n_converged"] / (ms / 1e3)) / plain_value},
             "relax_slab": {"kernel": "relax_dsmem_kernel<4> (8-CTA clusters, state in distributed shared memory)",
                            "bound": "hbm", "achieved": relax_gbs, "peak": hbm, "unit": "GB/s",
                            "frac": relax_gbs / hbm, "bytes_per_update": 32 + 8 / 4,
