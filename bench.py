@@ -42,7 +42,7 @@ FP64_NOMINAL_TFLOPS = 1.25          # B300 dense FP64 (DFMA = 2 flops)
 # DRAM traffic per start (read + write) of the two heavy kernels, from the ncu
 # capture of the 65536-start 4^4 case recorded under profiles/ (None = not
 # captured for the current kernel)
-TRAFFIC_POLISH_PER_START = (1.345e8 + 2.173e8) / 65536      # profiles/polish_kernel_4d_L4.md (line polish)
+TRAFFIC_POLISH_PER_START = (1.34528e8 + 2.18642e8) / 65536  # profiles/polish_kernel_4d_L4.md (line polish)
 TRAFFIC_RELAX_PER_START = (9.91e4 + 7.4575e7) / 65536       # profiles/relax32_sheet_4d_L4.md
 # DRAM traffic per launch of the large-lattice leg's kernels (its own workload,
 # 592 starts of 4D 16^4), from ncu: profiles/slab_traffic_4d_L16.md
