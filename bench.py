@@ -4,7 +4,8 @@
 Workload: 4D 4^4 periodic lattice (1024 links), eight von Mises orbits with
 kappa_j = 0.5 + 1.5 j/7 (seeds 1-8), 2^20 random starts per orbit, mixed
 precision (FP32 sweeps to max div^2 < 1e-10, FP64 polish to 1e-24),
-overrelaxation omega = 1.7, Faddeev-Popov Lanczos test, FP64 dedup.
+overrelaxation omega = 1.7, FP64 Lanczos Faddeev-Popov test of every distinct
+copy, FP64 dedup.
 One step = the whole path (starts -> sweeps -> polish -> dedup -> FP test) for
 all eight orbits' 2^20 starts, enqueued by one gc_enumerate_batch call as one
 captured CUDA graph (fresh orbit objects every step).
@@ -13,7 +14,9 @@ Prints one JSON line.  `value` = converged copies per second with the orbits
 resident on the device (CUDA events on the launch stream around the
 gc_enumerate_batch call of each of the K timed steps); `e2e` = the same metric
 through the C ABI with host buffers (link angles uploaded, distinct copies
-read back, every step).  The plain FP64 path is timed on a sample beside it.
+read back, every step).  The plain FP64 path is timed on a sample beside it,
+and the same steps with the FP32 Lanczos screen (`fp32_screen`).  The roofline
+denominators come from the library's own throughput probes (`peaks`).
 """
 from __future__ import annotations
 
@@ -35,15 +38,12 @@ import numpy as np  # noqa: E402
 import orbit_inputs as oi  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-SM_COUNT = 148
-SM_MAX_MHZ = 2032.0
-FP32_LANES_PER_SM = 128
-FP64_NOMINAL_TFLOPS = 1.25          # B300 dense FP64 (DFMA = 2 flops)
 # DRAM traffic per start (read + write) of the two heavy kernels, from the ncu
 # capture of the 65536-start 4^4 case recorded under profiles/ (None = not
 # captured for the current kernel)
 TRAFFIC_POLISH_PER_START = (1.34528e8 + 2.18642e8) / 65536  # profiles/polish_kernel_4d_L4.md (line polish)
 TRAFFIC_RELAX_PER_START = (9.91e4 + 7.4575e7) / 65536       # profiles/relax32_sheet_4d_L4.md
+TRAFFIC_FPTEST_PER_COPY = None                               # fp_test_kernel, not captured since its rewrite
 # DRAM traffic per launch of the large-lattice leg's kernels (its own workload,
 # 592 starts of 4D 16^4), from ncu: profiles/slab_traffic_4d_L16.md
 TRAFFIC_SLAB_NEWTON1 = 2.92208894464e11 + 5.7204921344e10
@@ -430,8 +430,9 @@ def run_ours(args):
     d, L = 4, 4
     V = L ** d
     side = torch.cuda.Stream()
+    # the first-region test of the workload: FP64 Lanczos for every distinct copy
     opt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=args.check_every,
-                                fp_mode=gb.GC_FP_AUTO, stream=side, use_graph=1, autotune=args.autotune)
+                                fp_mode=gb.GC_FP_LANCZOS, stream=side, use_graph=1, autotune=args.autotune)
 
     def barrier():
         torch.cuda.synchronize()
@@ -537,10 +538,48 @@ def run_ours(args):
     e2e = {"value": e2e_conv / e2e_s, "unit": "copies/s",
            "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
 
+    # --- the same steps with the FP32 Lanczos screen (GC_FP_AUTO: FP64 only
+    # for copies whose FP32 lambda_2 is at most 1e-3), a labelled variant
+    sopt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=args.check_every,
+                                 fp_mode=gb.GC_FP_AUTO, stream=side, use_graph=1, autotune=args.autotune)
+    with torch.cuda.stream(side):
+        hs = create(step_orbits(0))
+        gb.gc_enumerate_batch(hs, n_list, w.omega, w.eps, sopt)      # warm-up step
+        for h in hs:
+            gb.gc_destroy_orbit(h)
+        barrier()
+        s_ms, s_conv = 0.0, 0
+        for k in range(args.steps):
+            hs = create(step_orbits(k))
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(side)
+            gb.gc_enumerate_batch(hs, n_list, w.omega, w.eps, sopt)
+            ev1.record(side)
+            ev1.synchronize()
+            s_ms += ev0.elapsed_time(ev1)
+            s_conv += sum(gb.gc_orbit_stats(h)["n_converged"] for h in hs)
+            for h in hs:
+                gb.gc_destroy_orbit(h)
+        barrier()
+    s_ms_max, s_conv_all = reduce_timing(dist, s_ms, s_conv, device="cuda")
+    screen_leg = {"value": s_conv_all / (s_ms_max / 1000.0), "unit": "copies/s",
+                  "ms_per_step": s_ms_max / args.steps, "steps": args.steps,
+                  "fp_test": "GC_FP_AUTO: FP32 Lanczos screen of every copy, FP64 Lanczos for those with "
+                             "FP32 lambda_2 <= 1e-3"}
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
+
+    # --- measured throughput of the arithmetic units (the roofline denominators)
+    peaks = {"ffma": gb.gc_peak_probe(gb.GC_PEAK_FFMA, stream) / 1e12,
+             "ffma2": gb.gc_peak_probe(gb.GC_PEAK_FFMA2, stream) / 1e12,
+             "dfma": gb.gc_peak_probe(gb.GC_PEAK_DFMA, stream) / 1e12,
+             "rsqrt": gb.gc_peak_probe(gb.GC_PEAK_RSQ, stream) / 1e12,
+             "unit": "T lane operations/s (packed f32x2 counts two)",
+             "how": "gc_peak_probe: 4 CTAs x 256 threads per SM, 8 independent chains per thread, best of 3"}
 
     # --- plain FP64 path on a sample of orbit 0 (same options otherwise)
     o = orbits[0]
@@ -572,7 +611,7 @@ def run_ours(args):
     # kernel (the library's per-stage events).
     o = orbits[0]
     ropt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=ce,
-                                 fp_mode=gb.GC_FP_AUTO, stream=stream)
+                                 fp_mode=gb.GC_FP_LANCZOS, stream=stream)
     h = gb.gc_create_orbit(d, L, o.phi, o.orbit_id, args.starts)
     gb.gc_enumerate_copies(h, args.starts, w.omega, w.eps, ropt)
     rs = gb.gc_orbit_stats(h)
@@ -582,55 +621,57 @@ def run_ours(args):
     stage_ms = {"relax_fp32": rs["ms_relax"], "polish_fp64": rs["ms_polish"] - rs["ms_polish_redo"],
                 "polish_redo": rs["ms_polish_redo"],
                 "dedup": rs["ms_dedup"], "fp_test": rs["ms_fptest"]}
-    # the dominant throughput kernel; polish_redo is the few starts the line
-    # polish hands back (near-singular Faddeev-Popov operators), whose single-
-    # warp runs form a latency tail that other orbits' kernels fill in a batch
-    dom = max((k for k in stage_ms if k != "polish_redo"), key=stage_ms.get)
-    # FP32 pipe ops per site update: 8d for the staple's 2d complex products,
-    # 11 to blend and renormalise, and 3 per site at a check (the residual
-    # reuses the update's staple: dv = Re g Im S - Im g Re S, squared)
+    # Per kernel: algorithmic operations over its isolated duration, against
+    # the unit's throughput measured by gc_peak_probe on this GPU.
+    #  * FP32 sweeps (relax32_sheet_kernel): FP32 pipe ops per site update, 8d
+    #    for the staple's 2d complex products, 11 to blend and renormalise, and
+    #    3 per site at a check (the residual reuses the update's staple);
+    #  * line polish (polish_pairs_kernel): FP32 pipe ops per site, 12 (8d + 2)
+    #    + 2 per double-float residual pass, 2d + 3 per inner SOR sweep,
+    #    5d + 2d + 2 (weights, 1/D) + 58 (double-float rotation) per Newton
+    #    step, 33 to promote, 8d + 11 per fallback FP32 update; its FP64 ops
+    #    (8d + 14 per site of the final pass) beside it;
+    #  * first-region test (fp_test_kernel, FP64 Lanczos): per step and site
+    #    2d + 1 FMAs for M v, and 6 more for the recurrence, alpha, mean, norm
+    #    and the next vector: (2d + 7) FP64 ops.
+    # A packed f32x2 instruction does two lane operations, so the FP32 peak is
+    # the larger of the scalar and packed FMA probes.
+    fp32_peak = max(peaks["ffma"], peaks["ffma2"])
+    fp64_peak = peaks["dfma"]
     fp32_per_update = 8 * d + 11 + 3 / ce
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    fp64_peak = FP64_NOMINAL_TFLOPS / 2.0                        # DFMA per second, 1e12
-    # DRAM bytes per start from the ncu capture of the small case (65536 starts),
-    # scaled by starts (the traffic grows in proportion): see profiles/
-    traffic_per_start = {"polish_fp64": TRAFFIC_POLISH_PER_START, "relax_fp32": TRAFFIC_RELAX_PER_START}
-    n_launch_starts = args.starts
-    if dom == "relax_fp32":
-        achieved = rs["site_updates_fp32"] * fp32_per_update / (stage_ms[dom] / 1e3) / 1e12
-        roof = {"kernel": "relax32_sheet_kernel<8,1>", "bound": "alu", "achieved": achieved,
-                "peak": fp32_peak, "unit": "TOP/s (FP32 pipe ops)", "frac": achieved / fp32_peak}
-    elif dom == "polish_fp64":
-        # algorithmic FP32 pipe ops per site: 12 (8d + 2) + 2 per double-float
-        # residual pass, 2d + 3 per inner SOR sweep, 5d + 2d + 2 (weights, 1/D)
-        # + 58 (double-float rotation) per Newton step, 33 to promote, 8d + 11
-        # per fallback FP32 relaxation update; FP64 ops (8d + 14 per site of the
-        # final pass, 8d + 20 per fallback FP64 update) are reported beside it
-        fp32_ops = (rs["df_residual_passes"] * V * (12 * (8 * d + 2) + 2)
-                    + rs["newton_inner_sweeps"] * V * (2 * d + 3)
-                    + rs["newton_steps"] * V * (7 * d + 2 + 58)
-                    + rs["n_starts"] * V * 33
-                    + (rs["site_updates_fp32"] - rs_relax_updates) * (8 * d + 11))
-        fp64_ops = rs["fp64_residual_passes"] * V * (8 * d + 14) + rs["site_updates_fp64"] * (8 * d + 20)
-        # the line polish's own launch; the counters also hold the few starts
-        # polish_kernel reran from the redo list (about 1e-4 of the work)
-        sec = stage_ms[dom] / 1e3
-        achieved = fp32_ops / sec / 1e12
-        roof = {"kernel": "polish_pairs_kernel<4,4,16>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                "unit": "TOP/s (FP32 pipe ops)", "frac": achieved / fp32_peak,
-                "fp64": {"achieved": fp64_ops / sec / 1e12, "peak": fp64_peak,
-                         "unit": "T FP64 ops/s (DFMA counted once)",
-                         "frac": fp64_ops / sec / 1e12 / fp64_peak}}
-    else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None}
-    tb = traffic_per_start.get(dom)
-    roof["traffic"] = None if tb is None else tb * n_launch_starts
-    roof["traffic_unit"] = "bytes per launch (DRAM read + write)"
-    roof["peak_source"] = ("derived from unit counts and the 2032 MHz max SM clock: FP32 148 x 128 lanes; "
-                           "FP64 nominal 1.25 TFLOP/s (MEASURED_PEAKS.json has no FP32/FP64 figure)")
+    sec = {k: v / 1e3 for k, v in stage_ms.items()}
+    kernels = {}
+    a_relax = rs["sweeps_fp32"] * V * fp32_per_update / sec["relax_fp32"] / 1e12
+    kernels["relax_fp32"] = {"kernel": "relax32_sheet_kernel<8,1>", "bound": "alu", "achieved": a_relax,
+                             "peak": fp32_peak, "unit": "T FP32 lane ops/s", "frac": a_relax / fp32_peak,
+                             "ms": stage_ms["relax_fp32"], "traffic": TRAFFIC_RELAX_PER_START * args.starts}
+    fp32_ops = (rs["df_residual_passes"] * V * (12 * (8 * d + 2) + 2)
+                + rs["newton_inner_sweeps"] * V * (2 * d + 3)
+                + rs["newton_steps"] * V * (7 * d + 2 + 58)
+                + rs["n_starts"] * V * 33
+                + (rs["site_updates_fp32"] - rs_relax_updates) * (8 * d + 11))
+    fp64_pol = rs["fp64_residual_passes"] * V * (8 * d + 14) + rs["site_updates_fp64"] * (8 * d + 20)
+    a_pol = fp32_ops / (sec["polish_fp64"] + sec["polish_redo"]) / 1e12
+    kernels["polish"] = {"kernel": "polish_pairs_kernel<4,4,16> + polish_kernel<4,true> (redo)", "bound": "alu",
+                         "achieved": a_pol, "peak": fp32_peak, "unit": "T FP32 lane ops/s", "frac": a_pol / fp32_peak,
+                         "fp64_frac": fp64_pol / (sec["polish_fp64"] + sec["polish_redo"]) / 1e12 / fp64_peak,
+                         "ms": stage_ms["polish_fp64"] + stage_ms["polish_redo"],
+                         "traffic": TRAFFIC_POLISH_PER_START * args.starts}
+    a_fp = rs["lanczos_steps"] * V * (2 * d + 7) / sec["fp_test"] / 1e12
+    kernels["fp_test"] = {"kernel": "fp_test_kernel<4> (FP64 Lanczos)", "bound": "alu", "achieved": a_fp,
+                          "peak": fp64_peak, "unit": "T FP64 lane ops/s", "frac": a_fp / fp64_peak,
+                          "ms": stage_ms["fp_test"], "lanczos_steps_per_copy": rs["lanczos_steps"] / max(1, rs["fp_tests"]),
+                          "traffic": TRAFFIC_FPTEST_PER_COPY * rs["fp_tests"] if TRAFFIC_FPTEST_PER_COPY else None}
+    # the dominant kernel of the isolated pass; polish_redo is a latency tail
+    # of a few hundred starts that other orbits' kernels fill in a batch
+    dom = max(("relax_fp32", "polish", "fp_test"), key=lambda k_: kernels[k_]["ms"])
+    roof = dict(kernels[dom])
+    roof["traffic_unit"] = "bytes per launch (DRAM read + write, ncu, scaled from the profiled case)"
+    roof["peak_source"] = "measured on this GPU by gc_peak_probe (FFMA/FFMA2/DFMA), bench.py's peaks key"
     roof["stage_ms_isolated"] = stage_ms
     roof["polish_redo_starts"] = rs["polish_redo_starts"]
-    roof["launch_starts"] = n_launch_starts
+    roof["launch_starts"] = args.starts
+    roof["kernels"] = kernels
 
     uneven = uneven_leg(gb, torch, args.check_every) if args.uneven else None
     large = large_lattice_leg(gb, torch) if args.large else None
@@ -659,7 +700,7 @@ def run_ours(args):
         "config": {"workload": "4d_L4_vonmises_x8", "lattice": "4^4", "orbits": 8,
                    "starts_per_orbit": args.starts, "omega": 1.7, "eps32": 1e-10, "eps": 1e-24,
                    "check_every": ce, "precision": "fp32 sweeps + fp64 polish",
-                   "fp_test": "lanczos fp32 screen + fp64", "parallelism": f"weak x{world}", "launch": "one CUDA graph per step (8 orbits, 16 streams)",
+                   "fp_test": "FP64 Lanczos for every distinct copy (GC_FP_LANCZOS)", "parallelism": f"weak x{world}", "launch": "one CUDA graph per step (8 orbits, 16 streams)",
                    "timed": "device events around each step's batch launch; orbit creation outside",
                    "tuning": tuning,
                    "l2": "working set > L2 (1 GiB staging per batch + copy pool)"},
@@ -671,6 +712,8 @@ def run_ours(args):
         "large_lattice": large,
         "serving": serving,
         "roofline": roof,
+        "peaks": peaks,
+        "fp32_screen": screen_leg,
         "cpu_baseline": cpu,
         "cpu_baseline_configs": cpu_configs,
         "e2e": e2e,

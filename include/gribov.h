@@ -259,6 +259,22 @@ int gc_destroy_orbit(gc_orbit o);
 int gc_fp_test_static(int dim, int L, const double* d_links, const double* d_configs, uint64_t n,
                       double fp_tau, double* d_lambda2, int* d_region, void* stream);
 
+/* Throughput probe of one arithmetic unit on the current device (the paper
+ * has no counterpart: it measures the denominators of the kernels' rooflines
+ * on the GPU at hand).  kind: GC_PEAK_FFMA (FP32 FMA), GC_PEAK_FFMA2 (packed
+ * f32x2 FMA, counted as two), GC_PEAK_DFMA (FP64 FMA), GC_PEAK_RSQ (the
+ * special-function unit's approximate reciprocal square root).  Every thread
+ * of four 256-thread CTAs per SM runs eight independent chains; the best of
+ * three timed launches (after a warm-up) gives *ops_per_s, lane operations
+ * per second.  Synchronises `stream` (a cudaStream_t, NULL = default);
+ * allocates about 0.6 MB of scratch through the allocator hooks.
+ * GC_EINVAL for an unknown kind or a NULL ops_per_s. */
+#define GC_PEAK_FFMA 0
+#define GC_PEAK_FFMA2 1
+#define GC_PEAK_DFMA 2
+#define GC_PEAK_RSQ 3
+int gc_peak_probe(int kind, void* stream, double* ops_per_s);
+
 /* message of the last failing call on this thread ("" if none) */
 const char* gc_last_error(void);
 /* library version string */

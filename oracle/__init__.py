@@ -231,6 +231,15 @@ def f_norm(F, d, L):
     return np.asarray(F) / (d * L ** d)
 
 
+def n_distinct_f8(F, d, L) -> int:
+    """The paper's count of distinct minima (Section III, quantisation
+    paragraph): each minimum x = F/(dV) in [0, 1] is mapped to the integer
+    floor(x * 1e8) in [0, 1e8] (floor: the paper does not name the rounding),
+    and the distinct integers are counted."""
+    q = np.floor(f_norm(F, d, L) * 1e8).astype(np.int64)
+    return int(np.unique(q).size)
+
+
 # ----------------------------------------------------------------------------
 # Faddeev-Popov operator: Hessian of Eq. 3 in the gauge angles
 # ----------------------------------------------------------------------------
@@ -331,12 +340,20 @@ def dedup(d, L, theta, F, start_ids, converged, delta=1e-6):
     return rep_of, reps
 
 
+def lambda2_of_copy(args) -> float:
+    """lambda_2 of one canonical copy, args = (d, L, phi, theta)."""
+    d, L, phi, theta = args
+    return lambda2(d, L, fp_weights(d, L, phi, theta))
+
+
 def enumerate_copies(d, L, phi, seed, orbit_id, n_starts, omega=1.7, eps=1e-24,
                      check_every=1, max_sweeps=100_000, delta=1e-6, tau=1e-9,
-                     start0=0, nthreads=0, relaxed: Relaxed | None = None):
+                     start0=0, nthreads=0, relaxed: Relaxed | None = None, lam_map=map):
     """Whole pipeline on random starts start0 .. start0+n_starts-1.
 
     Returns (Relaxed, Copies) with copies sorted by (F, first_start).
+    lam_map maps lambda2_of_copy over the distinct copies (e.g. a process
+    pool's map for large tables; the values do not depend on it).
     """
     phi = _phi(phi, d, L)
     if relaxed is None:
@@ -352,17 +369,16 @@ def enumerate_copies(d, L, phi, seed, orbit_id, n_starts, omega=1.7, eps=1e-24,
     cth = np.array([theta[r] for r in reps]) if m else np.zeros((0, L ** d))
     cfirst = np.array([starts[r] for r in reps], dtype=np.int64)
     ccount = np.bincount(rep_of[rep_of >= 0], minlength=m).astype(np.int64)
-    lam = np.array([lambda2(d, L, fp_weights(d, L, phi, t)) for t in cth]) if m else np.zeros(0)
+    lam = np.array(list(lam_map(lambda2_of_copy, [(d, L, phi, t) for t in cth]))) if m else np.zeros(0)
     reg = np.array([region_flag(v, tau) for v in lam], dtype=np.int32)
     order = np.lexsort((cfirst, cF)) if m else np.zeros(0, np.int64)
     inv = np.empty(m, np.int64)
     inv[order] = np.arange(m)
     copy_of = np.full(len(rep_of), -1, np.int64)
     copy_of[rep_of >= 0] = inv[rep_of[rep_of >= 0]]
-    q = np.floor(f_norm(F[conv], d, L) * 1e8).astype(np.int64)
     if m == 0:
         lam = np.zeros(0)
         reg = np.zeros(0, np.int32)
     copies = Copies(cF[order], cth[order], cfirst[order], ccount[order], lam[order],
-                    reg[order], copy_of, int(np.unique(q).size))
+                    reg[order], copy_of, n_distinct_f8(F[conv], d, L))
     return relaxed, copies

@@ -46,6 +46,11 @@ GC_REGION_OUT = 0
 GC_REGION_IN = 1
 GC_REGION_MARGINAL = 2
 
+GC_PEAK_FFMA = 0
+GC_PEAK_FFMA2 = 1
+GC_PEAK_DFMA = 2
+GC_PEAK_RSQ = 3
+
 
 class GribovError(RuntimeError):
     def __init__(self, code, msg):
@@ -93,7 +98,7 @@ EXPORTED = ("gc_set_allocator", "gc_options_default", "gc_create_orbit", "gc_enu
             "gc_fetch_copies", "gc_fetch_minima_f8", "gc_fetch_starts", "gc_orbit_stats", "gc_destroy_orbit",
             "gc_last_error", "gc_version", "gc_fp_test_static", "gc_enumerate_batch",
             "gc_autotune", "gc_autotune_ex", "gc_server_create", "gc_server_submit",
-            "gc_server_wait", "gc_server_destroy")
+            "gc_server_wait", "gc_server_destroy", "gc_peak_probe")
 
 _lib = None
 _lock = threading.Lock()
@@ -153,6 +158,7 @@ def load(build_if_stale: bool = True):
         L.gc_server_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double, p_i,
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p)]
         L.gc_server_destroy.argtypes = [ctypes.c_void_p]
+        L.gc_peak_probe.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
         L.gc_last_error.restype = ctypes.c_char_p
         L.gc_version.restype = ctypes.c_char_p
         _lib = L
@@ -374,3 +380,12 @@ def gc_server_wait(server, ticket: int, timeout_s: float = -1.0, keep_orbit: boo
 
 def gc_server_destroy(server):
     _check(load().gc_server_destroy(server))
+
+
+def gc_peak_probe(kind: int, stream=None) -> float:
+    """Measured throughput of one arithmetic unit (GC_PEAK_*), lane operations per second."""
+    if stream is not None and not isinstance(stream, int):
+        stream = int(stream.cuda_stream)
+    v = ctypes.c_double()
+    _check(load().gc_peak_probe(kind, stream, ctypes.byref(v)))
+    return v.value

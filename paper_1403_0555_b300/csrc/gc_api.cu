@@ -2300,3 +2300,50 @@ extern "C" int gc_server_destroy(gc_server s) {
   delete s;
   return GC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Throughput probes of the arithmetic units (roofline denominators)
+// ---------------------------------------------------------------------------
+#include "gc_peaks.cuh"
+
+extern "C" int gc_peak_probe(int kind, void* stream, double* ops_per_s) {
+  if (!ops_per_s) return fail(GC_EINVAL, "gc_peak_probe: NULL ops_per_s");
+  if (kind < GC_PEAK_FFMA || kind > GC_PEAK_RSQ) return fail(GC_EINVAL, "gc_peak_probe: unknown kind %d", kind);
+  cudaStream_t s = (cudaStream_t)stream;
+  // four 256-thread CTAs per SM; iterations sized for ~10-40 ms per launch
+  const int threads = 256, grid = 4 * sm_count();
+  const int iters = kind == GC_PEAK_DFMA ? 1 << 12 : (kind == GC_PEAK_RSQ ? 1 << 15 : 1 << 17);
+  const double per_thread = 8.0 * iters * (kind == GC_PEAK_FFMA2 ? 2.0 : 1.0);
+  Buf out;
+  if (!out.ensure((size_t)grid * threads * sizeof(float), s)) return fail(GC_ENOMEM, "gc_peak_probe: no scratch");
+  cudaEvent_t e0, e1;
+  GC_CUDA(cudaEventCreate(&e0));
+  GC_CUDA(cudaEventCreate(&e1));
+  const float m = 1.0f - 0x1.0p-20f, c = 0x1.0p-21f;
+  auto launch = [&]() {
+    switch (kind) {
+      case GC_PEAK_FFMA: gc::peak_probe_kernel<gc::kPeakFFMA><<<grid, threads, 0, s>>>(out.as<float>(), iters, m, c); break;
+      case GC_PEAK_FFMA2: gc::peak_probe_kernel<gc::kPeakFFMA2><<<grid, threads, 0, s>>>(out.as<float>(), iters, m, c); break;
+      case GC_PEAK_DFMA: gc::peak_probe_kernel<gc::kPeakDFMA><<<grid, threads, 0, s>>>(out.as<float>(), iters, m, c); break;
+      default: gc::peak_probe_kernel<gc::kPeakRSQ><<<grid, threads, 0, s>>>(out.as<float>(), iters, m, c); break;
+    }
+  };
+  float best = 0.f;
+  int rc = GC_OK;
+  for (int rep = 0; rep < 4 && rc == GC_OK; ++rep) {   // the first launch is a warm-up
+    if (cudaEventRecord(e0, s) != cudaSuccess) rc = fail(GC_ECUDA, "gc_peak_probe: event record");
+    launch();
+    if (rc == GC_OK && cudaGetLastError() != cudaSuccess) rc = fail(GC_ECUDA, "gc_peak_probe: launch failed");
+    if (rc == GC_OK && cudaEventRecord(e1, s) != cudaSuccess) rc = fail(GC_ECUDA, "gc_peak_probe: event record");
+    if (rc == GC_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(GC_ECUDA, "gc_peak_probe: kernel failed");
+    float ms = 0.f;
+    if (rc == GC_OK) cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms > 0.f && (best == 0.f || ms < best)) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  out.release(s);
+  if (rc != GC_OK) return rc;
+  *ops_per_s = (double)grid * threads * per_thread / (best * 1e-3);
+  return GC_OK;
+}

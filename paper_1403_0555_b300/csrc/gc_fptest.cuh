@@ -54,8 +54,9 @@ template <typename R>
 struct FpSmem {
   size_t nbr, warp0, per_warp, total;
   __host__ __device__ static size_t align16s(size_t b) { return (b + 15) & ~size_t(15); }
+  // FP64 adds a fourth vector: the diagonal of M for lanczos64_min
   __host__ __device__ static size_t warp_bytes(int V, int d, int kmax) {
-    return align16s((size_t)V * d * sizeof(R)) + 3 * align16s((size_t)V * sizeof(R)) +
+    return align16s((size_t)V * d * sizeof(R)) + (sizeof(R) == 8 ? 4 : 3) * align16s((size_t)V * sizeof(R)) +
            3 * align16s((size_t)(kmax + 2) * sizeof(R));
   }
   __host__ __device__ FpSmem(int V, int d, int kmax, int warps) {
@@ -232,6 +233,234 @@ __device__ R lanczos_min(const R* w, R* vprev, R* vcur, R* z, R* alpha, R* beta,
   return theta;
 }
 
+// ---------------------------------------------------------------------------
+// FP64 Lanczos with the FP64 pipe kept for the recurrence itself.  On this
+// part an FP64 instruction costs the SM about 64 FP32 ones, so:
+//   * M v = D v - sum_mu [w_{x,mu} v_{x+mu} + w_{x-mu,mu} v_{x-mu}], with the
+//     diagonal D and the negated weights stored once per copy: 2d + 1 FMAs per
+//     site, and the whole step (recurrence, alpha, mean, norm, next vector)
+//     in 15 FP64 operations per site;
+//   * the mean and the squared norm of the new vector share one warp
+//     reduction that adds each level once;
+//   * convergence is first followed in FP32: the tridiagonal, rounded to FP32,
+//     by Sturm multisection every 8 steps, until those Ritz values stall;
+//   * from then on every check takes lambda_min of the FP64 tridiagonal from
+//     a bracket around the FP32 value by tri_min64 (division-free Sturm
+//     counts, Newton steps from below), and the run stops when two FP64
+//     values 8 steps apart agree to tol64.
+// The result is the smallest Ritz value of the FP64 Lanczos tridiagonal.
+// ---------------------------------------------------------------------------
+
+struct SturmPoint { int cnt; double p, dp; };
+
+__device__ __forceinline__ int dexp_of(double v) {
+  return (int)(((unsigned)__double2hiint(v) >> 20) & 0x7ffu) - 1023;
+}
+__device__ __forceinline__ unsigned dsign(double v) { return (unsigned)__double2hiint(v) >> 31; }
+__device__ __forceinline__ bool dzero(double v) {
+  return ((((unsigned)__double2hiint(v)) & 0x7fffffffu) | (unsigned)__double2loint(v)) == 0u;
+}
+
+// Sturm count and Newton quotient at x for the k x k tridiagonal (alpha,
+// beta2 = squared off-diagonal, beta2[i] couples rows i-1 and i), without
+// divisions: the leading minors' characteristic polynomials p_0 = 1,
+// p_1 = alpha_0 - x, p_{i+1} = (alpha_i - x) p_i - beta2_i p_{i-1}, and their
+// derivatives.  The number of sign changes along p_0 .. p_k is the number of
+// eigenvalues below x (a p_i that is exactly 0 takes the sign opposite to
+// p_{i-1}, the LDL^T convention of sturm_count).  Every 16 steps the pair is
+// rescaled by a power of two once it leaves [2^-400, 2^400]; signs and p/p'
+// do not change.
+__device__ inline SturmPoint sturm_point64(const double* alpha, const double* beta2, int k, double x) {
+  double pm = 1.0, dpm = 0.0;
+  double p = alpha[0] - x, dp = -1.0;
+  unsigned sp = 0u;
+  unsigned s = dzero(p) ? 1u : dsign(p);
+  int cnt = s != sp;
+  sp = s;
+  for (int i = 1; i < k; ++i) {
+    const double e = alpha[i] - x;
+    const double b2 = beta2[i];
+    const double pn = fma(e, p, -b2 * pm);
+    const double dpn = fma(e, dp, fma(-b2, dpm, -p));
+    pm = p; dpm = dp; p = pn; dp = dpn;
+    s = dzero(p) ? (sp ^ 1u) : dsign(p);
+    cnt += s != sp;
+    sp = s;
+    if ((i & 15) == 0) {
+      const int ea = dexp_of(p), eb = dexp_of(pm);
+      const int ex = ea > eb ? ea : eb;
+      if (ex > 400 || ex < -400) {
+        const double sc = __hiloint2double((1023 - ex) << 20, 0);
+        p *= sc; pm *= sc; dp *= sc; dpm *= sc;
+      }
+    }
+  }
+  SturmPoint r;
+  r.cnt = cnt; r.p = p; r.dp = dp;
+  return r;
+}
+
+// lambda_min of the tridiagonal to FP64 accuracy from a bracket
+// lo < lambda_min <= hi; *ok = false when the counts at the bracket's ends
+// contradict it.  Each round spreads the warp's 32 points over [lo, hi] --
+// evenly in the first round, geometrically towards lo (ratio 0.35) in the
+// later ones -- keeps the last point below lambda_min (count 0) and takes a
+// Newton step from it.  Below the smallest root of a polynomial with real
+// roots, Newton's iterates increase and stay below the root, so the step
+// gives the new lower end; the next point up gives the upper end.
+__device__ inline double tri_min64(const double* alpha, const double* beta2, int k, double lo, double hi,
+                                   int lane, bool* ok) {
+  *ok = true;
+  for (int round = 0; round < 8; ++round) {
+    double x;
+    if (lane == 0) x = lo;
+    else if (lane == 31) x = hi;
+    else if (round == 0) x = fma(hi - lo, (double)lane * (1.0 / 31.0), lo);
+    else x = fma(hi - lo, f2d_bits(exp2f((float)(31 - lane) * -1.51457317f)), lo);
+    const SturmPoint r = sturm_point64(alpha, beta2, k, x);
+    const unsigned m = __ballot_sync(0xffffffffu, r.cnt == 0);
+    if (!(m & 1u)) {            // lambda_min <= lo
+      if (round == 0) *ok = false;
+      return lo;                // later rounds: the Newton iterate met lambda_min to rounding
+    }
+    const int f = __ffs(~m);    // first point at or above lambda_min (1-based), 0: none
+    if (f == 0) { *ok = false; return hi; }
+    const int ls = f - 2;
+    const double xl = __shfl_sync(0xffffffffu, x, ls);
+    const double pl = __shfl_sync(0xffffffffu, r.p, ls);
+    const double dl = __shfl_sync(0xffffffffu, r.dp, ls);
+    const double xh = __shfl_sync(0xffffffffu, x, ls + 1);
+    double xn = xl - pl / dl;
+    if (!(xn >= xl && xn < xh)) xn = xl;
+    lo = xn;
+    hi = xh;
+    if (round >= 1 && hi - lo <= 1e-13 * fmax(fabs(lo), 1e-3)) break;
+  }
+  return lo;
+}
+
+// sums of a and b over the warp: the first level exchanges the half each lane
+// does not keep, so every level adds once
+__device__ __forceinline__ void warp_sum2(double& a, double& b, int lane) {
+  const bool up = (lane & 16) != 0;
+  double keep = up ? b : a;
+  const double send = up ? a : b;
+  keep += __shfl_xor_sync(0xffffffffu, send, 16);
+  for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+  a = __shfl_sync(0xffffffffu, keep, 0);
+  b = __shfl_sync(0xffffffffu, keep, 16);
+}
+
+// nw: negated weights [mu][x]; Dg: the diagonal of M; va, vb, vc: three
+// vectors; a64/b64: the tridiagonal; a32/b32: its FP32 image.
+template <int DD>
+__device__ double lanczos64_min(const double* nw, const double* Dg, double* va, double* vb, double* vc,
+                                double* a64, double* b64, float* a32, float* b32, int kmax, double tol32,
+                                double tol64, const uint4* nbr, int V, int lane, uint64_t seed,
+                                unsigned long long entry, int* steps) {
+  double* vcur = va;
+  double* vprev = vb;
+  double* z = vc;
+  // random start vector orthogonal to the constant mode (as in lanczos_min)
+  double s = 0.0;
+  for (int x = lane; x < V; x += 32) {
+    const U64x4 r = philox4x64_10(entry, (uint64_t)x, 0, 1, seed, 0x4C414E43ULL);
+    const double v = (double)(unsigned)(r.v[0] >> 40) * 0x1.0p-24 - 0.5;
+    vcur[x] = v;
+    vprev[x] = 0.0;
+    s += v;
+  }
+  s = warp_sum(s) / (double)V;
+  double nn = 0.0;
+  for (int x = lane; x < V; x += 32) { const double v = vcur[x] - s; vcur[x] = v; nn = fma(v, v, nn); }
+  const double inv0 = rsqrt(warp_sum(nn));
+  for (int x = lane; x < V; x += 32) vcur[x] *= inv0;
+  __syncwarp();
+  const double invV = 1.0 / (double)V;
+  const float bound = (float)(4 * DD + 1);
+  float t32 = bound, t32_prev = bound, t32_pp = bound;   // bound = no estimate yet
+  double t64 = (double)bound;
+  bool fine = false;                                      // FP64 checks have started
+  double b = 0.0;
+  int j = 0;
+  for (; j < kmax; ++j) {
+    double a = 0.0;
+    const double mb = -b;
+    for (int x = lane; x < V; x += 32) {
+      const uint4 nb = nbr[x];
+      const double vx = vcur[x];
+      double y = fma(Dg[x], vx, mb * vprev[x]);
+#pragma unroll
+      for (int mu = 0; mu < DD; ++mu) {
+        const unsigned wd = nb_word(nb, mu);
+        const int xp = wd & 0xffffu, xm = wd >> 16;
+        y = fma(nw[mu * V + x], vcur[xp], y);
+        y = fma(nw[mu * V + xm], vcur[xm], y);
+      }
+      z[x] = y;
+      a = fma(y, vx, a);
+    }
+    a = warp_sum(a);
+    double m = 0.0, zz = 0.0;
+    for (int x = lane; x < V; x += 32) {
+      const double v = fma(-a, vcur[x], z[x]);
+      z[x] = v;
+      m += v;
+      zz = fma(v, v, zz);
+    }
+    warp_sum2(m, zz, lane);
+    m *= invV;
+    const double bn2 = fmax(fma(-(double)V * m, m, zz), 0.0);   // |z - m|^2
+    if (lane == 0) {
+      a64[j] = a;
+      b64[j + 1] = bn2;
+      a32[j] = d2f_bits(a);
+      b32[j + 1] = d2f_bits(bn2);
+    }
+    __syncwarp();
+    const bool last = (j + 1 == kmax) || bn2 < 1e-24;
+    if (last || ((j + 1) % 8 == 0 && j + 1 >= 16)) {
+      // FP32 view: bracket from Cauchy interlacing, as in lanczos_min
+      float lo = -bound, hi = bound;
+      if (t32_prev < bound) {
+        const float slack = 2.f * tri_rel<float>() * fmaxf(fabsf(t32_prev), 1.f);
+        hi = t32_prev + slack;
+        if (t32_pp < bound) {
+          const float l = t32_prev - 4.f * fmaxf(t32_pp - t32_prev, slack);
+          if (sturm_count<float>(a32, b32, j + 1, l) == 0) lo = l;
+        }
+      }
+      t32 = tri_min<float>(a32, b32, j + 1, lo, hi, lane);
+      const bool stall32 = t32_prev < bound && fabsf(t32 - t32_prev) <= (float)tol32 * fmaxf(fabsf(t32), 1e-3f);
+      t32_pp = t32_prev;
+      t32_prev = t32;
+      if (fine || stall32 || last) {
+        // the FP32 value is within rounding (~2e-6 ||T||) of the FP64 one
+        const double c = f2d_bits(t32);
+        const double del = 2e-5 * fmax(1.0, fabs(c));
+        bool ok;
+        double t = tri_min64(a64, b64, j + 1, c - del, c + del, lane, &ok);
+        if (!ok) t = tri_min64(a64, b64, j + 1, -(double)bound, (double)bound, lane, &ok);
+        const bool stall64 = fine && fabs(t - t64) <= tol64 * fmax(fabs(t), 1e-3);
+        t64 = t;
+        fine = true;
+        if (last || stall64) { ++j; break; }
+      }
+    }
+    const double ib = rsqrt(bn2);
+    const double mib = -m * ib;
+    for (int x = lane; x < V; x += 32) z[x] = fma(z[x], ib, mib);
+    b = bn2 * ib;
+    double* t = vprev;
+    vprev = vcur;
+    vcur = z;
+    z = t;
+    __syncwarp();
+  }
+  *steps += j;
+  return t64;
+}
+
 __device__ inline void build_site_neighbours(const Geom& G, uint4* nbr) {
   for (int x = threadIdx.x; x < G.V; x += blockDim.x) {
     unsigned w[4] = {0u, 0u, 0u, 0u};
@@ -321,7 +550,7 @@ __global__ void __launch_bounds__(256) fp_screen_kernel(const FpArgs a) {
 // FP64 test: Lanczos (kFpLanczos) or full reorthogonalisation to dimension
 // V - 1 (kFpDense); kFpNone marks every copy untested.
 template <int DD>
-__global__ void __launch_bounds__(128) fp_test_kernel(const FpArgs a) {
+__global__ void __launch_bounds__(128, 8) fp_test_kernel(const FpArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Geom G = a.geom;
   const int V = G.V;
@@ -337,7 +566,7 @@ __global__ void __launch_bounds__(128) fp_test_kernel(const FpArgs a) {
   double* w64 = reinterpret_cast<double*>(base);
   unsigned char* vb = base + FpSmem<double>::align16s((size_t)V * DD * 8);
   const size_t vstride = FpSmem<double>::align16s((size_t)V * 8);
-  double* alpha = reinterpret_cast<double*>(vb + 3 * vstride);
+  double* alpha = reinterpret_cast<double*>(vb + 4 * vstride);
   double* beta = alpha + FpSmem<double>::align16s((size_t)(kmax + 2) * 8) / 8;
   double* h = beta + FpSmem<double>::align16s((size_t)(kmax + 2) * 8) / 8;
 
@@ -354,6 +583,8 @@ __global__ void __launch_bounds__(128) fp_test_kernel(const FpArgs a) {
     if (a.mode == kFpNone) {
       lam = __longlong_as_double(0x7ff8000000000000LL);
     } else {
+      const bool dense = a.mode == kFpDense;
+      const double sgn = dense ? 1.0 : -1.0;   // Lanczos mode keeps the weights negated
       for (int x = lane; x < V; x += 32) {
         const double2 gx = __ldcg(g + x);
         const uint4 nb = nbr[x];
@@ -362,7 +593,7 @@ __global__ void __launch_bounds__(128) fp_test_kernel(const FpArgs a) {
           const double2 hx = __ldcg(g + (nb_word(nb, mu) & 0xffffu));
           const double2 uu = a.links64[x * DD + mu];
           const double tx = fma(uu.x, hx.x, -uu.y * hx.y), ty = fma(uu.x, hx.y, uu.y * hx.x);
-          w64[mu * V + x] = fma(gx.x, tx, gx.y * ty);
+          w64[mu * V + x] = sgn * fma(gx.x, tx, gx.y * ty);
         }
       }
       __syncwarp();
@@ -370,11 +601,24 @@ __global__ void __launch_bounds__(128) fp_test_kernel(const FpArgs a) {
       double* v0 = reinterpret_cast<double*>(vb);
       double* v1 = reinterpret_cast<double*>(vb + vstride);
       double* v2 = reinterpret_cast<double*>(vb + 2 * vstride);
-      lam = a.mode == kFpDense
-                ? lanczos_min<double, true, DD>(w64, v0, v1, v2, alpha, beta, h, Q, k, 0.0, nbr, V,
-                                                lane, a.seed, key, &steps)
-                : lanczos_min<double, false, DD>(w64, v0, v1, v2, alpha, beta, h, nullptr, k,
-                                                 a.tol64, nbr, V, lane, a.seed, key, &steps);
+      double* v3 = reinterpret_cast<double*>(vb + 3 * vstride);
+      if (dense) {
+        lam = lanczos_min<double, true, DD>(w64, v0, v1, v2, alpha, beta, h, Q, k, 0.0, nbr, V, lane,
+                                            a.seed, key, &steps);
+      } else {
+        // the diagonal of M: D_x = sum_mu (w_{x,mu} + w_{x-mu,mu})
+        for (int x = lane; x < V; x += 32) {
+          const uint4 nb = nbr[x];
+          double dsum = 0.0;
+#pragma unroll
+          for (int mu = 0; mu < DD; ++mu) dsum -= w64[mu * V + x] + w64[mu * V + (nb_word(nb, mu) >> 16)];
+          v3[x] = dsum;
+        }
+        __syncwarp();
+        lam = lanczos64_min<DD>(w64, v3, v0, v1, v2, alpha, beta, reinterpret_cast<float*>(h),
+                                reinterpret_cast<float*>(h) + (kmax + 2), k, a.tol32, a.tol64, nbr, V,
+                                lane, a.seed, key, &steps);
+      }
       ++c64;
     }
     if (lane == 0) {

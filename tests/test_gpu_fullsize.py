@@ -5,8 +5,8 @@ any size.
 * 4D 4^4, eight von Mises orbits, 2^20 starts each, mixed precision, one
   gc_enumerate_batch call captured as one CUDA graph on a side stream with the
   autotuner on (the bench step).
-* 3D 6^3, 10^5 starts of a von Mises orbit and of the gauge-hidden cold orbit,
-  plain FP64 (bit-exact to the oracle start by start).
+* the uneven batch (13 lattice sizes x 2 orbits) in one captured graph.
+(The 3D 6^3 workload is compared in full in test_gpu_config2.py.)
 """
 import numpy as np
 import pytest
@@ -44,7 +44,7 @@ def test_bench_shape_4d_l4_x8_sampled():
     n = 1 << 20
     w = oi.workload_4d_4to4(n)
     side = torch.cuda.Stream()
-    opt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=4, fp_mode=gb.GC_FP_AUTO,
+    opt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=4, fp_mode=gb.GC_FP_LANCZOS,
                                 stream=side, use_graph=1, autotune=1)
     with torch.cuda.stream(side):
         hs = [gb.gc_create_orbit(d, L, o.phi, o.orbit_id, n) for o in w.orbits]
@@ -81,47 +81,11 @@ def test_bench_shape_4d_l4_x8_sampled():
             assert sum(same) >= len(pick) - 1
             for p in pick:
                 lam = oracle.lambda2(d, L, oracle.fp_weights(d, L, o.phi, c["theta"][p]))
-                assert abs(c["lambda2"][p] - lam) <= 1e-3 * max(abs(lam), 1e-2), (p, c["lambda2"][p], lam)
+                assert abs(c["lambda2"][p] - lam) <= 1e-9 * max(abs(lam), 1e-3), (p, c["lambda2"][p], lam)
                 assert c["region"][p] == oracle.region_flag(lam, 1e-9)
     finally:
         for h in hs:
             gb.gc_destroy_orbit(h)
-
-
-@pytest.mark.parametrize("which", [0, 4])
-def test_config2_3d_l6_plain_full_size_sampled(which):
-    import paper_1403_0555_b300 as gb
-    w = oi.workload_3d_6cubed()
-    o = w.orbits[which]                        # von Mises seed 1, and the cold orbit
-    d, L, n = o.d, o.L, w.n_starts
-    V = L ** d
-    opt = gb.gc_options_default(precision=gb.GC_FP64, check_every=1, keep_per_start=1)
-    h = gb.gc_create_orbit(d, L, o.phi, o.orbit_id)
-    try:
-        gb.gc_enumerate_copies(h, n, w.omega, w.eps, opt)
-        st = gb.gc_orbit_stats(h)
-        s = gb.gc_fetch_starts(h, 0, n)
-        c = gb.gc_fetch_copies(h, V)
-    finally:
-        gb.gc_destroy_orbit(h)
-    assert st["n_starts"] == n
-    _table_invariants(c, st, V)
-    rng = np.random.default_rng(5 + which)
-    idx = np.sort(rng.choice(n, 48, replace=False))
-    rel = oracle.relax_indices(d, L, o.phi, 1, o.orbit_id, idx, w.omega, w.eps)
-    # the plain path follows the oracle's trajectory exactly: status, sweeps, F
-    assert np.array_equal(s["status"][idx], rel.status.astype(np.int32))
-    assert np.array_equal(s["sweeps"][idx], rel.sweeps)
-    conv = rel.status == oracle.CONVERGED
-    _, th = oracle.canonical(rel.g)
-    F_or = oracle.functional(d, L, o.phi, th)
-    assert np.all(np.abs(s["F"][idx][conv] - F_or[conv]) <= 1e-12 * np.maximum(1.0, F_or[conv]))
-    # each sampled start's copy holds its configuration (within the dedup distance;
-    # the copy's angles are those of its lowest start)
-    for k in np.flatnonzero(conv):
-        ci = s["copy_idx"][idx[k]]
-        assert ci >= 0 and c["first_start"][ci] <= idx[k]
-        assert np.max(np.abs(wrap(c["theta"][ci] - th[k]))) <= 1e-6
 
 
 def test_uneven_batch_full_size_sampled():

@@ -5,9 +5,9 @@ The mixed path is not bitwise equal to the plain one (its FP32 trajectory
 rounds differently), so it is held to: (a) every converged copy satisfies the
 FP64 stopping rule when re-checked by the oracle's own divergence; (b) F of each
 copy matches Eq. 3 evaluated by the oracle; (c) start by start it reaches the
-same canonical copy as the plain path on at least 99% of starts (the design
-target is 99.9%; the measured rate is printed); (d) its distinct-copy set
-restricted to copies found by both paths is identical.
+same canonical copy as the plain path on at least 99.9% of starts (the measured
+rate is printed); (d) its distinct-copy set restricted to copies found by both
+paths is identical.
 """
 import numpy as np
 import pytest
@@ -46,7 +46,7 @@ def test_mixed_agrees_with_plain(d, L, kappa, n, variant):
     same = np.max(np.abs(wrap(th_p - th_m)), axis=1) < 1e-6
     print(f"\nmixed vs plain agreement {d}D L={L} variant {variant}: {same.mean():.5f} of {n} starts; "
           f"newton steps/start {mst['newton_steps'] / n:.2f}, fallbacks {mst['polish_fallbacks']}")
-    assert same.mean() >= 0.99
+    assert same.mean() >= 0.999
     # (d) copies found by both paths are the same configurations
     for i in np.flatnonzero(same)[:200]:
         assert abs(pc["F"][ps["copy_idx"][i]] - mc["F"][ms["copy_idx"][i]]) < 1e-10
@@ -65,7 +65,7 @@ def test_mixed_sampled_against_oracle():
     _, th = oracle.canonical(rel.g)
     th_m = mc["theta"][ms["copy_idx"][idx]]
     same = np.max(np.abs(wrap(th - th_m)), axis=1) < 1e-6
-    assert same.mean() >= 0.9
+    assert same.sum() >= len(idx) - 1       # 99.9 % agreement: a miss in 48 is rare
     F_or = oracle.functional(d, L, o.phi, th)
     assert np.all(np.abs(F_or[same] - ms["F"][idx][same]) < 1e-10 * np.maximum(1, F_or[same]))
 
@@ -87,3 +87,24 @@ def test_hard_start_through_the_cg_redo_matches_oracle():
     assert np.max(np.abs(wrap(th[0] - th_m))) < 1e-6
     lam = oracle.lambda2(d, L, oracle.fp_weights(d, L, phi, th[0]))
     assert 0 < lam < 1e-3
+
+
+def test_mixed_agrees_with_plain_on_the_bench_orbits():
+    """The bench's eight 4^4 orbits (kappa 0.5 .. 2.0), 2^16 starts each: the
+    mixed path (FP32 sweeps to 1e-10, FP64 polish) reaches the plain FP64
+    path's canonical copy on at least 99.9 % of the starts of every orbit."""
+    d, L, n = 4, 4, 1 << 16
+    w = oi.workload_4d_4to4(n)
+    tot = agree = 0
+    for j, o in enumerate(w.orbits):
+        ps, pc, _ = run_gpu(d, L, o.phi, o.orbit_id, n, check_every=1, fp_mode=3)
+        ms, mc, _ = run_gpu(d, L, o.phi, o.orbit_id, n, check_every=4, fp_mode=3, precision=1)
+        assert (ps["status"] == 1).all() and (ms["status"] == 1).all()
+        th_p = pc["theta"][ps["copy_idx"]]
+        th_m = mc["theta"][ms["copy_idx"]]
+        same = np.max(np.abs(wrap(th_p - th_m)), axis=1) < 1e-6
+        print(f"\norbit {j}: mixed vs plain {same.mean():.6f} ({n - int(same.sum())} of {n} differ)")
+        assert same.mean() >= 0.999
+        tot += n
+        agree += int(same.sum())
+    print(f"all orbits: {agree / tot:.6f}")

@@ -164,6 +164,12 @@ def test_1d_closed_form(L, Phi):
         assert np.min(np.abs(pred_all - f)) < 1e-12
     for p in pred_robust:                # and contains every well-separated copy
         assert np.min(np.abs(found - p)) < 1e-12
+    # the paper's count (F/(dV) quantised at 1e-8) of the closed-form copies
+    # that were found equals the pipeline's count
+    x_found = np.array([1 - math.cos((Phi + 2 * math.pi * k) / L) for k in range(L)
+                        if math.cos((Phi + 2 * math.pi * k) / L) > 0
+                        and np.min(np.abs(found - L * (1 - math.cos((Phi + 2 * math.pi * k) / L)))) < 1e-12])
+    assert cp.n_distinct_F8 == len(np.unique(np.floor(x_found * 1e8)))
     # every copy has all gauge-fixed link angles equal
     ang = oracle.link_angles_gauged(1, L, phi, cp.theta)[..., 0]
     spread = np.abs(np.angle(np.exp(1j * (ang - ang[:, :1]))))
@@ -222,7 +228,9 @@ def _jacobi_eigs(A, sweeps=60):
     A = A.copy()
     n = A.shape[0]
     for _ in range(sweeps):
-        off = np.sqrt(np.sum(A ** 2) - np.sum(np.diag(A) ** 2))
+        # off-diagonal norm from the entries themselves (sum A^2 - sum diag^2
+        # cancels to rounding noise long before the rotations have converged)
+        off = np.sqrt(2.0 * np.sum(np.triu(A, 1) ** 2))
         if off < 1e-14:
             break
         for p in range(n - 1):
@@ -422,3 +430,28 @@ def test_tables_I_and_III_statistics(d, N, n_orbits, n_starts):
     assert abs(fmin.mean() - t3["avg_Fmin"]) < 3.5 * se3, (fmin.mean(), t3)
     se1 = t1["std"] * math.sqrt(1 / t1["orbits"] + 1 / n_orbits)
     assert abs(nmin.mean() - t1["avg_minima"]) < 3.5 * se1, (nmin.mean(), t1)
+
+
+def test_n_distinct_f8_quantisation():
+    """The paper's distinct-minima count: x = F/(dV) mapped to floor(x * 1e8)
+    (Section III).  The cases are built so that a wrong normalisation (by V
+    or by d alone), rounding instead of the floor, or a count of raw F values
+    each gives a different answer."""
+    d, L = 2, 4                        # dV = 32 links
+    dV = d * L ** d
+    # two minima in one 1e-8 bin (floor), next-bin neighbour, and a value on a
+    # bin's lower edge: bins 12345678, 12345678, 12345679 and 25000000
+    x = np.array([0.1234567810, 0.1234567890, 0.1234567900000004, 0.25])
+    assert oracle.n_distinct_f8(x * dV, d, L) == 3
+    # rounding to nearest would split the first two (12345678 / 12345679)
+    assert len(np.unique(np.round(x * 1e8))) == 3 and len(np.unique(np.round(x[:2] * 1e8))) == 2
+    assert oracle.n_distinct_f8(x[:2] * dV, d, L) == 1
+    # normalised by V alone the pair 0.3 / 0.300000005 would fall into two bins
+    y = np.array([0.3, 0.300000005]) * dV
+    assert oracle.n_distinct_f8(y, d, L) == 1
+    assert len(np.unique(np.floor(y / L ** d * 1e8))) == 2
+    # raw F values are all distinct; the quantised count merges them
+    assert oracle.n_distinct_f8(np.array([1.0, 1.0 + 1e-9, 1.0 + 2e-9]) , d, L) == 1
+    # the ends of [0, 1] map to 0 and 1e8
+    assert oracle.n_distinct_f8(np.array([0.0, dV * 1.0]), d, L) == 2
+    assert oracle.n_distinct_f8(np.zeros(0), d, L) == 0
