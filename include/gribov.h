@@ -275,6 +275,19 @@ int gc_fp_test_static(int dim, int L, const double* d_links, const double* d_con
 #define GC_PEAK_RSQ 3
 int gc_peak_probe(int kind, void* stream, double* ops_per_s);
 
+/* Test hook of the copy table's bounded lock wait (the paper has no
+ * counterpart; it lets a test drive a device-side wait to its limit without
+ * faulting or hanging the GPU).  hold = 1 marks every bucket lock of o's copy
+ * table as taken, hold = 0 frees them all; spin_budget is the number of tries
+ * a lock wait makes before it gives up (0 restores the default, 2^22).  While
+ * the locks are held, a start whose copy is not yet in the table cannot insert
+ * it: its wait runs out, the start is marked GC_START_DEDUP_FAILED (counted in
+ * n_dedup_failed) and gc_enumerate_copies returns GC_ETIMEDOUT; a start whose
+ * copy is already in the table is unaffected (its search takes no lock).
+ * Synchronises the orbit's stream.  GC_ESTATE before the orbit's first
+ * enumeration (no table yet), GC_EINVAL for a NULL orbit or a negative budget. */
+int gc_test_dedup_locks(gc_orbit o, int hold, long long spin_budget);
+
 /* message of the last failing call on this thread ("" if none) */
 const char* gc_last_error(void);
 /* library version string */

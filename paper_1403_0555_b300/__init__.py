@@ -98,7 +98,7 @@ EXPORTED = ("gc_set_allocator", "gc_options_default", "gc_create_orbit", "gc_enu
             "gc_fetch_copies", "gc_fetch_minima_f8", "gc_fetch_starts", "gc_orbit_stats", "gc_destroy_orbit",
             "gc_last_error", "gc_version", "gc_fp_test_static", "gc_enumerate_batch",
             "gc_autotune", "gc_autotune_ex", "gc_server_create", "gc_server_submit",
-            "gc_server_wait", "gc_server_destroy", "gc_peak_probe")
+            "gc_server_wait", "gc_server_destroy", "gc_peak_probe", "gc_test_dedup_locks")
 
 _lib = None
 _lock = threading.Lock()
@@ -159,6 +159,7 @@ def load(build_if_stale: bool = True):
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p)]
         L.gc_server_destroy.argtypes = [ctypes.c_void_p]
         L.gc_peak_probe.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+        L.gc_test_dedup_locks.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong]
         L.gc_last_error.restype = ctypes.c_char_p
         L.gc_version.restype = ctypes.c_char_p
         _lib = L
@@ -389,3 +390,9 @@ def gc_peak_probe(kind: int, stream=None) -> float:
     v = ctypes.c_double()
     _check(load().gc_peak_probe(kind, stream, ctypes.byref(v)))
     return v.value
+
+
+def gc_test_dedup_locks(orbit, hold: bool, spin_budget: int = 0):
+    """Test hook: hold (or free) every lock of the orbit's copy table and set the
+    lock-wait budget (0 = default)."""
+    _check(load().gc_test_dedup_locks(orbit, 1 if hold else 0, spin_budget))

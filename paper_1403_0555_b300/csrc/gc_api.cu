@@ -2,7 +2,6 @@
 // admission, batch planning and kernel launches (declarations: gribov.h).
 #include "gribov.h"
 
-#include <cub/device/device_radix_sort.cuh>
 
 #include <algorithm>
 #include <cmath>
@@ -21,6 +20,7 @@
 #include "gc_fptest_lines.cuh"
 #include "gc_slab.cuh"
 #include "gc_table.cuh"
+#include "gc_sort.cuh"
 
 namespace {
 
@@ -120,7 +120,7 @@ struct gc_orbit_s {
   Buf s_redo;        // lattices beyond shared memory: starts the Newton polish leaves to FP64 sweeps
   Buf s_rate;        // ... and the FP32 sweeps' contraction per start
   Buf work, stats, scratch, theta_tmp;
-  Buf sort_keys, sort_idx, sort_tmp;  // fetch ordering: keys [2n], indices [2n], CUB scratch
+  Buf sort_keys, sort_idx, sort_tmp;  // fetch ordering: keys [2n], indices [2n], radix-sort histograms
   Buf f8_tmp;                         // F set fetch: keys [2n], starts [2n], counter
   size_t batch_cap = 0;
   uint64_t next_start = 0;
@@ -173,8 +173,10 @@ struct gc_orbit_s {
     T.nb_mask = nb - 1;
     T.nl_mask = nl - 1;
     T.f8_mask = f8cap - 1;
+    T.lock_spins = lock_spins;
     return T;
   }
+  long long lock_spins = gc::kLockSpins;   // gc_test_dedup_locks lowers it
 };
 
 namespace {
@@ -1526,32 +1528,83 @@ int read_count(gc_orbit o, unsigned* n_out) {
   return GC_OK;
 }
 
+// Stable radix sort (gc_sort.cuh) of n (key, value) pairs by key, over the
+// 8-bit digits that vary among the keys; ping-pongs between (k0, v0) and
+// (k1, v1) and leaves the sorted pairs in *kres / *vres.  scratch holds
+// 4 + 256 * sort_tiles(n) words.  Synchronises s once (to read which digits
+// vary).
+}  // namespace
+}  // extern "C"
+
+namespace {
+template <typename VT>
+int radix_sort_pairs(unsigned long long* k0, unsigned long long* k1, VT* v0, VT* v1, unsigned n,
+                     unsigned* scratch, cudaStream_t s, unsigned long long** kres, VT** vres,
+                     uint64_t* launches) {
+  unsigned long long* or_and = reinterpret_cast<unsigned long long*>(scratch);
+  unsigned* hist = scratch + 4;
+  GC_CUDA(cudaMemsetAsync(or_and, 0, 8, s));
+  GC_CUDA(cudaMemsetAsync(or_and + 1, 0xff, 8, s));
+  const unsigned blocks = std::max(1u, std::min<unsigned>((n + 255) / 256, 1024));
+  gc::key_bits_kernel<<<blocks, 256, 0, s>>>(k0, n, or_and);
+  unsigned long long h[2] = {0ull, 0ull};
+  GC_CUDA(cudaMemcpyAsync(h, or_and, 16, cudaMemcpyDeviceToHost, s));
+  GC_CUDA(cudaStreamSynchronize(s));
+  *launches += 1;
+  const unsigned long long vary = h[0] ^ h[1];
+  const unsigned tiles = gc::sort_tiles(n);
+  for (int shift = 0; shift < 64; shift += 8) {
+    if (((vary >> shift) & 255ull) == 0ull) continue;   // every key has this digit
+    gc::radix_hist_kernel<<<tiles, gc::kSortThreads, 0, s>>>(k0, n, shift, hist, tiles);
+    gc::radix_scan_kernel<<<1, 1024, 0, s>>>(hist, (unsigned)gc::kSortBins * tiles);
+    gc::radix_scatter_kernel<VT><<<tiles, gc::kSortThreads, 0, s>>>(k0, v0, k1, v1, n, shift, hist, tiles);
+    std::swap(k0, k1);
+    std::swap(v0, v1);
+    *launches += 3;
+  }
+  GC_CUDA(cudaGetLastError());
+  *kres = k0;
+  *vres = v0;
+  return GC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+namespace {
+
+size_t sort_scratch_bytes(unsigned n) { return (4 + (size_t)gc::kSortBins * gc::sort_tiles(n)) * 4; }
+
 // Device array of pool entries in (F, first start) order: two stable radix
-// sorts, by first start and then by F.  Returns nullptr for n = 0.
+// sorts, by first start and then by F's order-preserving bit key.  Returns
+// nullptr for n = 0.
 int device_order(gc_orbit o, unsigned n, const unsigned** order) {
   *order = nullptr;
   if (n == 0) return GC_OK;
   cudaStream_t s = o->last_stream;
-  if (!o->sort_keys.ensure((size_t)n * 16, s) || !o->sort_idx.ensure((size_t)n * 8, s))
+  if (!o->sort_keys.ensure((size_t)n * 16, s) || !o->sort_idx.ensure((size_t)n * 8, s) ||
+      !o->sort_tmp.ensure(sort_scratch_bytes(n), s))
     return fail(GC_ENOMEM, "cannot admit %u sort records", n);
   unsigned long long* k0 = o->sort_keys.as<unsigned long long>();
   unsigned long long* k1 = k0 + n;
   unsigned* i0 = o->sort_idx.as<unsigned>();
   unsigned* i1 = i0 + n;
-  size_t tmp = 0, tmp2 = 0;
-  GC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, k0, k1, i0, i1, (int)n, 0, 64, s));
-  GC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp2, k1, k0, i1, i0, (int)n, 0, 64, s));
-  tmp = std::max(tmp, tmp2);
-  if (!o->sort_tmp.ensure(tmp, s)) return fail(GC_ENOMEM, "cannot admit sort scratch");
+  unsigned* scratch = o->sort_tmp.as<unsigned>();
   const int blocks = (int)std::min<unsigned>((n + 255) / 256, 4096);
   GC_CUDA(cudaMemcpyAsync(k0, o->t_first.p, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
   gc::iota_kernel<<<blocks, 256, 0, s>>>(i0, n);
-  GC_CUDA(cub::DeviceRadixSort::SortPairs(o->sort_tmp.p, tmp, k0, k1, i0, i1, (int)n, 0, 64, s));
-  gc::f_keys_kernel<<<blocks, 256, 0, s>>>(o->t_F.as<double>(), i1, k0, n);
-  GC_CUDA(cub::DeviceRadixSort::SortPairs(o->sort_tmp.p, tmp, k0, k1, i1, i0, (int)n, 0, 64, s));
-  o->launches += 2;
-  GC_CUDA(cudaGetLastError());
-  *order = i0;
+  ++o->launches;
+  unsigned long long* kr = nullptr;
+  unsigned* ir = nullptr;
+  if (int rc = radix_sort_pairs<unsigned>(k0, k1, i0, i1, n, scratch, s, &kr, &ir, &o->launches)) return rc;
+  unsigned long long* kf = kr == k0 ? k1 : k0;
+  unsigned* ispare = ir == i0 ? i1 : i0;
+  gc::f_keys_kernel<<<blocks, 256, 0, s>>>(o->t_F.as<double>(), ir, kf, n);
+  ++o->launches;
+  unsigned long long* kr2 = nullptr;
+  unsigned* ir2 = nullptr;
+  if (int rc = radix_sort_pairs<unsigned>(kf, kr, ir, ispare, n, scratch, s, &kr2, &ir2, &o->launches)) return rc;
+  *order = ir2;
   return GC_OK;
 }
 
@@ -1577,18 +1630,20 @@ int gc_fetch_minima_f8(gc_orbit o, size_t capacity, size_t* n_minima, double* F_
   unsigned long long* c0 = k1 + n;
   unsigned long long* c1 = c0 + n;
   unsigned* ctr = reinterpret_cast<unsigned*>(c1 + n);
-  size_t tmp = 0;
-  GC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp, k0, k1, c0, c1, (int)n, 0, 64, s));
-  if (!o->sort_tmp.ensure(tmp, s)) return fail(GC_ENOMEM, "cannot admit sort scratch");
+  if (!o->sort_tmp.ensure(sort_scratch_bytes(n), s)) return fail(GC_ENOMEM, "cannot admit sort scratch");
   GC_CUDA(cudaMemsetAsync(ctr, 0, 4, s));
   const unsigned blocks = std::min<unsigned>((o->f8cap + 255) / 256, 4096);
   f8_compact_kernel<<<blocks, 256, 0, s>>>(o->t_f8.as<unsigned long long>(), o->t_f8n.as<unsigned long long>(),
                                            o->f8cap, k0, c0, ctr, n);
-  GC_CUDA(cub::DeviceRadixSort::SortPairs(o->sort_tmp.p, tmp, k0, k1, c0, c1, (int)n, 0, 64, s));
-  o->launches += 2;
+  ++o->launches;
+  unsigned long long* kr = nullptr;
+  unsigned long long* cr = nullptr;
+  if (int rc = radix_sort_pairs<unsigned long long>(k0, k1, c0, c1, n, o->sort_tmp.as<unsigned>(), s, &kr, &cr,
+                                                    &o->launches))
+    return rc;
   std::vector<unsigned long long> keys(k), starts(count ? k : 0);
-  GC_CUDA(cudaMemcpyAsync(keys.data(), k1, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
-  if (count) GC_CUDA(cudaMemcpyAsync(starts.data(), c1, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+  GC_CUDA(cudaMemcpyAsync(keys.data(), kr, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
+  if (count) GC_CUDA(cudaMemcpyAsync(starts.data(), cr, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
   GC_CUDA(cudaStreamSynchronize(s));
   for (unsigned i = 0; i < k; ++i) F_norm[i] = (double)keys[i] * 1e-8;
   if (count) for (unsigned i = 0; i < k; ++i) count[i] = starts[i];
@@ -2345,5 +2400,21 @@ extern "C" int gc_peak_probe(int kind, void* stream, double* ops_per_s) {
   out.release(s);
   if (rc != GC_OK) return rc;
   *ops_per_s = (double)grid * threads * per_thread / (best * 1e-3);
+  return GC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Test hook for the bounded lock wait of the dedup table
+// ---------------------------------------------------------------------------
+extern "C" int gc_test_dedup_locks(gc_orbit o, int hold, long long spin_budget) {
+  if (!o) return fail(GC_EINVAL, "gc_test_dedup_locks: NULL orbit");
+  if (spin_budget < 0) return fail(GC_EINVAL, "gc_test_dedup_locks: spin_budget %lld < 0", spin_budget);
+  if (!o->t_lock.p || o->nl == 0) return fail(GC_ESTATE, "gc_test_dedup_locks: the orbit has no table yet");
+  cudaStream_t s = o->last_stream;
+  GC_CUDA(cudaStreamSynchronize(s));
+  fill_i32(o->t_lock.as<int>(), hold ? 1 : 0, o->nl, s);
+  GC_CUDA(cudaGetLastError());
+  GC_CUDA(cudaStreamSynchronize(s));
+  o->lock_spins = spin_budget > 0 ? spin_budget : gc::kLockSpins;
   return GC_OK;
 }

@@ -43,6 +43,7 @@ struct TableView {
   unsigned int nb_mask, nl_mask, f8_mask;
   double wF, wT, tolF, delta2, f8_links;  // f8_links = d V (F_norm = F / (d V))
   int f8_only;             // GC_DEDUP_F8: the F set only, no configuration table
+  long long lock_spins;    // tries before a lock wait gives up (kLockSpins by default)
 };
 
 constexpr unsigned long long kF8Empty = ~0ULL;
@@ -55,9 +56,9 @@ __device__ __forceinline__ unsigned lock_of(const TableView& T, long long q) {
   return (unsigned)(mix64((unsigned long long)q) & T.nl_mask);
 }
 
-__device__ inline bool acquire(int* lk) {
+__device__ inline bool acquire(int* lk, long long spins) {
   unsigned ns = 32;
-  for (long long s = 0; s < kLockSpins; ++s) {
+  for (long long s = 0; s < spins; ++s) {
     if (atomicCAS(lk, 0, 1) == 0) { __threadfence(); return true; }
     __nanosleep(ns);
     if (ns < 1024) ns <<= 1;
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(256) dedup_kernel(const DedupArgs a) {
       if (l0 > l1) { tmp = l0; l0 = l1; l1 = tmp; }
       int ok = 0;
       unsigned ns = 64;
-      for (long long tries = 0; tries < kLockSpins; ++tries) {
+      for (long long tries = 0; tries < T.lock_spins; ++tries) {
         if (lane == 0) {
           ok = atomicCAS(&T.lock[l0], 0, 1) == 0;
           if (ok && l1 != l0 && atomicCAS(&T.lock[l1], 0, 1) != 0) { atomicExch(&T.lock[l0], 0); ok = 0; }
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(256) dedup_kernel(const DedupArgs a) {
         const unsigned le = lock_of(T, __ldcg(T.q + e));
         int ok = 1;
         const bool have = locked && (le == l0 || le == l1 || le == l2);
-        if (lane == 0 && !have) ok = acquire(&T.lock[le]);
+        if (lane == 0 && !have) ok = acquire(&T.lock[le], T.lock_spins);
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (ok) {
           __syncwarp();

@@ -24,6 +24,8 @@ def _table_invariants(c, st, V):
     assert int(c["count"].sum()) == st["n_converged"]           # every converged start counted once
     assert len(np.unique(c["first_start"])) == n                 # one representative per copy
     assert np.all(np.diff(c["F"]) >= 0)                          # fetched in F order
+    tie = np.diff(c["F"]) == 0                                   # equal F: by first start
+    assert np.all(np.diff(c["first_start"].astype(np.int64))[tie] > 0)
     assert np.all(np.abs(c["theta"][:, V - 1]) <= 1e-15)         # global phase fixed at site V-1
     assert np.all(c["F"] >= -1e-9)
 
