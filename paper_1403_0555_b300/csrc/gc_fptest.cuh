@@ -244,10 +244,16 @@ __device__ R lanczos_min(const R* w, R* vprev, R* vcur, R* z, R* alpha, R* beta,
 //     reduction that adds each level once;
 //   * convergence is first followed in FP32: the tridiagonal, rounded to FP32,
 //     by Sturm multisection every 8 steps, until those Ritz values stall;
-//   * from then on every check takes lambda_min of the FP64 tridiagonal from
-//     a bracket around the FP32 value by tri_min64 (division-free Sturm
-//     counts, Newton steps from below), and the run stops when two FP64
-//     values 8 steps apart agree to tol64.
+//   * from then on each check takes lambda_min of the FP64 tridiagonal by
+//     tri_min64 (division-free Sturm counts, Newton steps from below): the
+//     first from a bracket around the FP32 value (two rounds), the later ones
+//     warm-started just below the previous value (Cauchy interlacing bounds
+//     the new one by it) in one round; the run stops when two FP64 values
+//     8 steps apart agree to tol64.  On this part an FP64 instruction costs
+//     the pipe the same with one active lane as with 32, so each round uses
+//     all 32 lanes (32 points);
+//   * the normalisation's 1/sqrt in FP64 from the FP32 unit's estimate and
+//     two Newton steps, and comparisons on the integer pipe.
 // The result is the smallest Ritz value of the FP64 Lanczos tridiagonal.
 // ---------------------------------------------------------------------------
 
@@ -308,13 +314,19 @@ __device__ inline SturmPoint sturm_point64(const double* alpha, const double* be
 // Newton step from it.  Below the smallest root of a polynomial with real
 // roots, Newton's iterates increase and stay below the root, so the step
 // gives the new lower end; the next point up gives the upper end.
+// With near_hi there is one round only, its points crowding towards hi (at
+// hi - (hi - lo) 0.35^l): the warm start of a later check, whose root lies a
+// little below the previous check's value hi.  If the root is delta below hi,
+// the last point under it is within 1.9 delta of it, and the Newton step from
+// there is off by O(delta^2 / gap): negligible once the values stall.
 __device__ inline double tri_min64(const double* alpha, const double* beta2, int k, double lo, double hi,
-                                   int lane, bool* ok) {
+                                   int lane, bool* ok, bool near_hi = false) {
   *ok = true;
-  for (int round = 0; round < 8; ++round) {
+  for (int round = 0; round < (near_hi ? 1 : 8); ++round) {
     double x;
     if (lane == 0) x = lo;
     else if (lane == 31) x = hi;
+    else if (round == 0 && near_hi) x = fma(lo - hi, f2d_bits(exp2f((float)lane * -1.51457317f)), hi);
     else if (round == 0) x = fma(hi - lo, (double)lane * (1.0 / 31.0), lo);
     else x = fma(hi - lo, f2d_bits(exp2f((float)(31 - lane) * -1.51457317f)), lo);
     const SturmPoint r = sturm_point64(alpha, beta2, k, x);
@@ -337,6 +349,22 @@ __device__ inline double tri_min64(const double* alpha, const double* beta2, int
     if (round >= 1 && hi - lo <= 1e-13 * fmax(fabs(lo), 1e-3)) break;
   }
   return lo;
+}
+
+// 1/sqrt(x) for x > 0 in FP64: the special-function unit's FP32 estimate
+// (relative error < 2^-22) refined by two Newton steps y <- y (3 - x y^2) / 2,
+// each squaring the error (2^-44, then below FP64 rounding)
+__device__ __forceinline__ double rsqrt64(double x) {
+  double y = f2d_bits(rsqrt_sfu(d2f_bits(x)));
+  const double hx = 0.5 * x;
+  double e = fma(-hx * y, y, 0.5);
+  y = fma(y, e, y);
+  e = fma(-hx * y, y, 0.5);
+  return fma(y, e, y);
+}
+// ordering of non-negative doubles by their bit patterns (integer pipe)
+__device__ __forceinline__ bool dbelow(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b);
 }
 
 // sums of a and b over the warp: the first level exchanges the half each lane
@@ -373,13 +401,13 @@ __device__ double lanczos64_min(const double* nw, const double* Dg, double* va, 
   s = warp_sum(s) / (double)V;
   double nn = 0.0;
   for (int x = lane; x < V; x += 32) { const double v = vcur[x] - s; vcur[x] = v; nn = fma(v, v, nn); }
-  const double inv0 = rsqrt(warp_sum(nn));
+  const double inv0 = rsqrt64(warp_sum(nn));
   for (int x = lane; x < V; x += 32) vcur[x] *= inv0;
   __syncwarp();
   const double invV = 1.0 / (double)V;
   const float bound = (float)(4 * DD + 1);
   float t32 = bound, t32_prev = bound, t32_pp = bound;   // bound = no estimate yet
-  double t64 = (double)bound;
+  double t64 = (double)bound, d64 = 0.0;                  // last FP64 value and its last decrease
   bool fine = false;                                      // FP64 checks have started
   double b = 0.0;
   int j = 0;
@@ -410,7 +438,8 @@ __device__ double lanczos64_min(const double* nw, const double* Dg, double* va, 
     }
     warp_sum2(m, zz, lane);
     m *= invV;
-    const double bn2 = fmax(fma(-(double)V * m, m, zz), 0.0);   // |z - m|^2
+    double bn2 = fma(-(double)V * m, m, zz);   // |z - m|^2
+    if (__double_as_longlong(bn2) < 0) bn2 = 0.0;
     if (lane == 0) {
       a64[j] = a;
       b64[j + 1] = bn2;
@@ -418,36 +447,56 @@ __device__ double lanczos64_min(const double* nw, const double* Dg, double* va, 
       b32[j + 1] = d2f_bits(bn2);
     }
     __syncwarp();
-    const bool last = (j + 1 == kmax) || bn2 < 1e-24;
+    const bool last = (j + 1 == kmax) || dbelow(bn2, 1e-24);
+    // checks every 8 steps from step 16: FP32 until the FP32 view stalls, then FP64
     if (last || ((j + 1) % 8 == 0 && j + 1 >= 16)) {
-      // FP32 view: bracket from Cauchy interlacing, as in lanczos_min
-      float lo = -bound, hi = bound;
-      if (t32_prev < bound) {
-        const float slack = 2.f * tri_rel<float>() * fmaxf(fabsf(t32_prev), 1.f);
-        hi = t32_prev + slack;
-        if (t32_pp < bound) {
-          const float l = t32_prev - 4.f * fmaxf(t32_pp - t32_prev, slack);
-          if (sturm_count<float>(a32, b32, j + 1, l) == 0) lo = l;
+      bool stall32 = false;
+      if (!fine) {
+        // FP32 view: bracket from Cauchy interlacing, as in lanczos_min
+        float lo = -bound, hi = bound;
+        if (t32_prev < bound) {
+          const float slack = 2.f * tri_rel<float>() * fmaxf(fabsf(t32_prev), 1.f);
+          hi = t32_prev + slack;
+          if (t32_pp < bound) {
+            const float l = t32_prev - 4.f * fmaxf(t32_pp - t32_prev, slack);
+            if (sturm_count<float>(a32, b32, j + 1, l) == 0) lo = l;
+          }
         }
+        t32 = tri_min<float>(a32, b32, j + 1, lo, hi, lane);
+        stall32 = t32_prev < bound && fabsf(t32 - t32_prev) <= (float)tol32 * fmaxf(fabsf(t32), 1e-3f);
+        t32_pp = t32_prev;
+        t32_prev = t32;
       }
-      t32 = tri_min<float>(a32, b32, j + 1, lo, hi, lane);
-      const bool stall32 = t32_prev < bound && fabsf(t32 - t32_prev) <= (float)tol32 * fmaxf(fabsf(t32), 1e-3f);
-      t32_pp = t32_prev;
-      t32_prev = t32;
       if (fine || stall32 || last) {
-        // the FP32 value is within rounding (~2e-6 ||T||) of the FP64 one
-        const double c = f2d_bits(t32);
-        const double del = 2e-5 * fmax(1.0, fabs(c));
-        bool ok;
-        double t = tri_min64(a64, b64, j + 1, c - del, c + del, lane, &ok);
-        if (!ok) t = tri_min64(a64, b64, j + 1, -(double)bound, (double)bound, lane, &ok);
+        bool ok = false;
+        double t = 0.0;
+        if (fine) {
+          // warm start: lambda_min(T_k) <= the last value (interlacing); points
+          // crowd just below it
+          const double hi = t64 + 1e-14 * fmax(fabs(t64), 1.0);
+          const double w = fmax(8.0 * d64, 4e-5 * fmax(fabs(t64), 1e-3));
+          t = tri_min64(a64, b64, j + 1, t64 - w, hi, lane, &ok, true);
+        }
+        if (!ok) {
+          // from the FP32 value, within rounding (~2e-6 ||T||) of the FP64 one
+          if (fine) {
+            float lo = -bound;
+            const float hi = (float)t64 + 2e-5f * fmaxf(1.f, fabsf((float)t64));
+            t32 = tri_min<float>(a32, b32, j + 1, lo, hi, lane);
+          }
+          const double c = f2d_bits(t32);
+          const double del = 2e-5 * fmax(1.0, fabs(c));
+          t = tri_min64(a64, b64, j + 1, c - del, c + del, lane, &ok);
+          if (!ok) t = tri_min64(a64, b64, j + 1, -(double)bound, (double)bound, lane, &ok);
+        }
         const bool stall64 = fine && fabs(t - t64) <= tol64 * fmax(fabs(t), 1e-3);
+        d64 = fine ? fmax(t64 - t, 0.0) : 0.0;
         t64 = t;
         fine = true;
         if (last || stall64) { ++j; break; }
       }
     }
-    const double ib = rsqrt(bn2);
+    const double ib = rsqrt64(bn2);
     const double mib = -m * ib;
     for (int x = lane; x < V; x += 32) z[x] = fma(z[x], ib, mib);
     b = bn2 * ib;
