@@ -578,6 +578,7 @@ def run_ours(args):
              "ffma2": gb.gc_peak_probe(gb.GC_PEAK_FFMA2, stream) / 1e12,
              "dfma": gb.gc_peak_probe(gb.GC_PEAK_DFMA, stream) / 1e12,
              "rsqrt": gb.gc_peak_probe(gb.GC_PEAK_RSQ, stream) / 1e12,
+             "dfma_one_lane_per_warp": gb.gc_peak_probe(gb.GC_PEAK_DFMA_LANE1, stream) / 1e12,
              "unit": "T lane operations/s (packed f32x2 counts two)",
              "how": "gc_peak_probe: 4 CTAs x 256 threads per SM, 8 independent chains per thread, best of 3"}
 

@@ -263,16 +263,19 @@ int gc_fp_test_static(int dim, int L, const double* d_links, const double* d_con
  * has no counterpart: it measures the denominators of the kernels' rooflines
  * on the GPU at hand).  kind: GC_PEAK_FFMA (FP32 FMA), GC_PEAK_FFMA2 (packed
  * f32x2 FMA, counted as two), GC_PEAK_DFMA (FP64 FMA), GC_PEAK_RSQ (the
- * special-function unit's approximate reciprocal square root).  Every thread
- * of four 256-thread CTAs per SM runs eight independent chains; the best of
- * three timed launches (after a warm-up) gives *ops_per_s, lane operations
- * per second.  Synchronises `stream` (a cudaStream_t, NULL = default);
+ * special-function unit's approximate reciprocal square root),
+ * GC_PEAK_DFMA_LANE1 (FP64 FMA with one active lane per warp, counted once per
+ * warp instruction: equal to GC_PEAK_DFMA / 32 when the pipe's cost does not
+ * depend on the active lanes).  Every thread of four 256-thread CTAs per SM
+ * runs eight independent chains; the best of three timed launches (after a
+ * warm-up) gives *ops_per_s, lane operations per second.  Synchronises `stream` (a cudaStream_t, NULL = default);
  * allocates about 0.6 MB of scratch through the allocator hooks.
  * GC_EINVAL for an unknown kind or a NULL ops_per_s. */
 #define GC_PEAK_FFMA 0
 #define GC_PEAK_FFMA2 1
 #define GC_PEAK_DFMA 2
 #define GC_PEAK_RSQ 3
+#define GC_PEAK_DFMA_LANE1 4
 int gc_peak_probe(int kind, void* stream, double* ops_per_s);
 
 /* Test hook of the copy table's bounded lock wait (the paper has no

@@ -50,6 +50,7 @@ GC_PEAK_FFMA = 0
 GC_PEAK_FFMA2 = 1
 GC_PEAK_DFMA = 2
 GC_PEAK_RSQ = 3
+GC_PEAK_DFMA_LANE1 = 4
 
 
 class GribovError(RuntimeError):

@@ -2363,12 +2363,13 @@ extern "C" int gc_server_destroy(gc_server s) {
 
 extern "C" int gc_peak_probe(int kind, void* stream, double* ops_per_s) {
   if (!ops_per_s) return fail(GC_EINVAL, "gc_peak_probe: NULL ops_per_s");
-  if (kind < GC_PEAK_FFMA || kind > GC_PEAK_RSQ) return fail(GC_EINVAL, "gc_peak_probe: unknown kind %d", kind);
+  if (kind < GC_PEAK_FFMA || kind > GC_PEAK_DFMA_LANE1) return fail(GC_EINVAL, "gc_peak_probe: unknown kind %d", kind);
   cudaStream_t s = (cudaStream_t)stream;
   // four 256-thread CTAs per SM; iterations sized for ~10-40 ms per launch
   const int threads = 256, grid = 4 * sm_count();
-  const int iters = kind == GC_PEAK_DFMA ? 1 << 12 : (kind == GC_PEAK_RSQ ? 1 << 15 : 1 << 17);
-  const double per_thread = 8.0 * iters * (kind == GC_PEAK_FFMA2 ? 2.0 : 1.0);
+  const int iters = (kind == GC_PEAK_DFMA || kind == GC_PEAK_DFMA_LANE1) ? 1 << 12 : (kind == GC_PEAK_RSQ ? 1 << 15 : 1 << 17);
+  // lane operations per thread (one-lane DFMA: per warp instruction, i.e. per 32 threads)
+  const double per_thread = 8.0 * iters * (kind == GC_PEAK_FFMA2 ? 2.0 : 1.0) / (kind == GC_PEAK_DFMA_LANE1 ? 32.0 : 1.0);
   Buf out;
   if (!out.ensure((size_t)grid * threads * sizeof(float), s)) return fail(GC_ENOMEM, "gc_peak_probe: no scratch");
   cudaEvent_t e0, e1;
@@ -2380,6 +2381,7 @@ extern "C" int gc_peak_probe(int kind, void* stream, double* ops_per_s) {
       case GC_PEAK_FFMA: gc::peak_probe_kernel<gc::kPeakFFMA><<<grid, threads, 0, s>>>(out.as<float>(), iters, m, c); break;
       case GC_PEAK_FFMA2: gc::peak_probe_kernel<gc::kPeakFFMA2><<<grid, threads, 0, s>>>(out.as<float>(), iters, m, c); break;
       case GC_PEAK_DFMA: gc::peak_probe_kernel<gc::kPeakDFMA><<<grid, threads, 0, s>>>(out.as<float>(), iters, m, c); break;
+      case GC_PEAK_DFMA_LANE1: gc::peak_probe_kernel<gc::kPeakDFMA1><<<grid, threads, 0, s>>>(out.as<float>(), iters, m, c); break;
       default: gc::peak_probe_kernel<gc::kPeakRSQ><<<grid, threads, 0, s>>>(out.as<float>(), iters, m, c); break;
     }
   };

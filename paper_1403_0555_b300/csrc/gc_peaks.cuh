@@ -1,16 +1,18 @@
 // Throughput probes of the arithmetic units the enumerator's kernels are bound
-// by: FP32 FMA, packed f32x2 FMA, FP64 FMA and the special-function unit's
-// reciprocal square root.  They give the roofline denominators measured on the
-// GPU that runs the library (the paper has no counterpart).  Every thread runs
-// eight independent dependency chains of one instruction kind, unrolled eight
-// times, so the probe measures the unit's throughput rather than its latency,
-// and loop overhead is under 5 % of the issued instructions.
+// by: FP32 FMA, packed f32x2 FMA, FP64 FMA (all lanes, and one lane per warp:
+// whether an FP64 warp instruction costs the pipe by its active lanes) and the
+// special-function unit's reciprocal square root.  They give the roofline
+// denominators measured on the GPU that runs the library (the paper has no
+// counterpart).  Every thread runs eight independent dependency chains of one
+// instruction kind, unrolled eight times, so the probe measures the unit's
+// throughput rather than its latency, and loop overhead is under 5 % of the
+// issued instructions.
 #pragma once
 #include <cuda_runtime.h>
 
 namespace gc {
 
-enum { kPeakFFMA = 0, kPeakFFMA2 = 1, kPeakDFMA = 2, kPeakRSQ = 3 };
+enum { kPeakFFMA = 0, kPeakFFMA2 = 1, kPeakDFMA = 2, kPeakRSQ = 3, kPeakDFMA1 = 4 };
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
   float2 d;
@@ -60,15 +62,18 @@ __global__ void __launch_bounds__(256) peak_probe_kernel(float* out, int iters, 
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) r += a[u].x + a[u].y;
-  } else if constexpr (KIND == kPeakDFMA) {
+  } else if constexpr (KIND == kPeakDFMA || KIND == kPeakDFMA1) {
+    // kPeakDFMA1: only lane 0 of each warp runs the chains
     double a[8];
     const double md = (double)m, cd = (double)c;
 #pragma unroll
     for (int u = 0; u < 8; ++u) a[u] = (double)seed + (double)u;
+    if (KIND == kPeakDFMA || (threadIdx.x & 31) == 0) {
 #pragma unroll 8
-    for (int it = 0; it < iters; ++it) {
+      for (int it = 0; it < iters; ++it) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) a[u] = fma(a[u], md, cd);
+        for (int u = 0; u < 8; ++u) a[u] = fma(a[u], md, cd);
+      }
     }
     double s = 0.0;
 #pragma unroll
