@@ -43,7 +43,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # captured for the current kernel)
 TRAFFIC_POLISH_PER_START = (1.34528e8 + 2.18642e8) / 65536  # profiles/polish_kernel_4d_L4.md (line polish)
 TRAFFIC_RELAX_PER_START = (9.91e4 + 7.4575e7) / 65536       # profiles/relax32_sheet_4d_L4.md
-TRAFFIC_FPTEST_PER_COPY = None                               # fp_test_kernel, not captured since its rewrite
+TRAFFIC_FPTEST_PER_COPY = (1.84462080e8 + 3.86688e6) / 44636   # profiles/fp_test_lanczos64_4d_L4.md
 # DRAM traffic per launch of the large-lattice leg's kernels (its own workload,
 # 592 starts of 4D 16^4), from ncu: profiles/slab_traffic_4d_L16.md
 TRAFFIC_SLAB_NEWTON1 = 2.92208894464e11 + 5.7204921344e10

@@ -635,6 +635,16 @@ int launch_clusters(K kernel, const A& args, int threads, size_t smem, int csize
 // or, with `wide` (a handful of hard starts), of kSlabClusterWide CTAs where
 // that non-portable size fits
 constexpr int kSlabCluster = 8, kSlabClusterWide = 16;
+// Mixed path on lattices beyond shared memory: the first kSlabHeadSweeps sweeps
+// of every start are the plain path's FP64 sweeps (the oracle's operations),
+// then FP32 continues from that state.  A random start moves far in its first
+// sweeps, and there FP32 rounding can steer it into another basin: on 4D 8^4,
+// 3D 16^3 and 4D 16^4 (von Mises kappa = 1) 0.8-1.6 % of starts ended in a
+// different minimum than the FP64 path (F off by up to 33).  Measured
+// agreement with the FP64 path: 12 head sweeps, all of 1024 starts on 4D 8^4
+// and 3D 16^3 but 508 of 512 on 4D 16^4; 24 head sweeps, 512 of 512 on 4D
+// 16^4 (and 48 and 96 the same), for 20 % more time in its relaxation stage.
+constexpr int kSlabHeadSweeps = 24;
 template <class K1, class KC>
 int launch_slab(K1 k1, KC kc, const gc::SlabArgs& sa, size_t smem, int grid, bool cluster,
                 cudaStream_t s, bool wide = false) {
@@ -805,12 +815,32 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     if (ev) GC_CUDA(cudaEventRecord(ev[0], s));
     double2* st64 = o->s_config.as<double2>();
     if (mixed) {
-      // FP32 sweeps from the random starts
+      // FP64 head: the plain path's first sweeps from the random starts (no
+      // converged/not-converged counts: the FP32 phase decides every start)
+      {
+        gc::SlabArgs ha = sa;
+        ha.links = o->links64.p;
+        ha.state = st64;
+        ha.init = 1;
+        ha.check_every = kSlabHeadSweeps;
+        ha.max_sweeps = kSlabHeadSweeps;
+        ha.s_sweeps = kSweeps; ha.s_updates = kUpdates; ha.s_conv = -1; ha.s_nconv = -1;
+        const size_t nv = (size_t)b * V;
+        gc::SlabArgs keep = sa;
+        sa = ha;
+        if (int rc = launch(true, cluster)) return rc;
+        sa = keep;
+        gc::slab_demote_kernel<<<(int)std::min<size_t>((nv + 255) / 256, 4096), 256, 0, s>>>(
+            st64, o->s_state32.as<float2>(), nv);
+        ++o->launches;
+        GC_CUDA(cudaMemsetAsync(wctr, 0, 8, s));
+      }
+      // FP32 sweeps from there
       if (!o->s_rate.ensure((size_t)B * 4, s)) return fail(GC_ENOMEM, "cannot admit a batch of %zu starts", B);
       sa.links = o->links32.p;
       sa.state = o->s_state32.as<float2>();
       sa.rate = o->s_rate.as<float>();
-      sa.init = 1;
+      sa.init = 0;
       sa.s_sweeps = kSweeps32; sa.s_updates = kUpdates32; sa.s_conv = kConv32; sa.s_nconv = kNConv32;
       // the lattice in a cluster's distributed shared memory: one start per
       // cluster of 16 (else 8) CTAs of 256 threads, each holding at least two

@@ -986,6 +986,15 @@ __global__ void __launch_bounds__(1024, 1) slab_newton_kernel(const SlabNewtonAr
 }
 
 // FP32 state -> FP64, renormalised (the mixed path's hand-over to the FP64 sweeps)
+// FP64 state -> FP32 state (round to nearest) for the FP32 phase that follows
+// the FP64 head sweeps of the mixed path
+__global__ void slab_demote_kernel(const double2* s64, float2* s32, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = s64[i];
+    s32[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
 __global__ void slab_promote_kernel(const float2* s32, double2* s64, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double x = s32[i].x, y = s32[i].y;

@@ -61,26 +61,28 @@ def _agree(c_a, s_a, c_b, s_b, n):
     return same
 
 
-def test_hyperplane_mixed_path_agrees_with_the_plain_path():
-    """4D 8^4 (FP32 hyperplane sweeps, then Newton steps with an FP32 SOR inner
-    solve): every start converges to the FP64 tolerance, the oracle's
-    divergence of each copy is below it, and the copy is the plain path's
-    minimum in at least 90 % of the starts (the FP32 phase may settle a start
-    near a basin boundary elsewhere; 8^4 landscapes hold many close minima)."""
+@pytest.mark.parametrize("d,L,seed,n", [(3, 16, 3, 1024), (4, 8, 3, 1024), (2, 64, 3, 512), (4, 16, 1, 512)])
+def test_hyperplane_mixed_path_agrees_with_the_plain_path(d, L, seed, n):
+    """Lattices beyond shared memory, von Mises kappa = 1: the mixed path (the
+    plain path's first FP64 sweeps, FP32 sweeps, Newton steps with an FP32 SOR
+    inner solve, FP64 sweeps for what Newton leaves) converges every start to
+    the FP64 tolerance, the oracle's divergence of the copies is below it, and
+    start by start the copy is the plain path's on at least 99.9 % of the
+    starts (the whole sample at 512 starts)."""
     import paper_1403_0555_b300 as gb
-    d, L, n = 4, 8, 32
-    phi = oi.von_mises_orbit(d, L, 1.0, 3)
-    st_p, s_p, c_p = _plain(gb, d, L, phi, 3, n, precision=gb.GC_FP64, check_every=1)
-    st_m, s_m, c_m = _plain(gb, d, L, phi, 3, n, precision=gb.GC_MIXED, check_every=4)
+    phi = oi.von_mises_orbit(d, L, 1.0, seed)
+    st_p, s_p, c_p = _plain(gb, d, L, phi, seed, n, precision=gb.GC_FP64, check_every=1)
+    st_m, s_m, c_m = _plain(gb, d, L, phi, seed, n, precision=gb.GC_MIXED, check_every=4)
     assert st_m["n_converged"] == n and st_p["n_converged"] == n
     assert st_m["sweeps_fp32"] > 0 and st_m["newton_steps"] > 0 and st_m["newton_inner_sweeps"] > 0
     assert st_m["polish_fallbacks"] <= n // 8
-    for k in range(c_m["n_distinct"]):
+    for k in range(0, c_m["n_distinct"], max(1, c_m["n_distinct"] // 16)):
         t = c_m["theta"][k]
         dv = oracle.divergence(d, L, phi, np.stack([np.cos(t), np.sin(t)], axis=-1))
         assert np.max(dv ** 2) < 2e-24
     same = _agree(c_p, s_p, c_m, s_m, n)
-    assert same >= 0.9 * n, same
+    print(f"\n{d}D L={L}: mixed vs plain {same} of {n} starts")
+    assert same >= 0.999 * n, same
 
 
 def test_hyperplane_newton_fallback_to_fp64_sweeps():
