@@ -71,7 +71,7 @@ def parse():
     p.add_argument("--no-large", dest="large", action="store_false",
                    help="skip the large-lattice leg (4D 16^4, hyperplane path)")
     p.add_argument("--serve-requests", type=int, default=100,
-                   help="requests of the Poisson serving leg (0 skips it)")
+                   help="requests of each Poisson serving leg, above and below capacity (0 skips them)")
     return p.parse_args()
 
 
@@ -342,10 +342,14 @@ def large_lattice_leg(gb, torch, d=4, L=16, n=592, runs=2):
 # serving leg: Poisson arrivals at 200 requests/s of mixed-dimension requests
 # ----------------------------------------------------------------------------
 
-def serve_leg(gb, n_requests, opt):
+def serve_leg(gb, n_requests, opt, rate_hz=200.0, workers=16, seed=7):
+    """n_requests Poisson arrivals at rate_hz through gc_server_*: latency
+    (submission to completion, p50/p99/mean), achieved starts, converged
+    copies and site updates per second over the span from the first
+    submission to the last completion."""
     import threading
-    reqs = oi.request_stream(n_requests, rate_hz=200.0, seed=7)
-    srv = gb.gc_server_create(8, 0, opt)
+    reqs = oi.request_stream(n_requests, rate_hz=rate_hz, seed=seed)
+    srv = gb.gc_server_create(workers, 0, opt)
     results = []
     tickets = []
     failures = []
@@ -370,10 +374,12 @@ def serve_leg(gb, n_requests, opt):
             if status != 0:
                 r = t[1]
                 failures.append(f"{r.d}D L={r.L} n={r.n_starts}: {gb.gc_last_error()}")
-            conv = gb.gc_orbit_stats(orb)["n_converged"] if orb is not None else 0
+            conv = upd = 0
             if orb is not None:
+                st = gb.gc_orbit_stats(orb)
+                conv, upd = st["n_converged"], st["site_updates_fp32"] + st["site_updates_fp64"]
                 gb.gc_destroy_orbit(orb)
-            results.append((status, latency, conv, time.perf_counter()))
+            results.append((status, latency, conv, upd, time.perf_counter()))
             i += 1
 
     th = threading.Thread(target=collector)
@@ -388,17 +394,32 @@ def serve_leg(gb, n_requests, opt):
             tickets.append((tk, r))
     done.set()
     th.join()
-    span = max(x[3] for x in results) - t0
+    span = max(x[4] for x in results) - t0
+    info = gb.gc_server_state(srv)
     gb.gc_server_destroy(srv)
     lat = np.array([x[1] for x in results])
-    conv = sum(x[2] for x in results)
-    offered = sum(r.n_starts for r in reqs) / reqs[-1].arrival_s
-    return {"requests": n_requests, "rate_hz": 200.0, "workers": 8,
+    starts = sum(r.n_starts for r in reqs)
+    return {"requests": n_requests, "rate_hz": rate_hz, "workers": workers,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "converged_copies_per_s": conv / span, "offered_starts_per_s": offered,
+            "mean_latency_s": float(lat.mean()),
+            "converged_copies_per_s": sum(x[2] for x in results) / span,
+            "starts_per_s": starts / span, "site_updates_per_s": sum(x[3] for x in results) / span,
+            "offered_starts_per_s": starts / reqs[-1].arrival_s,
             "failed": int(sum(1 for x in results if x[0] != 0)), "failures": failures[:5], "span_s": span,
+            "loop_launches": info["loop_launches"], "admitted_on_device": info["admitted"],
             "mix": "dim in {2,3,4}, L from {4,6,8,12,16}/{4,5,6,8}/{3,4,5,6}, "
                    "n_starts log-uniform in [1e3, 1e6], von Mises(1.0) orbits"}
+
+
+def serving_legs(gb, n_requests, opt):
+    """The request stream at 200 requests/s (above the GPU's capacity for this
+    mix: latency is mostly queueing), then the same mix at half the
+    throughput that run achieved (below capacity: latency is service)."""
+    over = serve_leg(gb, n_requests, opt, rate_hz=200.0)
+    mean_n = (1e6 - 1e3) / math.log(1e3)                 # log-uniform [1e3, 1e6]
+    low = 0.5 * over["starts_per_s"] / mean_n
+    below = serve_leg(gb, n_requests, opt, rate_hz=low, seed=8)
+    return {"above_capacity": over, "below_capacity": below}
 
 
 # ----------------------------------------------------------------------------
@@ -681,7 +702,7 @@ def run_ours(args):
     if args.serve_requests > 0:
         sopt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=args.check_every,
                                      fp_mode=gb.GC_FP_AUTO)
-        serving = serve_leg(gb, args.serve_requests, sopt)
+        serving = serving_legs(gb, args.serve_requests, sopt)
 
     cpu_configs = oracle_configs() if args.cpu_configs else None
 

@@ -186,14 +186,21 @@ int gc_autotune(gc_orbit o, int precision, int* r_warps, int* p_warps, int* f_wa
 int gc_autotune_ex(gc_orbit o, int precision, int mode, int* r_warps, int* p_warps,
                    int* f_warps, int* check_every);
 
-/* Serving with continuous batching.  Requests (an orbit and a start count)
- * queue in arrival order; `workers` threads, each on its own stream, start the
- * head request as soon as its device-memory estimate fits the budget, so
- * requests that arrive while others run are admitted as memory frees up and
- * their kernels overlap on the GPU.  A request's state stays on the device;
- * its result is a finished orbit handed to the caller (fetch, then destroy).
- * A request's result does not depend on what else runs.
- *   mem_budget_bytes: 0 = half the free device memory at creation.
+/* Serving with continuous batching and device-side admission.  The server
+ * owns a device arena of mem_budget_bytes (0 = half the free device memory,
+ * at most 16 GiB) and a request loop resident on the GPU: one warp that polls
+ * a mailbox in pinned memory, keeps the queue of waiting requests and the
+ * arena's region table in device memory, and admits requests in arrival
+ * order as soon as a free region fits their device-memory estimate.  Each
+ * admitted request runs on one of `workers` host threads (each on its own
+ * stream) with all of its device state carved from its region, so requests
+ * that arrive while others run are admitted as memory frees up and their
+ * kernels overlap on the GPU.  When it is done, its results move out of the
+ * arena (the orbit handed to the caller) and the region goes back to the loop.
+ * A request's result does not depend on what else runs.  The loop sleeps
+ * between polls and ends after about 0.2 s without work (its state stays on
+ * the device; gc_server_state then reports loop_status GC_ETIMEDOUT); the next
+ * mail starts it again.
  *   gc_server_submit: GC_ENOMEM if the request alone exceeds the budget.
  *   gc_server_wait:   blocks up to timeout_s (< 0: no limit); GC_ETIMEDOUT if
  *     not finished (the ticket stays valid).  On completion *status is the
@@ -201,14 +208,28 @@ int gc_autotune_ex(gc_orbit o, int precision, int mode, int* r_warps, int* p_war
  *     completion, and *orbit the finished orbit (NULL on failure; if the
  *     caller passes NULL for orbit, the library destroys it).  The ticket is
  *     then retired.
- *   gc_server_destroy: finishes queued and running requests, frees orbits
- *     nobody collected. */
+ *   gc_server_state:  a snapshot of the loop and its admission counters.
+ *   gc_server_destroy: finishes submitted requests, stops the loop, frees
+ *     orbits nobody collected. */
 typedef struct gc_server_s* gc_server;
+typedef struct {
+  int loop_status;          /* GC_OK, or GC_ETIMEDOUT when the loop's last launch
+                               ended on its idle limit                          */
+  int loop_running;         /* 1 while a launch of the loop runs                 */
+  uint64_t loop_launches;   /* launches of the loop so far                       */
+  uint64_t admitted;        /* requests the loop admitted                        */
+  uint64_t released;        /* regions mailed back                               */
+  uint64_t waiting;         /* requests read by the loop, not yet admitted       */
+  uint64_t bytes_in_use;    /* arena bytes of admitted regions                   */
+  uint64_t budget_bytes;    /* the arena's size                                  */
+  uint32_t regions;         /* entries of the region table (used and free)       */
+} gc_server_info;
 int gc_server_create(int workers, size_t mem_budget_bytes, const gc_options* opt, gc_server* out);
 int gc_server_submit(gc_server s, int dim, int L, const double* link_angles, uint64_t orbit_id,
                      uint64_t n_starts, double omega, double eps, uint64_t* ticket);
 int gc_server_wait(gc_server s, uint64_t ticket, double timeout_s, int* status, double* latency_s,
                    gc_orbit* orbit);
+int gc_server_state(gc_server s, gc_server_info* out);
 int gc_server_destroy(gc_server s);
 
 /* Distinct copies sorted by (F, first_start).  capacity = 0 only sets

@@ -83,6 +83,14 @@ class gc_options(ctypes.Structure):
     ]
 
 
+class gc_server_info(ctypes.Structure):
+    _fields_ = [("loop_status", ctypes.c_int), ("loop_running", ctypes.c_int),
+                ("loop_launches", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("released", ctypes.c_uint64), ("waiting", ctypes.c_uint64),
+                ("bytes_in_use", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64),
+                ("regions", ctypes.c_uint32)]
+
+
 class gc_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "n_starts", "n_converged", "n_not_converged", "n_dedup_failed", "n_distinct",
@@ -99,7 +107,7 @@ EXPORTED = ("gc_set_allocator", "gc_options_default", "gc_create_orbit", "gc_enu
             "gc_fetch_copies", "gc_fetch_minima_f8", "gc_fetch_starts", "gc_orbit_stats", "gc_destroy_orbit",
             "gc_last_error", "gc_version", "gc_fp_test_static", "gc_enumerate_batch",
             "gc_autotune", "gc_autotune_ex", "gc_server_create", "gc_server_submit",
-            "gc_server_wait", "gc_server_destroy", "gc_peak_probe", "gc_test_dedup_locks")
+            "gc_server_wait", "gc_server_destroy", "gc_peak_probe", "gc_test_dedup_locks", "gc_server_state")
 
 _lib = None
 _lock = threading.Lock()
@@ -159,6 +167,7 @@ def load(build_if_stale: bool = True):
         L.gc_server_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double, p_i,
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p)]
         L.gc_server_destroy.argtypes = [ctypes.c_void_p]
+        L.gc_server_state.argtypes = [ctypes.c_void_p, ctypes.POINTER(gc_server_info)]
         L.gc_peak_probe.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
         L.gc_test_dedup_locks.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong]
         L.gc_last_error.restype = ctypes.c_char_p
@@ -397,3 +406,10 @@ def gc_test_dedup_locks(orbit, hold: bool, spin_budget: int = 0):
     """Test hook: hold (or free) every lock of the orbit's copy table and set the
     lock-wait budget (0 = default)."""
     _check(load().gc_test_dedup_locks(orbit, 1 if hold else 0, spin_budget))
+
+
+def gc_server_state(server) -> dict:
+    """Snapshot of the device-resident request loop and its admission counters."""
+    info = gc_server_info()
+    _check(load().gc_server_state(server, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in gc_server_info._fields_}

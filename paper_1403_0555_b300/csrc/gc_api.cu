@@ -21,6 +21,7 @@
 #include "gc_slab.cuh"
 #include "gc_table.cuh"
 #include "gc_sort.cuh"
+#include "gc_serve.cuh"
 
 namespace {
 
@@ -46,8 +47,36 @@ gc_alloc_fn g_alloc = nullptr;
 gc_free_fn g_free = nullptr;
 void* g_actx = nullptr;
 
+// Serving: while a worker thread runs a request, the device memory it
+// allocates is carved from the region of the server's arena that the
+// device-side admission gave the request (bump allocation, 256-byte aligned;
+// what does not fit comes from the allocator hooks).  Frees of arena memory
+// are no-ops: the region goes back whole when the request is done.
+struct ArenaScope {
+  char* base = nullptr;
+  size_t size = 0, used = 0, overflow = 0;
+};
+thread_local ArenaScope* t_scope = nullptr;
+std::mutex g_arena_mu;
+std::vector<std::pair<char*, size_t>> g_arenas;
+
+bool in_arena(const void* p) {
+  std::lock_guard<std::mutex> lk(g_arena_mu);
+  for (const auto& a : g_arenas)
+    if ((const char*)p >= a.first && (const char*)p < a.first + a.second) return true;
+  return false;
+}
+
 void* dev_alloc(size_t n, cudaStream_t s) {
   if (n == 0) n = 16;
+  if (t_scope) {
+    const size_t off = (t_scope->used + 255) & ~size_t(255);
+    if (off + n <= t_scope->size) {
+      t_scope->used = off + n;
+      return t_scope->base + off;
+    }
+    t_scope->overflow += n;
+  }
   if (g_alloc) return g_alloc(n, (void*)s, g_actx);
   void* p = nullptr;
   if (cudaMalloc(&p, n) != cudaSuccess) { cudaGetLastError(); return nullptr; }
@@ -55,6 +84,7 @@ void* dev_alloc(size_t n, cudaStream_t s) {
 }
 void dev_free(void* p, cudaStream_t s) {
   if (!p) return;
+  if (in_arena(p)) return;
   if (g_free) g_free(p, (void*)s, g_actx);
   else cudaFree(p);
 }
@@ -2178,20 +2208,23 @@ extern "C" int gc_autotune(gc_orbit o, int precision, int* r_warps, int* p_warps
 // ---------------------------------------------------------------------------
 // Serving: continuous batching of enumeration requests
 // ---------------------------------------------------------------------------
-// Requests (an orbit and a start count) queue in arrival order.  Worker
-// threads, each with its own stream, take the head request whenever the
-// device-memory budget admits it, so requests that arrive while others run
-// start as soon as resources free up and their kernels overlap on the GPU.
-// A request's state (links, copy table, staging) lives on the device for its
-// whole life; its result is the orbit itself, handed to the caller.  Results
-// do not depend on the mix: a request touches only its own orbit object, and
-// every kernel's per-start arithmetic and the dedup outcome are independent of
-// what else runs.
+// Requests (an orbit and a start count) go through a mailbox to the
+// device-resident request loop (gc_serve.cuh), which admits them in arrival
+// order as soon as a region of the server's device arena fits their memory
+// estimate.  Worker threads, each with its own stream, run the admitted
+// requests with every device allocation carved from the request's region, so
+// requests that arrive while others run start as memory frees up and their
+// kernels overlap on the GPU.  When a request is done its results (the copy
+// table and the links) move out of the arena and the region is mailed back;
+// its result is the orbit itself, handed to the caller.  Results do not depend
+// on the mix: a request touches only its own orbit object, and every kernel's
+// per-start arithmetic and the dedup outcome are independent of what else runs.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <map>
 #include <thread>
+#include <atomic>
 
 namespace {
 
@@ -2203,8 +2236,9 @@ struct Request {
   std::vector<double> phi;
   uint64_t orbit_id = 0, n = 0;
   double omega = 1.7, eps = 1e-24;
-  size_t bytes = 0;            // admitted device memory estimate
-  Clock::time_point submitted, finished;
+  size_t bytes = 0;            // device memory estimate (the admitted region's size)
+  size_t offset = 0;           // the admitted region's offset in the arena
+  Clock::time_point submitted, admitted, finished;
   int status = GC_OK;
   std::string message;
   bool done = false;
@@ -2232,23 +2266,130 @@ size_t request_bytes(int dim, int L, uint64_t n, int precision) {
     const double fp = (double)gc::slab_fp_scratch_bytes<double>(dim, Vi);
     extra = sm_count() * std::max(newton, fp) + batch * 8;
   }
-  return (size_t)(V * dim * 24 + cap * per_copy + batch * per_start + extra + (1 << 20));
+  const double b = V * dim * 24 + cap * per_copy + batch * per_start + extra + (1 << 20);
+  return ((size_t)b + 4095) & ~size_t(4095);
+}
+
+// Move an orbit's long-lived buffers out of a server arena (after its request
+// ran there) into memory of the allocator hooks, and drop its staging, so the
+// region can go back while the caller keeps the orbit.
+int rehome_orbit(gc_orbit o, cudaStream_t s) {
+  for (Buf* b : {&o->links64, &o->links32, &o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_count,
+                 &o->t_next, &o->t_lam, &o->t_region, &o->t_head, &o->t_lock, &o->t_f8, &o->t_f8n,
+                 &o->t_counters, &o->t_newlist, &o->work, &o->stats}) {
+    if (!b->p || !in_arena(b->p)) continue;
+    Buf nb;
+    if (!nb.ensure(b->n, s)) return fail(GC_ENOMEM, "cannot move a served orbit's results (%zu bytes)", b->n);
+    GC_CUDA(cudaMemcpyAsync(nb.p, b->p, b->n, cudaMemcpyDeviceToDevice, s));
+    *b = nb;
+  }
+  for (Buf* b : {&o->s_status, &o->s_sweeps, &o->s_resid, &o->s_F, &o->s_fprint, &o->s_config, &o->s_state32,
+                 &o->s_copy, &o->s_redo, &o->s_rate, &o->scratch, &o->theta_tmp, &o->sort_keys, &o->sort_idx,
+                 &o->sort_tmp, &o->f8_tmp})
+    b->release(s);
+  GC_CUDA(cudaStreamSynchronize(s));
+  return GC_OK;
 }
 
 }  // namespace
 
+// Serving: the host side of the device-resident request loop (gc_serve.cuh).
+//   submit  -> mailbox (pinned) -> serve_loop_kernel admits by the device-side
+//   budget -> completion ring (pinned) -> dispatcher thread -> a worker runs
+//   the request in its admitted region -> results moved out -> region mailed
+//   back.
 struct gc_server_s {
   gc_options opt{};
-  size_t budget = 0, in_use = 0;
+  size_t budget = 0;
   int device = 0;
-  std::mutex mu;
+  char* arena = nullptr;
+  gc::ServeHostShared* H = nullptr;   // host view of the pinned block
+  gc::ServeHostShared* Hd = nullptr;  // its device address
+  gc::ServeDevState* D = nullptr;     // device memory
+  cudaStream_t loop_stream = nullptr, ctl_stream = nullptr;
+  long long idle_limit = 10000;       // polls; with 20 us sleeps about 0.2 s idle
+  unsigned sleep_ns = 20000;
+  uint64_t loop_launches = 0;
+  std::mutex mu;                      // requests, tickets, mailbox writes
   std::condition_variable cv_work, cv_done;
-  std::deque<std::shared_ptr<Request>> queue;
+  std::deque<std::shared_ptr<Request>> ready;          // admitted, waiting for a worker
   std::map<uint64_t, std::shared_ptr<Request>> all;
   uint64_t next_ticket = 1;
-  bool stopping = false;
+  bool stopping = false, dispatcher_stop = false;
   std::vector<std::thread> workers;
+  std::thread dispatcher;
   std::vector<cudaStream_t> streams;
+
+  static volatile int* vstatus(gc::ServeHostShared* h) { return reinterpret_cast<volatile int*>(&h->loop_status); }
+
+  int launch_loop() {
+    *vstatus(H) = gc::kLoopRunning;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    gc::serve_loop_kernel<<<1, 32, 0, loop_stream>>>(Hd, D, idle_limit, sleep_ns);
+    ++loop_launches;
+    GC_CUDA(cudaGetLastError());
+    return GC_OK;
+  }
+
+  // Write one mailbox entry (caller holds mu) and make sure a loop will read it.
+  int mail(unsigned op, uint64_t ticket, uint64_t bytes) {
+    volatile unsigned long long* head = &H->mail_head;
+    volatile unsigned long long* tail = &H->mail_tail;
+    for (long long spins = 0; *head - *tail >= gc::kMailSlots; ++spins) {   // ring full (bounded)
+      if (spins > 2000000) return fail(GC_ETIMEDOUT, "serving mailbox full");
+      std::this_thread::sleep_for(std::chrono::microseconds(5));
+    }
+    const unsigned long long h = *head;
+    volatile gc::MailEntry* e = &H->mail[h % gc::kMailSlots];
+    e->ticket = ticket;
+    e->bytes = bytes;
+    e->op = op;
+    std::atomic_thread_fence(std::memory_order_release);
+    *head = h + 1;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    // the loop reads this mail unless it had already decided to end; then
+    // start it again (kLoopExiting resolves within one poll)
+    int st = *vstatus(H);
+    for (long long spins = 0; st == gc::kLoopExiting && spins < 2000000; ++spins) {
+      std::this_thread::sleep_for(std::chrono::microseconds(1));
+      st = *vstatus(H);
+    }
+    if (st == gc::kLoopStopped || st == gc::kLoopTimedOut || st == gc::kLoopExiting) return launch_loop();
+    return GC_OK;
+  }
+
+  void dispatch() {
+    cudaSetDevice(device);
+    volatile unsigned long long* dhead = &H->done_head;
+    volatile unsigned long long* dtail = &H->done_tail;
+    for (;;) {
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dispatcher_stop) return;
+      }
+      const unsigned long long dh = *dhead;
+      std::atomic_thread_fence(std::memory_order_acquire);
+      unsigned long long t = *dtail;
+      if (t == dh) {
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+        continue;
+      }
+      for (; t < dh; ++t) {
+        volatile gc::DoneEntry* e = &H->done[t % gc::kMailSlots];
+        const uint64_t ticket = e->ticket, off = e->offset;
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = all.find(ticket);
+        if (it != all.end()) {
+          it->second->offset = off;
+          it->second->admitted = Clock::now();
+          ready.push_back(it->second);
+        }
+      }
+      std::atomic_thread_fence(std::memory_order_release);
+      *dtail = dh;
+      cv_work.notify_all();
+    }
+  }
 
   void worker(int k) {
     cudaSetDevice(device);
@@ -2256,34 +2397,33 @@ struct gc_server_s {
       std::shared_ptr<Request> r;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv_work.wait(lk, [&] {
-          return stopping || (!queue.empty() && in_use + queue.front()->bytes <= budget);
-        });
-        if (stopping && queue.empty()) return;
-        if (queue.empty() || in_use + queue.front()->bytes > budget) continue;
-        r = queue.front();
-        queue.pop_front();
-        in_use += r->bytes;
+        cv_work.wait(lk, [&] { return stopping || !ready.empty(); });
+        if (ready.empty()) {
+          if (stopping) return;
+          continue;
+        }
+        r = ready.front();
+        ready.pop_front();
       }
-      cv_work.notify_all();
       gc_options o = opt;
       o.stream = streams[k];
       o.keep_per_start = 0;
+      ArenaScope scope;
+      scope.base = arena + r->offset;
+      scope.size = r->bytes;
+      t_scope = &scope;
       gc_orbit orb = nullptr;
       int rc = gc_create_orbit(r->dim, r->L, r->phi.data(), r->orbit_id, 0, &orb);
       if (rc == GC_OK) rc = gc_enumerate_copies(orb, r->n, r->omega, r->eps, &o);
+      t_scope = nullptr;
+      if (rc == GC_OK) rc = rehome_orbit(orb, streams[k]);
       std::string msg = rc == GC_OK ? "" : gc_last_error();
-      if (orb) {
-        // keep the results (copy table), release the staging of the batches
-        for (Buf* b : {&orb->s_status, &orb->s_sweeps, &orb->s_resid, &orb->s_F, &orb->s_fprint,
-                       &orb->s_config, &orb->s_state32, &orb->s_copy, &orb->s_redo, &orb->s_rate, &orb->scratch})
-          b->release(streams[k]);
-        cudaStreamSynchronize(streams[k]);
-      }
       if (rc != GC_OK && orb) {
+        cudaStreamSynchronize(streams[k]);
         gc_destroy_orbit(orb);
         orb = nullptr;
       }
+      cudaStreamSynchronize(streams[k]);   // nothing of the request still uses its region
       {
         std::lock_guard<std::mutex> lk(mu);
         r->status = rc;
@@ -2291,10 +2431,9 @@ struct gc_server_s {
         r->orbit = orb;
         r->finished = Clock::now();
         r->done = true;
-        in_use -= r->bytes;
+        mail(gc::kMailFree, r->ticket, r->offset);
       }
       cv_done.notify_all();
-      cv_work.notify_all();
     }
   }
 };
@@ -2310,14 +2449,58 @@ extern "C" int gc_server_create(int workers, size_t mem_budget_bytes, const gc_o
   if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return fail(GC_ECUDA, "no CUDA device"); }
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
-  s->budget = mem_budget_bytes ? mem_budget_bytes : free_b / 2;
+  s->budget = mem_budget_bytes ? mem_budget_bytes : std::min<size_t>(free_b / 2, 16ull << 30);
+  s->budget &= ~size_t(4095);
+  auto undo = [&](int rc) {
+    if (s->loop_stream) cudaStreamDestroy(s->loop_stream);
+    if (s->ctl_stream) cudaStreamDestroy(s->ctl_stream);
+    if (s->H) cudaFreeHost(s->H);
+    if (s->D) cudaFree(s->D);
+    if (s->arena) {
+      {
+        std::lock_guard<std::mutex> lk(g_arena_mu);
+        for (size_t i = 0; i < g_arenas.size(); ++i)
+          if (g_arenas[i].first == s->arena) { g_arenas.erase(g_arenas.begin() + i); break; }
+      }
+      dev_free(s->arena, nullptr);
+    }
+    delete s;
+    return rc;
+  };
+  if (cudaStreamCreateWithFlags(&s->loop_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->ctl_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return undo(fail(GC_ECUDA, "cudaStreamCreate failed"));
+  s->arena = static_cast<char*>(dev_alloc(s->budget, s->ctl_stream));
+  if (!s->arena) return undo(fail(GC_ENOMEM, "cannot allocate the serving arena (%.1f MiB)", s->budget / 1048576.0));
+  if (cudaHostAlloc((void**)&s->H, sizeof(gc::ServeHostShared), cudaHostAllocMapped) != cudaSuccess) {
+    s->H = nullptr;
+    return undo(fail(GC_ENOMEM, "cannot allocate the pinned mailbox"));
+  }
+  std::memset((void*)s->H, 0, sizeof(gc::ServeHostShared));
+  s->H->loop_status = gc::kLoopStopped;
+  if (cudaHostGetDevicePointer((void**)&s->Hd, s->H, 0) != cudaSuccess)
+    return undo(fail(GC_ECUDA, "the mailbox is not mapped into the device"));
+  if (cudaMalloc((void**)&s->D, sizeof(gc::ServeDevState)) != cudaSuccess) {
+    s->D = nullptr;
+    return undo(fail(GC_ENOMEM, "cannot allocate the serving state"));
+  }
+  gc::serve_init_kernel<<<1, 32, 0, s->ctl_stream>>>(s->D, (unsigned long long)s->budget);
+  if (cudaStreamSynchronize(s->ctl_stream) != cudaSuccess) return undo(fail(GC_ECUDA, "serve_init_kernel failed"));
+  {
+    std::lock_guard<std::mutex> lk(g_arena_mu);
+    g_arenas.emplace_back(s->arena, s->budget);
+  }
   s->streams.resize(workers);
   for (int k = 0; k < workers; ++k)
     if (cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) != cudaSuccess) {
       for (int j = 0; j < k; ++j) cudaStreamDestroy(s->streams[j]);
-      delete s;
-      return fail(GC_ECUDA, "cudaStreamCreate failed");
+      return undo(fail(GC_ECUDA, "cudaStreamCreate failed"));
     }
+  if (int rc = s->launch_loop()) {
+    for (auto st : s->streams) cudaStreamDestroy(st);
+    return undo(rc);
+  }
+  s->dispatcher = std::thread(&gc_server_s::dispatch, s);
   for (int k = 0; k < workers; ++k) s->workers.emplace_back(&gc_server_s::worker, s, k);
   *out = s;
   return GC_OK;
@@ -2329,7 +2512,7 @@ extern "C" int gc_server_submit(gc_server s, int dim, int L, const double* link_
   if (dim < 1 || dim > gc::kMaxDim || L < 2) return fail(GC_EINVAL, "bad lattice %d^%d", L, dim);
   if (!(omega > 0.0 && omega < 2.0) || !(eps > 0.0)) return fail(GC_EINVAL, "bad omega or eps");
   const double Vd = std::pow((double)L, dim);
-  if (Vd > gc::kMaxSites) return fail(GC_EINVAL, "lattice of %.0f sites exceeds %d", Vd, gc::kMaxSites);
+  if (Vd > gc::kMaxSlabSites) return fail(GC_EINVAL, "lattice of %.0f sites exceeds %d", Vd, gc::kMaxSlabSites);
   auto r = std::make_shared<Request>();
   r->dim = dim; r->L = L; r->orbit_id = orbit_id; r->n = n_starts; r->omega = omega; r->eps = eps;
   r->phi.assign(link_angles, link_angles + (size_t)Vd * dim);
@@ -2337,16 +2520,16 @@ extern "C" int gc_server_submit(gc_server s, int dim, int L, const double* link_
   if (r->bytes > s->budget)
     return fail(GC_ENOMEM, "request needs ~%.1f MiB, above the %.1f MiB budget", r->bytes / 1048576.0,
                 s->budget / 1048576.0);
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (s->stopping) return fail(GC_ESTATE, "server is shutting down");
-    r->ticket = s->next_ticket++;
-    r->submitted = Clock::now();
-    s->queue.push_back(r);
-    s->all[r->ticket] = r;
-    *ticket = r->ticket;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stopping) return fail(GC_ESTATE, "server is shutting down");
+  r->ticket = s->next_ticket++;
+  r->submitted = Clock::now();
+  s->all[r->ticket] = r;
+  *ticket = r->ticket;
+  if (int rc = s->mail(gc::kMailAdmit, r->ticket, r->bytes)) {
+    s->all.erase(r->ticket);
+    return rc;
   }
-  s->cv_work.notify_all();
   return GC_OK;
 }
 
@@ -2371,17 +2554,60 @@ extern "C" int gc_server_wait(gc_server s, uint64_t ticket, double timeout_s, in
   return GC_OK;
 }
 
+extern "C" int gc_server_state(gc_server s, gc_server_info* out) {
+  if (!s || !out) return fail(GC_EINVAL, "gc_server_state: NULL argument");
+  std::memset(out, 0, sizeof *out);
+  gc::ServeDevState snap;
+  // the loop may be running: the copy is a snapshot
+  GC_CUDA(cudaMemcpyAsync(&snap, s->D, sizeof snap, cudaMemcpyDeviceToHost, s->ctl_stream));
+  GC_CUDA(cudaStreamSynchronize(s->ctl_stream));
+  const int st = *gc_server_s::vstatus(s->H);
+  out->loop_status = st == gc::kLoopTimedOut ? GC_ETIMEDOUT : GC_OK;
+  out->loop_running = (st == gc::kLoopRunning || st == gc::kLoopExiting) ? 1 : 0;
+  out->loop_launches = s->loop_launches;
+  out->admitted = snap.admitted;
+  out->released = snap.freed;
+  out->waiting = snap.wait_tail - snap.wait_head;
+  out->bytes_in_use = snap.in_use;
+  out->budget_bytes = s->budget;
+  out->regions = snap.n_regions;
+  return GC_OK;
+}
+
 extern "C" int gc_server_destroy(gc_server s) {
   if (!s) return fail(GC_EINVAL, "gc_server_destroy: NULL server");
+  // finish every submitted request (they are admitted as regions free up)
   {
-    std::lock_guard<std::mutex> lk(s->mu);
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv_done.wait(lk, [&] {
+      for (auto& kv : s->all)
+        if (!kv.second->done) return false;
+      return true;
+    });
     s->stopping = true;
+    s->mail(gc::kMailStop, 0, 0);
   }
   s->cv_work.notify_all();
   for (auto& t : s->workers) t.join();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->dispatcher_stop = true;
+  }
+  s->dispatcher.join();
+  cudaStreamSynchronize(s->loop_stream);     // the loop ends on the stop mail (bounded by its idle limit)
   for (auto& kv : s->all)
     if (kv.second->orbit) gc_destroy_orbit(kv.second->orbit);
   for (auto st : s->streams) cudaStreamDestroy(st);
+  cudaStreamDestroy(s->loop_stream);
+  cudaStreamDestroy(s->ctl_stream);
+  cudaFreeHost(s->H);
+  cudaFree(s->D);
+  {
+    std::lock_guard<std::mutex> lk(g_arena_mu);
+    for (size_t i = 0; i < g_arenas.size(); ++i)
+      if (g_arenas[i].first == s->arena) { g_arenas.erase(g_arenas.begin() + i); break; }
+  }
+  dev_free(s->arena, nullptr);
   delete s;
   return GC_OK;
 }

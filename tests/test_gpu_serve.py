@@ -85,3 +85,69 @@ def test_concurrent_shapes_of_one_dimension_all_succeed():
             gb.gc_destroy_orbit(orb)
     finally:
         gb.gc_server_destroy(srv)
+
+
+def test_device_loop_admits_by_budget_and_times_out_when_idle():
+    """The request loop runs on the GPU: with an arena for about one and a half
+    requests, admissions wait for regions to come back (never more bytes in use
+    than the budget, some requests waiting), every request completes with the
+    result it has alone, every region comes back; after about 0.2 s without
+    work the loop's launch ends with GC_ETIMEDOUT, and the next request starts
+    it again."""
+    import paper_1403_0555_b300 as gb
+    d, L, n = 4, 4, 40_000
+    opt = gb.gc_options_default(precision=1, check_every=4)
+    phi = oi.von_mises_orbit(d, L, 1.0, 7)
+    # the estimate of one request: the smallest budget that takes it (bisection in MiB)
+    def takes(mib):
+        srv = gb.gc_server_create(1, mib << 20, opt)
+        try:
+            gb.gc_server_submit(srv, d, L, phi, 7, n)
+            return True
+        except gb.GribovError as e:
+            assert e.code == gb.GC_ENOMEM
+            return False
+        finally:
+            gb.gc_server_destroy(srv)
+    lo, hi = 1, 4096
+    assert takes(hi) and not takes(lo)
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        lo, hi = (lo, mid) if takes(mid) else (mid, hi)
+    est = hi << 20
+    srv = gb.gc_server_create(4, est * 3 // 2, opt)
+    try:
+        tickets = [(gb.gc_server_submit(srv, d, L, oi.von_mises_orbit(d, L, 1.0, 30 + i), 30 + i, n), i)
+                   for i in range(6)]
+        seen_waiting = 0
+        for _ in range(200):
+            s = gb.gc_server_state(srv)
+            assert s["bytes_in_use"] <= s["budget_bytes"]
+            seen_waiting = max(seen_waiting, s["waiting"])
+            if s["admitted"] == len(tickets):
+                break
+            time.sleep(0.005)
+        assert seen_waiting >= 1
+        for t, i in tickets:
+            status, latency, orb = gb.gc_server_wait(srv, t, 120.0)
+            assert status == gb.GC_OK and orb is not None
+            served = gb.gc_fetch_copies(orb, L ** d)
+            gb.gc_destroy_orbit(orb)
+            _, alone, _ = run_gpu(d, L, oi.von_mises_orbit(d, L, 1.0, 30 + i), 30 + i, n, keep_per_start=0,
+                                  precision=1, check_every=4)
+            for k in ("F", "first_start", "count", "region", "lambda2", "theta"):
+                assert np.array_equal(served[k], alone[k]), k
+        time.sleep(0.2)
+        s = gb.gc_server_state(srv)
+        assert s["admitted"] == 6 and s["released"] == 6 and s["bytes_in_use"] == 0 and s["waiting"] == 0
+        time.sleep(0.6)                                   # idle: the loop's launch ends
+        s = gb.gc_server_state(srv)
+        assert s["loop_running"] == 0 and s["loop_status"] == gb.GC_ETIMEDOUT
+        launches = s["loop_launches"]
+        t = gb.gc_server_submit(srv, d, L, oi.von_mises_orbit(d, L, 1.0, 40), 40, 5000)
+        status, latency, orb = gb.gc_server_wait(srv, t, 120.0, keep_orbit=False)
+        assert status == gb.GC_OK
+        s = gb.gc_server_state(srv)
+        assert s["loop_launches"] == launches + 1 and s["admitted"] == 7
+    finally:
+        gb.gc_server_destroy(srv)
