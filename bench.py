@@ -357,30 +357,41 @@ def serve_leg(gb, n_requests, opt, rate_hz=200.0, workers=16, seed=7):
     done = threading.Event()
 
     def collector():
-        i = 0
+        # collect in completion order (a result held until an earlier, longer
+        # request finishes would keep its copy table on the device)
+        outstanding = []
+        seen = 0
         while True:
             with lock:
-                have = i < len(tickets)
-                t = tickets[i] if have else None
-            if not have:
+                outstanding += tickets[seen:]
+                seen = len(tickets)
+            if not outstanding:
                 if done.is_set():
                     with lock:
-                        if i >= len(tickets):
+                        if seen == len(tickets):
                             return
-                    continue
                 time.sleep(0.0005)
                 continue
-            status, latency, orb = gb.gc_server_wait(srv, t[0], -1.0)
-            if status != 0:
-                r = t[1]
-                failures.append(f"{r.d}D L={r.L} n={r.n_starts}: {gb.gc_last_error()}")
-            conv = upd = 0
-            if orb is not None:
-                st = gb.gc_orbit_stats(orb)
-                conv, upd = st["n_converged"], st["site_updates_fp32"] + st["site_updates_fp64"]
-                gb.gc_destroy_orbit(orb)
-            results.append((status, latency, conv, upd, time.perf_counter()))
-            i += 1
+            keep = []
+            for t in outstanding:
+                try:
+                    status, latency, orb = gb.gc_server_wait(srv, t[0], 0.0)
+                except gb.GribovError as e:
+                    if e.code == gb.GC_ETIMEDOUT:
+                        keep.append(t)
+                        continue
+                    raise
+                if status != 0:
+                    r = t[1]
+                    failures.append(f"{r.d}D L={r.L} n={r.n_starts}: {gb.gc_last_error()}")
+                conv = upd = 0
+                if orb is not None:
+                    st = gb.gc_orbit_stats(orb)
+                    conv, upd = st["n_converged"], st["site_updates_fp32"] + st["site_updates_fp64"]
+                    gb.gc_destroy_orbit(orb)
+                results.append((status, latency, conv, upd, time.perf_counter()))
+            outstanding = keep
+            time.sleep(0.001)
 
     th = threading.Thread(target=collector)
     th.start()

@@ -187,11 +187,13 @@ int gc_autotune_ex(gc_orbit o, int precision, int mode, int* r_warps, int* p_war
                    int* f_warps, int* check_every);
 
 /* Serving with continuous batching and device-side admission.  The server
- * owns a device arena of mem_budget_bytes (0 = half the free device memory,
- * at most 16 GiB) and a request loop resident on the GPU: one warp that polls
+ * owns a device arena of mem_budget_bytes (0 = half the device's memory,
+ * halved until the allocator gives it) and a request loop resident on the
+ * GPU: one warp that polls
  * a mailbox in pinned memory, keeps the queue of waiting requests and the
  * arena's region table in device memory, and admits requests in arrival
- * order as soon as a free region fits their device-memory estimate.  Each
+ * order as soon as a free region fits their device-memory need (links,
+ * a copy pool reserved for n_starts copies, one staging batch).  Each
  * admitted request runs on one of `workers` host threads (each on its own
  * stream) with all of its device state carved from its region, so requests
  * that arrive while others run are admitted as memory frees up and their

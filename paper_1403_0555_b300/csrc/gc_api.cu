@@ -207,7 +207,14 @@ struct gc_orbit_s {
     return T;
   }
   long long lock_spins = gc::kLockSpins;   // gc_test_dedup_locks lowers it
+  // an orbit a server ran: its results live in the region the server admitted
+  // (offset region_off of its arena) until the orbit is destroyed
+  gc_server_s* served_by = nullptr;
+  uint64_t region_off = 0;
 };
+
+// Serving (defined with the server): mail a served orbit's region back
+void server_release_region(gc_orbit o);
 
 namespace {
 
@@ -253,9 +260,12 @@ __global__ void f8_compact_kernel(const unsigned long long* set, const unsigned 
 }
 
 // Grow (or create) the copy pool so that it holds at least `need` entries.
-int table_reserve(gc_orbit o, unsigned long long need, unsigned cur, cudaStream_t s) {
-  if (need <= o->cap && o->cap) return GC_OK;
-  unsigned long long want = std::max<unsigned long long>(need, o->cap ? 2ULL * o->cap : 1024ULL);
+// exact: a pool of exactly max(need, 1024) entries even when smaller than the
+// current one (moving a served orbit's table out of the serving arena).
+int table_reserve(gc_orbit o, unsigned long long need, unsigned cur, cudaStream_t s, bool exact = false) {
+  if (!exact && need <= o->cap && o->cap) return GC_OK;
+  unsigned long long want = exact ? std::max<unsigned long long>(need, 1024ULL)
+                                  : std::max<unsigned long long>(need, o->cap ? 2ULL * o->cap : 1024ULL);
   if (want > 0x7fffffffULL) return fail(GC_ENOMEM, "copy pool would exceed 2^31 entries");
   const unsigned ncap = (unsigned)want;
   const size_t V = o->V;
@@ -522,6 +532,7 @@ int gc_destroy_orbit(gc_orbit o) {
   for (auto& e : o->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : o->ev_pool) cudaEventDestroy(e);
+  if (o->served_by) server_release_region(o);   // its results' region goes back to the server
   delete o;
   return GC_OK;
 }
@@ -2225,6 +2236,7 @@ extern "C" int gc_autotune(gc_orbit o, int precision, int* r_warps, int* p_warps
 #include <map>
 #include <thread>
 #include <atomic>
+#include <set>
 
 namespace {
 
@@ -2245,18 +2257,22 @@ struct Request {
   gc_orbit orbit = nullptr;
 };
 
-// Device bytes a request holds while it runs: links, a copy pool sized for
-// min(n, 65536) copies (it grows on demand), the quantised-minimum set,
-// buckets and one staging batch; beyond shared memory (the hyperplane path,
-// the same test as gc_create_orbit's) also the per-SM scratch of the Newton
-// polish and of the first-region test.
-size_t request_bytes(int dim, int L, uint64_t n, int precision) {
+// Device bytes a request holds while it runs, as the library allocates them:
+// the links (FP64 and FP32), a copy pool reserved for n copies (every start
+// may find a new one; the worker creates the orbit with max_copies = n so the
+// pool never grows), its buckets and the paper-style F set (table_reserve's
+// sizes), locks and counters, and one staging batch; beyond shared memory (the
+// hyperplane path, the same test as gc_create_orbit's) also the per-SM
+// scratch of the Newton polish and of the first-region test.  The dense
+// first-region test adds its basis slots (at most 1 GiB).
+size_t request_bytes(int dim, int L, uint64_t n, int precision, int fp_mode) {
   const double V = std::pow((double)L, dim);
-  const double cap = (double)std::min<uint64_t>(n, 65536);
-  const double per_copy = V * 16 + 64 + 4 * 8 + 2 * 4;
+  const double cap = (double)std::max<uint64_t>(n, 1024);
+  const double pool = cap * (V * 16 + 8 + 8 + 4 + 8 + 8 + 4 + 8 + 4 + 8) +
+                      (double)next_pow2(2ull * (uint64_t)cap) * 4 + (double)next_pow2(4ull * (uint64_t)cap) * 16;
   const double per_start = V * 16 + (precision == GC_MIXED ? V * 8 : 0) + 48;
   double batch = std::min((double)n, std::max(4096.0, (double)(1ull << 30) / per_start));
-  double extra = 0.0;
+  double extra = fp_mode == GC_FP_DENSE ? (double)(1ull << 30) : 0.0;
   const int Vi = (int)V;
   if (V <= gc::kMaxSlabSites &&
       (Vi > gc::kMaxSites || gc::Smem(Vi, dim, 16, (size_t)Vi * 16, 1).total > max_smem_optin())) {
@@ -2264,16 +2280,25 @@ size_t request_bytes(int dim, int L, uint64_t n, int precision) {
     const int Ps = (Vi / L + 3) / 4 * 4;
     const double newton = precision == GC_MIXED ? (double)gc::slab_newton_scratch_floats(dim, Vi, L, Ps) * 4 : 0.0;
     const double fp = (double)gc::slab_fp_scratch_bytes<double>(dim, Vi);
-    extra = sm_count() * std::max(newton, fp) + batch * 8;
+    extra = sm_count() * std::max(newton, fp) + batch * 8 + batch * 4;
   }
-  const double b = V * dim * 24 + cap * per_copy + batch * per_start + extra + (1 << 20);
+  const double b = V * dim * 24 + pool + batch * per_start + extra + (1u << 16) * 4 + (4 << 20);
   return ((size_t)b + 4095) & ~size_t(4095);
 }
 
 // Move an orbit's long-lived buffers out of a server arena (after its request
 // ran there) into memory of the allocator hooks, and drop its staging, so the
-// region can go back while the caller keeps the orbit.
+// region can go back while the caller keeps the orbit.  The copy table moves
+// at the size it uses (table_reserve with exact capacity: entries copied,
+// buckets re-threaded, the F set rehashed).
 int rehome_orbit(gc_orbit o, cudaStream_t s) {
+  GC_CUDA(cudaStreamSynchronize(s));
+  if (o->t_cfg.p && in_arena(o->t_cfg.p)) {
+    unsigned cur = 0;
+    GC_CUDA(cudaMemcpy(&cur, o->n_entries(), 4, cudaMemcpyDeviceToHost));
+    cur = std::min(cur, o->cap);
+    if (int rc = table_reserve(o, cur, cur, s, true)) return rc;
+  }
   for (Buf* b : {&o->links64, &o->links32, &o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_count,
                  &o->t_next, &o->t_lam, &o->t_region, &o->t_head, &o->t_lock, &o->t_f8, &o->t_f8n,
                  &o->t_counters, &o->t_newlist, &o->work, &o->stats}) {
@@ -2319,6 +2344,7 @@ struct gc_server_s {
   std::vector<std::thread> workers;
   std::thread dispatcher;
   std::vector<cudaStream_t> streams;
+  std::set<gc_orbit> live;            // finished orbits whose results hold a region
 
   static volatile int* vstatus(gc::ServeHostShared* h) { return reinterpret_cast<volatile int*>(&h->loop_status); }
 
@@ -2413,17 +2439,22 @@ struct gc_server_s {
       scope.size = r->bytes;
       t_scope = &scope;
       gc_orbit orb = nullptr;
-      int rc = gc_create_orbit(r->dim, r->L, r->phi.data(), r->orbit_id, 0, &orb);
+      int rc = gc_create_orbit(r->dim, r->L, r->phi.data(), r->orbit_id, r->n, &orb);
       if (rc == GC_OK) rc = gc_enumerate_copies(orb, r->n, r->omega, r->eps, &o);
       t_scope = nullptr;
-      if (rc == GC_OK) rc = rehome_orbit(orb, streams[k]);
       std::string msg = rc == GC_OK ? "" : gc_last_error();
+      cudaStreamSynchronize(streams[k]);
       if (rc != GC_OK && orb) {
-        cudaStreamSynchronize(streams[k]);
         gc_destroy_orbit(orb);
         orb = nullptr;
       }
-      cudaStreamSynchronize(streams[k]);   // nothing of the request still uses its region
+      if (orb) {
+        // the staging goes (later allocations of the orbit, e.g. a fetch's,
+        // come from the allocator hooks); the results stay in the region
+        for (Buf* b : {&orb->s_status, &orb->s_sweeps, &orb->s_resid, &orb->s_F, &orb->s_fprint, &orb->s_config,
+                       &orb->s_state32, &orb->s_copy, &orb->s_redo, &orb->s_rate, &orb->scratch, &orb->theta_tmp})
+          b->release(streams[k]);
+      }
       {
         std::lock_guard<std::mutex> lk(mu);
         r->status = rc;
@@ -2431,12 +2462,30 @@ struct gc_server_s {
         r->orbit = orb;
         r->finished = Clock::now();
         r->done = true;
-        mail(gc::kMailFree, r->ticket, r->offset);
+        if (orb) {
+          orb->served_by = this;
+          orb->region_off = r->offset;
+          live.insert(orb);
+        } else {
+          mail(gc::kMailFree, r->ticket, r->offset);
+        }
       }
       cv_done.notify_all();
     }
   }
 };
+
+std::mutex g_srv_mu;                  // live servers (a served orbit may outlive its server's handle use)
+std::set<gc_server_s*> g_servers;
+
+void server_release_region(gc_orbit o) {
+  std::lock_guard<std::mutex> g(g_srv_mu);
+  gc_server_s* s = o->served_by;
+  o->served_by = nullptr;
+  if (!s || !g_servers.count(s)) return;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->live.erase(o)) s->mail(gc::kMailFree, 0, o->region_off);
+}
 
 extern "C" int gc_server_create(int workers, size_t mem_budget_bytes, const gc_options* opt, gc_server* out) {
   if (!out) return fail(GC_EINVAL, "gc_server_create: out is NULL");
@@ -2449,7 +2498,9 @@ extern "C" int gc_server_create(int workers, size_t mem_budget_bytes, const gc_o
   if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return fail(GC_ECUDA, "no CUDA device"); }
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
-  s->budget = mem_budget_bytes ? mem_budget_bytes : std::min<size_t>(free_b / 2, 16ull << 30);
+  // default: half the device, at most 16 GiB, halved until the allocator
+  // gives it (free memory is not a guide when a caching allocator holds it)
+  s->budget = mem_budget_bytes ? mem_budget_bytes : total_b / 2;
   s->budget &= ~size_t(4095);
   auto undo = [&](int rc) {
     if (s->loop_stream) cudaStreamDestroy(s->loop_stream);
@@ -2471,6 +2522,10 @@ extern "C" int gc_server_create(int workers, size_t mem_budget_bytes, const gc_o
       cudaStreamCreateWithFlags(&s->ctl_stream, cudaStreamNonBlocking) != cudaSuccess)
     return undo(fail(GC_ECUDA, "cudaStreamCreate failed"));
   s->arena = static_cast<char*>(dev_alloc(s->budget, s->ctl_stream));
+  while (!s->arena && !mem_budget_bytes && s->budget > (256ull << 20)) {
+    s->budget = (s->budget / 2) & ~size_t(4095);
+    s->arena = static_cast<char*>(dev_alloc(s->budget, s->ctl_stream));
+  }
   if (!s->arena) return undo(fail(GC_ENOMEM, "cannot allocate the serving arena (%.1f MiB)", s->budget / 1048576.0));
   if (cudaHostAlloc((void**)&s->H, sizeof(gc::ServeHostShared), cudaHostAllocMapped) != cudaSuccess) {
     s->H = nullptr;
@@ -2502,6 +2557,10 @@ extern "C" int gc_server_create(int workers, size_t mem_budget_bytes, const gc_o
   }
   s->dispatcher = std::thread(&gc_server_s::dispatch, s);
   for (int k = 0; k < workers; ++k) s->workers.emplace_back(&gc_server_s::worker, s, k);
+  {
+    std::lock_guard<std::mutex> g(g_srv_mu);
+    g_servers.insert(s);
+  }
   *out = s;
   return GC_OK;
 }
@@ -2516,7 +2575,7 @@ extern "C" int gc_server_submit(gc_server s, int dim, int L, const double* link_
   auto r = std::make_shared<Request>();
   r->dim = dim; r->L = L; r->orbit_id = orbit_id; r->n = n_starts; r->omega = omega; r->eps = eps;
   r->phi.assign(link_angles, link_angles + (size_t)Vd * dim);
-  r->bytes = request_bytes(dim, L, n_starts, s->opt.precision);
+  r->bytes = request_bytes(dim, L, n_starts, s->opt.precision, s->opt.fp_mode);
   if (r->bytes > s->budget)
     return fail(GC_ENOMEM, "request needs ~%.1f MiB, above the %.1f MiB budget", r->bytes / 1048576.0,
                 s->budget / 1048576.0);
@@ -2546,11 +2605,14 @@ extern "C" int gc_server_wait(gc_server s, uint64_t ticket, double timeout_s, in
     return fail(GC_ETIMEDOUT, "request %llu not finished within %g s", (unsigned long long)ticket, timeout_s);
   if (status) *status = r->status;
   if (latency_s) *latency_s = std::chrono::duration<double>(r->finished - r->submitted).count();
+  gc_orbit drop = nullptr;
   if (orbit) *orbit = r->orbit;
-  else if (r->orbit) gc_destroy_orbit(r->orbit);
+  else drop = r->orbit;
   r->orbit = nullptr;
   s->all.erase(it);
   if (r->status != GC_OK) g_err = r->message;
+  lk.unlock();
+  if (drop) gc_destroy_orbit(drop);   // mails its region back
   return GC_OK;
 }
 
@@ -2585,18 +2647,36 @@ extern "C" int gc_server_destroy(gc_server s) {
       return true;
     });
     s->stopping = true;
-    s->mail(gc::kMailStop, 0, 0);
   }
   s->cv_work.notify_all();
   for (auto& t : s->workers) t.join();
+  // orbits nobody collected are destroyed; collected orbits still alive move
+  // their results out of the arena (the caller keeps them)
+  std::vector<gc_orbit> uncollected;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto& kv : s->all)
+      if (kv.second->orbit) uncollected.push_back(kv.second->orbit);
+    s->all.clear();
+  }
+  for (gc_orbit o : uncollected) gc_destroy_orbit(o);
+  {
+    std::lock_guard<std::mutex> g(g_srv_mu);
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (gc_orbit o : s->live) {
+      rehome_orbit(o, s->ctl_stream);
+      o->served_by = nullptr;
+    }
+    s->live.clear();
+    g_servers.erase(s);
+    s->mail(gc::kMailStop, 0, 0);
+  }
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->dispatcher_stop = true;
   }
   s->dispatcher.join();
   cudaStreamSynchronize(s->loop_stream);     // the loop ends on the stop mail (bounded by its idle limit)
-  for (auto& kv : s->all)
-    if (kv.second->orbit) gc_destroy_orbit(kv.second->orbit);
   for (auto st : s->streams) cudaStreamDestroy(st);
   cudaStreamDestroy(s->loop_stream);
   cudaStreamDestroy(s->ctl_stream);
