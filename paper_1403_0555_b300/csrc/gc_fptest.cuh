@@ -158,6 +158,7 @@ __device__ R lanczos_min(const R* w, R* vprev, R* vcur, R* z, R* alpha, R* beta,
   const R bound = (R)(4 * DD + 1);
   R b = 0;
   R theta = bound, theta_prev = bound, theta_pp = bound;   // bound = no estimate yet
+  int stalls = 0;
   int j = 0;
   for (; j < kmax; ++j) {
     if (REORTH) {
@@ -220,7 +221,13 @@ __device__ R lanczos_min(const R* w, R* vprev, R* vcur, R* z, R* alpha, R* beta,
       }
       theta = tri_min<R>(alpha, beta, j + 1, lo, hi, lane);
       if (last) { ++j; break; }
-      if (fabs(theta - theta_prev) <= (R)tol * fmax(fabs(theta), (R)1e-3)) { ++j; break; }
+      // stop when the value holds over two checks in a row (16 steps): one
+      // stall can be a plateau above lambda_2 that later steps leave
+      if (fabs(theta - theta_prev) <= (R)tol * fmax(fabs(theta), (R)1e-3)) {
+        if (++stalls == 2) { ++j; break; }
+      } else {
+        stalls = 0;
+      }
       theta_pp = theta_prev;
       theta_prev = theta;
     }

@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(256, 2) fp_screen_pairs_kernel(const FpArgs a)
     const float bound = (float)(4 * D + 1);
     float bprev = 0.f, theta = bound, theta_prev = bound, theta_pp = bound;
     const int kk = V - 1 < kmax ? V - 1 : kmax;
+    int stalls = 0;
     int j = 0;
     for (; j < kk; ++j) {
       // z = M v - b v_prev, alpha = z . v
@@ -220,7 +221,12 @@ __global__ void __launch_bounds__(256, 2) fp_screen_pairs_kernel(const FpArgs a)
         }
         theta = tri_min<float>(alpha, beta, j + 1, lo, hi, h);
         if (last) { ++j; break; }
-        if (fabsf(theta - theta_prev) <= (float)a.tol32 * fmaxf(fabsf(theta), 1e-3f)) { ++j; break; }
+        // two checks in a row (16 steps), as in lanczos_min
+        if (fabsf(theta - theta_prev) <= (float)a.tol32 * fmaxf(fabsf(theta), 1e-3f)) {
+          if (++stalls == 2) { ++j; break; }
+        } else {
+          stalls = 0;
+        }
         theta_pp = theta_prev;
         theta_prev = theta;
       }
