@@ -43,7 +43,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # captured for the current kernel)
 TRAFFIC_POLISH_PER_START = (1.34528e8 + 2.18642e8) / 65536  # profiles/polish_kernel_4d_L4.md (line polish)
 TRAFFIC_RELAX_PER_START = (9.91e4 + 7.4575e7) / 65536       # profiles/relax32_sheet_4d_L4.md
-TRAFFIC_FPTEST_PER_COPY = (1.84462080e8 + 3.86688e6) / 44636   # profiles/fp_test_lanczos64_4d_L4.md
+TRAFFIC_FPTEST_PER_COPY = None   # not yet captured for fp_test_pairs_kernel
 # DRAM traffic per launch of the large-lattice leg's kernels (its own workload,
 # 592 starts of 4D 16^4), from ncu: profiles/slab_traffic_4d_L16.md
 TRAFFIC_SLAB_NEWTON1 = 2.92208894464e11 + 5.7204921344e10
@@ -664,9 +664,14 @@ def run_ours(args):
     #    5d + 2d + 2 (weights, 1/D) + 58 (double-float rotation) per Newton
     #    step, 33 to promote, 8d + 11 per fallback FP32 update; its FP64 ops
     #    (8d + 14 per site of the final pass) beside it;
-    #  * first-region test (fp_test_kernel, FP64 Lanczos): per step and site
-    #    2d + 1 FMAs for M v, and 6 more for the recurrence, alpha, mean, norm
-    #    and the next vector: (2d + 7) FP64 ops.
+    #  * first-region test (fp_test_pairs_kernel, FP64 Lanczos seeded by an
+    #    FP32 Ritz vector): FP64 ops per site, 6d for the weights cos(phi^theta)
+    #    (two complex products per link), 2d for the diagonal of M, 3 to
+    #    normalise the seed, and per FP64 step 2d + 1 FMAs for M v and 6 more
+    #    for the recurrence, alpha, mean, norm and the next vector (2d + 7);
+    #    FP32 ops per site and FP32 step, 4d for M v (differences and FMAs)
+    #    and 7 for the recurrence in the recording pass, 4d + 4 in the replay
+    #    pass that sums the Ritz vector.
     # A packed f32x2 instruction does two lane operations, so the FP32 peak is
     # the larger of the scalar and packed FMA probes.
     fp32_peak = max(peaks["ffma"], peaks["ffma2"])
@@ -690,10 +695,18 @@ def run_ours(args):
                          "fp64_frac": fp64_pol / (sec["polish_fp64"] + sec["polish_redo"]) / 1e12 / fp64_peak,
                          "ms": stage_ms["polish_fp64"] + stage_ms["polish_redo"],
                          "traffic": TRAFFIC_POLISH_PER_START * args.starts}
-    a_fp = rs["lanczos_steps"] * V * (2 * d + 7) / sec["fp_test"] / 1e12
-    kernels["fp_test"] = {"kernel": "fp_test_kernel<4> (FP64 Lanczos)", "bound": "alu", "achieved": a_fp,
+    steps64 = rs["lanczos_steps_fp64"]
+    steps32 = rs["lanczos_steps"] - steps64
+    fp64_ops = rs["fp_tests_fp64"] * V * (8 * d + 3) + steps64 * V * (2 * d + 7)
+    fp32_fp = steps32 * V * ((4 * d + 7) + (4 * d + 4))
+    a_fp = fp64_ops / sec["fp_test"] / 1e12
+    kernels["fp_test"] = {"kernel": "fp_test_pairs_kernel<4,4> (FP64 Lanczos from an FP32 Ritz vector)",
+                          "bound": "alu", "achieved": a_fp,
                           "peak": fp64_peak, "unit": "T FP64 lane ops/s", "frac": a_fp / fp64_peak,
-                          "ms": stage_ms["fp_test"], "lanczos_steps_per_copy": rs["lanczos_steps"] / max(1, rs["fp_tests"]),
+                          "fp32_frac": fp32_fp / sec["fp_test"] / 1e12 / fp32_peak,
+                          "ms": stage_ms["fp_test"],
+                          "fp32_steps_per_copy": steps32 / max(1, rs["fp_tests"]),
+                          "fp64_steps_per_copy": steps64 / max(1, rs["fp_tests_fp64"]),
                           "traffic": TRAFFIC_FPTEST_PER_COPY * rs["fp_tests"] if TRAFFIC_FPTEST_PER_COPY else None}
     # the dominant kernel of the isolated pass; polish_redo is a latency tail
     # of a few hundred starts that other orbits' kernels fill in a batch

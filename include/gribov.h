@@ -124,6 +124,8 @@ typedef struct {
                                     shared memory, the FP64 sweeps of the starts
                                     the Newton polish left plus the final pass */
   uint64_t polish_redo_starts;   /* starts it reran                              */
+  uint64_t lanczos_steps_fp64;   /* part of lanczos_steps taken in FP64 (Lanczos
+                                    mode: the FP64 steps after the FP32 seed)   */
 } gc_stats;
 
 /* Device memory hooks (e.g. a framework's caching allocator).  alloc returns

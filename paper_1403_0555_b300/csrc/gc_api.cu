@@ -129,7 +129,7 @@ enum StatSlot {
   kSweeps = 0, kUpdates = 1, kConv = 2, kNConv = 3, kNewton = 4, kFallback = 5, kUpd64 = 6,
   kPass = 7, kPConv = 8, kPNConv = 9, kNew = 10, kHit = 11, kDFail = 12, kTests = 13,
   kTests64 = 14, kLanczos = 15, kSweeps32 = 16, kUpdates32 = 17, kConv32 = 18, kNConv32 = 19, kInner = 20, kUpd32Fallback = 21,
-  kPassDF = 22, kRedo = 23, kNumStats = 24
+  kPassDF = 22, kRedo = 23, kLanczos64 = 24, kNumStats = 25
 };
 
 struct gc_orbit_s {
@@ -1065,7 +1065,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       fa.seed = opt.seed;
       fa.scratch = o->scratch.as<unsigned char>();
       fa.stats = stats;
-      fa.s_tests = kTests; fa.s_tests64 = kTests64; fa.s_steps = kLanczos;
+      fa.s_tests = kTests; fa.s_tests64 = kTests64; fa.s_steps = kLanczos; fa.s_steps64 = kLanczos64;
       // fp32: the screen, one copy per CTA.  FP64: one copy per cluster of 16
       // (else 8) CTAs: in auto mode it takes the few copies the screen leaves,
       // which one CTA each would run as a latency tail (a copy on one CTA:
@@ -1516,6 +1516,7 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       fa.margin32 = 1e-3;
       fa.tol32 = 1e-5;
       fa.tol64 = 1e-12;
+      fa.extra32 = 16;
       fa.seed = opt.seed;
       fa.stats = stats;
       int fgrid = 0;
@@ -1538,12 +1539,20 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
         fa.mode = gc::kFpLanczos;
         fa.count_tests = 0;
       }
-      if (int rc = launch_grid(fp64_kern, f_warps * 32, f_smem, f_warps, b, &fgrid)) return rc;
-      if (opt.fp_mode == GC_FP_DENSE) {
-        fgrid = std::min(fgrid, dense_grid);
-        fa.scratch = o->scratch.as<double>();
+      if (fa.mode == gc::kFpLanczos && d == 4 && o->L == 4) {
+        // lines of each parity fill a warp: the FP32 seed in registers
+        auto k = gc::fp_test_pairs_kernel<4, 4>;
+        const size_t sm = gc::FpTestPairSmem<4, 4>::bytes(8, kmax32, std::min(kmax64, gc::FpTestPairSmem<4, 4>::kMax64));
+        if (int rc = launch_grid(k, 256, sm, 8, b, &fgrid)) return rc;
+        k<<<fgrid, 256, sm, s>>>(fa);
+      } else {
+        if (int rc = launch_grid(fp64_kern, f_warps * 32, f_smem, f_warps, b, &fgrid)) return rc;
+        if (opt.fp_mode == GC_FP_DENSE) {
+          fgrid = std::min(fgrid, dense_grid);
+          fa.scratch = o->scratch.as<double>();
+        }
+        fp64_kern<<<fgrid, f_warps * 32, f_smem, s>>>(fa);
       }
-      fp64_kern<<<fgrid, f_warps * 32, f_smem, s>>>(fa);
       ++o->launches;
       GC_CUDA(cudaGetLastError());
     }
@@ -1838,6 +1847,7 @@ int gc_orbit_stats(gc_orbit o, gc_stats* out) {
   out->fp_tests = st[kTests];
   out->fp_tests_fp64 = st[kTests64];
   out->lanczos_steps = st[kLanczos];
+  out->lanczos_steps_fp64 = st[kLanczos64];
   out->ms_relax = o->ms[0];
   out->ms_polish = o->ms[1];
   out->ms_dedup = o->ms[2];
@@ -1994,6 +2004,7 @@ extern "C" int gc_fp_test_static(int dim, int L, const double* d_links, const do
   fa.margin32 = 1e-3;
   fa.tol32 = 1e-5;
   fa.tol64 = 1e-12;
+  fa.extra32 = 16;
   fa.scratch = reinterpret_cast<double*>(s + lay.q0);
   fa.seed = 1;
   fa.stats = reinterpret_cast<unsigned long long*>(s + lay.stats);

@@ -230,6 +230,11 @@ __device__ __forceinline__ float d2f_bits(double x) {
   if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
   return __uint_as_float(sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
 }
+// the same to nearest (ties away from zero): half an FP32 unit in the last
+// place added to the magnitude's bit pattern before truncation
+__device__ __forceinline__ float d2f_near(double x) {
+  return d2f_bits(__longlong_as_double(__double_as_longlong(x) + 0x10000000LL));
+}
 // max of two non-negative doubles by their bit patterns (integer compare)
 __device__ __forceinline__ double dmax_pos(double a, double b) {
   return __double_as_longlong(a) > __double_as_longlong(b) ? a : b;

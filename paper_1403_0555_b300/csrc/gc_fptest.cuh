@@ -40,24 +40,44 @@ struct FpArgs {
   double* lambda2;
   int* region;
   int mode, kmax32, kmax64, count_tests;
+  int extra32;                 // Lanczos mode: FP32 steps after the FP32 Ritz values stall
   double tau, margin32, tol32, tol64;
   double* scratch;             // dense mode: one (V x V) slot per warp of the grid
   uint64_t seed;
-  unsigned long long* stats;   // [13] tests, [14] FP64 decisions, [15] Lanczos steps
+  unsigned long long* stats;   // [13] tests, [14] FP64 decisions, [15] Lanczos steps (FP32 and FP64),
+                               // [24] FP64 Lanczos steps
 };
 
 // Shared memory: the site-order neighbour table (uint4 per site, per mu the
 // packed pair (x + mu) | (x - mu) << 16), then per warp the link weights
-// [mu][x], three Lanczos vectors and the tridiagonal (alpha, beta^2 and, for
-// full reorthogonalisation, the projection coefficients), in arithmetic R.
+// [mu][x], the Lanczos vectors and the tridiagonal, in arithmetic R.
+//   FP32 (screen): three vectors; alpha and beta^2.
+//   FP64: four vector slots (three Lanczos vectors and the diagonal of M) that
+//   the FP32 seed phase of the Lanczos mode uses first for its weights and
+//   five vectors; a tail with alpha, beta^2 and a third array (dense mode:
+//   projection coefficients), or the seed phase's eight FP32 arrays of
+//   kmax32_of(kmax) + 2 entries.
+__host__ __device__ inline int kmax32_of(int kmax) { return kmax < 160 ? kmax : 160; }
+
 template <typename R>
 struct FpSmem {
   size_t nbr, warp0, per_warp, total;
   __host__ __device__ static size_t align16s(size_t b) { return (b + 15) & ~size_t(15); }
-  // FP64 adds a fourth vector: the diagonal of M for lanczos64_min
+  __host__ __device__ static size_t max2(size_t a, size_t b) { return a > b ? a : b; }
+  // FP64 vector region: 4 slots of V doubles, or the seed phase's layout
+  __host__ __device__ static size_t slot(int V) { return align16s((size_t)V * sizeof(R)); }
+  __host__ __device__ static size_t seed_w32(int V, int d) { return align16s((size_t)V * d * 4); }
+  __host__ __device__ static size_t seed_vec(int V) { return align16s((size_t)V * 4); }
+  __host__ __device__ static size_t vec_bytes(int V, int d) {
+    return sizeof(R) == 8 ? max2(4 * slot(V), seed_w32(V, d) + 5 * seed_vec(V)) : 3 * slot(V);
+  }
+  __host__ __device__ static size_t tri(int kmax) { return align16s((size_t)(kmax + 2) * sizeof(R)); }
+  __host__ __device__ static size_t tri32(int kmax) { return align16s((size_t)(kmax32_of(kmax) + 2) * 4); }
+  __host__ __device__ static size_t tail_bytes(int kmax) {
+    return sizeof(R) == 8 ? max2(3 * tri(kmax), 8 * tri32(kmax)) : 3 * tri(kmax);
+  }
   __host__ __device__ static size_t warp_bytes(int V, int d, int kmax) {
-    return align16s((size_t)V * d * sizeof(R)) + (sizeof(R) == 8 ? 4 : 3) * align16s((size_t)V * sizeof(R)) +
-           3 * align16s((size_t)(kmax + 2) * sizeof(R));
+    return align16s((size_t)V * d * sizeof(R)) + vec_bytes(V, d) + tail_bytes(kmax);
   }
   __host__ __device__ FpSmem(int V, int d, int kmax, int warps) {
     nbr = 0;
@@ -94,15 +114,16 @@ __device__ __forceinline__ S tri_rel() { return sizeof(S) == 4 ? (S)2e-7 : (S)1e
 
 // smallest eigenvalue of the tridiagonal, given a bracket lo <= lambda_min <= hi,
 // by 32-way multisection, entirely in the arithmetic of the Lanczos vectors
+// (kth > 1: the kth smallest, given lo below it and hi above it)
 template <typename S>
-__device__ inline S tri_min(const S* alpha, const S* beta2, int k, S lo, S hi, int lane) {
-  const S rel = tri_rel<S>();
+__device__ inline S tri_min(const S* alpha, const S* beta2, int k, S lo, S hi, int lane, S rel = tri_rel<S>(),
+                            int kth = 1) {
   for (int round = 0; round < 14; ++round) {
     const S scale = fabs(lo) > (S)1 ? fabs(lo) : (S)1;
     if (hi - lo <= rel * scale) break;
     const S step = (hi - lo) / (S)33;
     const S x = lo + step * (S)(lane + 1);
-    const bool below = sturm_count<S>(alpha, beta2, k, x) >= 1;  // lambda_min < x
+    const bool below = sturm_count<S>(alpha, beta2, k, x) >= kth;  // lambda_kth < x
     const unsigned m = __ballot_sync(0xffffffffu, below);
     const int first = m ? __ffs(m) - 1 : 32;                      // first point above lambda_min
     const S nlo = lo + step * (S)first;
@@ -517,6 +538,366 @@ __device__ double lanczos64_min(const double* nw, const double* Dg, double* va, 
   return t64;
 }
 
+// ---------------------------------------------------------------------------
+// FP64 Lanczos seeded by an FP32 Ritz vector (the Lanczos mode's test).
+// The FP64 pipe is the scarce unit, so the Lanczos process first runs in FP32
+// (lanczos32_ritz): from the random start until its Ritz values stall, plus
+// `extra` steps; the eigenvector s of the FP32 tridiagonal T_k for its
+// smallest eigenvalue comes from two inverse iterations, and a second pass
+// regenerates the Lanczos vectors q_j from the recorded recurrence
+// coefficients and sums y = sum_j s_j q_j.  The FP64 Lanczos process then
+// starts from y (lanczos64_seeded): its first Rayleigh quotient already holds
+// lambda_2 to roughly the square of the FP32 Ritz vector's error, and a few
+// FP64 steps take it to FP64 accuracy.  The result is the smallest Ritz value
+// of the FP64 tridiagonal, as in lanczos64_min; only its start vector differs.
+// ---------------------------------------------------------------------------
+
+// the random start (Philox draws, projected off the constant mode,
+// normalised), shared by both FP32 passes so they start from the same bits
+__device__ __forceinline__ void ritz_start(float* v, float* vprev, int V, int lane, uint64_t seed,
+                                           unsigned long long entry) {
+  float s = 0.f;
+  for (int x = lane; x < V; x += 32) {
+    const U64x4 r = philox4x64_10(entry, (uint64_t)x, 0, 1, seed, 0x4C414E43ULL);
+    const float v0 = (float)(unsigned)(r.v[0] >> 40) * 0x1.0p-24f - 0.5f;
+    v[x] = v0;
+    vprev[x] = 0.f;
+    s += v0;
+  }
+  s = warp_sum(s) / (float)V;
+  float nn = 0.f;
+  for (int x = lane; x < V; x += 32) { const float t = v[x] - s; v[x] = t; nn = fmaf(t, t, nn); }
+  const float inv0 = 1.f / sqrtf(warp_sum(nn));
+  for (int x = lane; x < V; x += 32) v[x] *= inv0;
+  __syncwarp();
+}
+
+// M q_j - b q_{j-1} at site x with explicit FMAs: both passes round alike
+template <int DD>
+__device__ __forceinline__ float ritz_mv(const float* w, const float* vcur, const float* vprev, const uint4 nb,
+                                         int x, int V, float b) {
+  return fmaf(-b, vprev[x], matvec_site<DD, float>(w, vcur, nb, x, V));
+}
+
+// the FP32 tridiagonal and the recurrence record of the first pass
+struct Ritz32 {
+  float* al;    // alpha_j
+  float* be2;   // beta_j^2 (beta2[i] couples rows i-1 and i)
+  float* mm;    // mean removed from step j's new direction
+  float* bn;    // beta_j
+  float* s;     // eigenvector of T_k for its smallest eigenvalue
+  float* s2;    //                      for its second smallest
+  float* pd;    // LDL^T pivots of T_k - sigma (reciprocals)
+  float* pl;    // LDL^T multipliers
+};
+
+// Eigenvectors of the k x k tridiagonal (alpha, beta) for its smallest
+// eigenvalue theta (s) and the next one up (s2), by inverse iteration with the
+// shift sigma just below theta on the LDL^T factors of T_k - sigma (a zero
+// pivot replaced by a tiny one): two iterations for s; three for s2, each
+// followed by removing its component along s, so s2 converges to the
+// eigenvector whose eigenvalue is the next closest to sigma at the rate
+// (theta_2 - sigma) / (theta_3 - sigma), fastest when theta_2 is near theta.
+// Both scaled to a largest entry of 1.  One lane runs it.
+__device__ inline void ritz_coeffs32(const float* al, const float* bn, int k, float theta, float* pd, float* pl,
+                                     float* s, float* s2) {
+  const float sigma = theta - 2.f * tri_rel<float>() * fmaxf(fabsf(theta), 1.f);
+  float dd = al[0] - sigma;
+  if (fabsf(dd) < 1e-30f) dd = 1e-30f;
+  float rd = __fdividef(1.f, dd);
+  pd[0] = rd;
+  for (int i = 1; i < k; ++i) {
+    const float l = bn[i] * rd;
+    dd = (al[i] - sigma) - l * bn[i];
+    if (fabsf(dd) < 1e-30f) dd = 1e-30f;
+    rd = __fdividef(1.f, dd);
+    pl[i] = l;
+    pd[i] = rd;
+  }
+  // x <- (T - sigma)^-1 x, scaled to a largest entry of 1
+  auto solve = [&](float* x) {
+    float u = x[0];
+    for (int i = 1; i < k; ++i) { u = fmaf(-pl[i], u, x[i]); x[i] = u; }
+    float xn = u * pd[k - 1];
+    x[k - 1] = xn;
+    float big = fabsf(xn);
+    for (int i = k - 2; i >= 0; --i) {
+      xn = fmaf(-pl[i + 1], xn, x[i] * pd[i]);
+      x[i] = xn;
+      big = fmaxf(big, fabsf(xn));
+    }
+    const float sc = big > 0.f ? __fdividef(1.f, big) : 1.f;
+    for (int i = 0; i < k; ++i) x[i] *= sc;
+  };
+  for (int i = 0; i < k; ++i) { s[i] = 1.f; s2[i] = (i & 1) ? -1.f : 1.f; }
+  solve(s);
+  solve(s);
+  float ss = 0.f;
+  for (int i = 0; i < k; ++i) ss = fmaf(s[i], s[i], ss);
+  const float iss = __fdividef(1.f, ss);
+  for (int it = 0; it < 3; ++it) {
+    float p = 0.f;
+    for (int i = 0; i < k; ++i) p = fmaf(s[i], s2[i], p);
+    p *= iss;
+    for (int i = 0; i < k; ++i) s2[i] = fmaf(-p, s[i], s2[i]);
+    solve(s2);
+  }
+  float p = 0.f;
+  for (int i = 0; i < k; ++i) p = fmaf(s[i], s2[i], p);
+  p *= iss;
+  for (int i = 0; i < k; ++i) s2[i] = fmaf(-p, s[i], s2[i]);
+}
+
+// Returns the smallest FP32 Ritz value; y and y2 receive the (unnormalised)
+// Ritz vectors of the smallest and second smallest Ritz values (y2 zero when
+// T_k has one row).  w: weights [mu][x] (positive); q, qp, z: work vectors.
+template <int DD>
+__device__ float lanczos32_ritz(const float* w, float* q, float* qp, float* z, float* y, float* y2,
+                                const Ritz32 R, int kmax, double tol32, int extra, const uint4* nbr, int V,
+                                int lane, uint64_t seed, unsigned long long entry, int* steps) {
+  ritz_start(q, qp, V, lane, seed, entry);
+  const float bound = (float)(4 * DD + 1);
+  float b = 0.f, theta = bound, theta_prev = bound, theta_pp = bound;
+  int stalls = 0, kend = kmax, j = 0;
+  bool settled = false;
+  for (; j < kend; ++j) {
+    float a = 0.f;
+    for (int x = lane; x < V; x += 32) {
+      const float mv = ritz_mv<DD>(w, q, qp, nbr[x], x, V, b);
+      z[x] = mv;
+      a = fmaf(mv, q[x], a);
+    }
+    a = warp_sum(a);
+    float m = 0.f, zz = 0.f;
+    for (int x = lane; x < V; x += 32) {
+      const float v = fmaf(-a, q[x], z[x]);
+      z[x] = v;
+      m += v;
+      zz = fmaf(v, v, zz);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      m += __shfl_xor_sync(0xffffffffu, m, o);
+      zz += __shfl_xor_sync(0xffffffffu, zz, o);
+    }
+    m /= (float)V;
+    const float bn = sqrtf(fmaxf(zz - (float)V * m * m, 0.f));
+    if (lane == 0) { R.al[j] = a; R.be2[j + 1] = bn * bn; R.mm[j] = m; R.bn[j + 1] = bn; }
+    __syncwarp();
+    const bool last = (j + 1 == kend) || bn < 1e-12f;
+    if (last || (!settled && (j + 1) % 8 == 0 && j + 1 >= 24)) {
+      float lo = -bound, hi = bound;
+      if (theta_prev < bound) {
+        const float slack = 2.f * tri_rel<float>() * fmaxf(fabsf(theta_prev), 1.f);
+        hi = theta_prev + slack;
+        if (theta_pp < bound) {
+          const float l = theta_prev - 4.f * fmaxf(theta_pp - theta_prev, slack);
+          if (sturm_count<float>(R.al, R.be2, j + 1, l) == 0) lo = l;
+        }
+      }
+      // the stall test needs 1e-6; the final value (the inverse iteration's
+      // shift) the full FP32 resolution
+      theta = tri_min<float>(R.al, R.be2, j + 1, lo, hi, lane, last ? tri_rel<float>() : 1e-6f);
+      if (last) { ++j; break; }
+      // two checks in a row (16 steps) as in lanczos_min, then `extra` steps more
+      if (fabsf(theta - theta_prev) <= (float)tol32 * fmaxf(fabsf(theta), 1e-3f)) {
+        if (++stalls == 2) {
+          settled = true;
+          kend = j + 1 + extra < kmax ? j + 1 + extra : kmax;
+        }
+      } else {
+        stalls = 0;
+      }
+      theta_pp = theta_prev;
+      theta_prev = theta;
+    }
+    const float ib = 1.f / bn;
+    for (int x = lane; x < V; x += 32) { qp[x] = q[x]; q[x] = (z[x] - m) * ib; }
+    b = bn;
+    __syncwarp();
+  }
+  const int k = j;
+  *steps += k;
+  if (lane == 0) ritz_coeffs32(R.al, R.bn, k, theta, R.pd, R.pl, R.s, R.s2);
+  __syncwarp();
+  // second pass: the same vectors again, summed with the Ritz coefficients
+  ritz_start(q, qp, V, lane, seed, entry);
+  const float s0 = R.s[0], t0 = R.s2[0];
+  for (int x = lane; x < V; x += 32) { y[x] = s0 * q[x]; y2[x] = t0 * q[x]; }
+  b = 0.f;
+  for (int i = 0; i + 1 < k; ++i) {
+    const float a = R.al[i], m = R.mm[i], bn = R.bn[i + 1];
+    const float ib = 1.f / bn;
+    for (int x = lane; x < V; x += 32) z[x] = (fmaf(-a, q[x], ritz_mv<DD>(w, q, qp, nbr[x], x, V, b)) - m) * ib;
+    __syncwarp();
+    const float si = R.s[i + 1], ti = R.s2[i + 1];
+    for (int x = lane; x < V; x += 32) {
+      qp[x] = q[x];
+      q[x] = z[x];
+      y[x] = fmaf(si, z[x], y[x]);
+      y2[x] = fmaf(ti, z[x], y2[x]);
+    }
+    b = bn;
+    __syncwarp();
+  }
+  return theta;
+}
+
+// The smallest eigenpair of the symmetric 2 x 2 matrix [[a, b], [b, c]]:
+// (cs, sn) with the eigenvector cs e1 + sn e2, by the Jacobi rotation that
+// diagonalises it.
+__device__ inline void rr2_rotation(double a, double b, double c, double* cs, double* sn) {
+  if (b == 0.0) {
+    *cs = a <= c ? 1.0 : 0.0;
+    *sn = a <= c ? 0.0 : 1.0;
+    return;
+  }
+  const double zeta = (c - a) / (2.0 * b);
+  const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+  const double co = 1.0 / sqrt(fma(t, t, 1.0)), si = t * co;
+  // eigenvalues a - t b (vector (co, -si)) and c + t b (vector (si, co))
+  if (a - t * b <= c + t * b) { *cs = co; *sn = -si; } else { *cs = si; *sn = co; }
+}
+
+// out = M v (weights negated [mu][x], diagonal Dg), all in shared memory
+template <int DD>
+__device__ __forceinline__ void mv64(const double* nw, const double* Dg, const double* v, double* out,
+                                     const uint4* nbr, int V, int lane) {
+  for (int x = lane; x < V; x += 32) {
+    const uint4 nb = nbr[x];
+    double yv = Dg[x] * v[x];
+#pragma unroll
+    for (int mu = 0; mu < DD; ++mu) {
+      const unsigned wd = nb_word(nb, mu);
+      const int xp = wd & 0xffffu, xm = wd >> 16;
+      yv = fma(nw[mu * V + x], v[xp], yv);
+      yv = fma(nw[mu * V + xm], v[xm], yv);
+    }
+    out[x] = yv;
+  }
+  __syncwarp();
+}
+
+// FP64 Rayleigh-Ritz on span{e1, e2}: e1 in va (normalised, off the constant
+// mode), y2 in vb (off the constant mode); vc is scratch.  Leaves in va the
+// unit vector of the span with the smallest Rayleigh quotient.  Near-equal
+// lambda_2 and lambda_3 leave a component of the lambda_3 eigenvector in the
+// FP32 Ritz vector that Lanczos steps remove slowly; the second Ritz vector
+// removes most of it at once.
+template <int DD>
+__device__ void rayleigh_ritz2_64(const double* nw, const double* Dg, double* va, double* vb, double* vc,
+                                  const uint4* nbr, int V, int lane) {
+  double p = 0.0, q2 = 0.0;
+  for (int x = lane; x < V; x += 32) { p = fma(va[x], vb[x], p); q2 = fma(vb[x], vb[x], q2); }
+  warp_sum2(p, q2, lane);
+  const double r2 = fma(-p, p, q2);   // |vb - (va . vb) va|^2
+  if (!(r2 > 1e-12 * q2)) return;     // vb (nearly) along va: no second direction
+  const double ir = rsqrt64(r2);
+  for (int x = lane; x < V; x += 32) vb[x] = fma(-p, va[x], vb[x]) * ir;
+  __syncwarp();
+  mv64<DD>(nw, Dg, va, vc, nbr, V, lane);
+  double a11 = 0.0, a12 = 0.0;
+  for (int x = lane; x < V; x += 32) { a11 = fma(va[x], vc[x], a11); a12 = fma(vb[x], vc[x], a12); }
+  warp_sum2(a11, a12, lane);
+  mv64<DD>(nw, Dg, vb, vc, nbr, V, lane);
+  double a22 = 0.0;
+  for (int x = lane; x < V; x += 32) a22 = fma(vb[x], vc[x], a22);
+  a22 = warp_sum(a22);
+  double cs, sn;
+  rr2_rotation(a11, a12, a22, &cs, &sn);
+  for (int x = lane; x < V; x += 32) va[x] = fma(cs, va[x], sn * vb[x]);
+  __syncwarp();
+}
+
+// FP64 Lanczos from the start vector in va (normalised, orthogonal to the
+// constant mode).  The step is lanczos64_min's; lambda_min of the FP64
+// tridiagonal is taken after every step (T_1 is the seed's Rayleigh quotient;
+// later ones by tri_min64 warm-started just below the previous value, whose
+// window the last decrease sets), and the run stops when two successive
+// values agree to tol64 twice in a row.  theta32 (the FP32 Ritz value) seeds
+// the bracket when the warm start misses.
+template <int DD>
+__device__ double lanczos64_seeded(const double* nw, const double* Dg, double* va, double* vb, double* vc,
+                                   double* a64, double* b64, int kmax, double tol64, float theta32,
+                                   const uint4* nbr, int V, int lane, int* steps) {
+  double* vcur = va;
+  double* vprev = vb;
+  double* z = vc;
+  for (int x = lane; x < V; x += 32) vprev[x] = 0.0;
+  __syncwarp();
+  const double invV = 1.0 / (double)V;
+  const double bound = (double)(4 * DD + 1);
+  double t64 = bound, d64 = 0.0, b = 0.0;
+  int stalls = 0, j = 0;
+  for (; j < kmax; ++j) {
+    double a = 0.0;
+    const double mb = -b;
+    for (int x = lane; x < V; x += 32) {
+      const uint4 nb = nbr[x];
+      const double vx = vcur[x];
+      double yv = fma(Dg[x], vx, mb * vprev[x]);
+#pragma unroll
+      for (int mu = 0; mu < DD; ++mu) {
+        const unsigned wd = nb_word(nb, mu);
+        const int xp = wd & 0xffffu, xm = wd >> 16;
+        yv = fma(nw[mu * V + x], vcur[xp], yv);
+        yv = fma(nw[mu * V + xm], vcur[xm], yv);
+      }
+      z[x] = yv;
+      a = fma(yv, vx, a);
+    }
+    a = warp_sum(a);
+    double m = 0.0, zz = 0.0;
+    for (int x = lane; x < V; x += 32) {
+      const double v = fma(-a, vcur[x], z[x]);
+      z[x] = v;
+      m += v;
+      zz = fma(v, v, zz);
+    }
+    warp_sum2(m, zz, lane);
+    m *= invV;
+    double bn2 = fma(-(double)V * m, m, zz);   // |z - m|^2
+    if (__double_as_longlong(bn2) < 0) bn2 = 0.0;
+    if (lane == 0) { a64[j] = a; b64[j + 1] = bn2; }
+    __syncwarp();
+    const bool last = (j + 1 == kmax) || dbelow(bn2, 1e-24);
+    double t;
+    if (j == 0) {
+      t = a;
+    } else {
+      bool ok = false;
+      const double hi = t64 + 1e-14 * fmax(fabs(t64), 1.0);
+      const double wdw = fmax(8.0 * d64, 4e-5 * fmax(fabs(t64), 1e-3));
+      t = tri_min64(a64, b64, j + 1, t64 - wdw, hi, lane, &ok, true);
+      if (!ok) {
+        const double c = f2d_bits(theta32);
+        const double del = 2e-5 * fmax(1.0, fabs(c));
+        t = tri_min64(a64, b64, j + 1, fmin(c, t64) - del, t64 + del, lane, &ok);
+        if (!ok) t = tri_min64(a64, b64, j + 1, -bound, bound, lane, &ok);
+      }
+    }
+    const bool stall = j > 0 && fabs(t - t64) <= tol64 * fmax(fabs(t), 1e-3);
+    d64 = j > 0 ? fmax(t64 - t, 0.0) : 0.0;
+    t64 = t;
+    if (last) { ++j; break; }
+    if (stall) {
+      if (++stalls == 2) { ++j; break; }
+    } else {
+      stalls = 0;
+    }
+    const double ib = rsqrt64(bn2);
+    const double mib = -m * ib;
+    for (int x = lane; x < V; x += 32) z[x] = fma(z[x], ib, mib);
+    b = bn2 * ib;
+    double* tt = vprev;
+    vprev = vcur;
+    vcur = z;
+    z = tt;
+    __syncwarp();
+  }
+  *steps += j;
+  return t64;
+}
+
 __device__ inline void build_site_neighbours(const Geom& G, uint4* nbr) {
   for (int x = threadIdx.x; x < G.V; x += blockDim.x) {
     unsigned w[4] = {0u, 0u, 0u, 0u};
@@ -606,7 +987,7 @@ __global__ void __launch_bounds__(256) fp_screen_kernel(const FpArgs a) {
 // FP64 test: Lanczos (kFpLanczos) or full reorthogonalisation to dimension
 // V - 1 (kFpDense); kFpNone marks every copy untested.
 template <int DD>
-__global__ void __launch_bounds__(128, 8) fp_test_kernel(const FpArgs a) {
+__global__ void __launch_bounds__(128, 4) fp_test_kernel(const FpArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Geom G = a.geom;
   const int V = G.V;
@@ -621,16 +1002,17 @@ __global__ void __launch_bounds__(128, 8) fp_test_kernel(const FpArgs a) {
   unsigned char* base = smem + lay.warp0 + (size_t)warp * lay.per_warp;
   double* w64 = reinterpret_cast<double*>(base);
   unsigned char* vb = base + FpSmem<double>::align16s((size_t)V * DD * 8);
-  const size_t vstride = FpSmem<double>::align16s((size_t)V * 8);
-  double* alpha = reinterpret_cast<double*>(vb + 4 * vstride);
-  double* beta = alpha + FpSmem<double>::align16s((size_t)(kmax + 2) * 8) / 8;
-  double* h = beta + FpSmem<double>::align16s((size_t)(kmax + 2) * 8) / 8;
+  const size_t vstride = FpSmem<double>::slot(V);
+  unsigned char* tail = vb + FpSmem<double>::vec_bytes(V, DD);
+  double* alpha = reinterpret_cast<double*>(tail);
+  double* beta = alpha + FpSmem<double>::tri(kmax) / 8;
+  double* h = beta + FpSmem<double>::tri(kmax) / 8;
 
   const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   double* Q = a.mode == kFpDense ? a.scratch + (size_t)gwarp * V * V : nullptr;
   unsigned long long c_tests = 0, c64 = 0;
-  int steps = 0;
+  int steps = 0, steps64 = 0;
   for (long long li = gwarp; li < (long long)n; li += nwarps) {
     const unsigned e = a.list[li];
     const double2* g = a.cfg + (size_t)e * V;
@@ -659,9 +1041,49 @@ __global__ void __launch_bounds__(128, 8) fp_test_kernel(const FpArgs a) {
       double* v2 = reinterpret_cast<double*>(vb + 2 * vstride);
       double* v3 = reinterpret_cast<double*>(vb + 3 * vstride);
       if (dense) {
+        int sd = 0;
         lam = lanczos_min<double, true, DD>(w64, v0, v1, v2, alpha, beta, h, Q, k, 0.0, nbr, V, lane,
-                                            a.seed, key, &steps);
+                                            a.seed, key, &sd);
+        steps += sd;
+        steps64 += sd;
       } else {
+        // FP32 seed: the weights' FP32 image (positive) and five FP32 vectors
+        // in the vector region, the FP32 tridiagonal in the tail
+        float* w32 = reinterpret_cast<float*>(vb);
+        float* q32 = reinterpret_cast<float*>(vb + FpSmem<double>::seed_w32(V, DD));
+        float* qp32 = q32 + FpSmem<double>::seed_vec(V) / 4;
+        float* z32 = qp32 + FpSmem<double>::seed_vec(V) / 4;
+        float* y32 = z32 + FpSmem<double>::seed_vec(V) / 4;
+        float* y2_32 = y32 + FpSmem<double>::seed_vec(V) / 4;
+        for (int i = lane; i < V * DD; i += 32) w32[i] = -d2f_near(w64[i]);
+        __syncwarp();
+        const size_t t32 = FpSmem<double>::tri32(kmax) / 4;
+        float* f = reinterpret_cast<float*>(tail);
+        const Ritz32 R{f, f + t32, f + 2 * t32, f + 3 * t32, f + 4 * t32, f + 5 * t32, f + 6 * t32, f + 7 * t32};
+        const int k32 = kmax32_of(k);
+        const float th32 = lanczos32_ritz<DD>(w32, q32, qp32, z32, y32, y2_32, R, k32, a.tol32, a.extra32, nbr,
+                                              V, lane, a.seed, key, &steps);
+        // the two Ritz vectors in FP64 (into slots 0 and 1, which they do not
+        // overlap), off the constant mode; the first normalised
+        double sm = 0.0, sm2 = 0.0;
+        for (int x = lane; x < V; x += 32) {
+          const double t = f2d_bits(y32[x]), t2 = f2d_bits(y2_32[x]);
+          v0[x] = t; v1[x] = t2;
+          sm += t; sm2 += t2;
+        }
+        warp_sum2(sm, sm2, lane);
+        sm /= (double)V;
+        sm2 /= (double)V;
+        double nn = 0.0;
+        for (int x = lane; x < V; x += 32) {
+          const double t = v0[x] - sm;
+          v0[x] = t;
+          v1[x] -= sm2;
+          nn = fma(t, t, nn);
+        }
+        const double inv = rsqrt64(warp_sum(nn));
+        for (int x = lane; x < V; x += 32) v0[x] *= inv;
+        __syncwarp();
         // the diagonal of M: D_x = sum_mu (w_{x,mu} + w_{x-mu,mu})
         for (int x = lane; x < V; x += 32) {
           const uint4 nb = nbr[x];
@@ -671,9 +1093,11 @@ __global__ void __launch_bounds__(128, 8) fp_test_kernel(const FpArgs a) {
           v3[x] = dsum;
         }
         __syncwarp();
-        lam = lanczos64_min<DD>(w64, v3, v0, v1, v2, alpha, beta, reinterpret_cast<float*>(h),
-                                reinterpret_cast<float*>(h) + (kmax + 2), k, a.tol32, a.tol64, nbr, V,
-                                lane, a.seed, key, &steps);
+        rayleigh_ritz2_64<DD>(w64, v3, v0, v1, v2, nbr, V, lane);
+        int s64 = 0;
+        lam = lanczos64_seeded<DD>(w64, v3, v0, v1, v2, alpha, beta, k, a.tol64, th32, nbr, V, lane, &s64);
+        steps += s64;
+        steps64 += s64;
       }
       ++c64;
     }
@@ -688,6 +1112,7 @@ __global__ void __launch_bounds__(128, 8) fp_test_kernel(const FpArgs a) {
     if (a.count_tests) atomicAdd(&a.stats[13], c_tests);
     atomicAdd(&a.stats[14], c64);
     atomicAdd(&a.stats[15], (unsigned long long)steps);
+    atomicAdd(&a.stats[24], (unsigned long long)steps64);
   }
 }
 

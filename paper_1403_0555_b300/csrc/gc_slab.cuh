@@ -1070,7 +1070,7 @@ struct SlabFpArgs {
   unsigned char* scratch;          // per CTA: weights [d][V], vprev, vcur, z [V] (R), wrap [V]
   size_t scratch_bytes;            // per CTA (a multiple of 16)
   unsigned long long* stats;
-  int s_tests, s_tests64, s_steps;
+  int s_tests, s_tests64, s_steps, s_steps64;
   int count_tests;                 // R = double: also count the copies as tests (no screen ran)
 };
 
@@ -1318,6 +1318,7 @@ __global__ void __launch_bounds__(1024, 1) slab_fp_lanczos_kernel(const SlabFpAr
     atomicAdd(&a.stats[a.s_steps], my_steps);
     if (sizeof(R) == 4 || a.count_tests) atomicAdd(&a.stats[a.s_tests], my_tests);
     if (sizeof(R) == 8) atomicAdd(&a.stats[a.s_tests64], my_tests);
+    if (sizeof(R) == 8) atomicAdd(&a.stats[a.s_steps64], my_steps);
   }
   if constexpr (CL) cg::this_cluster().sync();   // no CTA leaves while its slots may be read
 }

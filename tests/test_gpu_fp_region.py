@@ -52,3 +52,29 @@ def test_every_copy_region_and_lambda2_against_dense(j):
     assert np.array_equal(c_a["region"], reg)
     # a Ritz value never lies below the smallest eigenvalue (to rounding)
     assert np.all(c_l["lambda2"] >= lam - 1e-12 * np.maximum(1.0, np.abs(lam)))
+
+
+@pytest.mark.parametrize("d,L,kappa", [(3, 6, 1.0), (2, 16, 1.0), (4, 3, 0.5)])
+def test_lanczos_mode_other_lattices_against_dense(d, L, kappa):
+    """The Lanczos mode on lattices outside the 4^4 line layout (the generic
+    kernel: FP32 Ritz seed then FP64 Lanczos, vectors in shared memory): the
+    flag of every copy equals the dense eigensolve's, lambda_2 within 1e-9
+    relative, and never below the smallest eigenvalue."""
+    import paper_1403_0555_b300 as gb
+    n = 1 << 12
+    phi = oi.von_mises_orbit(d, L, kappa, 3)
+    _, c, st = run_gpu(d, L, phi, 3, n, precision=gb.GC_MIXED, check_every=4,
+                       fp_mode=gb.GC_FP_LANCZOS, keep_per_start=0)
+    assert c["n_distinct"] > 10
+    assert st["fp_tests_fp64"] == st["fp_tests"] == c["n_distinct"]
+    assert 0 < st["lanczos_steps_fp64"] < st["lanczos_steps"]
+    with oracle_pool() as pool:
+        lam = np.array(pool.map(oracle.lambda2_of_copy,
+                                [(d, L, phi, th) for th in c["theta"]], chunksize=16))
+    reg = np.array([oracle.region_flag(x, 1e-9) for x in lam], dtype=np.int32)
+    rel = np.abs(c["lambda2"] - lam) / np.maximum(np.abs(lam), 1e-3)
+    print(f"\n{d}D L={L}: {len(lam)} copies, IN/MARGINAL/OUT {np.bincount(reg, minlength=3)[[1, 2, 0]]}, "
+          f"max rel err {rel.max():.2e}, FP64 steps per copy {st['lanczos_steps_fp64'] / st['fp_tests']:.2f}")
+    assert np.array_equal(c["region"], reg)
+    assert rel.max() <= 1e-9
+    assert np.all(c["lambda2"] >= lam - 1e-12 * np.maximum(1.0, np.abs(lam)))
