@@ -638,17 +638,25 @@ def run_ours(args):
              "mixed_over_plain": value / (ps["n_converged"] / (pms / 1000.0))}
 
     # --- roofline of the dominant kernel.  Inside the timed batches the
-    # orbits' kernels overlap, so each kernel's own duration is taken from one
-    # isolated single-orbit pass of the same shape (2^20 starts of the
-    # kappa = 0.5 orbit), with CUDA events on the launch stream around every
-    # kernel (the library's per-stage events).
-    o = orbits[0]
+    # orbits' kernels overlap, so each kernel's own duration is taken from
+    # isolated single-orbit passes of the step's eight orbits (2^20 starts
+    # each), with CUDA events on the launch stream around every kernel (the
+    # library's per-stage events); each kernel's work and time are summed
+    # over the eight launches, and the dominant kernel is the one with the
+    # most time in the step.
     ropt = gb.gc_options_default(precision=gb.GC_MIXED, check_every=ce,
                                  fp_mode=gb.GC_FP_LANCZOS, stream=stream)
-    h = gb.gc_create_orbit(d, L, o.phi, o.orbit_id, args.starts)
-    gb.gc_enumerate_copies(h, args.starts, w.omega, w.eps, ropt)
-    rs = gb.gc_orbit_stats(h)
-    gb.gc_destroy_orbit(h)
+    rs = None
+    per_orbit_ms = []
+    for o in orbits:
+        h = gb.gc_create_orbit(d, L, o.phi, o.orbit_id, args.starts)
+        gb.gc_enumerate_copies(h, args.starts, w.omega, w.eps, ropt)
+        st = gb.gc_orbit_stats(h)
+        gb.gc_destroy_orbit(h)
+        per_orbit_ms.append({k: round(st[k], 2) for k in ("ms_relax", "ms_polish", "ms_dedup", "ms_fptest")}
+                            | {"copies": st["n_distinct"]})
+        rs = st if rs is None else {k: rs[k] + st[k] for k in rs}
+    n_launch = len(orbits)
     # FP32 site updates of the bulk sweeps (the rest are polish fallbacks)
     rs_relax_updates = rs["sweeps_fp32"] * V
     stage_ms = {"relax_fp32": rs["ms_relax"], "polish_fp64": rs["ms_polish"] - rs["ms_polish_redo"],
@@ -662,8 +670,10 @@ def run_ours(args):
     #  * line polish (polish_pairs_kernel): FP32 pipe ops per site, 12 (8d + 2)
     #    + 2 per double-float residual pass, 2d + 3 per inner SOR sweep,
     #    5d + 2d + 2 (weights, 1/D) + 58 (double-float rotation) per Newton
-    #    step, 33 to promote, 8d + 11 per fallback FP32 update; its FP64 ops
-    #    (8d + 14 per site of the final pass) beside it;
+    #    step, 33 to promote, 8d + 11 per fallback FP32 update; its FP64 ops,
+    #    the binding unit, 8d + 11 per site of the final pass (8d for the
+    #    staple, 3 for the residual, 2 for the functional, 4 for the canonical
+    #    copy, 2 to join the double-float halves);
     #  * first-region test (fp_test_pairs_kernel, FP64 Lanczos seeded by an
     #    FP32 Ritz vector): FP64 ops per site, 6d for the weights cos(phi^theta)
     #    (two complex products per link), 2d for the diagonal of M, 3 to
@@ -682,18 +692,20 @@ def run_ours(args):
     a_relax = rs["sweeps_fp32"] * V * fp32_per_update / sec["relax_fp32"] / 1e12
     kernels["relax_fp32"] = {"kernel": "relax32_sheet_kernel<8,1>", "bound": "alu", "achieved": a_relax,
                              "peak": fp32_peak, "unit": "T FP32 lane ops/s", "frac": a_relax / fp32_peak,
-                             "ms": stage_ms["relax_fp32"], "traffic": TRAFFIC_RELAX_PER_START * args.starts}
+                             "ms": stage_ms["relax_fp32"], "launches": n_launch,
+                             "traffic": TRAFFIC_RELAX_PER_START * args.starts}
     fp32_ops = (rs["df_residual_passes"] * V * (12 * (8 * d + 2) + 2)
                 + rs["newton_inner_sweeps"] * V * (2 * d + 3)
                 + rs["newton_steps"] * V * (7 * d + 2 + 58)
                 + rs["n_starts"] * V * 33
                 + (rs["site_updates_fp32"] - rs_relax_updates) * (8 * d + 11))
-    fp64_pol = rs["fp64_residual_passes"] * V * (8 * d + 14) + rs["site_updates_fp64"] * (8 * d + 20)
-    a_pol = fp32_ops / (sec["polish_fp64"] + sec["polish_redo"]) / 1e12
+    fp64_pol = rs["fp64_residual_passes"] * V * (8 * d + 11) + rs["site_updates_fp64"] * (8 * d + 20)
+    t_pol = sec["polish_fp64"] + sec["polish_redo"]
+    a_pol = fp64_pol / t_pol / 1e12
     kernels["polish"] = {"kernel": "polish_pairs_kernel<4,4,16> + polish_kernel<4,true> (redo)", "bound": "alu",
-                         "achieved": a_pol, "peak": fp32_peak, "unit": "T FP32 lane ops/s", "frac": a_pol / fp32_peak,
-                         "fp64_frac": fp64_pol / (sec["polish_fp64"] + sec["polish_redo"]) / 1e12 / fp64_peak,
-                         "ms": stage_ms["polish_fp64"] + stage_ms["polish_redo"],
+                         "achieved": a_pol, "peak": fp64_peak, "unit": "T FP64 lane ops/s", "frac": a_pol / fp64_peak,
+                         "fp32_frac": fp32_ops / t_pol / 1e12 / fp32_peak,
+                         "ms": stage_ms["polish_fp64"] + stage_ms["polish_redo"], "launches": n_launch,
                          "traffic": TRAFFIC_POLISH_PER_START * args.starts}
     steps64 = rs["lanczos_steps_fp64"]
     steps32 = rs["lanczos_steps"] - steps64
@@ -704,19 +716,22 @@ def run_ours(args):
                           "bound": "alu", "achieved": a_fp,
                           "peak": fp64_peak, "unit": "T FP64 lane ops/s", "frac": a_fp / fp64_peak,
                           "fp32_frac": fp32_fp / sec["fp_test"] / 1e12 / fp32_peak,
-                          "ms": stage_ms["fp_test"],
+                          "ms": stage_ms["fp_test"], "launches": n_launch,
                           "fp32_steps_per_copy": steps32 / max(1, rs["fp_tests"]),
                           "fp64_steps_per_copy": steps64 / max(1, rs["fp_tests_fp64"]),
-                          "traffic": TRAFFIC_FPTEST_PER_COPY * rs["fp_tests"] if TRAFFIC_FPTEST_PER_COPY else None}
-    # the dominant kernel of the isolated pass; polish_redo is a latency tail
-    # of a few hundred starts that other orbits' kernels fill in a batch
+                          "traffic": (TRAFFIC_FPTEST_PER_COPY * rs["fp_tests"] / n_launch
+                                      if TRAFFIC_FPTEST_PER_COPY else None)}
+    # the dominant kernel: the most time over the step's eight orbits
     dom = max(("relax_fp32", "polish", "fp_test"), key=lambda k_: kernels[k_]["ms"])
     roof = dict(kernels[dom])
     roof["traffic_unit"] = "bytes per launch (DRAM read + write, ncu, scaled from the profiled case)"
     roof["peak_source"] = "measured on this GPU by gc_peak_probe (FFMA/FFMA2/DFMA), bench.py's peaks key"
+    roof["ms_per_launch"] = roof["ms"] / n_launch
     roof["stage_ms_isolated"] = stage_ms
+    roof["stage_ms_per_orbit"] = per_orbit_ms
     roof["polish_redo_starts"] = rs["polish_redo_starts"]
     roof["launch_starts"] = args.starts
+    roof["isolated_passes"] = f"{n_launch} orbits x {args.starts} starts, one at a time; ms summed"
     roof["kernels"] = kernels
 
     uneven = uneven_leg(gb, torch, args.check_every) if args.uneven else None

@@ -591,16 +591,33 @@ struct Ritz32 {
   float* pl;    // LDL^T multipliers
 };
 
+// x <- (T_k - sigma)^-1 x on the LDL^T factors (reciprocal pivots pd,
+// multipliers pl), scaled to a largest entry of 1
+__device__ __forceinline__ void ldl_solve32(const float* pd, const float* pl, int k, float* x) {
+  float u = x[0];
+  for (int i = 1; i < k; ++i) { u = fmaf(-pl[i], u, x[i]); x[i] = u; }
+  float xn = u * pd[k - 1];
+  x[k - 1] = xn;
+  float big = fabsf(xn);
+  for (int i = k - 2; i >= 0; --i) {
+    xn = fmaf(-pl[i + 1], xn, x[i] * pd[i]);
+    x[i] = xn;
+    big = fmaxf(big, fabsf(xn));
+  }
+  const float sc = big > 0.f ? __fdividef(1.f, big) : 1.f;
+  for (int i = 0; i < k; ++i) x[i] *= sc;
+}
+
 // Eigenvectors of the k x k tridiagonal (alpha, beta) for its smallest
 // eigenvalue theta (s) and the next one up (s2), by inverse iteration with the
 // shift sigma just below theta on the LDL^T factors of T_k - sigma (a zero
-// pivot replaced by a tiny one): two iterations for s; three for s2, each
-// followed by removing its component along s, so s2 converges to the
-// eigenvector whose eigenvalue is the next closest to sigma at the rate
+// pivot replaced by a tiny one): two iterations for s; two for s2, each
+// after removing its component along s, so s2 converges to the eigenvector
+// whose eigenvalue is the next closest to sigma at the rate
 // (theta_2 - sigma) / (theta_3 - sigma), fastest when theta_2 is near theta.
 // Both scaled to a largest entry of 1.  One lane runs it.
-__device__ inline void ritz_coeffs32(const float* al, const float* bn, int k, float theta, float* pd, float* pl,
-                                     float* s, float* s2) {
+__device__ inline void ritz_coeffs32(const float* al, const float* bn, int k, float theta, float* pd,
+                                           float* pl, float* s, float* s2) {
   const float sigma = theta - 2.f * tri_rel<float>() * fmaxf(fabsf(theta), 1.f);
   float dd = al[0] - sigma;
   if (fabsf(dd) < 1e-30f) dd = 1e-30f;
@@ -614,38 +631,30 @@ __device__ inline void ritz_coeffs32(const float* al, const float* bn, int k, fl
     pl[i] = l;
     pd[i] = rd;
   }
-  // x <- (T - sigma)^-1 x, scaled to a largest entry of 1
-  auto solve = [&](float* x) {
-    float u = x[0];
-    for (int i = 1; i < k; ++i) { u = fmaf(-pl[i], u, x[i]); x[i] = u; }
-    float xn = u * pd[k - 1];
-    x[k - 1] = xn;
-    float big = fabsf(xn);
-    for (int i = k - 2; i >= 0; --i) {
-      xn = fmaf(-pl[i + 1], xn, x[i] * pd[i]);
-      x[i] = xn;
-      big = fmaxf(big, fabsf(xn));
-    }
-    const float sc = big > 0.f ? __fdividef(1.f, big) : 1.f;
-    for (int i = 0; i < k; ++i) x[i] *= sc;
-  };
   for (int i = 0; i < k; ++i) { s[i] = 1.f; s2[i] = (i & 1) ? -1.f : 1.f; }
-  solve(s);
-  solve(s);
-  float ss = 0.f;
-  for (int i = 0; i < k; ++i) ss = fmaf(s[i], s[i], ss);
-  const float iss = __fdividef(1.f, ss);
-  for (int it = 0; it < 3; ++it) {
-    float p = 0.f;
-    for (int i = 0; i < k; ++i) p = fmaf(s[i], s2[i], p);
-    p *= iss;
-    for (int i = 0; i < k; ++i) s2[i] = fmaf(-p, s[i], s2[i]);
-    solve(s2);
+  // s: two solves; s2: (project off s, solve) twice, then project off s
+#pragma unroll 1
+  for (int it = 0; it < 4; ++it) {
+    float* x = it < 2 ? s : s2;
+    if (it >= 2) {
+      float p = 0.f, ss = 0.f;
+      for (int i = 0; i < k; ++i) { p = fmaf(s[i], s2[i], p); ss = fmaf(s[i], s[i], ss); }
+      p = __fdividef(p, ss);
+      for (int i = 0; i < k; ++i) s2[i] = fmaf(-p, s[i], s2[i]);
+    }
+    ldl_solve32(pd, pl, k, x);
   }
-  float p = 0.f;
-  for (int i = 0; i < k; ++i) p = fmaf(s[i], s2[i], p);
-  p *= iss;
+  float p = 0.f, ss = 0.f;
+  for (int i = 0; i < k; ++i) { p = fmaf(s[i], s2[i], p); ss = fmaf(s[i], s[i], ss); }
+  p = __fdividef(p, ss);
   for (int i = 0; i < k; ++i) s2[i] = fmaf(-p, s[i], s2[i]);
+}
+
+// FP32 Ritz values resolve lambda only to ~ eps32 ||T|| absolute (the Sturm
+// counts' backward error), so the stall test of the FP32 phase takes
+// tol32 |theta| with that floor
+__device__ __forceinline__ bool ritz32_stalled(float theta, float prev, double tol32) {
+  return fabsf(theta - prev) <= fmaxf((float)tol32 * fabsf(theta), 2e-6f);
 }
 
 // Returns the smallest FP32 Ritz value; y and y2 receive the (unnormalised)
@@ -699,7 +708,7 @@ __device__ float lanczos32_ritz(const float* w, float* q, float* qp, float* z, f
       theta = tri_min<float>(R.al, R.be2, j + 1, lo, hi, lane, last ? tri_rel<float>() : 1e-6f);
       if (last) { ++j; break; }
       // two checks in a row (16 steps) as in lanczos_min, then `extra` steps more
-      if (fabsf(theta - theta_prev) <= (float)tol32 * fmaxf(fabsf(theta), 1e-3f)) {
+      if (ritz32_stalled(theta, theta_prev, tol32)) {
         if (++stalls == 2) {
           settled = true;
           kend = j + 1 + extra < kmax ? j + 1 + extra : kmax;

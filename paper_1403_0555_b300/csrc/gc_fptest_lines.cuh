@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(256, 2) fp_test_pairs_kernel(const FpArgs a) {
             // iteration's shift) the full FP32 resolution
             theta = tri_min<float>(R.al, R.be2, j + 1, lo, hi, h, last ? tri_rel<float>() : 1e-6f);
             if (last) { ++j; break; }
-            if (fabsf(theta - theta_prev) <= (float)a.tol32 * fmaxf(fabsf(theta), 1e-3f)) {
+            if (ritz32_stalled(theta, theta_prev, a.tol32)) {
               if (++stalls == 2) {
                 settled = true;
                 kend = j + 1 + a.extra32 < kk ? j + 1 + a.extra32 : kk;

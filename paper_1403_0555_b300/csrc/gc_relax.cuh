@@ -466,9 +466,10 @@ __device__ __forceinline__ void df_to_fp64(unsigned char* slot, int tl, int T, i
 
 // One FP64 pass over an FP64 state in colour-position order: returns the
 // team's max_x div(x)^2 and writes record i: the functional (Eq. 3) as
-// sum_x [d - Re(conj(g_x) S+_x)] with S+ the forward half of the staple, the
-// fingerprint cos(phi^theta) of link (site 0, mu 0) and the canonical copy
-// g'_x = g_x conj(g_{V-1}) in site order.
+// d V - (1/2) sum_x Re(conj(g_x) S_x) (the staple S_x holds each link once
+// forward and once backward, so the sum counts every cos(phi^theta) twice),
+// the fingerprint cos(phi^theta) of link (site 0, mu 0) and the canonical
+// copy g'_x = g_x conj(g_{V-1}) in site order.
 template <int DD>
 __device__ __forceinline__ double final_pass64(const Links64& u,
                                                const double2* __restrict__ g, const uint4* nbp,
@@ -480,22 +481,22 @@ __device__ __forceinline__ double final_pass64(const Links64& u,
   double r = 0.0, Fp = 0.0;
   for (int p = tl; p < V; p += T) {
     const uint4 nb = nbp[p];
-    double fx = 0.0, fy = 0.0, bx = 0.0, by = 0.0;
+    double sx = 0.0, sy = 0.0;
 #pragma unroll
     for (int mu = 0; mu < DD; ++mu) {
       const unsigned wd = nb_word(nb, mu);
       const int xp = wd & 0xffffu, xm = wd >> 16;
       const double2 a = u(mu, p), h = g[xp];
-      fx = fma(a.x, h.x, fx); fx = fma(-a.y, h.y, fx);
-      fy = fma(a.x, h.y, fy); fy = fma(a.y, h.x, fy);
+      sx = fma(a.x, h.x, sx); sx = fma(-a.y, h.y, sx);
+      sy = fma(a.x, h.y, sy); sy = fma(a.y, h.x, sy);
       const double2 b = u(mu, xm), k = g[xm];
-      bx = fma(b.x, k.x, bx); bx = fma(b.y, k.y, bx);
-      by = fma(b.x, k.y, by); by = fma(-b.y, k.x, by);
+      sx = fma(b.x, k.x, sx); sx = fma(b.y, k.y, sx);
+      sy = fma(b.x, k.y, sy); sy = fma(-b.y, k.x, sy);
     }
     const double2 gx = g[p];
-    const double dv = fma(gx.x, fy + by, -gx.y * (fx + bx));
+    const double dv = fma(gx.x, sy, -gx.y * sx);
     r = dmax_pos(r, dv * dv);
-    Fp += (double)DD - fma(gx.x, fx, gx.y * fy);
+    Fp = fma(gx.x, sx, fma(gx.y, sy, Fp));
     config[(size_t)i * V + site[p]] =
         make_double2(fma(gx.x, gc.x, gx.y * gc.y), fma(gx.y, gc.x, -gx.x * gc.y));
     if (p == 0) {   // site 0 sits at position 0
@@ -506,7 +507,7 @@ __device__ __forceinline__ double final_pass64(const Links64& u,
   }
   for (int o = T >> 1; o > 0; o >>= 1) r = dmax_pos(r, __shfl_xor_sync(mask, r, o));
   Fp = team_sum(Fp, T, mask);
-  if (tl == 0) Fout[i] = Fp;
+  if (tl == 0) Fout[i] = fma(-0.5, Fp, (double)(DD * V));
   return r;
 }
 
@@ -1909,7 +1910,8 @@ __global__ void __launch_bounds__(32 * TEAMS, 1) polish_pairs_kernel(const Polis
           const int P = i / L, K = i % L;
           const unsigned e = own_el(P);
           const unsigned so = s_st + 16u * e, uo = s_u64 + 16u * e + (unsigned)(K * D) * SS;
-          double fx = 0.0, fy = 0.0, bx = 0.0, by = 0.0;
+          // the staple S_x = sum_mu [u_{x,mu} g_{x+mu} + conj(u_{x-mu,mu}) g_{x-mu}]
+          double sx = 0.0, sy = 0.0;
 #pragma unroll
           for (int mu = 0; mu < D; ++mu) {
             double2 A, H, B, G;
@@ -1925,15 +1927,17 @@ __global__ void __launch_bounds__(32 * TEAMS, 1) polish_pairs_kernel(const Polis
               B = lds_d2<0>(s_u64 + em16 + (unsigned)(K * D + mu) * SS);
               G = lds_d2<0>(s_st + em16 + (unsigned)K * SS);
             }
-            fx = fma(A.x, H.x, fx); fx = fma(-A.y, H.y, fx);
-            fy = fma(A.x, H.y, fy); fy = fma(A.y, H.x, fy);
-            bx = fma(B.x, G.x, bx); bx = fma(B.y, G.y, bx);
-            by = fma(B.x, G.y, by); by = fma(-B.y, G.x, by);
+            sx = fma(A.x, H.x, sx); sx = fma(-A.y, H.y, sx);
+            sy = fma(A.x, H.y, sy); sy = fma(A.y, H.x, sy);
+            sx = fma(B.x, G.x, sx); sx = fma(B.y, G.y, sx);
+            sy = fma(B.x, G.y, sy); sy = fma(-B.y, G.x, sy);
           }
           const double2 gx = lds_d2<0>(so + (unsigned)K * SS);
-          const double dv = fma(gx.x, fy + by, -gx.y * (fx + bx));
+          // divergence Im(conj(g_x) S_x); and Re(conj(g_x) S_x), whose sum
+          // over the sites counts every link's cos(phi^theta) twice
+          const double dv = fma(gx.x, sy, -gx.y * sx);
           r = dmax_pos(r, dv * dv);
-          Fp += (double)D - fma(gx.x, fx, gx.y * fy);
+          Fp = fma(gx.x, sx, fma(gx.y, sy, Fp));
           const int x = K + L * (P ? line[1] : line[0]);
           a.config[(size_t)idx * V + x] =
               make_double2(fma(gx.x, gc.x, gx.y * gc.y), fma(gx.y, gc.x, -gx.x * gc.y));
@@ -1950,7 +1954,7 @@ __global__ void __launch_bounds__(32 * TEAMS, 1) polish_pairs_kernel(const Polis
         }
         const bool pass = dless_pos(r, a.eps);
         if (pass && h == 0) {
-          a.F[idx] = Fp;
+          a.F[idx] = fma(-0.5, Fp, (double)(D * V));   // Eq. 3: sum over links of 1 - cos(phi^theta)
           a.resid[idx] = r;
           a.status[idx] = kConverged;
           ++c_conv;
