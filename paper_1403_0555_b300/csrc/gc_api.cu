@@ -142,7 +142,7 @@ struct gc_orbit_s {
   Buf links64, links32;
   // copy table
   unsigned cap = 0, nb = 0, nl = 0, f8cap = 0;
-  Buf t_cfg, t_F, t_q, t_t, t_first, t_count, t_next, t_lam, t_region, t_head, t_lock, t_f8, t_f8n;
+  Buf t_cfg, t_F, t_q, t_t, t_first, t_rep, t_count, t_next, t_lam, t_region, t_head, t_lock, t_f8, t_f8n;
   Buf t_counters;    // n_entries, n_new (u32) | n_f8 (u64) | err[4] (i32) | n_redo (u32)
   Buf t_newlist;     // new entries of a batch [cap], then those left to FP64 [cap]
   // batch staging
@@ -186,6 +186,7 @@ struct gc_orbit_s {
     T.q = t_q.as<long long>();
     T.t = t_t.as<int>();
     T.first_start = t_first.as<unsigned long long>();
+    T.rep_start = t_rep.as<unsigned long long>();
     T.count = t_count.as<unsigned long long>();
     T.next = t_next.as<int>();
     T.lambda2 = t_lam.as<double>();
@@ -269,9 +270,10 @@ int table_reserve(gc_orbit o, unsigned long long need, unsigned cur, cudaStream_
   if (want > 0x7fffffffULL) return fail(GC_ENOMEM, "copy pool would exceed 2^31 entries");
   const unsigned ncap = (unsigned)want;
   const size_t V = o->V;
-  Buf cfg, F, q, t, first, count, next, lam, region;
+  Buf cfg, F, q, t, first, rep, count, next, lam, region;
   bool ok = cfg.ensure(ncap * V * sizeof(double2), s) && F.ensure(ncap * 8ull, s) &&
             q.ensure(ncap * 8ull, s) && t.ensure(ncap * 4ull, s) && first.ensure(ncap * 8ull, s) &&
+            rep.ensure(ncap * 8ull, s) &&
             count.ensure(ncap * 8ull, s) && next.ensure(ncap * 4ull, s) && lam.ensure(ncap * 8ull, s) &&
             region.ensure(ncap * 4ull, s);
   Buf newlist;
@@ -283,7 +285,7 @@ int table_reserve(gc_orbit o, unsigned long long need, unsigned cur, cudaStream_
   Buf f8, f8n;
   ok = ok && f8.ensure(nf8 * 8ull, s) && f8n.ensure(nf8 * 8ull, s);
   if (!ok) {
-    for (Buf* b : {&cfg, &F, &q, &t, &first, &count, &next, &lam, &region, &newlist, &head, &f8, &f8n})
+    for (Buf* b : {&cfg, &F, &q, &t, &first, &rep, &count, &next, &lam, &region, &newlist, &head, &f8, &f8n})
       b->release(s);
     return fail(GC_ENOMEM, "cannot admit a copy pool of %u entries (%.1f MiB)", ncap,
                 ncap * (V * 16.0 + 64.0) / 1048576.0);
@@ -294,6 +296,7 @@ int table_reserve(gc_orbit o, unsigned long long need, unsigned cur, cudaStream_
     GC_CUDA(cudaMemcpyAsync(q.p, o->t_q.p, cur * 8ull, cudaMemcpyDeviceToDevice, s));
     GC_CUDA(cudaMemcpyAsync(t.p, o->t_t.p, cur * 4ull, cudaMemcpyDeviceToDevice, s));
     GC_CUDA(cudaMemcpyAsync(first.p, o->t_first.p, cur * 8ull, cudaMemcpyDeviceToDevice, s));
+    GC_CUDA(cudaMemcpyAsync(rep.p, o->t_rep.p, cur * 8ull, cudaMemcpyDeviceToDevice, s));
     GC_CUDA(cudaMemcpyAsync(count.p, o->t_count.p, cur * 8ull, cudaMemcpyDeviceToDevice, s));
     GC_CUDA(cudaMemcpyAsync(lam.p, o->t_lam.p, cur * 8ull, cudaMemcpyDeviceToDevice, s));
     GC_CUDA(cudaMemcpyAsync(region.p, o->t_region.p, cur * 4ull, cudaMemcpyDeviceToDevice, s));
@@ -309,16 +312,41 @@ int table_reserve(gc_orbit o, unsigned long long need, unsigned cur, cudaStream_
                                               f8n.as<unsigned long long>(), nf8 - 1, o->err());
     ++o->launches;
   }
-  for (Buf* b : {&o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_count, &o->t_next, &o->t_lam,
-                 &o->t_region, &o->t_newlist, &o->t_head, &o->t_f8, &o->t_f8n})
+  for (Buf* b : {&o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_rep, &o->t_count, &o->t_next,
+                 &o->t_lam, &o->t_region, &o->t_newlist, &o->t_head, &o->t_f8, &o->t_f8n})
     b->release(s);
-  o->t_cfg = cfg; o->t_F = F; o->t_q = q; o->t_t = t; o->t_first = first; o->t_count = count;
+  o->t_cfg = cfg; o->t_F = F; o->t_q = q; o->t_t = t; o->t_first = first; o->t_rep = rep; o->t_count = count;
   o->t_next = next; o->t_lam = lam; o->t_region = region; o->t_newlist = newlist; o->t_head = head;
   o->t_f8 = f8; o->t_f8n = f8n;
   o->cap = ncap; o->nb = nnb; o->f8cap = nf8;
   if (cur) {
     const unsigned blocks = std::min<unsigned>((cur + 255) / 256, 4096);
     gc::relink_kernel<<<blocks, 256, 0, s>>>(o->view(), cur);
+    ++o->launches;
+  }
+  GC_CUDA(cudaGetLastError());
+  return GC_OK;
+}
+
+// Deduplication of one batch: find or insert each start's copy, then count
+// the starts per copy (and the paper-style F set), then give every copy the
+// batch created the configuration and F of its lowest start.
+int launch_dedup(gc_orbit o, const gc::DedupArgs& da, cudaStream_t s) {
+  const long long b = da.n;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((b + 7) / 8, (long long)sm_count() * 8));
+  gc::dedup_kernel<<<blocks, 256, 0, s>>>(da);
+  gc::CountArgs ca{};
+  ca.tab = da.tab;
+  ca.n = da.n;
+  ca.start0 = da.start0;
+  ca.status = da.status;
+  ca.F = da.F;
+  ca.copy_of = da.copy_of;
+  const int cblocks = (int)std::max<long long>(1, std::min<long long>((b + 255) / 256, (long long)sm_count() * 8));
+  gc::count_kernel<<<cblocks, 256, 0, s>>>(ca);
+  o->launches += 2;
+  if (!da.tab.f8_only) {
+    gc::fixup_kernel<<<sm_count() * 4, 256, 0, s>>>(da.tab, da.V, da.start0, da.F, da.config);
     ++o->launches;
   }
   GC_CUDA(cudaGetLastError());
@@ -523,7 +551,7 @@ int gc_destroy_orbit(gc_orbit o) {
   if (!o) return fail(GC_EINVAL, "gc_destroy_orbit: NULL orbit");
   cudaStreamSynchronize(o->last_stream);
   cudaStream_t s = nullptr;
-  for (Buf* b : {&o->links64, &o->links32, &o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_count,
+  for (Buf* b : {&o->links64, &o->links32, &o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_rep, &o->t_count,
                  &o->t_next, &o->t_lam, &o->t_region, &o->t_head, &o->t_lock, &o->t_f8, &o->t_f8n, &o->t_counters,
                  &o->t_newlist, &o->s_status, &o->s_sweeps, &o->s_resid, &o->s_F, &o->s_fprint,
                  &o->s_config, &o->s_state32, &o->s_copy, &o->s_redo, &o->s_rate, &o->work, &o->stats, &o->scratch, &o->theta_tmp,
@@ -1030,12 +1058,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     da.config = st64;
     da.copy_of = o->s_copy.as<int>();
     da.stats = stats;
-    {
-      const int blocks = (int)std::max<long long>(1, std::min<long long>((b + 7) / 8, (long long)sm_count() * 8));
-      gc::dedup_kernel<<<blocks, 256, 0, s>>>(da);
-      ++o->launches;
-      GC_CUDA(cudaGetLastError());
-    }
+    if (int rc = launch_dedup(o, da, s)) return rc;
     if (ev) GC_CUDA(cudaEventRecord(ev[4], s));
     if (opt.fp_mode != GC_FP_NONE) {
       // first-region test of the batch's new copies: Lanczos with vectors in
@@ -1487,12 +1510,7 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     da.config = ra.config;
     da.copy_of = o->s_copy.as<int>();
     da.stats = stats;
-    {
-      const int blocks = (int)std::max<long long>(1, std::min<long long>((b + 7) / 8, (long long)sm_count() * 8));
-      gc::dedup_kernel<<<blocks, 256, 0, s>>>(da);
-      ++o->launches;
-      GC_CUDA(cudaGetLastError());
-    }
+    if (int rc = launch_dedup(o, da, s)) return rc;
     if (ev) GC_CUDA(cudaEventRecord(ev[4], s));
     // Faddeev-Popov test of the copies this batch created
     if (opt.fp_mode != GC_FP_NONE) {
@@ -2310,7 +2328,7 @@ int rehome_orbit(gc_orbit o, cudaStream_t s) {
     cur = std::min(cur, o->cap);
     if (int rc = table_reserve(o, cur, cur, s, true)) return rc;
   }
-  for (Buf* b : {&o->links64, &o->links32, &o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_count,
+  for (Buf* b : {&o->links64, &o->links32, &o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_rep, &o->t_count,
                  &o->t_next, &o->t_lam, &o->t_region, &o->t_head, &o->t_lock, &o->t_f8, &o->t_f8n,
                  &o->t_counters, &o->t_newlist, &o->work, &o->stats}) {
     if (!b->p || !in_arena(b->p)) continue;

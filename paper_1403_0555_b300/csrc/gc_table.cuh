@@ -7,14 +7,21 @@
 // share the fingerprint c0 = cos(phi^theta) of link (site 0, mu 0) to far
 // below wT, so candidates live in the 3 x 3 neighbouring (F, c0) buckets.
 //
-// Concurrency: an insert holds the locks of its three F-neighbour buckets
-// (taken in ascending lock index, so no cycle can form); every entry it may
-// read or change has q within +-1 of its own and so sits under a held lock.
-// That makes the outcome independent of the interleaving: each distinct copy
-// ends with count = number of starts that reached it, first_start = the
-// lowest of those start indices, and the representative configuration and F
-// of that lowest start.  Every lock wait is bounded; a start whose wait runs
-// out is marked kDedupFailed and the call reports a timeout.
+// Three kernels per batch.  dedup_kernel (a warp per start) finds or inserts
+// each converged start's copy and records it in copy_of; an insert holds the
+// locks of its three F-neighbour buckets (taken in ascending lock index, so
+// no cycle can form), so every entry it may read or change sits under a held
+// lock and no copy is inserted twice.  count_kernel (a thread per start)
+// then adds each start to its copy's count and first start, and to the
+// paper-style F set, with the starts of a warp that share a copy (or an F
+// key) grouped first, so a copy that most starts reach costs one atomic per
+// warp instead of one per start.  fixup_kernel gives every copy created in
+// the batch the configuration and F of its lowest start.  The outcome is
+// independent of the interleaving: count = number of starts that reached the
+// copy, first_start = the lowest of those start indices, and the
+// representative configuration and F of that start.  Every lock wait is
+// bounded; a start whose wait runs out is marked kDedupFailed and the call
+// reports a timeout.
 #pragma once
 #include "gc_common.cuh"
 
@@ -26,6 +33,7 @@ struct TableView {
   long long* q;            // F bucket
   int* t;                  // fingerprint bucket
   unsigned long long* first_start;
+  unsigned long long* rep_start;   // start whose configuration cfg holds
   unsigned long long* count;
   int* next;
   double* lambda2;
@@ -70,39 +78,54 @@ __device__ inline void release(int* lk) {
   atomicExch(lk, 0);
 }
 
-// warp-wide configuration comparison (all 32 lanes)
+// warp-wide configuration comparison (all 32 lanes): 128 sites a round, the
+// loads of a round issued before any comparison so that one round costs one
+// memory latency
 __device__ inline bool same_copy(const double2* __restrict__ a, const double2* __restrict__ b, int V,
                                  double delta2, int lane) {
-  for (int x0 = 0; x0 < V; x0 += 32) {
-    const int x = x0 + lane;
+  for (int x0 = 0; x0 < V; x0 += 128) {
+    double2 p[4], r[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int x = x0 + 32 * c + lane;
+      if (x < V) { p[c] = __ldcg(a + x); r[c] = b[x]; }
+    }
     bool ok = true;
-    if (x < V) {
-      const double2 p = __ldcg(a + x), r = b[x];
-      const double dx = p.x - r.x, dy = p.y - r.y;
-      ok = dx * dx + dy * dy <= delta2;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int x = x0 + 32 * c + lane;
+      if (x < V) {
+        const double dx = p[c].x - r[c].x, dy = p[c].y - r[c].y;
+        ok = ok && dx * dx + dy * dy <= delta2;
+      }
     }
     if (!__all_sync(0xffffffffu, ok)) return false;
   }
   return true;
 }
 
-// Search the 3 x 3 (F, fingerprint) neighbourhood for a copy equal to `mine`.
+// Search the 3 x 3 (F, fingerprint) neighbourhood for a copy equal to `mine`:
+// lanes 0-8 walk the nine bucket lists side by side, and each entry whose
+// (F, fingerprint) buckets and F match is compared by the whole warp.
 // Safe without locks: entries are only ever prepended, and a representative
 // that is being replaced differs from its successor far below delta.
 __device__ inline int table_search(const TableView& T, long long q, int t, double F,
                                    const double2* mine, int V, int lane) {
-  for (int dq = -1; dq <= 1; ++dq) {
-    for (int dt = -1; dt <= 1; ++dt) {
-      const long long qq = q + dq;
-      const int tt = t + dt;
-      unsigned guard = 0;
-      for (int e = __ldcg(T.head + bucket_of(T, qq, tt)); e >= 0 && guard <= T.cap;
-           e = __ldcg(T.next + e), ++guard) {
-        if (__ldcg(T.q + e) != qq || __ldcg(T.t + e) != tt) continue;
-        if (fabs(__ldcg(T.F + e) - F) > T.tolF) continue;
-        if (same_copy(T.cfg + (size_t)e * V, mine, V, T.delta2, lane)) return e;
-      }
+  const long long qq = q + lane / 3 - 1;
+  const int tt = t + lane % 3 - 1;
+  int e = lane < 9 ? __ldcg(T.head + bucket_of(T, qq, tt)) : -1;
+  for (unsigned depth = 0; depth <= T.cap; ++depth) {
+    const bool cand = e >= 0 && __ldcg(T.q + e) == qq && __ldcg(T.t + e) == tt &&
+                      fabs(__ldcg(T.F + e) - F) <= T.tolF;
+    unsigned m = __ballot_sync(0xffffffffu, cand);
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1;
+      const int ce = __shfl_sync(0xffffffffu, e, src);
+      if (same_copy(T.cfg + (size_t)ce * V, mine, V, T.delta2, lane)) return ce;
     }
+    if (e >= 0) e = __ldcg(T.next + e);
+    if (!__any_sync(0xffffffffu, e >= 0)) break;
   }
   return -1;
 }
@@ -120,7 +143,7 @@ struct DedupArgs {
   unsigned long long* stats; // [10] new, [11] hits, [12] failures
 };
 
-__global__ void __launch_bounds__(256) dedup_kernel(const DedupArgs a) {
+__global__ void __launch_bounds__(256, 4) dedup_kernel(const DedupArgs a) {
   const TableView& T = a.tab;
   const int lane = threadIdx.x & 31;
   const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -134,66 +157,50 @@ __global__ void __launch_bounds__(256) dedup_kernel(const DedupArgs a) {
     const int t = (int)floor((a.fprint[i] + 1.0) / T.wT);
     const unsigned long long start = a.start0 + (unsigned long long)i;
     const double2* mine = a.config + (size_t)i * V;
-    // paper-style quantised minimum (lock-free set)
-    if (lane == 0) {
-      const unsigned long long k8 = (unsigned long long)floor((F / T.f8_links) * 1e8);
-      unsigned slot = (unsigned)(mix64(k8) & T.f8_mask);
-      bool placed = false;
-      for (unsigned p = 0; p <= T.f8_mask; ++p) {
-        const unsigned long long prev = atomicCAS(&T.f8[slot], kF8Empty, k8);
-        if (prev == kF8Empty) { atomicAdd(T.n_f8, 1ULL); placed = true; break; }
-        if (prev == k8) { placed = true; break; }
-        slot = (slot + 1) & T.f8_mask;
-      }
-      if (placed) atomicAdd(&T.f8n[slot], 1ULL);
-      else atomicExch(&T.err[2], 1);
-      if (T.f8_only) a.copy_of[i] = -1;
-    }
-    if (T.f8_only) continue;   // uniform across the warp
-    // fast path: most starts land on a copy that is already in the table
-    int e = table_search(T, q, t, F, mine, V, lane);
-    bool locked = false;
-    unsigned l0 = 0, l1 = 0, l2 = 0;
-    if (e < 0) {
-      // slow path: take the three F-neighbour locks (ascending, distinct) with
-      // non-blocking tries; between tries search again without locks, so that
-      // starts waiting on a copy another warp is inserting take the hit path as
-      // soon as it is published instead of queueing on the lock
+    if (T.f8_only) { if (lane == 0) a.copy_of[i] = -1; continue; }   // uniform across the warp
+    // Search; most starts land on a copy that is already in the table.  On a
+    // miss, try once for the three F-neighbour locks (ascending, distinct,
+    // non-blocking) and search again: under the locks that search decides
+    // the insert; without them, after a backoff, a start waiting on a copy
+    // another warp is inserting takes the hit path as soon as it is
+    // published instead of queueing on the lock.  (One search call site.)
+    unsigned l0 = lock_of(T, q - 1), l1 = lock_of(T, q), l2 = lock_of(T, q + 1);
+    {
       unsigned tmp;
-      l0 = lock_of(T, q - 1); l1 = lock_of(T, q); l2 = lock_of(T, q + 1);
       if (l0 > l1) { tmp = l0; l0 = l1; l1 = tmp; }
       if (l1 > l2) { tmp = l1; l1 = l2; l2 = tmp; }
       if (l0 > l1) { tmp = l0; l0 = l1; l1 = tmp; }
-      int ok = 0;
-      unsigned ns = 64;
-      for (long long tries = 0; tries < T.lock_spins; ++tries) {
-        if (lane == 0) {
-          ok = atomicCAS(&T.lock[l0], 0, 1) == 0;
-          if (ok && l1 != l0 && atomicCAS(&T.lock[l1], 0, 1) != 0) { atomicExch(&T.lock[l0], 0); ok = 0; }
-          if (ok && l2 != l1 && atomicCAS(&T.lock[l2], 0, 1) != 0) {
-            if (l1 != l0) atomicExch(&T.lock[l1], 0);
-            atomicExch(&T.lock[l0], 0);
-            ok = 0;
-          }
-          if (ok) __threadfence();
-        }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (ok) break;
-        __nanosleep(ns);
-        if (ns < 2048) ns <<= 1;
-        e = table_search(T, q, t, F, mine, V, lane);
-        if (e >= 0) break;
-      }
-      if (!ok && e < 0) {
-        if (lane == 0) { atomicExch(&T.err[0], 1); a.status[i] = kDedupFailed; a.copy_of[i] = -1; }
-        ++c_fail;
-        continue;
-      }
     }
-    if (e < 0) {
-      locked = true;
-      __syncwarp();
+    int e = -1;
+    bool locked = false, failed = false;
+    long long tries = 0;
+    unsigned ns = 64;
+    for (;;) {
       e = table_search(T, q, t, F, mine, V, lane);
+      if (e >= 0 || locked) break;
+      int ok = 0;
+      if (lane == 0) {
+        ok = atomicCAS(&T.lock[l0], 0, 1) == 0;
+        if (ok && l1 != l0 && atomicCAS(&T.lock[l1], 0, 1) != 0) { atomicExch(&T.lock[l0], 0); ok = 0; }
+        if (ok && l2 != l1 && atomicCAS(&T.lock[l2], 0, 1) != 0) {
+          if (l1 != l0) atomicExch(&T.lock[l1], 0);
+          atomicExch(&T.lock[l0], 0);
+          ok = 0;
+        }
+        if (ok) __threadfence();
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (ok) { locked = true; __syncwarp(); continue; }
+      if (++tries >= T.lock_spins) { failed = true; break; }
+      __nanosleep(ns);
+      if (ns < 2048) ns <<= 1;
+    }
+    if (failed) {
+      if (lane == 0) { atomicExch(&T.err[0], 1); a.status[i] = kDedupFailed; a.copy_of[i] = -1; }
+      ++c_fail;
+      continue;
+    }
+    if (locked) {
       if (e < 0) {
         if (lane == 0) e = (int)atomicAdd(T.n_entries, 1u);
         e = __shfl_sync(0xffffffffu, e, 0);
@@ -205,7 +212,7 @@ __global__ void __launch_bounds__(256) dedup_kernel(const DedupArgs a) {
           for (int x = lane; x < V; x += 32) T.cfg[(size_t)e * V + x] = mine[x];
           if (lane == 0) {
             T.F[e] = F; T.q[e] = q; T.t[e] = t;
-            T.first_start[e] = start; T.count[e] = 1ULL;
+            T.first_start[e] = start; T.rep_start[e] = start; T.count[e] = 0ULL;
             T.lambda2[e] = __longlong_as_double(0x7ff8000000000000LL);
             T.region[e] = -1;
             // Lock-free prepend: two q values may hash to one list, and their
@@ -213,7 +220,7 @@ __global__ void __launch_bounds__(256) dedup_kernel(const DedupArgs a) {
             // visible before e is published.
             const unsigned b = bucket_of(T, q, t);
             int old = __ldcg(T.head + b);
-            for (int tries = 0; tries < (1 << 24); ++tries) {
+            for (int k = 0; k < (1 << 24); ++k) {
               T.next[e] = old;
               __threadfence();
               const int seen = atomicCAS(T.head + b, old, e);
@@ -227,37 +234,7 @@ __global__ void __launch_bounds__(256) dedup_kernel(const DedupArgs a) {
         }
       }
     }
-    if (e >= 0) {
-      // existing copy: count it; the lowest start index keeps its configuration
-      unsigned long long old = 0;
-      if (lane == 0) {
-        atomicAdd(&T.count[e], 1ULL);
-        old = atomicMin(&T.first_start[e], start);
-      }
-      old = __shfl_sync(0xffffffffu, old, 0);
-      if (start < old) {
-        // rewrite the representative under the lock of the entry's F bucket
-        // (held already on the slow path)
-        const unsigned le = lock_of(T, __ldcg(T.q + e));
-        int ok = 1;
-        const bool have = locked && (le == l0 || le == l1 || le == l2);
-        if (lane == 0 && !have) ok = acquire(&T.lock[le], T.lock_spins);
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (ok) {
-          __syncwarp();
-          const bool still = __ldcg(T.first_start + e) == start;
-          if (still) {
-            for (int x = lane; x < V; x += 32) T.cfg[(size_t)e * V + x] = mine[x];
-            if (lane == 0) T.F[e] = F;
-          }
-          __syncwarp();
-          if (lane == 0 && !have) release(&T.lock[le]);
-        } else if (lane == 0) {
-          atomicExch(&T.err[0], 1);
-        }
-      }
-      ++c_hit;
-    }
+    if (e >= 0) ++c_hit;   // counted, with its first start, by count_kernel
     __syncwarp();
     if (locked && lane == 0) {
       if (l2 != l1) release(&T.lock[l2]);
@@ -271,6 +248,72 @@ __global__ void __launch_bounds__(256) dedup_kernel(const DedupArgs a) {
     atomicAdd(&a.stats[10], c_new);
     atomicAdd(&a.stats[11], c_hit);
     atomicAdd(&a.stats[12], c_fail);
+  }
+}
+
+struct CountArgs {
+  TableView tab;
+  long long n;
+  uint64_t start0;
+  const int8_t* status;
+  const double* F;
+  const int* copy_of;
+};
+
+// A thread per start (whole warps, start index increasing with the lane):
+// starts of one warp that reached the same copy add their number to its
+// count in one atomic, and the group's lowest start (its first lane) to its
+// first start; likewise every start that converged (also one whose dedup
+// failed) adds itself to the set of floor(F/(dV) 1e8) keys (Section III).
+__global__ void __launch_bounds__(256) count_kernel(const CountArgs a) {
+  const TableView& T = a.tab;
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = w0 * 32; base < a.n; base += nw * 32) {
+    const long long i = base + lane;
+    const bool in = i < a.n;
+    const int8_t st = in ? a.status[i] : (int8_t)0;
+    const int e = in ? a.copy_of[i] : -1;
+    const unsigned me = __match_any_sync(0xffffffffu, e);
+    if (e >= 0 && lane == __ffs(me) - 1) {
+      atomicAdd(&T.count[e], (unsigned long long)__popc(me));
+      atomicMin(&T.first_start[e], a.start0 + (unsigned long long)i);
+    }
+    const bool conv = st == kConverged || st == kDedupFailed;
+    const unsigned long long k8 = conv ? (unsigned long long)floor((a.F[i] / T.f8_links) * 1e8) : kF8Empty;
+    const unsigned m8 = __match_any_sync(0xffffffffu, k8);
+    if (conv && lane == __ffs(m8) - 1) {
+      unsigned slot = (unsigned)(mix64(k8) & T.f8_mask);
+      bool placed = false;
+      for (unsigned p = 0; p <= T.f8_mask; ++p) {
+        const unsigned long long prev = atomicCAS(&T.f8[slot], kF8Empty, k8);
+        if (prev == kF8Empty) { atomicAdd(T.n_f8, 1ULL); placed = true; break; }
+        if (prev == k8) { placed = true; break; }
+        slot = (slot + 1) & T.f8_mask;
+      }
+      if (placed) atomicAdd(&T.f8n[slot], (unsigned long long)__popc(m8));
+      else atomicExch(&T.err[2], 1);
+    }
+  }
+}
+
+// A warp per copy created in this batch: if its lowest start is not the one
+// whose configuration it holds, take that start's configuration and F.
+__global__ void __launch_bounds__(256) fixup_kernel(const TableView T, int V, uint64_t start0,
+                                                    const double* __restrict__ F,
+                                                    const double2* __restrict__ config) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned n = *T.n_new;
+  for (long long j = w0; j < (long long)n; j += nw) {
+    const unsigned e = T.new_list[j];
+    const unsigned long long fs = T.first_start[e];
+    if (fs == T.rep_start[e]) continue;   // uniform across the warp
+    const size_t i = (size_t)(fs - start0);
+    for (int x = lane; x < V; x += 32) T.cfg[(size_t)e * V + x] = __ldcg(config + i * V + x);
+    if (lane == 0) { T.F[e] = F[i]; T.rep_start[e] = fs; }
   }
 }
 
