@@ -1045,6 +1045,8 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     da.tab = o->view();
     da.tab.wF = 1e-9 * std::max(1.0, (double)d * V * 1e-3);
     da.tab.wT = 1e-5;
+    da.tab.inv_wF = 1.0 / da.tab.wF;
+    da.tab.inv_wT = 1.0 / da.tab.wT;
     da.tab.tolF = da.tab.wF;
     da.tab.delta2 = opt.dedup_delta * opt.dedup_delta;
     da.tab.f8_links = (double)d * V;
@@ -1497,6 +1499,8 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     da.tab = o->view();
     da.tab.wF = 1e-9 * std::max(1.0, (double)d * V * 1e-3);
     da.tab.wT = 1e-5;
+    da.tab.inv_wF = 1.0 / da.tab.wF;
+    da.tab.inv_wT = 1.0 / da.tab.wT;
     da.tab.tolF = da.tab.wF;
     da.tab.delta2 = opt.dedup_delta * opt.dedup_delta;
     da.tab.f8_links = (double)d * V;

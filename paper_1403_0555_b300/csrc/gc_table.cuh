@@ -50,6 +50,7 @@ struct TableView {
   unsigned int cap;
   unsigned int nb_mask, nl_mask, f8_mask;
   double wF, wT, tolF, delta2, f8_links;  // f8_links = d V (F_norm = F / (d V))
+  double inv_wF, inv_wT;   // 1 / wF, 1 / wT: bucket keys by multiplication
   int f8_only;             // GC_DEDUP_F8: the F set only, no configuration table
   long long lock_spins;    // tries before a lock wait gives up (kLockSpins by default)
 };
@@ -90,13 +91,17 @@ __device__ inline bool same_copy(const double2* __restrict__ a, const double2* _
       const int x = x0 + 32 * c + lane;
       if (x < V) { p[c] = __ldcg(a + x); r[c] = b[x]; }
     }
+    // FP64 differences; their squares and the test against delta^2 in FP32
+    // (a relative blur of 1e-7 on a threshold that copies of one stationary
+    // point undercut, and distinct copies exceed, by many orders)
     bool ok = true;
+    const float d2 = (float)delta2;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int x = x0 + 32 * c + lane;
       if (x < V) {
-        const double dx = p[c].x - r[c].x, dy = p[c].y - r[c].y;
-        ok = ok && dx * dx + dy * dy <= delta2;
+        const float dx = d2f_bits(p[c].x - r[c].x), dy = d2f_bits(p[c].y - r[c].y);
+        ok = ok && fmaf(dx, dx, dy * dy) <= d2;
       }
     }
     if (!__all_sync(0xffffffffu, ok)) return false;
@@ -153,8 +158,8 @@ __global__ void __launch_bounds__(256, 4) dedup_kernel(const DedupArgs a) {
   for (long long i = warp0; i < a.n; i += nwarps) {
     if (a.status[i] != kConverged) { if (lane == 0) a.copy_of[i] = -1; continue; }
     const double F = a.F[i];
-    const long long q = (long long)floor(F / T.wF);
-    const int t = (int)floor((a.fprint[i] + 1.0) / T.wT);
+    const long long q = (long long)floor(F * T.inv_wF);
+    const int t = (int)floor((a.fprint[i] + 1.0) * T.inv_wT);
     const unsigned long long start = a.start0 + (unsigned long long)i;
     const double2* mine = a.config + (size_t)i * V;
     if (T.f8_only) { if (lane == 0) a.copy_of[i] = -1; continue; }   // uniform across the warp
