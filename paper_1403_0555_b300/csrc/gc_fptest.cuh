@@ -14,7 +14,10 @@
 //   kFpAuto     -- FP32 Lanczos screen; copies with lambda_2 clearly above 0
 //                  are accepted, the rest go to a second list that the FP64
 //                  kernel decides by FP64 Lanczos;
-//   kFpLanczos  -- FP64 Lanczos for every copy;
+//   kFpLanczos  -- FP64 Lanczos for every copy, started from the FP64
+//                  Rayleigh-Ritz vector of the two lowest Ritz vectors of an
+//                  FP32 Lanczos run (lanczos32_ritz, rayleigh_ritz2_64,
+//                  lanczos64_seeded; fp_test_pairs_kernel on 4^4);
 //   kFpDense    -- FP64 Lanczos with full reorthogonalisation run to
 //                  dimension V-1 (the whole spectrum; a dense-solver grade
 //                  lambda_2), basis vectors in a global scratch slot per warp;
@@ -262,27 +265,21 @@ __device__ R lanczos_min(const R* w, R* vprev, R* vcur, R* z, R* alpha, R* beta,
 }
 
 // ---------------------------------------------------------------------------
-// FP64 Lanczos with the FP64 pipe kept for the recurrence itself.  On this
-// part an FP64 instruction costs the SM about 64 FP32 ones, so:
+// FP64 helpers of the Lanczos mode.  On this part an FP64 instruction costs
+// the SM about 64 FP32 ones, so:
 //   * M v = D v - sum_mu [w_{x,mu} v_{x+mu} + w_{x-mu,mu} v_{x-mu}], with the
 //     diagonal D and the negated weights stored once per copy: 2d + 1 FMAs per
-//     site, and the whole step (recurrence, alpha, mean, norm, next vector)
-//     in 15 FP64 operations per site;
+//     site, and the whole Lanczos step (recurrence, alpha, mean, norm, next
+//     vector) in 15 FP64 operations per site;
 //   * the mean and the squared norm of the new vector share one warp
-//     reduction that adds each level once;
-//   * convergence is first followed in FP32: the tridiagonal, rounded to FP32,
-//     by Sturm multisection every 8 steps, until those Ritz values stall;
-//   * from then on each check takes lambda_min of the FP64 tridiagonal by
-//     tri_min64 (division-free Sturm counts, Newton steps from below): the
-//     first from a bracket around the FP32 value (two rounds), the later ones
-//     warm-started just below the previous value (Cauchy interlacing bounds
-//     the new one by it) in one round; the run stops when two FP64 values
-//     8 steps apart agree to tol64.  On this part an FP64 instruction costs
-//     the pipe the same with one active lane as with 32, so each round uses
-//     all 32 lanes (32 points);
+//     reduction that adds each level once (warp_sum2);
+//   * lambda_min of the FP64 tridiagonal by tri_min64 (division-free Sturm
+//     counts, Newton steps from below), warm-started just below the previous
+//     value (Cauchy interlacing bounds the new one by it); on this part an
+//     FP64 instruction costs the pipe the same with one active lane as with
+//     32, so each round uses all 32 lanes (32 points);
 //   * the normalisation's 1/sqrt in FP64 from the FP32 unit's estimate and
-//     two Newton steps, and comparisons on the integer pipe.
-// The result is the smallest Ritz value of the FP64 Lanczos tridiagonal.
+//     two Newton steps (rsqrt64), and comparisons on the integer pipe.
 // ---------------------------------------------------------------------------
 
 struct SturmPoint { int cnt; double p, dp; };
@@ -407,137 +404,6 @@ __device__ __forceinline__ void warp_sum2(double& a, double& b, int lane) {
   b = __shfl_sync(0xffffffffu, keep, 16);
 }
 
-// nw: negated weights [mu][x]; Dg: the diagonal of M; va, vb, vc: three
-// vectors; a64/b64: the tridiagonal; a32/b32: its FP32 image.
-template <int DD>
-__device__ double lanczos64_min(const double* nw, const double* Dg, double* va, double* vb, double* vc,
-                                double* a64, double* b64, float* a32, float* b32, int kmax, double tol32,
-                                double tol64, const uint4* nbr, int V, int lane, uint64_t seed,
-                                unsigned long long entry, int* steps) {
-  double* vcur = va;
-  double* vprev = vb;
-  double* z = vc;
-  // random start vector orthogonal to the constant mode (as in lanczos_min)
-  double s = 0.0;
-  for (int x = lane; x < V; x += 32) {
-    const U64x4 r = philox4x64_10(entry, (uint64_t)x, 0, 1, seed, 0x4C414E43ULL);
-    const double v = (double)(unsigned)(r.v[0] >> 40) * 0x1.0p-24 - 0.5;
-    vcur[x] = v;
-    vprev[x] = 0.0;
-    s += v;
-  }
-  s = warp_sum(s) / (double)V;
-  double nn = 0.0;
-  for (int x = lane; x < V; x += 32) { const double v = vcur[x] - s; vcur[x] = v; nn = fma(v, v, nn); }
-  const double inv0 = rsqrt64(warp_sum(nn));
-  for (int x = lane; x < V; x += 32) vcur[x] *= inv0;
-  __syncwarp();
-  const double invV = 1.0 / (double)V;
-  const float bound = (float)(4 * DD + 1);
-  float t32 = bound, t32_prev = bound, t32_pp = bound;   // bound = no estimate yet
-  double t64 = (double)bound, d64 = 0.0;                  // last FP64 value and its last decrease
-  bool fine = false;                                      // FP64 checks have started
-  double b = 0.0;
-  int j = 0;
-  for (; j < kmax; ++j) {
-    double a = 0.0;
-    const double mb = -b;
-    for (int x = lane; x < V; x += 32) {
-      const uint4 nb = nbr[x];
-      const double vx = vcur[x];
-      double y = fma(Dg[x], vx, mb * vprev[x]);
-#pragma unroll
-      for (int mu = 0; mu < DD; ++mu) {
-        const unsigned wd = nb_word(nb, mu);
-        const int xp = wd & 0xffffu, xm = wd >> 16;
-        y = fma(nw[mu * V + x], vcur[xp], y);
-        y = fma(nw[mu * V + xm], vcur[xm], y);
-      }
-      z[x] = y;
-      a = fma(y, vx, a);
-    }
-    a = warp_sum(a);
-    double m = 0.0, zz = 0.0;
-    for (int x = lane; x < V; x += 32) {
-      const double v = fma(-a, vcur[x], z[x]);
-      z[x] = v;
-      m += v;
-      zz = fma(v, v, zz);
-    }
-    warp_sum2(m, zz, lane);
-    m *= invV;
-    double bn2 = fma(-(double)V * m, m, zz);   // |z - m|^2
-    if (__double_as_longlong(bn2) < 0) bn2 = 0.0;
-    if (lane == 0) {
-      a64[j] = a;
-      b64[j + 1] = bn2;
-      a32[j] = d2f_bits(a);
-      b32[j + 1] = d2f_bits(bn2);
-    }
-    __syncwarp();
-    const bool last = (j + 1 == kmax) || dbelow(bn2, 1e-24);
-    // checks every 8 steps from step 16: FP32 until the FP32 view stalls, then FP64
-    if (last || ((j + 1) % 8 == 0 && j + 1 >= 16)) {
-      bool stall32 = false;
-      if (!fine) {
-        // FP32 view: bracket from Cauchy interlacing, as in lanczos_min
-        float lo = -bound, hi = bound;
-        if (t32_prev < bound) {
-          const float slack = 2.f * tri_rel<float>() * fmaxf(fabsf(t32_prev), 1.f);
-          hi = t32_prev + slack;
-          if (t32_pp < bound) {
-            const float l = t32_prev - 4.f * fmaxf(t32_pp - t32_prev, slack);
-            if (sturm_count<float>(a32, b32, j + 1, l) == 0) lo = l;
-          }
-        }
-        t32 = tri_min<float>(a32, b32, j + 1, lo, hi, lane);
-        stall32 = t32_prev < bound && fabsf(t32 - t32_prev) <= (float)tol32 * fmaxf(fabsf(t32), 1e-3f);
-        t32_pp = t32_prev;
-        t32_prev = t32;
-      }
-      if (fine || stall32 || last) {
-        bool ok = false;
-        double t = 0.0;
-        if (fine) {
-          // warm start: lambda_min(T_k) <= the last value (interlacing); points
-          // crowd just below it
-          const double hi = t64 + 1e-14 * fmax(fabs(t64), 1.0);
-          const double w = fmax(8.0 * d64, 4e-5 * fmax(fabs(t64), 1e-3));
-          t = tri_min64(a64, b64, j + 1, t64 - w, hi, lane, &ok, true);
-        }
-        if (!ok) {
-          // from the FP32 value, within rounding (~2e-6 ||T||) of the FP64 one
-          if (fine) {
-            float lo = -bound;
-            const float hi = (float)t64 + 2e-5f * fmaxf(1.f, fabsf((float)t64));
-            t32 = tri_min<float>(a32, b32, j + 1, lo, hi, lane);
-          }
-          const double c = f2d_bits(t32);
-          const double del = 2e-5 * fmax(1.0, fabs(c));
-          t = tri_min64(a64, b64, j + 1, c - del, c + del, lane, &ok);
-          if (!ok) t = tri_min64(a64, b64, j + 1, -(double)bound, (double)bound, lane, &ok);
-        }
-        const bool stall64 = fine && fabs(t - t64) <= tol64 * fmax(fabs(t), 1e-3);
-        d64 = fine ? fmax(t64 - t, 0.0) : 0.0;
-        t64 = t;
-        fine = true;
-        if (last || stall64) { ++j; break; }
-      }
-    }
-    const double ib = rsqrt64(bn2);
-    const double mib = -m * ib;
-    for (int x = lane; x < V; x += 32) z[x] = fma(z[x], ib, mib);
-    b = bn2 * ib;
-    double* t = vprev;
-    vprev = vcur;
-    vcur = z;
-    z = t;
-    __syncwarp();
-  }
-  *steps += j;
-  return t64;
-}
-
 // ---------------------------------------------------------------------------
 // FP64 Lanczos seeded by an FP32 Ritz vector (the Lanczos mode's test).
 // The FP64 pipe is the scarce unit, so the Lanczos process first runs in FP32
@@ -549,7 +415,7 @@ __device__ double lanczos64_min(const double* nw, const double* Dg, double* va, 
 // starts from y (lanczos64_seeded): its first Rayleigh quotient already holds
 // lambda_2 to roughly the square of the FP32 Ritz vector's error, and a few
 // FP64 steps take it to FP64 accuracy.  The result is the smallest Ritz value
-// of the FP64 tridiagonal, as in lanczos64_min; only its start vector differs.
+// of the FP64 tridiagonal; only the start vector differs from a random one.
 // ---------------------------------------------------------------------------
 
 // the random start (Philox draws, projected off the constant mode,
@@ -818,7 +684,7 @@ __device__ void rayleigh_ritz2_64(const double* nw, const double* Dg, double* va
 }
 
 // FP64 Lanczos from the start vector in va (normalised, orthogonal to the
-// constant mode).  The step is lanczos64_min's; lambda_min of the FP64
+// constant mode).  Each step takes 15 FP64 ops per site; lambda_min of the FP64
 // tridiagonal is taken after every step (T_1 is the seed's Rayleigh quotient;
 // later ones by tri_min64 warm-started just below the previous value, whose
 // window the last decrease sets), and the run stops when two successive
