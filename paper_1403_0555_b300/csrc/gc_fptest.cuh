@@ -523,6 +523,14 @@ __device__ __forceinline__ bool ritz32_stalled(float theta, float prev, double t
   return fabsf(theta - prev) <= fmaxf((float)tol32 * fabsf(theta), 2e-6f);
 }
 
+// The FP32 phase checks its smallest Ritz value at step 48 and every 16
+// steps after; one stall between two checks ends it (16 extra steps later).
+// Each check is a Sturm multisection over the whole tridiagonal, so checks
+// are kept few: the Ritz vector that matters needs the extra steps anyway.
+__device__ __forceinline__ bool ritz32_check_due(int steps) {
+  return steps >= 48 && ((steps - 48) & 15) == 0;
+}
+
 // Returns the smallest FP32 Ritz value; y and y2 receive the (unnormalised)
 // Ritz vectors of the smallest and second smallest Ritz values (y2 zero when
 // T_k has one row).  w: weights [mu][x] (positive); q, qp, z: work vectors.
@@ -533,7 +541,7 @@ __device__ float lanczos32_ritz(const float* w, float* q, float* qp, float* z, f
   ritz_start(q, qp, V, lane, seed, entry);
   const float bound = (float)(4 * DD + 1);
   float b = 0.f, theta = bound, theta_prev = bound, theta_pp = bound;
-  int stalls = 0, kend = kmax, j = 0;
+  int kend = kmax, j = 0;
   bool settled = false;
   for (; j < kend; ++j) {
     float a = 0.f;
@@ -559,7 +567,7 @@ __device__ float lanczos32_ritz(const float* w, float* q, float* qp, float* z, f
     if (lane == 0) { R.al[j] = a; R.be2[j + 1] = bn * bn; R.mm[j] = m; R.bn[j + 1] = bn; }
     __syncwarp();
     const bool last = (j + 1 == kend) || bn < 1e-12f;
-    if (last || (!settled && (j + 1) % 8 == 0 && j + 1 >= 24)) {
+    if (last || (!settled && ritz32_check_due(j + 1))) {
       float lo = -bound, hi = bound;
       if (theta_prev < bound) {
         const float slack = 2.f * tri_rel<float>() * fmaxf(fabsf(theta_prev), 1.f);
@@ -573,14 +581,10 @@ __device__ float lanczos32_ritz(const float* w, float* q, float* qp, float* z, f
       // shift) the full FP32 resolution
       theta = tri_min<float>(R.al, R.be2, j + 1, lo, hi, lane, last ? tri_rel<float>() : 1e-6f);
       if (last) { ++j; break; }
-      // two checks in a row (16 steps) as in lanczos_min, then `extra` steps more
+      // one stall over 16 steps, then `extra` steps more
       if (ritz32_stalled(theta, theta_prev, tol32)) {
-        if (++stalls == 2) {
-          settled = true;
-          kend = j + 1 + extra < kmax ? j + 1 + extra : kmax;
-        }
-      } else {
-        stalls = 0;
+        settled = true;
+        kend = j + 1 + extra < kmax ? j + 1 + extra : kmax;
       }
       theta_pp = theta_prev;
       theta_prev = theta;

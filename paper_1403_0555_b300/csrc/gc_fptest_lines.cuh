@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(256, 2) fp_test_pairs_kernel(const FpArgs a) {
       });
       __syncwarp();
       float theta_prev = bound, theta_pp = bound, b = 0.f;
-      int stalls = 0, kend = pass ? k - 1 : kk, j = 0;
+      int kend = pass ? k - 1 : kk, j = 0;
       bool settled = false;
       for (; j < kend; ++j) {
         // z = M q_j - b q_{j-1} (and its product with q_j for alpha)
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(256, 2) fp_test_pairs_kernel(const FpArgs a) {
           if (h == 0) { R.al[j] = al; R.be2[j + 1] = bn * bn; R.mm[j] = m; R.bn[j + 1] = bn; }
           __syncwarp();
           const bool last = (j + 1 == kend) || bn < 1e-12f;
-          if (last || (!settled && (j + 1) % 8 == 0 && j + 1 >= 24)) {
+          if (last || (!settled && ritz32_check_due(j + 1))) {
             float lo = -bound, hi = bound;
             if (theta_prev < bound) {
               const float slack = 2.f * tri_rel<float>() * fmaxf(fabsf(theta_prev), 1.f);
@@ -520,13 +520,10 @@ __global__ void __launch_bounds__(256, 2) fp_test_pairs_kernel(const FpArgs a) {
             // iteration's shift) the full FP32 resolution
             theta = tri_min<float>(R.al, R.be2, j + 1, lo, hi, h, last ? tri_rel<float>() : 1e-6f);
             if (last) { ++j; break; }
+            // one stall over 16 steps, then extra32 steps more
             if (ritz32_stalled(theta, theta_prev, a.tol32)) {
-              if (++stalls == 2) {
-                settled = true;
-                kend = j + 1 + a.extra32 < kk ? j + 1 + a.extra32 : kk;
-              }
-            } else {
-              stalls = 0;
+              settled = true;
+              kend = j + 1 + a.extra32 < kk ? j + 1 + a.extra32 : kk;
             }
             theta_pp = theta_prev;
             theta_prev = theta;
