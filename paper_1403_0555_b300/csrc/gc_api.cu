@@ -1356,8 +1356,12 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       auto k = gc::relax32_sheet_kernel<kWarps, 1>;
       const size_t sm = gc::relax32_sheet_smem<kWarps>();
       if (int rc = launch_grid(k, 32 * kWarps, sm, kWarps, b, &grid)) return rc;
+      // the batch's starts first, drawn at full occupancy into the FP32 state buffer
+      const int sblocks = (int)std::min<long long>(((long long)b * V + 255) / 256, (long long)sm_count() * 16);
+      gc::start32_kernel<<<sblocks, 256, 0, s>>>(ra.seed, ra.orbit_id, ra.start0, (long long)b, V,
+                                                 ra.state32);
       k<<<grid, 32 * kWarps, sm, s>>>(ra);
-      ++o->launches;
+      o->launches += 2;
     } else if (mixed && opt.relax_variant != GC_RELAX_GENERIC && d == 3 && o->L == 8) {
       constexpr int kTeams = 4;
       auto k = gc::relax32_lines_kernel<3, 8, kTeams>;

@@ -1117,6 +1117,35 @@ __device__ __noinline__ void line_start32(uint64_t seed, uint64_t orbit_id, uint
   }
 }
 
+// The same starts, drawn ahead by a kernel of their own into the batch's
+// FP32 state buffer (site order), so that the sweep kernel, whose warps are
+// few, loads them instead of running the Philox rounds itself.
+__global__ void __launch_bounds__(256) start32_kernel(uint64_t seed, uint64_t orbit_id, uint64_t start0,
+                                                      long long n, int V, float2* __restrict__ out) {
+  const long long total = n * (long long)V;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long i = t / V;
+    out[t] = random_unit32(seed, orbit_id, start0 + (uint64_t)i, (uint64_t)(t - i * V));
+  }
+}
+
+// A line's L drawn sites (site order, from start32_kernel) into the team's
+// shared copy in line_start32's paired layout
+template <int L>
+__device__ __forceinline__ void line_load32(const float2* __restrict__ src, unsigned dst, unsigned slot_bytes) {
+  constexpr int H = L / 2;
+  float2 v[L];
+#pragma unroll
+  for (int k = 0; k < L; ++k) v[k] = __ldcs(src + k);
+#pragma unroll
+  for (int k = 0; k < L; ++k) {
+    const unsigned p = dst + (unsigned)(k % H) * slot_bytes + 4u * (unsigned)(k / H);
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(p), "f"(v[k].x) : "memory");
+    asm volatile("st.shared.f32 [%0+8], %1;" ::"r"(p), "f"(v[k].y) : "memory");
+  }
+}
+
 __device__ __forceinline__ void team_bar(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -1490,11 +1519,12 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) relax32_sheet_kernel(const R
     if (j == 0) v = atomicAdd(a.work_ctr, 1ULL);
     return (long long)__shfl_sync(0xffffffffu, v, 0);
   };
+  // the start, drawn ahead by start32_kernel into this start's slice of the
+  // FP32 state buffer (which receives the final state at the end)
   auto init = [&](long long idx) {
 #pragma unroll
     for (int r = 0; r < 2; ++r)
-      line_start32(a.seed, a.orbit_id, a.start0 + idx, L * (x1[r] + L * (x2 + L * x3)), L,
-                   own + r * ROLE, SLOT);
+      line_load32<L>(a.state32 + (size_t)idx * V + L * (x1[r] + L * (x2 + L * x3)), own + r * ROLE, SLOT);
   };
   auto reload = [&]() {
     static_for<2>([&](auto RC) {
