@@ -244,6 +244,20 @@ int gc_server_destroy(gc_server s);
 int gc_fetch_copies(gc_orbit o, size_t capacity, size_t* n_distinct, double* F, double* theta,
                     uint64_t* first_start, uint64_t* count, double* lambda2, int* region);
 
+/* The same fetch, returning once the copies are enqueued.  The call waits
+ * for the orbit's earlier work (it reads the number of distinct copies), then
+ * enqueues the ordering and gathering kernels on the orbit's stream and the
+ * device-to-host copies into the arrays on a separate read-back stream, after
+ * them.  The arrays must be page-locked (pinned) for the copies to run
+ * asynchronously, and must stay valid and unread until gc_fetch_wait(o)
+ * returns; a later fetch of the same orbit, and gc_destroy_orbit, wait for
+ * the copies first.  Meanwhile other orbits' work (for example the next
+ * batch) can run on the GPU beside the copies.  Errors as gc_fetch_copies. */
+int gc_fetch_copies_async(gc_orbit o, size_t capacity, size_t* n_distinct, double* F, double* theta,
+                          uint64_t* first_start, uint64_t* count, double* lambda2, int* region);
+/* Waits for the copies of the orbit's last gc_fetch_copies_async. */
+int gc_fetch_wait(gc_orbit o);
+
 /* The paper's set of minima (Section III: minima told apart by F quantised
  * at 1e-8): the distinct keys floor(F/(dV) * 1e8) of every converged start so
  * far, in both dedup modes, in increasing order.  n_minima receives their

@@ -105,7 +105,8 @@ class gc_stats(ctypes.Structure):
 
 
 EXPORTED = ("gc_set_allocator", "gc_options_default", "gc_create_orbit", "gc_enumerate_copies",
-            "gc_fetch_copies", "gc_fetch_minima_f8", "gc_fetch_starts", "gc_orbit_stats", "gc_destroy_orbit",
+            "gc_fetch_copies", "gc_fetch_copies_async", "gc_fetch_wait", "gc_fetch_minima_f8",
+            "gc_fetch_starts", "gc_orbit_stats", "gc_destroy_orbit",
             "gc_last_error", "gc_version", "gc_fp_test_static", "gc_enumerate_batch",
             "gc_autotune", "gc_autotune_ex", "gc_server_create", "gc_server_submit",
             "gc_server_wait", "gc_server_destroy", "gc_peak_probe", "gc_test_dedup_locks", "gc_server_state")
@@ -146,6 +147,8 @@ def load(build_if_stale: bool = True):
         L.gc_fetch_copies.argtypes = [ctypes.c_void_p, ctypes.c_size_t,
                                       ctypes.POINTER(ctypes.c_size_t), p_d, p_d, p_u64, p_u64,
                                       p_d, p_i]
+        L.gc_fetch_copies_async.argtypes = L.gc_fetch_copies.argtypes
+        L.gc_fetch_wait.argtypes = [ctypes.c_void_p]
         L.gc_fetch_minima_f8.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
                                          p_d, p_u64]
         L.gc_fetch_starts.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, p_i,
@@ -302,11 +305,13 @@ def gc_fetch_minima_f8(orbit, capacity: int | None = None) -> dict:
 
 
 def gc_fetch_copies(orbit, V: int, capacity: int | None = None, theta: bool = True,
-                    out: dict | None = None) -> dict:
+                    out: dict | None = None, async_: bool = False) -> dict:
     """Distinct copies sorted by (F, first start).  `out` may hold preallocated
     arrays (for example in pinned host memory) named like the result's keys,
     each with at least as many rows as are fetched; the result then holds views
-    of them."""
+    of them.  With async_ the device-to-host copies are only enqueued
+    (gc_fetch_copies_async): the arrays, which should then be pinned, hold the
+    copies once gc_fetch_wait(orbit) returns."""
     lib = load()
     n = ctypes.c_size_t()
     _check(lib.gc_fetch_copies(orbit, 0, ctypes.byref(n), None, None, None, None, None, None))
@@ -329,12 +334,23 @@ def gc_fetch_copies(orbit, V: int, capacity: int | None = None, theta: bool = Tr
         lam = np.empty(m)
         reg = np.empty(m, np.int32)
     if m:
-        _check(lib.gc_fetch_copies(orbit, m, ctypes.byref(n), _ptr(F, ctypes.c_double),
+        fetch = lib.gc_fetch_copies_async if async_ else lib.gc_fetch_copies
+        _check(fetch(orbit, m, ctypes.byref(n), _ptr(F, ctypes.c_double),
                                    _ptr(th, ctypes.c_double), _ptr(first, ctypes.c_uint64),
                                    _ptr(count, ctypes.c_uint64), _ptr(lam, ctypes.c_double),
                                    _ptr(reg, ctypes.c_int)))
     return {"n_distinct": n.value, "F": F, "theta": th, "first_start": first, "count": count,
             "lambda2": lam, "region": reg}
+
+
+def gc_fetch_copies_async(orbit, V: int, capacity: int | None = None, theta: bool = True,
+                          out: dict | None = None) -> dict:
+    """gc_fetch_copies with the device-to-host copies left in flight (read-back stream)."""
+    return gc_fetch_copies(orbit, V, capacity, theta, out, async_=True)
+
+
+def gc_fetch_wait(orbit) -> None:
+    _check(load().gc_fetch_wait(orbit))
 
 
 def gc_fetch_starts(orbit, first: int, n: int) -> dict:

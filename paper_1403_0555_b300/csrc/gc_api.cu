@@ -169,6 +169,8 @@ struct gc_orbit_s {
   size_t ev_used = 0;
   bool err_unchecked = false;
   cudaStream_t last_stream = nullptr;    // stream of the orbit's most recent work
+  cudaEvent_t fetch_ev[2] = {};          // asynchronous fetch: gathered | copied to the host
+  bool fetch_pending = false;            // copies of gc_fetch_copies_async not yet waited for
   int last_precision = GC_FP64;
   cudaEvent_t ev[8] = {};
 
@@ -418,6 +420,45 @@ int fit_warps(int max_warps, F bytes_for) {
   return 0;
 }
 
+// A non-blocking stream per device for an orbit's own set-up copies, and a
+// read-back on a given stream.  The API never copies on the legacy default
+// stream: a copy there waits for every blocking stream's work, so reading one
+// orbit's results would wait for another batch still running.
+constexpr int kMaxDevicesForCopies = 64;
+std::mutex g_copy_mu;
+cudaStream_t g_copy_stream[kMaxDevicesForCopies] = {};
+
+cudaStream_t copy_stream() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesForCopies) return nullptr;
+  std::lock_guard<std::mutex> lk(g_copy_mu);
+  if (!g_copy_stream[dev] && cudaStreamCreateWithFlags(&g_copy_stream[dev], cudaStreamNonBlocking) != cudaSuccess)
+    g_copy_stream[dev] = nullptr;
+  return g_copy_stream[dev];
+}
+
+// the stream of gc_fetch_copies_async's device-to-host copies (per device)
+cudaStream_t g_d2h_stream[kMaxDevicesForCopies] = {};
+
+cudaStream_t d2h_stream() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesForCopies) return nullptr;
+  std::lock_guard<std::mutex> lk(g_copy_mu);
+  if (!g_d2h_stream[dev] && cudaStreamCreateWithFlags(&g_d2h_stream[dev], cudaStreamNonBlocking) != cudaSuccess)
+    g_d2h_stream[dev] = nullptr;
+  return g_d2h_stream[dev];
+}
+
+// waits for the orbit's pending asynchronous fetch (its staging buffer is
+// then free, and the host arrays hold the copies)
+cudaError_t finish_fetch(gc_orbit_s* o);
+
+cudaError_t read_back(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -510,7 +551,8 @@ int gc_create_orbit(int dim, int L, const double* link_angles, uint64_t orbit_id
     u64[i] = make_double2(std::cos(link_angles[i]), std::sin(link_angles[i]));
     u32[i] = make_float2((float)u64[i].x, (float)u64[i].y);
   }
-  cudaStream_t s = nullptr;
+  cudaStream_t s = copy_stream();
+  o->last_stream = s;
   int rc = GC_OK;
   if (!o->links64.ensure(u64.size() * sizeof(double2), s) || !o->links32.ensure(u32.size() * sizeof(float2), s) ||
       !o->t_counters.ensure(64, s) || !o->stats.ensure(kNumStats * 8, s) || !o->work.ensure(64, s) ||
@@ -518,11 +560,13 @@ int gc_create_orbit(int dim, int L, const double* link_angles, uint64_t orbit_id
     rc = fail(GC_ENOMEM, "cannot admit orbit buffers");
   }
   if (rc == GC_OK) {
-    cudaError_t e = cudaMemcpy(o->links64.p, u64.data(), u64.size() * sizeof(double2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(o->links32.p, u32.data(), u32.size() * sizeof(float2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(o->t_counters.p, 0, 64);
-    if (e == cudaSuccess) e = cudaMemset(o->stats.p, 0, kNumStats * 8);
-    if (e == cudaSuccess) e = cudaMemset(o->t_lock.p, 0, (size_t)o->nl * 4);
+    cudaError_t e = cudaMemcpyAsync(o->links64.p, u64.data(), u64.size() * sizeof(double2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(o->links32.p, u32.data(), u32.size() * sizeof(float2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(o->t_counters.p, 0, 64, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(o->stats.p, 0, kNumStats * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(o->t_lock.p, 0, (size_t)o->nl * 4, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host vectors go out of scope
     if (e != cudaSuccess) rc = fail(GC_ECUDA, "orbit upload: %s", cudaGetErrorString(e));
   }
   if (rc == GC_OK) {
@@ -537,7 +581,9 @@ int gc_create_orbit(int dim, int L, const double* link_angles, uint64_t orbit_id
     for (auto& e : o->ev)
       if (cudaEventCreate(&e) != cudaSuccess) { rc = fail(GC_ECUDA, "cudaEventCreate failed"); break; }
   }
-  if (rc == GC_OK && cudaStreamSynchronize(nullptr) != cudaSuccess)
+  // the set-up (uploads, fills of the copy pool) is complete before any
+  // other stream can use the orbit
+  if (rc == GC_OK && cudaStreamSynchronize(s) != cudaSuccess)
     rc = fail(GC_ECUDA, "orbit set-up: %s", cudaGetErrorString(cudaGetLastError()));
   if (rc != GC_OK) {
     gc_destroy_orbit(o);
@@ -550,6 +596,9 @@ int gc_create_orbit(int dim, int L, const double* link_angles, uint64_t orbit_id
 int gc_destroy_orbit(gc_orbit o) {
   if (!o) return fail(GC_EINVAL, "gc_destroy_orbit: NULL orbit");
   cudaStreamSynchronize(o->last_stream);
+  finish_fetch(o);
+  for (auto& e : o->fetch_ev)
+    if (e) cudaEventDestroy(e);
   cudaStream_t s = nullptr;
   for (Buf* b : {&o->links64, &o->links32, &o->t_cfg, &o->t_F, &o->t_q, &o->t_t, &o->t_first, &o->t_rep, &o->t_count,
                  &o->t_next, &o->t_lam, &o->t_region, &o->t_head, &o->t_lock, &o->t_f8, &o->t_f8n, &o->t_counters,
@@ -609,10 +658,16 @@ void harvest_timing(gc_orbit o) {
   o->ev_used = 0;
 }
 
+cudaError_t finish_fetch(gc_orbit_s* o) {
+  if (!o->fetch_pending) return cudaSuccess;
+  o->fetch_pending = false;
+  return cudaEventSynchronize(o->fetch_ev[1]);
+}
+
 int check_errors(gc_orbit o) {
   if (!o->err_unchecked) return GC_OK;
   int flags[4] = {0, 0, 0, 0};
-  GC_CUDA(cudaMemcpy(flags, o->err(), 16, cudaMemcpyDeviceToHost));
+  GC_CUDA(read_back(flags, o->err(), 16, o->last_stream));
   o->err_unchecked = false;
   if (flags[1]) return fail(GC_ENOMEM, "copy pool overflow");
   if (flags[2]) return fail(GC_ENOMEM, "quantised-minimum set overflow");
@@ -1629,7 +1684,7 @@ int read_count(gc_orbit o, unsigned* n_out) {
   harvest_timing(o);
   if (int rc = check_errors(o)) return rc;
   unsigned n = 0;
-  GC_CUDA(cudaMemcpy(&n, o->n_entries(), 4, cudaMemcpyDeviceToHost));
+  GC_CUDA(read_back(&n, o->n_entries(), 4, o->last_stream));
   *n_out = std::min(n, o->cap);
   return GC_OK;
 }
@@ -1724,7 +1779,7 @@ int gc_fetch_minima_f8(gc_orbit o, size_t capacity, size_t* n_minima, double* F_
   if (int rc = read_count(o, &n_pool)) return rc;   // synchronises, checks the error flags
   if (!o->f8cap) return GC_OK;
   unsigned long long nf8 = 0;
-  GC_CUDA(cudaMemcpy(&nf8, o->n_f8(), 8, cudaMemcpyDeviceToHost));
+  GC_CUDA(read_back(&nf8, o->n_f8(), 8, o->last_stream));
   const unsigned n = (unsigned)std::min<unsigned long long>(nf8, o->f8cap);
   *n_minima = n;
   if (capacity == 0 || n == 0 || !F_norm) return GC_OK;
@@ -1756,10 +1811,16 @@ int gc_fetch_minima_f8(gc_orbit o, size_t capacity, size_t* n_minima, double* F_
   return GC_OK;
 }
 
-int gc_fetch_copies(gc_orbit o, size_t capacity, size_t* n_distinct, double* F, double* theta,
-                    uint64_t* first_start, uint64_t* count, double* lambda2, int* region) {
+}  // extern "C"
+
+namespace {
+// The body of both fetches; `wait` leaves the device-to-host copies for
+// gc_fetch_wait when false.
+int fetch_copies_impl(gc_orbit o, size_t capacity, size_t* n_distinct, double* F, double* theta,
+                      uint64_t* first_start, uint64_t* count, double* lambda2, int* region, bool wait) {
   if (!o) return fail(GC_EINVAL, "gc_fetch_copies: NULL orbit");
   if (!n_distinct) return fail(GC_EINVAL, "gc_fetch_copies: n_distinct is NULL");
+  GC_CUDA(finish_fetch(o));   // the staging buffer of an earlier asynchronous fetch is in use until then
   unsigned n = 0;
   if (int rc = read_count(o, &n)) return rc;
   *n_distinct = n;
@@ -1792,13 +1853,48 @@ int gc_fetch_copies(gc_orbit o, size_t capacity, size_t* n_distinct, double* F, 
     ++o->launches;
   }
   GC_CUDA(cudaGetLastError());
-  if (F) GC_CUDA(cudaMemcpyAsync(F, sF, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
-  if (first_start) GC_CUDA(cudaMemcpyAsync(first_start, sfirst, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
-  if (count) GC_CUDA(cudaMemcpyAsync(count, scount, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
-  if (lambda2) GC_CUDA(cudaMemcpyAsync(lambda2, slam, (size_t)k * 8, cudaMemcpyDeviceToHost, s));
-  if (region) GC_CUDA(cudaMemcpyAsync(region, sreg, (size_t)k * 4, cudaMemcpyDeviceToHost, s));
-  if (theta) GC_CUDA(cudaMemcpyAsync(theta, sth, (size_t)k * V * 8, cudaMemcpyDeviceToHost, s));
-  GC_CUDA(cudaStreamSynchronize(s));
+  // the copies: on the orbit's stream (synchronous fetch), or on the read-back
+  // stream after the gathering (asynchronous: the orbit's stream, which other
+  // orbits of a batch share, stays free of them)
+  cudaStream_t c = s;
+  if (!wait) {
+    for (auto& e : o->fetch_ev)
+      if (!e) GC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c = d2h_stream();
+    GC_CUDA(cudaEventRecord(o->fetch_ev[0], s));
+    GC_CUDA(cudaStreamWaitEvent(c, o->fetch_ev[0], 0));
+  }
+  if (F) GC_CUDA(cudaMemcpyAsync(F, sF, (size_t)k * 8, cudaMemcpyDeviceToHost, c));
+  if (first_start) GC_CUDA(cudaMemcpyAsync(first_start, sfirst, (size_t)k * 8, cudaMemcpyDeviceToHost, c));
+  if (count) GC_CUDA(cudaMemcpyAsync(count, scount, (size_t)k * 8, cudaMemcpyDeviceToHost, c));
+  if (lambda2) GC_CUDA(cudaMemcpyAsync(lambda2, slam, (size_t)k * 8, cudaMemcpyDeviceToHost, c));
+  if (region) GC_CUDA(cudaMemcpyAsync(region, sreg, (size_t)k * 4, cudaMemcpyDeviceToHost, c));
+  if (theta) GC_CUDA(cudaMemcpyAsync(theta, sth, (size_t)k * V * 8, cudaMemcpyDeviceToHost, c));
+  if (wait) {
+    GC_CUDA(cudaStreamSynchronize(s));
+  } else {
+    GC_CUDA(cudaEventRecord(o->fetch_ev[1], c));
+    o->fetch_pending = true;
+  }
+  return GC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int gc_fetch_copies(gc_orbit o, size_t capacity, size_t* n_distinct, double* F, double* theta,
+                    uint64_t* first_start, uint64_t* count, double* lambda2, int* region) {
+  return fetch_copies_impl(o, capacity, n_distinct, F, theta, first_start, count, lambda2, region, true);
+}
+
+int gc_fetch_copies_async(gc_orbit o, size_t capacity, size_t* n_distinct, double* F, double* theta,
+                          uint64_t* first_start, uint64_t* count, double* lambda2, int* region) {
+  return fetch_copies_impl(o, capacity, n_distinct, F, theta, first_start, count, lambda2, region, false);
+}
+
+int gc_fetch_wait(gc_orbit o) {
+  if (!o) return fail(GC_EINVAL, "gc_fetch_wait: NULL orbit");
+  GC_CUDA(finish_fetch(o));
   return GC_OK;
 }
 
@@ -1841,13 +1937,13 @@ int gc_orbit_stats(gc_orbit o, gc_stats* out) {
   GC_CUDA(cudaStreamSynchronize(o->last_stream));
   harvest_timing(o);
   unsigned long long st[kNumStats] = {};
-  GC_CUDA(cudaMemcpy(st, o->stats.p, sizeof st, cudaMemcpyDeviceToHost));
+  GC_CUDA(read_back(st, o->stats.p, sizeof st, o->last_stream));
   unsigned long long nf8 = 0;
-  GC_CUDA(cudaMemcpy(&nf8, o->n_f8(), 8, cudaMemcpyDeviceToHost));
+  GC_CUDA(read_back(&nf8, o->n_f8(), 8, o->last_stream));
   unsigned n = 0;
   if (int rc = read_count(o, &n)) return rc;
   std::vector<int> reg(n);
-  if (n) GC_CUDA(cudaMemcpy(reg.data(), o->t_region.p, (size_t)n * 4, cudaMemcpyDeviceToHost));
+  if (n) GC_CUDA(read_back(reg.data(), o->t_region.p, (size_t)n * 4, o->last_stream));
   out->n_starts = o->n_starts;
   out->n_converged = st[kConv] + st[kPConv];
   out->n_not_converged = st[kNConv] + st[kPNConv];
@@ -2080,7 +2176,7 @@ int autotune_shape(gc_orbit like, const gc_options& base, double omega, double e
   std::vector<double> phi((size_t)like->V * like->d);
   {
     std::vector<double2> u((size_t)like->V * like->d);
-    GC_CUDA(cudaMemcpy(u.data(), like->links64.p, u.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+    GC_CUDA(read_back(u.data(), like->links64.p, u.size() * sizeof(double2), like->last_stream));
     for (size_t i = 0; i < u.size(); ++i) phi[i] = std::atan2(u[i].y, u[i].x);
   }
   gc_orbit tmp = nullptr;
@@ -2205,6 +2301,10 @@ extern "C" int gc_enumerate_batch(gc_orbit* orbits, int n_orbits, const uint64_t
     if (cudaEventRecord(join[k], pool[k]) != cudaSuccess && rc == GC_OK) rc = fail(GC_ECUDA, "join record failed");
     if (cudaStreamWaitEvent(origin, join[k], 0) != cudaSuccess && rc == GC_OK) rc = fail(GC_ECUDA, "join wait failed");
   }
+  // later calls on these orbits (fetch, stats, more starts) follow the join on
+  // the caller's stream, not the shared pool streams, where another batch's
+  // work may already be queued behind this one
+  for (int i = 0; i < n_orbits; ++i) orbits[i]->last_stream = origin;
   if (opt.use_graph) {
     const cudaError_t e = cudaStreamEndCapture(origin, &graph);
     if (rc != GC_OK) cudaGetLastError();   // a failed capture's error is not left for the next call
@@ -2332,7 +2432,7 @@ int rehome_orbit(gc_orbit o, cudaStream_t s) {
   GC_CUDA(cudaStreamSynchronize(s));
   if (o->t_cfg.p && in_arena(o->t_cfg.p)) {
     unsigned cur = 0;
-    GC_CUDA(cudaMemcpy(&cur, o->n_entries(), 4, cudaMemcpyDeviceToHost));
+    GC_CUDA(read_back(&cur, o->n_entries(), 4, s));
     cur = std::min(cur, o->cap);
     if (int rc = table_reserve(o, cur, cur, s, true)) return rc;
   }
