@@ -42,7 +42,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # capture of the 65536-start 4^4 case recorded under profiles/ (None = not
 # captured for the current kernel)
 TRAFFIC_POLISH_PER_START = (1.34815744e8 + 2.18701568e8) / 65536  # profiles/polish_kernel_4d_L4.md (line polish)
-TRAFFIC_RELAX_PER_START = (9.91e4 + 7.4575e7) / 65536       # profiles/relax32_sheet_4d_L4.md
+TRAFFIC_RELAX_PER_START = (1.34264832e8 + 7.5560448e7) / 65536   # profiles/relax32_sheet_4d_L4.md
 TRAFFIC_FPTEST_PER_COPY = (1.83724288e8 + 4.308224e6) / 44636   # profiles/fp_test_pairs_4d_L4.md
 # DRAM traffic per launch of the large-lattice leg's kernels (its own workload,
 # 592 starts of 4D 16^4), from ncu: profiles/slab_traffic_4d_L16.md
@@ -695,13 +695,16 @@ def run_ours(args):
         gb.gc_enumerate_copies(h, args.starts, w.omega, w.eps, ropt)
         st = gb.gc_orbit_stats(h)
         gb.gc_destroy_orbit(h)
-        per_orbit_ms.append({k: round(st[k], 2) for k in ("ms_relax", "ms_polish", "ms_dedup", "ms_fptest")}
+        per_orbit_ms.append({k: round(st[k], 2) for k in ("ms_starts", "ms_relax", "ms_polish", "ms_dedup",
+                                                           "ms_fptest")}
                             | {"copies": st["n_distinct"]})
         rs = st if rs is None else {k: rs[k] + st[k] for k in rs}
     n_launch = len(orbits)
     # FP32 site updates of the bulk sweeps (the rest are polish fallbacks)
     rs_relax_updates = rs["sweeps_fp32"] * V
-    stage_ms = {"relax_fp32": rs["ms_relax"], "polish_fp64": rs["ms_polish"] - rs["ms_polish_redo"],
+    # the relax stage holds the start draw (start32_kernel) and the FP32 sweeps
+    stage_ms = {"start_draw": rs["ms_starts"], "relax_fp32": rs["ms_relax"] - rs["ms_starts"],
+                "polish_fp64": rs["ms_polish"] - rs["ms_polish_redo"],
                 "polish_redo": rs["ms_polish_redo"],
                 "dedup": rs["ms_dedup"], "fp_test": rs["ms_fptest"]}
     # Per kernel: algorithmic operations over its isolated duration, against

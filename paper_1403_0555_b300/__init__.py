@@ -101,7 +101,7 @@ class gc_stats(ctypes.Structure):
         "ms_relax", "ms_polish", "ms_dedup", "ms_fptest")] + [
         ("kernel_launches", ctypes.c_uint64), ("df_residual_passes", ctypes.c_uint64),
         ("ms_polish_redo", ctypes.c_double), ("polish_redo_starts", ctypes.c_uint64),
-        ("lanczos_steps_fp64", ctypes.c_uint64)]
+        ("lanczos_steps_fp64", ctypes.c_uint64), ("ms_starts", ctypes.c_double)]
 
 
 EXPORTED = ("gc_set_allocator", "gc_options_default", "gc_create_orbit", "gc_enumerate_copies",

@@ -132,6 +132,9 @@ enum StatSlot {
   kPassDF = 22, kRedo = 23, kLanczos64 = 24, kNumStats = 25
 };
 
+// timing events per enqueued batch (stage boundaries; harvest_timing)
+constexpr size_t kEvPerBatch = 7;
+
 struct gc_orbit_s {
   int d = 0, L = 0, V = 0, ncolor = 0;
   bool slab = false;   // beyond shared memory: sweeps stream hyperplanes (gc_slab.cuh)
@@ -162,10 +165,11 @@ struct gc_orbit_s {
   std::vector<int32_t> rec_copy;
   // host-side accumulators
   uint64_t n_starts = 0;
-  double ms[5] = {0, 0, 0, 0, 0};   // relax, polish (all launches), dedup, FP test, polish redo
+  double ms[6] = {0, 0, 0, 0, 0, 0};   // relax, polish (all launches), dedup, FP test, polish redo,
+                                       // start draw (part of relax)
   uint64_t launches = 0;   // kernels this orbit launched
   uint64_t enqueued = 0;   // starts enqueued so far (bounds the copy count without a sync)
-  std::vector<cudaEvent_t> ev_pool;      // timing events of enqueued batches (5 per batch)
+  std::vector<cudaEvent_t> ev_pool;      // timing events of enqueued batches (kEvPerBatch per batch)
   size_t ev_used = 0;
   bool err_unchecked = false;
   cudaStream_t last_stream = nullptr;    // stream of the orbit's most recent work
@@ -648,11 +652,15 @@ int validate_options(const gc_options& opt, double omega, double eps) {
 // (the orbit's work must be complete).
 void harvest_timing(gc_orbit o) {
   // per batch: before relax | after relax | after the first polish launch |
-  // after the redo polish launch | after dedup | after the FP test
-  for (size_t k = 0; k + 5 < o->ev_used; k += 6) {
-    float t[5] = {0, 0, 0, 0, 0};
+  // after the redo polish launch | after dedup | after the FP test | after
+  // the start draw (inside the relax stage; at its start where the sweeps
+  // draw their own starts)
+  for (size_t k = 0; k + kEvPerBatch <= o->ev_used; k += kEvPerBatch) {
+    float t[5] = {0, 0, 0, 0, 0}, t_start = 0;
     for (int j = 0; j < 5; ++j) cudaEventElapsedTime(&t[j], o->ev_pool[k + j], o->ev_pool[k + j + 1]);
+    cudaEventElapsedTime(&t_start, o->ev_pool[k], o->ev_pool[k + 6]);
     o->ms[0] += t[0]; o->ms[1] += t[1] + t[2]; o->ms[2] += t[3]; o->ms[3] += t[4]; o->ms[4] += t[2];
+    o->ms[5] += t_start;
   }
   cudaGetLastError();
   o->ev_used = 0;
@@ -888,13 +896,13 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     }
     cudaEvent_t* ev = nullptr;
     if (timing) {
-      while (o->ev_pool.size() < o->ev_used + 6) {
+      while (o->ev_pool.size() < o->ev_used + kEvPerBatch) {
         cudaEvent_t e;
         GC_CUDA(cudaEventCreate(&e));
         o->ev_pool.push_back(e);
       }
       ev = o->ev_pool.data() + o->ev_used;
-      o->ev_used += 6;
+      o->ev_used += kEvPerBatch;
     }
     GC_CUDA(cudaMemsetAsync(wctr, 0, 32, s));
     GC_CUDA(cudaMemsetAsync(o->n_new(), 0, 4, s));
@@ -936,7 +944,10 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     // clusters unless GC_RELAX_GENERIC: a start's sweep count is not known in
     // advance, and a long start on one CTA sets the batch's end
     const bool cluster = opt.relax_variant != GC_RELAX_GENERIC;
-    if (ev) GC_CUDA(cudaEventRecord(ev[0], s));
+    if (ev) {
+      GC_CUDA(cudaEventRecord(ev[0], s));
+      GC_CUDA(cudaEventRecord(ev[6], s));   // the sweeps draw their own starts
+    }
     double2* st64 = o->s_config.as<double2>();
     if (mixed) {
       // FP64 head: the plain path's first sweeps from the random starts (no
@@ -1363,13 +1374,13 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     // timing events of this batch
     cudaEvent_t* ev = nullptr;
     if (timing) {
-      while (o->ev_pool.size() < o->ev_used + 6) {
+      while (o->ev_pool.size() < o->ev_used + kEvPerBatch) {
         cudaEvent_t e;
         GC_CUDA(cudaEventCreate(&e));
         o->ev_pool.push_back(e);
       }
       ev = o->ev_pool.data() + o->ev_used;
-      o->ev_used += 6;
+      o->ev_used += kEvPerBatch;
     }
     GC_CUDA(cudaMemsetAsync(wctr, 0, 32, s));   // relax, polish, redo polish counters; redo count
     GC_CUDA(cudaMemsetAsync(o->n_new(), 0, 4, s));
@@ -1407,7 +1418,7 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     if (ev) GC_CUDA(cudaEventRecord(ev[0], s));
     const bool line_variant = mixed && opt.relax_variant != GC_RELAX_GENERIC;
     if (line_variant && d == 4 && o->L == 4) {
-      constexpr int kWarps = 8;    // 224 registers: two warps per SM sub-partition
+      constexpr int kWarps = 8;    // 198 registers: two warps per SM sub-partition
       auto k = gc::relax32_sheet_kernel<kWarps, 1>;
       const size_t sm = gc::relax32_sheet_smem<kWarps>();
       if (int rc = launch_grid(k, 32 * kWarps, sm, kWarps, b, &grid)) return rc;
@@ -1415,9 +1426,11 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       const int sblocks = (int)std::min<long long>(((long long)b * V + 255) / 256, (long long)sm_count() * 16);
       gc::start32_kernel<<<sblocks, 256, 0, s>>>(ra.seed, ra.orbit_id, ra.start0, (long long)b, V,
                                                  ra.state32);
+      if (ev) GC_CUDA(cudaEventRecord(ev[6], s));
       k<<<grid, 32 * kWarps, sm, s>>>(ra);
       o->launches += 2;
     } else if (mixed && opt.relax_variant != GC_RELAX_GENERIC && d == 3 && o->L == 8) {
+      if (ev) GC_CUDA(cudaEventRecord(ev[6], s));   // the sweeps draw their own starts
       constexpr int kTeams = 4;
       auto k = gc::relax32_lines_kernel<3, 8, kTeams>;
       const size_t sm = gc::relax32_lines_smem<3, 8, kTeams>();
@@ -1425,6 +1438,7 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       k<<<grid, 64 * kTeams, sm, s>>>(ra);
       ++o->launches;
     } else {
+      if (ev) GC_CUDA(cudaEventRecord(ev[6], s));
       auto launch = [&](auto kern) -> int {
         if (int rc = launch_grid(kern, r_warps * 32, r_smem, (long long)r_warps * tpw, b, &grid)) return rc;
         kern<<<grid, r_warps * 32, r_smem, s>>>(ra);
@@ -1975,6 +1989,7 @@ int gc_orbit_stats(gc_orbit o, gc_stats* out) {
   out->ms_dedup = o->ms[2];
   out->ms_fptest = o->ms[3];
   out->ms_polish_redo = o->ms[4];
+  out->ms_starts = o->ms[5];
   out->polish_redo_starts = st[kRedo];
   out->kernel_launches = o->launches;
   out->df_residual_passes = st[kPassDF];
