@@ -546,15 +546,16 @@ def run_ours(args):
                 "lambda2": pinned((cap,), torch.float64), "region": pinned((cap,), torch.int32)}
 
     out_sets = [out_set(), out_set()]
-    # Step k + 1 is launched (asynchronous batch, on the other of two streams)
-    # before step k's copies have reached the host: each step's fetch orders
-    # and gathers its copies on the device once the step is done
-    # (gc_fetch_copies_async), and their device-to-host copies run beside the
-    # next step's kernels until gc_fetch_wait.  Every step still uploads its
-    # link angles and reads back all its distinct copies inside the timed
-    # region.  Both streams are warmed up first (the caching allocator keeps
-    # its blocks per stream).
-    e_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    # Step k + 1 is enqueued (asynchronous batch) before step k's copies are
+    # fetched, so the GPU always has the next step queued: each step's fetch
+    # waits for that step, orders its copies on the step's stream, and leaves
+    # the gathering and the device-to-host copies in flight
+    # (gc_fetch_copies_async) beside the next step's kernels; gc_fetch_wait
+    # completes them a step later.  Steps rotate over three streams, so that
+    # destroying step k - 1's orbits (which synchronises their stream) never
+    # waits for the step just enqueued.  Every step still uploads its link
+    # angles and reads back all its distinct copies inside the timed region.
+    e_streams = [torch.cuda.Stream() for _ in range(3)]
     e_opts = []
     for st_ in e_streams:
         eo = gb.gc_options_default(precision=gb.GC_MIXED, check_every=args.check_every,
@@ -564,23 +565,23 @@ def run_ours(args):
     acc = {"conv": 0, "h2d": 0, "d2h": 0}
 
     def e2e_launch(k):
-        with torch.cuda.stream(e_streams[k % 2]):
+        with torch.cuda.stream(e_streams[k % 3]):
             hs = []
             for o in step_orbits(k):
                 phi = np.ascontiguousarray(o.phi)
                 hs.append(gb.gc_create_orbit(d, L, phi, o.orbit_id, args.starts))
                 acc["h2d"] += phi.nbytes
-            gb.gc_enumerate_batch(hs, n_list, w.omega, w.eps, e_opts[k % 2])
+            gb.gc_enumerate_batch(hs, n_list, w.omega, w.eps, e_opts[k % 3])
         return hs
 
     def e2e_fetch(hs, bufs):
         for h in hs:
+            acc["conv"] += gb.gc_orbit_stats(h)["n_converged"]
             try:
                 res = gb.gc_fetch_copies(h, V, out=bufs, async_=True)
             except ValueError:          # more copies than the pinned arrays hold
                 res = gb.gc_fetch_copies(h, V)
             acc["d2h"] += sum(res[k_].nbytes for k_ in ("F", "theta", "first_start", "count", "lambda2", "region"))
-            acc["conv"] += gb.gc_orbit_stats(h)["n_converged"]
 
     def e2e_finish(hs):
         for h in hs:
@@ -588,16 +589,16 @@ def run_ours(args):
             gb.gc_destroy_orbit(h)
 
     def e2e_steps(nsteps):
-        pending = None
-        for k in range(nsteps):
-            hs = e2e_launch(k)
-            if pending is not None:
-                e2e_finish(pending)
-            e2e_fetch(hs, out_sets[k % 2])
-            pending = hs
-        e2e_finish(pending)
+        prev, older = e2e_launch(0), None
+        for k in range(1, nsteps + 1):
+            hs = e2e_launch(k) if k < nsteps else None
+            if older is not None:
+                e2e_finish(older)
+            e2e_fetch(prev, out_sets[(k - 1) % 2])
+            older, prev = prev, hs
+        e2e_finish(older)
 
-    e2e_steps(2)                        # warm-up of both streams
+    e2e_steps(3)                        # warm-up of the three streams
     acc = {"conv": 0, "h2d": 0, "d2h": 0}
     barrier()
     t0 = time.perf_counter()
@@ -608,9 +609,10 @@ def run_ours(args):
     e2e_s, e2e_conv = reduce_timing(dist, e2e_s, e2e_conv, device="cuda")
     e2e = {"value": e2e_conv / e2e_s, "unit": "copies/s",
            "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
-           "pipeline": "asynchronous batches on two streams; each step's copies ordered and gathered on "
-                       "the device after the step, their device-to-host copies (gc_fetch_copies_async) "
-                       "beside the next step's kernels; host wall clock over all K steps"}
+           "pipeline": "asynchronous batches on three streams, step k+1 enqueued before step k's fetch; "
+                       "each step's copies ordered on the device after the step, gathered and copied to "
+                       "the host (gc_fetch_copies_async) beside the next step's kernels; host wall clock "
+                       "over all K steps"}
 
     # --- the same steps with the FP32 Lanczos screen (GC_FP_AUTO: FP64 only
     # for copies whose FP32 lambda_2 is at most 1e-3), a labelled variant
@@ -656,28 +658,39 @@ def run_ours(args):
              "unit": "T lane operations/s (packed f32x2 counts two)",
              "how": "gc_peak_probe: 4 CTAs x 256 threads per SM, 8 independent chains per thread, best of 3"}
 
-    # --- plain FP64 path on a sample of orbit 0 (same options otherwise)
-    o = orbits[0]
-    popt = gb.gc_options_default(precision=gb.GC_FP64, check_every=args.check_every,
-                                 fp_mode=gb.GC_FP_AUTO, stream=stream)
-    stream = torch.cuda.current_stream()
-    h = gb.gc_create_orbit(d, L, o.phi, o.orbit_id)
-    gb.gc_enumerate_copies(h, 2048, w.omega, w.eps, popt)       # warm-up
-    s0 = gb.gc_orbit_stats(h)
-    barrier()
-    p0 = torch.cuda.Event(enable_timing=True)
-    p1 = torch.cuda.Event(enable_timing=True)
-    p0.record(stream)
-    gb.gc_enumerate_copies(h, args.plain_starts, w.omega, w.eps, popt)
-    p1.record(stream)
-    barrier()
-    pms = p0.elapsed_time(p1)
-    ps = stats_delta(s0, gb.gc_orbit_stats(h))
-    gb.gc_destroy_orbit(h)
-    plain = {"value": ps["n_converged"] / (pms / 1000.0), "unit": "copies/s",
-             "site_updates_per_s": ps["site_updates_fp64"] / (pms / 1000.0),
-             "sample": f"{args.plain_starts} starts of orbit kappa=0.5",
-             "mixed_over_plain": value / (ps["n_converged"] / (pms / 1000.0))}
+    # --- plain FP64 path, run the way the headline step runs: the eight
+    # orbits as one graph-captured gc_enumerate_batch call with the FP64
+    # Lanczos test of every copy, plain_starts starts in all (an equal share
+    # per orbit), launch shapes tuned (mode 1, result-neutral), so that
+    # mixed_over_plain compares the precisions alone.  A first call of the
+    # same size captures the graph and warms the allocator.
+    pn = max(1, args.plain_starts // len(orbits))
+    with torch.cuda.stream(side):
+        h = gb.gc_create_orbit(d, L, orbits[0].phi, orbits[0].orbit_id)
+        gb.gc_autotune(h, gb.GC_FP64, mode=1)
+        gb.gc_destroy_orbit(h)
+        popt = gb.gc_options_default(precision=gb.GC_FP64, check_every=args.check_every,
+                                     fp_mode=gb.GC_FP_LANCZOS, stream=side, use_graph=1, autotune=1)
+        hs = [gb.gc_create_orbit(d, L, o.phi, o.orbit_id, 2 * pn) for o in orbits]
+        gb.gc_enumerate_batch(hs, [pn] * len(hs), w.omega, w.eps, popt)       # warm-up
+        s0 = [gb.gc_orbit_stats(h) for h in hs]
+        barrier()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(side)
+        gb.gc_enumerate_batch(hs, [pn] * len(hs), w.omega, w.eps, popt)
+        p1.record(side)
+        barrier()
+        pms = p0.elapsed_time(p1)
+        ps = [stats_delta(a_, gb.gc_orbit_stats(h)) for a_, h in zip(s0, hs)]
+        for h in hs:
+            gb.gc_destroy_orbit(h)
+    p_conv = sum(x["n_converged"] for x in ps)
+    p_upd = sum(x["site_updates_fp64"] for x in ps)
+    plain = {"value": p_conv / (pms / 1000.0), "unit": "copies/s",
+             "site_updates_per_s": p_upd / (pms / 1000.0),
+             "sample": f"{pn} starts of each of the eight orbits, one graph-captured batch, FP64 Lanczos test",
+             "mixed_over_plain": value / (p_conv / (pms / 1000.0))}
 
     # --- roofline of the dominant kernel.  Inside the timed batches the
     # orbits' kernels overlap, so each kernel's own duration is taken from

@@ -248,10 +248,10 @@ int gc_fetch_copies(gc_orbit o, size_t capacity, size_t* n_distinct, double* F, 
                     uint64_t* first_start, uint64_t* count, double* lambda2, int* region);
 
 /* The same fetch, returning once the copies are enqueued.  The call waits
- * for the orbit's earlier work (it reads the number of distinct copies), then
- * enqueues the ordering and gathering kernels on the orbit's stream and the
- * device-to-host copies into the arrays on a separate read-back stream, after
- * them.  The arrays must be page-locked (pinned) for the copies to run
+ * for the orbit's earlier work (it reads the number of distinct copies) and
+ * orders the copies on the orbit's stream (waiting for that short sort),
+ * then enqueues the gathering kernels and the device-to-host copies into the
+ * arrays on a separate read-back stream, after the ordering.  The arrays must be page-locked (pinned) for the copies to run
  * asynchronously, and must stay valid and unread until gc_fetch_wait(o)
  * returns; a later fetch of the same orbit, and gc_destroy_orbit, wait for
  * the copies first.  Meanwhile other orbits' work (for example the next

@@ -453,6 +453,41 @@ cudaStream_t d2h_stream() {
   return g_d2h_stream[dev];
 }
 
+// The fetch's angle table on this device ([t_j | cos t_j | sin t_j] for
+// j = -kAngleSteps/2 ... kAngleSteps/2, t_j the double nearest
+// 2 pi j / kAngleSteps), filled once per device from an extended-precision
+// host computation; nullptr if it cannot be set up.
+double* g_angle_table[kMaxDevicesForCopies] = {};
+
+const double* angle_table() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesForCopies) return nullptr;
+  std::lock_guard<std::mutex> lk(g_copy_mu);
+  if (g_angle_table[dev]) return g_angle_table[dev];
+  static double host[3 * gc::kAngleTable];
+  const long double two_pi = 2.0L * acosl(-1.0L);
+  for (int j = 0; j < gc::kAngleTable; ++j) {
+    const double t = (double)((long double)(j - gc::kAngleSteps / 2) * two_pi / gc::kAngleSteps);
+    host[j] = t;
+    host[gc::kAngleTable + j] = (double)cosl((long double)t);
+    host[2 * gc::kAngleTable + j] = (double)sinl((long double)t);
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, sizeof host) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  cudaStream_t c = nullptr;
+  if (cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMemcpyAsync(p, host, sizeof host, cudaMemcpyHostToDevice, c) != cudaSuccess ||
+      cudaStreamSynchronize(c) != cudaSuccess) {
+    if (c) cudaStreamDestroy(c);
+    cudaFree(p);
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaStreamDestroy(c);
+  g_angle_table[dev] = static_cast<double*>(p);
+  return g_angle_table[dev];
+}
+
 // waits for the orbit's pending asynchronous fetch (its staging buffer is
 // then free, and the host arrays hold the copies)
 cudaError_t finish_fetch(gc_orbit_s* o);
@@ -1423,7 +1458,7 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
       const size_t sm = gc::relax32_sheet_smem<kWarps>();
       if (int rc = launch_grid(k, 32 * kWarps, sm, kWarps, b, &grid)) return rc;
       // the batch's starts first, drawn at full occupancy into the FP32 state buffer
-      const int sblocks = (int)std::min<long long>(((long long)b * V + 255) / 256, (long long)sm_count() * 16);
+      const int sblocks = (int)std::min<long long>((long long)b, (long long)sm_count() * 16);
       gc::start32_kernel<<<sblocks, 256, 0, s>>>(ra.seed, ra.orbit_id, ra.start0, (long long)b, V,
                                                  ra.state32);
       if (ev) GC_CUDA(cudaEventRecord(ev[6], s));
@@ -1854,22 +1889,10 @@ int fetch_copies_impl(gc_orbit o, size_t capacity, size_t* n_distinct, double* F
   double* slam = reinterpret_cast<double*>(scount + k);
   int* sreg = reinterpret_cast<int*>(slam + k);
   double* sth = reinterpret_cast<double*>(st + (((size_t)k * 36 + 15) & ~size_t(15)));
-  {
-    const int blocks = (int)std::min<unsigned>((k + 255) / 256, 4096);
-    gc::gather_meta_kernel<<<blocks, 256, 0, s>>>(order, k, o->t_F.as<double>(), o->t_first.as<unsigned long long>(),
-                                                  o->t_count.as<unsigned long long>(), o->t_lam.as<double>(),
-                                                  o->t_region.as<int>(), sF, sfirst, scount, slam, sreg);
-    ++o->launches;
-  }
-  if (theta) {
-    const int blocks = (int)std::min<size_t>(((size_t)k * V + 255) / 256, 8192);
-    gc::gather_angles_kernel<<<blocks, 256, 0, s>>>(order, k, (int)V, o->t_cfg.as<double2>(), sth);
-    ++o->launches;
-  }
-  GC_CUDA(cudaGetLastError());
-  // the copies: on the orbit's stream (synchronous fetch), or on the read-back
-  // stream after the gathering (asynchronous: the orbit's stream, which other
-  // orbits of a batch share, stays free of them)
+  // The gathering and the copies run on the orbit's stream (synchronous
+  // fetch), or on the read-back stream after the ordering (asynchronous: the
+  // orbit's stream, which the other orbits of a batch share and whose next
+  // fetch synchronises it, stays free of them).
   cudaStream_t c = s;
   if (!wait) {
     for (auto& e : o->fetch_ev)
@@ -1878,6 +1901,22 @@ int fetch_copies_impl(gc_orbit o, size_t capacity, size_t* n_distinct, double* F
     GC_CUDA(cudaEventRecord(o->fetch_ev[0], s));
     GC_CUDA(cudaStreamWaitEvent(c, o->fetch_ev[0], 0));
   }
+  {
+    const int blocks = (int)std::min<unsigned>((k + 255) / 256, 4096);
+    gc::gather_meta_kernel<<<blocks, 256, 0, c>>>(order, k, o->t_F.as<double>(), o->t_first.as<unsigned long long>(),
+                                                  o->t_count.as<unsigned long long>(), o->t_lam.as<double>(),
+                                                  o->t_region.as<int>(), sF, sfirst, scount, slam, sreg);
+    ++o->launches;
+  }
+  if (theta) {
+    const double* table = angle_table();
+    if (!table) return fail(GC_ENOMEM, "cannot set up the fetch's angle table");
+    const int threads = (int)std::min<size_t>(256, (V + 31) / 32 * 32);   // a copy's sites
+    const int blocks = (int)std::min<unsigned>(k, (unsigned)sm_count() * 16);
+    gc::gather_angles_kernel<<<blocks, threads, 0, c>>>(order, k, (int)V, o->t_cfg.as<double2>(), table, sth);
+    ++o->launches;
+  }
+  GC_CUDA(cudaGetLastError());
   if (F) GC_CUDA(cudaMemcpyAsync(F, sF, (size_t)k * 8, cudaMemcpyDeviceToHost, c));
   if (first_start) GC_CUDA(cudaMemcpyAsync(first_start, sfirst, (size_t)k * 8, cudaMemcpyDeviceToHost, c));
   if (count) GC_CUDA(cudaMemcpyAsync(count, scount, (size_t)k * 8, cudaMemcpyDeviceToHost, c));

@@ -1122,12 +1122,10 @@ __device__ __noinline__ void line_start32(uint64_t seed, uint64_t orbit_id, uint
 // few, loads them instead of running the Philox rounds itself.
 __global__ void __launch_bounds__(256) start32_kernel(uint64_t seed, uint64_t orbit_id, uint64_t start0,
                                                       long long n, int V, float2* __restrict__ out) {
-  const long long total = n * (long long)V;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long i = t / V;
-    out[t] = random_unit32(seed, orbit_id, start0 + (uint64_t)i, (uint64_t)(t - i * V));
-  }
+  // a block per start at a time, its threads over the start's sites
+  for (long long i = blockIdx.x; i < n; i += gridDim.x)
+    for (int x = threadIdx.x; x < V; x += blockDim.x)
+      out[i * V + x] = random_unit32(seed, orbit_id, start0 + (uint64_t)i, (uint64_t)x);
 }
 
 // A line's L drawn sites (site order, from start32_kernel) into the team's

@@ -372,13 +372,55 @@ __global__ void gather_meta_kernel(const unsigned* __restrict__ order, unsigned 
 }
 
 // canonical angles theta'_x = arg g'_x of the copies in sorted order
+// The canonical angles theta' = arg(c + i s) of the fetched copies, without a
+// double-precision arctangent (9 FP64 operations per site; the FP64
+// arctangent cost about 46).  Range reduction by angle subtraction: a rough FP32
+// estimate of the angle picks the nearest t_j = 2 pi j / kAngleSteps,
+// j in [-kAngleSteps/2, kAngleSteps/2]; rotating (c, s) back by t_j leaves
+// x = s cos t_j - c sin t_j = sin(theta - t_j) with |theta - t_j| <= pi /
+// kAngleSteps plus the estimate's error, and theta = t_j + arcsin x, the
+// arcsine summed as its Maclaurin series x + x^3/6 + 3x^5/40 + 5x^7/112 +
+// 35x^9/1152 (the first omitted term, 63x^11/2816, is below 1e-22 for
+// |x| <= 0.0123).  |(c, s)| = 1 to rounding, so the arcsine of the rotated
+// sine is the angle to within 1e-18.  The table holds t_j (the double
+// nearest 2 pi j / kAngleSteps) and the cosine and sine of that double,
+// computed on the host in extended precision.
+constexpr int kAngleSteps = 256;
+constexpr int kAngleTable = kAngleSteps + 1;   // [t_j | cos t_j | sin t_j], j + kAngleSteps/2
+
+// A float within 2^-20 relative of a double in [-1, 1] from its high word
+// (integer operations only: the exponent re-biased, 20 mantissa bits kept);
+// magnitudes below 2^-126 give a signed zero.
+__device__ __forceinline__ float rough_float(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v);
+  const unsigned mag = hi & 0x7fffffffu;
+  const unsigned bits = mag < (897u << 20) ? 0u : ((mag - (896u << 20)) << 3);
+  return __uint_as_float(bits | (hi & 0x80000000u));
+}
+
 __global__ void gather_angles_kernel(const unsigned* __restrict__ order, unsigned k, int V,
-                                     const double2* __restrict__ cfg, double* __restrict__ theta) {
-  const size_t n = (size_t)k * V;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t c = i / (unsigned)V, x = i - c * (unsigned)V;
-    const double2 z = cfg[(size_t)order[c] * V + x];
-    theta[i] = atan2(z.y, z.x);
+                                     const double2* __restrict__ cfg, const double* __restrict__ table,
+                                     double* __restrict__ theta) {
+  __shared__ double tab[3 * kAngleTable];
+  for (int i = threadIdx.x; i < 3 * kAngleTable; i += blockDim.x) tab[i] = table[i];
+  __syncthreads();
+  const float to_step = (float)kAngleSteps / 6.28318530717958647692f;
+  // a block per copy at a time, its threads over the copy's sites
+  for (unsigned c = blockIdx.x; c < k; c += gridDim.x) {
+    const double2* __restrict__ src = cfg + (size_t)order[c] * V;
+    double* __restrict__ dst = theta + (size_t)c * V;
+    for (int x = threadIdx.x; x < V; x += blockDim.x) {
+      const double2 z = src[x];
+      const float est = atan2f(rough_float(z.y), rough_float(z.x));
+      const int j = min(max(__float2int_rn(est * to_step), -kAngleSteps / 2), kAngleSteps / 2) + kAngleSteps / 2;
+      const double tj = tab[j], cj = tab[kAngleTable + j], sj = tab[2 * kAngleTable + j];
+      const double r = fma(z.y, cj, -(z.x * sj));
+      const double r2 = r * r;
+      double q = fma(r2, 35.0 / 1152.0, 5.0 / 112.0);
+      q = fma(r2, q, 3.0 / 40.0);
+      q = fma(r2, q, 1.0 / 6.0);
+      dst[x] = tj + fma(r * r2, q, r);
+    }
   }
 }
 

@@ -101,15 +101,16 @@ def test_autotune_mode2_equals_fixed_depth():
 
 
 def test_async_fetch_pipelined_equals_sync_fetch():
-    """Two batches in flight: each batch's copies are fetched asynchronously into
-    pinned host arrays, the next batch is launched on another stream, and only
-    then does gc_fetch_wait complete the copies.  Every array equals the
+    """Batches in flight as the bench's end-to-end leg runs them: batch k + 1 is
+    launched (asynchronously, on the next of three streams) before batch k's
+    copies are fetched asynchronously into pinned host arrays, and
+    gc_fetch_wait completes them a batch later.  Every array equals the
     synchronous fetch's."""
     import torch
     import paper_1403_0555_b300 as gb
     orbits = _orbits()
     ref = _single(gb, orbits, 2000, gb.gc_options_default(precision=1, check_every=4))
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    streams = [torch.cuda.Stream() for _ in range(3)]
 
     def pinned_set(V, cap):
         p = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
@@ -119,33 +120,34 @@ def test_async_fetch_pipelined_equals_sync_fetch():
                 "lambda2": p((cap,), torch.float64), "region": p((cap,), torch.int32)}
 
     def launch(k):
-        with torch.cuda.stream(streams[k % 2]):
-            opt = gb.gc_options_default(precision=1, check_every=4, stream=streams[k % 2])
+        with torch.cuda.stream(streams[k % 3]):
+            opt = gb.gc_options_default(precision=1, check_every=4, stream=streams[k % 3])
             opt.async_ = 1
             hs = [gb.gc_create_orbit(d, L, phi, oid) for d, L, phi, oid in orbits]
             gb.gc_enumerate_batch(hs, [2000] * len(hs), 1.7, 1e-24, opt)
         return hs
 
-    results, pending = [], None
-    for k in range(3):
-        hs = launch(k)
-        if pending is not None:
-            for h in pending[0]:
-                gb.gc_fetch_wait(h)
-            results.append([(dict((k_, np.array(v)) if isinstance(v, np.ndarray) else (k_, v)
-                                  for k_, v in c.items()), gb.gc_orbit_stats(h))
-                            for h, c in zip(*pending)])
-            for h in pending[0]:
-                gb.gc_destroy_orbit(h)
-        fetched = []
-        for h, (d, L, _, _) in zip(hs, orbits):
-            fetched.append(gb.gc_fetch_copies_async(h, L ** d, out=pinned_set(L ** d, 4000)))
-        pending = (hs, fetched)
-    for h in pending[0]:
-        gb.gc_fetch_wait(h)
-    results.append([(c, gb.gc_orbit_stats(h)) for h, c in zip(*pending)])
-    for h in pending[0]:
-        gb.gc_destroy_orbit(h)
-    assert len(results) == 3
+    def fetch(hs):
+        return [gb.gc_fetch_copies_async(h, L ** d, out=pinned_set(L ** d, 4000))
+                for h, (d, L, _, _) in zip(hs, orbits)]
+
+    def finish(pending):
+        hs, fetched = pending
+        for h in hs:
+            gb.gc_fetch_wait(h)
+        out = [(c, gb.gc_orbit_stats(h)) for h, c in zip(hs, fetched)]
+        for h in hs:
+            gb.gc_destroy_orbit(h)
+        return out
+
+    n = 4
+    results, prev, older = [], launch(0), None
+    for k in range(1, n + 1):
+        hs = launch(k) if k < n else None
+        if older is not None:
+            results.append(finish(older))
+        older, prev = (prev, fetch(prev)), hs
+    results.append(finish(older))
+    assert len(results) == n
     for r in results:
         _same(ref, r)

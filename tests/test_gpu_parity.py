@@ -3,8 +3,11 @@
 Plain FP64 path: the sweeps use explicitly rounded IEEE operations in the
 oracle's order, so every start follows the oracle's trajectory exactly; the
 tests demand identical statuses, sweep counts, copy sets, multiplicities and
-first starts, angles within 1e-9 rad and F within 1e-12 (relative, absolute
-below 1).  Lambda_2 (dense mode) within 1e-9.
+first starts, F within 1e-12 (relative, absolute below 1) and lambda_2 (dense
+mode) within 1e-9.  The canonical angles are within 2e-15 rad: the
+configurations are the oracle's to rounding (the canonical product's), so
+the fetch's angle (table reduction and arcsine series) is held to the
+oracle's arctangent at a few units in the last place.
 """
 import math
 
@@ -31,7 +34,7 @@ def test_2d_4x4_uniform_full_parity():
                           fp_mode=2, check_every=1)
     relaxed, cp = oracle.enumerate_copies(o.d, o.L, o.phi, 1, o.orbit_id, w.n_starts, w.omega, w.eps)
     assert_starts_equal(gs, relaxed, cp, _oracle_F(o.d, o.L, o.phi, relaxed))
-    assert_copies_equal(gc_, cp, lam_tol=1e-9)
+    assert_copies_equal(gc_, cp, theta_tol=2e-15, lam_tol=1e-9)
     assert st["n_distinct_F8"] == cp.n_distinct_F8
     assert st["n_converged"] == int((relaxed.status == 1).sum())
     assert st["n_in"] == int((cp.region == oracle.REGION_IN).sum())
@@ -49,7 +52,7 @@ def test_small_lattices_parity(d, L, omega, check_every):
     gs, gc_, st = run_gpu(d, L, phi, 7, n, omega, 1e-24, fp_mode=2, check_every=check_every)
     relaxed, cp = oracle.enumerate_copies(d, L, phi, 1, 7, n, omega, 1e-24, check_every=check_every)
     assert_starts_equal(gs, relaxed, cp, _oracle_F(d, L, phi, relaxed))
-    assert_copies_equal(gc_, cp, lam_tol=1e-9)
+    assert_copies_equal(gc_, cp, theta_tol=2e-15, lam_tol=1e-9)
     assert st["n_distinct_F8"] == cp.n_distinct_F8
 
 
