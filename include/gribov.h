@@ -261,6 +261,27 @@ int gc_fetch_copies_async(gc_orbit o, size_t capacity, size_t* n_distinct, doubl
 /* Waits for the copies of the orbit's last gc_fetch_copies_async. */
 int gc_fetch_wait(gc_orbit o);
 
+/* Checkpoint / resume: restores into a new orbit (created by gc_create_orbit
+ * with the same dimension, size, link angles and orbit id, no starts run
+ * yet) the state a run reached, from what gc_fetch_copies (n copies, in any
+ * order) and gc_fetch_minima_f8 (n_minima quantised minima and their counts)
+ * returned for it.  next_start is the first start index of the next call:
+ * the number of starts the run had taken, above every first_start.  Later
+ * calls then draw starts next_start, next_start + 1, ... and deduplicate
+ * against the restored copies, so the results equal those of the run
+ * continued without the break (angles to rounding: the configurations are
+ * rebuilt as (cos theta', sin theta')).  The restored copies keep their
+ * counts, first starts, lambda_2 and region flags and are not tested again.
+ * The orbit's counters (gc_orbit_stats' starts, sweeps and timings) count
+ * only the work after the restore.  Host arrays; the call synchronises the
+ * orbit's stream.  Errors: GC_ESTATE if the orbit has run starts or holds
+ * copies, or belongs to a server; GC_EINVAL for NULL arrays, a first_start
+ * at or above next_start, a zero count, a region flag outside -1..2 or a
+ * negative F_norm; GC_ENOMEM if the copy pool cannot hold n copies. */
+int gc_load_copies(gc_orbit o, size_t n, const double* F, const double* theta, const uint64_t* first_start,
+                   const uint64_t* count, const double* lambda2, const int* region, size_t n_minima,
+                   const double* F_norm, const uint64_t* minima_count, uint64_t next_start);
+
 /* The paper's set of minima (Section III: minima told apart by F quantised
  * at 1e-8): the distinct keys floor(F/(dV) * 1e8) of every converged start so
  * far, in both dedup modes, in increasing order.  n_minima receives their

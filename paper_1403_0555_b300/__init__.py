@@ -105,7 +105,7 @@ class gc_stats(ctypes.Structure):
 
 
 EXPORTED = ("gc_set_allocator", "gc_options_default", "gc_create_orbit", "gc_enumerate_copies",
-            "gc_fetch_copies", "gc_fetch_copies_async", "gc_fetch_wait", "gc_fetch_minima_f8",
+            "gc_fetch_copies", "gc_fetch_copies_async", "gc_fetch_wait", "gc_fetch_minima_f8", "gc_load_copies",
             "gc_fetch_starts", "gc_orbit_stats", "gc_destroy_orbit",
             "gc_last_error", "gc_version", "gc_fp_test_static", "gc_enumerate_batch",
             "gc_autotune", "gc_autotune_ex", "gc_server_create", "gc_server_submit",
@@ -151,6 +151,8 @@ def load(build_if_stale: bool = True):
         L.gc_fetch_wait.argtypes = [ctypes.c_void_p]
         L.gc_fetch_minima_f8.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
                                          p_d, p_u64]
+        L.gc_load_copies.argtypes = [ctypes.c_void_p, ctypes.c_size_t, p_d, p_d, p_u64, p_u64, p_d, p_i,
+                                     ctypes.c_size_t, p_d, p_u64, ctypes.c_uint64]
         L.gc_fetch_starts.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, p_i,
                                       p_i, p_d, ctypes.POINTER(ctypes.c_int64)]
         L.gc_orbit_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(gc_stats)]
@@ -351,6 +353,27 @@ def gc_fetch_copies_async(orbit, V: int, capacity: int | None = None, theta: boo
 
 def gc_fetch_wait(orbit) -> None:
     _check(load().gc_fetch_wait(orbit))
+
+
+def gc_load_copies(orbit, copies: dict, minima: dict, next_start: int) -> None:
+    """Restore a run's state into a new orbit (checkpoint / resume): `copies` as
+    gc_fetch_copies returned them (angles included), `minima` as
+    gc_fetch_minima_f8 returned them, next_start the number of starts the run
+    had taken.  Later calls continue from start next_start."""
+    n = int(copies["n_distinct"])
+    if len(copies["F"]) < n or copies["theta"] is None:
+        raise ValueError("copies must hold every distinct copy with its angles")
+    c = lambda a, dt: np.ascontiguousarray(np.asarray(a)[:n], dtype=dt)
+    F, th = c(copies["F"], np.float64), c(copies["theta"], np.float64)
+    first, count = c(copies["first_start"], np.uint64), c(copies["count"], np.uint64)
+    lam, reg = c(copies["lambda2"], np.float64), c(copies["region"], np.int32)
+    m = int(minima["n_minima"])
+    Fn = np.ascontiguousarray(np.asarray(minima["F_norm"])[:m], dtype=np.float64)
+    mc = np.ascontiguousarray(np.asarray(minima["count"])[:m], dtype=np.uint64)
+    _check(load().gc_load_copies(orbit, n, _ptr(F, ctypes.c_double), _ptr(th, ctypes.c_double),
+                                 _ptr(first, ctypes.c_uint64), _ptr(count, ctypes.c_uint64),
+                                 _ptr(lam, ctypes.c_double), _ptr(reg, ctypes.c_int), m,
+                                 _ptr(Fn, ctypes.c_double), _ptr(mc, ctypes.c_uint64), int(next_start)))
 
 
 def gc_fetch_starts(orbit, first: int, n: int) -> dict:

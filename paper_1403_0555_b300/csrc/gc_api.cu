@@ -334,6 +334,19 @@ int table_reserve(gc_orbit o, unsigned long long need, unsigned cur, cudaStream_
   return GC_OK;
 }
 
+// The copy table's bucket widths for a d-dimensional lattice of V sites: F
+// buckets of wF (far above the spread of F among one copy's starts) and
+// fingerprint buckets of wT; the identity radius delta; F_norm = F / (d V).
+void set_table_widths(gc::TableView& T, int d, int V, double delta) {
+  T.wF = 1e-9 * std::max(1.0, (double)d * V * 1e-3);
+  T.wT = 1e-5;
+  T.inv_wF = 1.0 / T.wF;
+  T.inv_wT = 1.0 / T.wT;
+  T.tolF = T.wF;
+  T.delta2 = delta * delta;
+  T.f8_links = (double)d * V;
+}
+
 // Deduplication of one batch: find or insert each start's copy, then count
 // the starts per copy (and the paper-style F set), then give every copy the
 // batch created the configuration and F of its lowest start.
@@ -1144,13 +1157,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     }
     gc::DedupArgs da{};
     da.tab = o->view();
-    da.tab.wF = 1e-9 * std::max(1.0, (double)d * V * 1e-3);
-    da.tab.wT = 1e-5;
-    da.tab.inv_wF = 1.0 / da.tab.wF;
-    da.tab.inv_wT = 1.0 / da.tab.wT;
-    da.tab.tolF = da.tab.wF;
-    da.tab.delta2 = opt.dedup_delta * opt.dedup_delta;
-    da.tab.f8_links = (double)d * V;
+    set_table_widths(da.tab, d, V, opt.dedup_delta);
     da.tab.f8_only = opt.dedup_mode == GC_DEDUP_F8;
     da.V = V;
     da.n = b;
@@ -1605,13 +1612,7 @@ int enumerate_impl(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     // deduplication
     gc::DedupArgs da{};
     da.tab = o->view();
-    da.tab.wF = 1e-9 * std::max(1.0, (double)d * V * 1e-3);
-    da.tab.wT = 1e-5;
-    da.tab.inv_wF = 1.0 / da.tab.wF;
-    da.tab.inv_wT = 1.0 / da.tab.wT;
-    da.tab.tolF = da.tab.wF;
-    da.tab.delta2 = opt.dedup_delta * opt.dedup_delta;
-    da.tab.f8_links = (double)d * V;
+    set_table_widths(da.tab, d, V, opt.dedup_delta);
     da.tab.f8_only = opt.dedup_mode == GC_DEDUP_F8;
     da.V = V;
     da.n = b;
@@ -1948,6 +1949,97 @@ int gc_fetch_copies_async(gc_orbit o, size_t capacity, size_t* n_distinct, doubl
 int gc_fetch_wait(gc_orbit o) {
   if (!o) return fail(GC_EINVAL, "gc_fetch_wait: NULL orbit");
   GC_CUDA(finish_fetch(o));
+  return GC_OK;
+}
+
+int gc_load_copies(gc_orbit o, size_t n, const double* F, const double* theta, const uint64_t* first_start,
+                   const uint64_t* count, const double* lambda2, const int* region, size_t n_minima,
+                   const double* F_norm, const uint64_t* minima_count, uint64_t next_start) {
+  if (!o) return fail(GC_EINVAL, "gc_load_copies: NULL orbit");
+  if (o->served_by) return fail(GC_ESTATE, "gc_load_copies: the orbit belongs to a server");
+  if (o->next_start != 0 || o->n_starts != 0)
+    return fail(GC_ESTATE, "gc_load_copies: the orbit has run starts already (restore into a new orbit)");
+  if (n && (!F || !theta || !first_start || !count || !lambda2 || !region))
+    return fail(GC_EINVAL, "gc_load_copies: NULL copy array");
+  if (n_minima && (!F_norm || !minima_count)) return fail(GC_EINVAL, "gc_load_copies: NULL minima array");
+  if (n > 0x7fffffffULL || n_minima > 0x3fffffffULL) return fail(GC_EINVAL, "gc_load_copies: too many records");
+  for (size_t i = 0; i < n; ++i) {
+    if (first_start[i] >= next_start)
+      return fail(GC_EINVAL, "copy %zu: first start %llu not below next_start %llu", i,
+                  (unsigned long long)first_start[i], (unsigned long long)next_start);
+    if (count[i] == 0) return fail(GC_EINVAL, "copy %zu: count 0", i);
+    if (region[i] < -1 || region[i] > 2) return fail(GC_EINVAL, "copy %zu: region flag %d", i, region[i]);
+  }
+  std::vector<unsigned long long> k8(n_minima);
+  for (size_t i = 0; i < n_minima; ++i) {
+    const double k = std::nearbyint(F_norm[i] * 1e8);   // the fetch gives key * 1e-8
+    if (!(k >= 0.0 && k < 9.0e15)) return fail(GC_EINVAL, "minimum %zu: F_norm %g out of range", i, F_norm[i]);
+    k8[i] = (unsigned long long)k;
+  }
+  cudaStream_t s = o->last_stream;
+  unsigned cur = 0;
+  if (int rc = read_count(o, &cur)) return rc;
+  unsigned long long nf8 = 0;
+  GC_CUDA(read_back(&nf8, o->n_f8(), 8, s));
+  if (cur || nf8) return fail(GC_ESTATE, "gc_load_copies: the orbit's table is not empty");
+  // room for the copies, and an F set at most half full
+  const unsigned long long need = std::max<unsigned long long>(n, (n_minima + 1) / 2);
+  if (int rc = table_reserve(o, need, 0, s)) return rc;
+  const size_t V = o->V;
+  const size_t off_F = 0, off_first = off_F + n * 8, off_count = off_first + n * 8, off_lam = off_count + n * 8,
+               off_reg = off_lam + n * 8, off_th = (off_reg + n * 4 + 15) & ~size_t(15),
+               off_k8 = off_th + n * V * 8, off_c8 = off_k8 + n_minima * 8, bytes = off_c8 + n_minima * 8 + 16;
+  Buf tmp;
+  if (!tmp.ensure(bytes, s)) return fail(GC_ENOMEM, "cannot admit %zu copies to restore", n);
+  unsigned char* d = tmp.as<unsigned char>();
+  int rc = GC_OK;
+  auto up = [&](size_t off, const void* src, size_t nb) {
+    if (rc == GC_OK && nb && cudaMemcpyAsync(d + off, src, nb, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      rc = fail(GC_ECUDA, "gc_load_copies: upload failed");
+  };
+  up(off_F, F, n * 8);
+  up(off_first, first_start, n * 8);
+  up(off_count, count, n * 8);
+  up(off_lam, lambda2, n * 8);
+  up(off_reg, region, n * 4);
+  up(off_th, theta, n * V * 8);
+  up(off_k8, k8.data(), n_minima * 8);
+  up(off_c8, minima_count, n_minima * 8);
+  if (rc == GC_OK && n) {
+    gc::TableView T = o->view();
+    set_table_widths(T, o->d, (int)V, 0.0);
+    const int blocks = (int)std::min<size_t>((n + 7) / 8, (size_t)sm_count() * 8);
+    gc::restore_kernel<<<blocks, 256, 0, s>>>(T, (unsigned)n, (int)V, reinterpret_cast<const double*>(d + off_th),
+                                             reinterpret_cast<const double*>(d + off_F),
+                                             reinterpret_cast<const unsigned long long*>(d + off_first),
+                                             reinterpret_cast<const unsigned long long*>(d + off_count),
+                                             reinterpret_cast<const double*>(d + off_lam),
+                                             reinterpret_cast<const int*>(d + off_reg), o->links64.as<double2>());
+    gc::relink_kernel<<<std::min<unsigned>(((unsigned)n + 255) / 256, 4096), 256, 0, s>>>(T, (unsigned)n);
+    o->launches += 2;
+  }
+  if (rc == GC_OK && n_minima) {
+    const unsigned blocks = std::min<unsigned>(((unsigned)n_minima + 255) / 256, 4096);
+    f8_rehash_kernel<<<blocks, 256, 0, s>>>(reinterpret_cast<const unsigned long long*>(d + off_k8),
+                                              reinterpret_cast<const unsigned long long*>(d + off_c8),
+                                              (unsigned)n_minima, o->t_f8.as<unsigned long long>(),
+                                              o->t_f8n.as<unsigned long long>(), o->f8cap - 1, o->err());
+    ++o->launches;
+  }
+  const unsigned n32 = (unsigned)n;
+  const unsigned long long m64 = n_minima;
+  if (rc == GC_OK && cudaGetLastError() != cudaSuccess) rc = fail(GC_ECUDA, "gc_load_copies: launch failed");
+  if (rc == GC_OK && (cudaMemcpyAsync(o->n_entries(), &n32, 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                      cudaMemcpyAsync(o->n_f8(), &m64, 8, cudaMemcpyHostToDevice, s) != cudaSuccess))
+    rc = fail(GC_ECUDA, "gc_load_copies: counter upload failed");
+  const cudaError_t e = cudaStreamSynchronize(s);   // the staging buffer and the counters' sources
+  tmp.release(s);
+  if (rc != GC_OK) return rc;
+  if (e != cudaSuccess) return fail(GC_ECUDA, "gc_load_copies: %s", cudaGetErrorString(e));
+  o->err_unchecked = true;   // the F set's insertions report a full set there
+  if (int r = check_errors(o)) return r;
+  o->next_start = next_start;
+  o->enqueued = n;   // the bound on the pool's entries that admission grows the pool from
   return GC_OK;
 }
 

@@ -743,15 +743,26 @@ __device__ double lanczos64_seeded(const double* nw, const double* Dg, double* v
     if (j == 0) {
       t = a;
     } else {
-      bool ok = false;
-      const double hi = t64 + 1e-14 * fmax(fabs(t64), 1.0);
-      const double wdw = fmax(8.0 * d64, 4e-5 * fmax(fabs(t64), 1e-3));
-      t = tri_min64(a64, b64, j + 1, t64 - wdw, hi, lane, &ok, true);
-      if (!ok) {
-        const double c = f2d_bits(theta32);
-        const double del = 2e-5 * fmax(1.0, fabs(c));
-        t = tri_min64(a64, b64, j + 1, fmin(c, t64) - del, t64 + del, lane, &ok);
-        if (!ok) t = tri_min64(a64, b64, j + 1, -bound, bound, lane, &ok);
+      // brackets tried in turn (one call site, so the multisection is
+      // compiled once): the warm window below the last value, a window around
+      // the FP32 Ritz value, then the Gershgorin interval
+      bool ok = false, near = true;
+      double lo = t64 - fmax(8.0 * d64, 4e-5 * fmax(fabs(t64), 1e-3));
+      double hi = t64 + 1e-14 * fmax(fabs(t64), 1.0);
+#pragma unroll 1
+      for (int attempt = 0;; ++attempt) {
+        t = tri_min64(a64, b64, j + 1, lo, hi, lane, &ok, near);
+        if (ok || attempt == 2) break;
+        near = false;
+        if (attempt == 0) {
+          const double c = f2d_bits(theta32);
+          const double del = 2e-5 * fmax(1.0, fabs(c));
+          lo = fmin(c, t64) - del;
+          hi = t64 + del;
+        } else {
+          lo = -bound;
+          hi = bound;
+        }
       }
     }
     const bool stall = j > 0 && fabs(t - t64) <= tol64 * fmax(fabs(t), 1e-3);

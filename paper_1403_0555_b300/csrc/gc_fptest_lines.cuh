@@ -736,15 +736,26 @@ __global__ void __launch_bounds__(256, 2) fp_test_pairs_kernel(const FpArgs a) {
       if (j64 == 0) {
         t = av;
       } else {
-        bool ok = false;
-        const double hi = t64 + 1e-14 * fmax(fabs(t64), 1.0);
-        const double wdw = fmax(8.0 * d64, 4e-5 * fmax(fabs(t64), 1e-3));
-        t = tri_min64(a64, b64, j64 + 1, t64 - wdw, hi, h, &ok, true);
-        if (!ok) {
-          const double c = f2d_bits(theta);
-          const double del = 2e-5 * fmax(1.0, fabs(c));
-          t = tri_min64(a64, b64, j64 + 1, fmin(c, t64) - del, t64 + del, h, &ok);
-          if (!ok) t = tri_min64(a64, b64, j64 + 1, -dbound, dbound, h, &ok);
+        // brackets tried in turn (one call site, so the multisection is
+        // compiled once): the warm window below the last value, a window
+        // around the FP32 Ritz value, then the Gershgorin interval
+        bool ok = false, near = true;
+        double lo = t64 - fmax(8.0 * d64, 4e-5 * fmax(fabs(t64), 1e-3));
+        double hi = t64 + 1e-14 * fmax(fabs(t64), 1.0);
+#pragma unroll 1
+        for (int attempt = 0;; ++attempt) {
+          t = tri_min64(a64, b64, j64 + 1, lo, hi, h, &ok, near);
+          if (ok || attempt == 2) break;
+          near = false;
+          if (attempt == 0) {
+            const double c = f2d_bits(theta);
+            const double del = 2e-5 * fmax(1.0, fabs(c));
+            lo = fmin(c, t64) - del;
+            hi = t64 + del;
+          } else {
+            lo = -dbound;
+            hi = dbound;
+          }
         }
       }
       const bool stall = j64 > 0 && fabs(t - t64) <= a.tol64 * fmax(fabs(t), 1e-3);

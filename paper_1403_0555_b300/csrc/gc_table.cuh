@@ -330,6 +330,44 @@ __global__ void relink_kernel(TableView T, unsigned n) {
   }
 }
 
+// Restore (gc_load_copies): entry e of an empty table from the e-th fetched
+// copy.  The canonical configuration is rebuilt from its angles, and the F
+// and fingerprint buckets from F and the configuration: the fingerprint is
+// cos(phi^theta) of link (site 0, mu 0), Re[conj(g_0) u_{0,0} g_1], which a
+// global phase leaves unchanged.  Count, first start (also the
+// representative's start), lambda_2 and region are the fetched ones.  A warp
+// per copy; relink_kernel then links the entries into their buckets.
+__global__ void restore_kernel(TableView T, unsigned n, int V, const double* __restrict__ theta,
+                               const double* __restrict__ F, const unsigned long long* __restrict__ first,
+                               const unsigned long long* __restrict__ count, const double* __restrict__ lam,
+                               const int* __restrict__ region, const double2* __restrict__ links64) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long e = w0; e < (long long)n; e += nw) {
+    for (int x = lane; x < V; x += 32) {
+      double sn, cs;
+      sincos(theta[(size_t)e * V + x], &sn, &cs);
+      T.cfg[(size_t)e * V + x] = make_double2(cs, sn);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const double2 g0 = T.cfg[(size_t)e * V], g1 = T.cfg[(size_t)e * V + 1], u = links64[0];
+      const double tx = fma(u.x, g1.x, -u.y * g1.y), ty = fma(u.x, g1.y, u.y * g1.x);
+      const double w = fma(g0.x, tx, g0.y * ty);
+      T.F[e] = F[e];
+      T.q[e] = (long long)floor(F[e] * T.inv_wF);
+      T.t[e] = (int)floor((w + 1.0) * T.inv_wT);
+      T.first_start[e] = first[e];
+      T.rep_start[e] = first[e];
+      T.count[e] = count[e];
+      T.lambda2[e] = lam[e];
+      T.region[e] = region[e];
+    }
+    __syncwarp();
+  }
+}
+
 __global__ void fill_int_kernel(int* p, int v, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
 }
