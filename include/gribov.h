@@ -126,9 +126,11 @@ typedef struct {
   uint64_t polish_redo_starts;   /* starts it reran                              */
   uint64_t lanczos_steps_fp64;   /* part of lanczos_steps taken in FP64 (Lanczos
                                     mode: the FP64 steps after the FP32 seed)   */
-  double ms_starts;              /* part of ms_relax: the kernel drawing the
-                                    random starts ahead of the 4^4 FP32 sweeps
-                                    (0 where the sweeps draw their own)         */
+  double ms_starts;              /* part of ms_relax before the FP32 sweeps: the
+                                    kernel drawing the random starts ahead of
+                                    the 4^4 FP32 sweeps; beyond shared memory
+                                    (mixed) the FP64 head sweeps from the random
+                                    starts; 0 where the sweeps draw their own  */
 } gc_stats;
 
 /* Device memory hooks (e.g. a framework's caching allocator).  alloc returns

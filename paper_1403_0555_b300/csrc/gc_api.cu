@@ -700,9 +700,10 @@ int validate_options(const gc_options& opt, double omega, double eps) {
 // (the orbit's work must be complete).
 void harvest_timing(gc_orbit o) {
   // per batch: before relax | after relax | after the first polish launch |
-  // after the redo polish launch | after dedup | after the FP test | after
-  // the start draw (inside the relax stage; at its start where the sweeps
-  // draw their own starts)
+  // after the redo polish launch | after dedup | after the FP test | where
+  // the FP32 sweeps begin inside the relax stage (after the start draw, or on
+  // lattices beyond shared memory after the FP64 head sweeps; at the stage's
+  // start where the sweeps draw their own starts)
   for (size_t k = 0; k + kEvPerBatch <= o->ev_used; k += kEvPerBatch) {
     float t[5] = {0, 0, 0, 0, 0}, t_start = 0;
     for (int j = 0; j < 5; ++j) cudaEventElapsedTime(&t[j], o->ev_pool[k + j], o->ev_pool[k + j + 1]);
@@ -994,7 +995,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
     const bool cluster = opt.relax_variant != GC_RELAX_GENERIC;
     if (ev) {
       GC_CUDA(cudaEventRecord(ev[0], s));
-      GC_CUDA(cudaEventRecord(ev[6], s));   // the sweeps draw their own starts
+      if (!mixed) GC_CUDA(cudaEventRecord(ev[6], s));   // the sweeps draw their own starts
     }
     double2* st64 = o->s_config.as<double2>();
     if (mixed) {
@@ -1018,6 +1019,7 @@ int enumerate_slab(gc_orbit o, uint64_t n_starts, double omega, double eps, cons
         ++o->launches;
         GC_CUDA(cudaMemsetAsync(wctr, 0, 8, s));
       }
+      if (ev) GC_CUDA(cudaEventRecord(ev[6], s));   // the FP32 sweeps start here
       // FP32 sweeps from there
       if (!o->s_rate.ensure((size_t)B * 4, s)) return fail(GC_ENOMEM, "cannot admit a batch of %zu starts", B);
       sa.links = o->links32.p;
