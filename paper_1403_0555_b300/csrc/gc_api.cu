@@ -1915,7 +1915,11 @@ int fetch_copies_impl(gc_orbit o, size_t capacity, size_t* n_distinct, double* F
     const double* table = angle_table();
     if (!table) return fail(GC_ENOMEM, "cannot set up the fetch's angle table");
     const int threads = (int)std::min<size_t>(256, (V + 31) / 32 * 32);   // a copy's sites
-    const int blocks = (int)std::min<unsigned>(k, (unsigned)sm_count() * 16);
+    // the synchronous fetch has the GPU to itself; the asynchronous one runs
+    // beside the next batch's kernels, where a block per SM disturbs them
+    // least (pipelined steps of the 4^4 bench workload: 685 ms against 701
+    // with 16 blocks per SM)
+    const int blocks = (int)std::min<unsigned>(k, (unsigned)sm_count() * (wait ? 16 : 1));
     gc::gather_angles_kernel<<<blocks, threads, 0, c>>>(order, k, (int)V, o->t_cfg.as<double2>(), table, sth);
     ++o->launches;
   }
