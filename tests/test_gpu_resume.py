@@ -18,6 +18,7 @@ CASES = [
     (2, 6, None, 3, 0, 1500, 3000, 2),
     (3, 4, None, 5, 1, 2000, 4000, 1),
     (4, 4, 0.5, 1, 1, 4096, 4096, 1),
+    (2, 64, 1.0, 1, 0, 48, 48, 1),        # beyond shared memory: hyperplane sweeps, slab Lanczos
 ]
 
 
