@@ -151,3 +151,29 @@ def test_async_fetch_pipelined_equals_sync_fetch():
     assert len(results) == n
     for r in results:
         _same(ref, r)
+
+
+@pytest.mark.parametrize("capacity,theta", [(7, True), (None, False)])
+def test_async_fetch_partial_and_without_angles(capacity, theta):
+    """A fetch of the first `capacity` copies, or of every copy without the
+    angles, gives asynchronously (pinned arrays, completed by gc_fetch_wait)
+    exactly what the synchronous fetch gives."""
+    import torch
+    import paper_1403_0555_b300 as gb
+    d, L, phi, oid = _orbits()[3]
+    V = L ** d
+    h = gb.gc_create_orbit(d, L, phi, oid)
+    gb.gc_enumerate_copies(h, 3000, 1.7, 1e-24, gb.gc_options_default(precision=1, check_every=4))
+    ref = gb.gc_fetch_copies(h, V, capacity, theta=theta)
+    m = len(ref["F"])
+    assert m == (min(capacity, ref["n_distinct"]) if capacity else ref["n_distinct"]) and m > 0
+    p = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+    out = {"F": p((m,), torch.float64), "theta": p((m, V), torch.float64) if theta else None,
+           "first_start": p((m,), torch.int64).view(np.uint64), "count": p((m,), torch.int64).view(np.uint64),
+           "lambda2": p((m,), torch.float64), "region": p((m,), torch.int32)}
+    got = gb.gc_fetch_copies_async(h, V, capacity, theta=theta, out=out)
+    gb.gc_fetch_wait(h)
+    assert got["n_distinct"] == ref["n_distinct"]
+    for k in ("F", "first_start", "count", "region", "lambda2") + (("theta",) if theta else ()):
+        assert np.array_equal(got[k], ref[k], equal_nan=True), k
+    gb.gc_destroy_orbit(h)
