@@ -41,7 +41,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM traffic per start (read + write) of the two heavy kernels, from the ncu
 # capture of the 65536-start 4^4 case recorded under profiles/ (None = not
 # captured for the current kernel)
-TRAFFIC_POLISH_PER_START = (1.34815744e8 + 2.18701568e8) / 65536  # profiles/polish_kernel_4d_L4.md (line polish)
+TRAFFIC_POLISH_PER_START = (1.34413568e8 + 2.15169792e8) / 65536  # profiles/polish_kernel_4d_L4.md (line polish)
 TRAFFIC_RELAX_PER_START = (1.34264832e8 + 7.5560448e7) / 65536   # profiles/relax32_sheet_4d_L4.md
 TRAFFIC_FPTEST_PER_COPY = (1.84442112e8 + 4.820736e6) / 44636   # profiles/fp_test_pairs_4d_L4.md
 # DRAM traffic per launch of the large-lattice leg's kernels (its own workload,
@@ -781,7 +781,7 @@ def run_ours(args):
     fp64_pol = fp64_pairs + fp64_redo
     t_pairs, t_redo = sec["polish_fp64"], sec["polish_redo"]
     a_pol = fp64_pairs / t_pairs / 1e12
-    kernels["polish"] = {"kernel": "polish_pairs_kernel<4,4,16>", "bound": "alu",
+    kernels["polish"] = {"kernel": "polish_pairs_kernel<4,4,12>", "bound": "alu",
                          "achieved": a_pol, "peak": fp64_peak, "unit": "T FP64 lane ops/s", "frac": a_pol / fp64_peak,
                          "fp32_frac": fp32_pairs / t_pairs / 1e12 / fp32_peak,
                          "ms": stage_ms["polish_fp64"], "launches": n_launch,
