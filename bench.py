@@ -43,7 +43,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # captured for the current kernel)
 TRAFFIC_POLISH_PER_START = (1.34413568e8 + 2.15169792e8) / 65536  # profiles/polish_kernel_4d_L4.md (line polish)
 TRAFFIC_RELAX_PER_START = (1.34264832e8 + 7.5560448e7) / 65536   # profiles/relax32_sheet_4d_L4.md
-TRAFFIC_FPTEST_PER_COPY = (1.84442112e8 + 4.820736e6) / 44636   # profiles/fp_test_pairs_4d_L4.md
+TRAFFIC_FPTEST_PER_COPY = (1.843584e8 + 3.775488e6) / 44636   # profiles/fp_test_pairs_4d_L4.md
 # DRAM traffic per launch of the large-lattice leg's kernels (its own workload,
 # 592 starts of 4D 16^4), from ncu: profiles/slab_traffic_4d_L16.md
 TRAFFIC_SLAB_NEWTON1 = 2.92208894464e11 + 5.7204921344e10

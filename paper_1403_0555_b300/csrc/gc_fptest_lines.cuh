@@ -316,7 +316,7 @@ __device__ __forceinline__ void sts_d1(unsigned base, double v) {
 }
 
 template <int D, int L>
-__global__ void __launch_bounds__(256, 2) fp_test_pairs_kernel(const FpArgs a) {
+__global__ void __launch_bounds__(384, 1) fp_test_pairs_kernel(const FpArgs a) {
   using LG = LineGeom<D, L>;
   using SM = FpTestPairSmem<D, L>;
   constexpr int NLH = LG::NLH, V = LG::V;
