@@ -14,9 +14,13 @@ Prints one JSON line.  `value` = converged copies per second with the orbits
 resident on the device (CUDA events on the launch stream around the
 gc_enumerate_batch call of each of the K timed steps); `e2e` = the same metric
 through the C ABI with host buffers (link angles uploaded, distinct copies
-read back, every step).  The plain FP64 path is timed on a sample beside it,
-and the same steps with the FP32 Lanczos screen (`fp32_screen`).  The roofline
-denominators come from the library's own throughput probes (`peaks`).
+read back into pinned arrays, every step; steps pipelined so that each step's
+read-back runs beside the next step's kernels).  The plain FP64 path is timed
+beside it as the same kind of batch on a sample of starts, and so are the same
+steps with the FP32 Lanczos screen (`fp32_screen`).  `roofline` is the kernel
+with the most time in isolated single-orbit passes, against the library's own
+measured unit throughputs (`peaks`); `roofline.kernels` lists every kernel of
+the step with its binding unit.
 """
 from __future__ import annotations
 
